@@ -1,0 +1,183 @@
+"""Seeded synthetic inputs for the batched fermion-determinant path.
+
+This module only *generates inputs*: the honeycomb hopping (adjacency) matrix ``A``, the hopping
+exponential ``E = exp(delta*kappa*A)`` with its inverse, and Gaussian auxiliary fields ``phi``.
+It holds none of the determinant arithmetic (no slice products, no QR, no assembly, no force);
+the CPU oracle and the GPU library both consume the arrays made here and share nothing else.
+
+The paper works with a generic ``M_t = exp(K_t)`` (Section 2).  The concrete model used by every
+workload is a Hubbard-type model on a periodic L x L honeycomb lattice with time slices
+``B_t = E diag(exp(i phi_t))``; ``phi_{t,x}`` are iid normal with variance ``delta*U``.
+
+Seeds: workload ``k`` uses ``seed = 1000 + k``; configuration ``c`` of a batch draws its field
+from ``numpy.random.default_rng([seed, c])``.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List
+
+import numpy as np
+
+__all__ = [
+    "honeycomb_adjacency",
+    "honeycomb_spectrum",
+    "hopping_exp",
+    "field",
+    "Problem",
+    "make_problem",
+    "workload",
+    "WORKLOADS",
+]
+
+
+def honeycomb_adjacency(L: int) -> np.ndarray:
+    """Adjacency matrix of the periodic L x L honeycomb lattice, Nx = 2 L^2 sites.
+
+    Site (i, j, s) with s = 0 (A sublattice) or 1 (B sublattice) has index 2*(i*L + j) + s.
+    A(i, j) is bonded to B(i, j), B(i-1, j) and B(i, j-1) (indices mod L), so every site has
+    three neighbours and the lattice is bipartite.  Entries are 0 or 1.
+    """
+    if L < 2:
+        raise ValueError("honeycomb lattice needs L >= 2 (L = 1 has multiple bonds)")
+    nx = 2 * L * L
+    A = np.zeros((nx, nx), dtype=np.float64)
+
+    def idx(i: int, j: int, s: int) -> int:
+        return 2 * ((i % L) * L + (j % L)) + s
+
+    for i in range(L):
+        for j in range(L):
+            a = idx(i, j, 0)
+            for (bi, bj) in ((i, j), (i - 1, j), (i, j - 1)):
+                b = idx(bi, bj, 1)
+                A[a, b] = 1.0
+                A[b, a] = 1.0
+    return A
+
+
+def honeycomb_spectrum(L: int) -> np.ndarray:
+    """Eigenvalues of :func:`honeycomb_adjacency` from momentum space (sorted ascending).
+
+    For momentum k = 2 pi (m, n) / L the two bands are +-|1 + e^{i k1} + e^{i k2}|.
+    Used to pin the lattice independently of a numerical eigen-solver.
+    """
+    ev = []
+    for m in range(L):
+        for n in range(L):
+            f = 1.0 + np.exp(2j * np.pi * m / L) + np.exp(2j * np.pi * n / L)
+            ev += [abs(f), -abs(f)]
+    return np.sort(np.asarray(ev))
+
+
+def hopping_exp(A: np.ndarray, delta: float, kappa: float = 1.0, sign: float = +1.0) -> np.ndarray:
+    """``exp(sign*delta*kappa*A)`` for a real symmetric ``A`` via its eigen-decomposition.
+
+    The result is symmetric; it is symmetrised explicitly so that row-major and column-major
+    storage hold identical bytes.
+    """
+    lam, U = np.linalg.eigh(A)
+    E = (U * np.exp(sign * delta * kappa * lam)[None, :]) @ U.T
+    return 0.5 * (E + E.T)
+
+
+def field(seed: int, c: int, nt: int, nx: int, delta: float, U: float) -> np.ndarray:
+    """Auxiliary field phi[t, x] ~ N(0, delta*U) iid (variance delta*U), float64, shape (nt, nx).
+
+    Row t-1 is the field of time slice t in the product B_Nt ... B_1.
+    """
+    rng = np.random.default_rng([int(seed), int(c)])
+    return rng.normal(0.0, np.sqrt(delta * U), size=(nt, nx)).astype(np.float64)
+
+
+@dataclasses.dataclass
+class Problem:
+    """One configuration: lattice size, time discretisation and the arrays the library takes."""
+
+    L: int
+    nt: int
+    n_stab: int
+    beta: float
+    U: float
+    kappa: float
+    E: np.ndarray  # (nx, nx) float64, exp(delta*kappa*A)
+    Einv: np.ndarray  # (nx, nx) float64, exp(-delta*kappa*A)
+    phi: np.ndarray  # (nt, nx) float64
+    A: np.ndarray  # (nx, nx) adjacency (for closed forms and invariants)
+
+    @property
+    def nx(self) -> int:
+        return 2 * self.L * self.L
+
+    @property
+    def delta(self) -> float:
+        return self.beta / self.nt
+
+
+_CACHE: dict = {}
+
+
+def _lattice(L: int, delta: float, kappa: float):
+    key = (L, float(delta), float(kappa))
+    if key not in _CACHE:
+        A = honeycomb_adjacency(L)
+        _CACHE[key] = (A, hopping_exp(A, delta, kappa, +1.0), hopping_exp(A, delta, kappa, -1.0))
+    return _CACHE[key]
+
+
+def make_problem(L: int, nt: int, beta: float, U: float, n_stab: int, seed: int, c: int,
+                 kappa: float = 1.0, zero_field: bool = False) -> Problem:
+    delta = beta / nt
+    A, E, Einv = _lattice(L, delta, kappa)
+    nx = 2 * L * L
+    phi = np.zeros((nt, nx)) if zero_field else field(seed, c, nt, nx, delta, U)
+    return Problem(L=L, nt=nt, n_stab=n_stab, beta=beta, U=U, kappa=kappa, E=E, Einv=Einv,
+                   phi=phi, A=A)
+
+
+# Named workloads.  Index k uses seed 1000 + k.
+#   tiny8      : L=2 (Nx=8),  beta=2,  Nt=16,  U=2,   n_stab=4,  1 config
+#   batch18    : L=3 (Nx=18), beta=8,  Nt=64,  U=3,   n_stab=8,  256 configs
+#   cold72     : L=6 (Nx=72), beta=64, Nt=512, U=3.5, n_stab=16, 64 configs
+#   force72    : L=6 (Nx=72), beta=32, Nt=256, U=3,   n_stab=8,  32 configs
+#   uneven512  : Nx in {8,...,288} x Nt in {32,...,1024}, delta=1/16, U=3, 512 configs
+WORKLOADS = {
+    "tiny8": dict(index=0, L=2, nt=16, beta=2.0, U=2.0, n_stab=4, batch=1),
+    "batch18": dict(index=1, L=3, nt=64, beta=8.0, U=3.0, n_stab=8, batch=256),
+    "cold72": dict(index=2, L=6, nt=512, beta=64.0, U=3.5, n_stab=16, batch=64),
+    "force72": dict(index=3, L=6, nt=256, beta=32.0, U=3.0, n_stab=8, batch=32),
+}
+
+UNEVEN_L = (2, 3, 4, 5, 6, 7, 8, 12)
+UNEVEN_NT = (32, 64, 128, 256, 512, 1024)
+
+
+def _uneven(batch: int = 512, n_stab: int = 16) -> List[Problem]:
+    seed = 1004
+    pairs = [(L, nt) for L in UNEVEN_L for nt in UNEVEN_NT]  # 48 pairs
+    order = []
+    i = 0
+    while len(order) < batch:
+        order.append(pairs[i % len(pairs)])
+        i += 1
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(len(order))
+    probs = []
+    for c, k in enumerate(perm):
+        L, nt = order[k]
+        beta = nt / 16.0
+        probs.append(make_problem(L, nt, beta, 3.0, min(n_stab, nt), seed, c))
+    return probs
+
+
+def workload(name: str, batch: int | None = None, n_stab: int | None = None,
+             zero_field: bool = False) -> List[Problem]:
+    """The configurations of a named workload (optionally truncated to ``batch``)."""
+    if name == "uneven512":
+        return _uneven(batch or 512, n_stab or 16)
+    w = WORKLOADS[name]
+    b = w["batch"] if batch is None else batch
+    ns = w["n_stab"] if n_stab is None else n_stab
+    seed = 1000 + w["index"]
+    return [make_problem(w["L"], w["nt"], w["beta"], w["U"], ns, seed, c, zero_field=zero_field)
+            for c in range(b)]
