@@ -1,0 +1,128 @@
+/*
+ * fd.h -- C ABI of the batched, stabilised fermion-determinant library for NVIDIA GB300 (sm_103a).
+ *
+ * What it computes (arXiv 2604.02130, "Stable and Efficient Algorithms for the Fermion
+ * Determinant"):
+ *   time slices   B_t = E diag(exp(i phi_t)),   E = exp(delta*kappa*A)          (Section 2)
+ *   product       P = B_Nt ... B_2 B_1  (slice 1 acts first; the order of the block fermion
+ *                 matrix of Section 2, whose top-right block is +M_{Nt-1})
+ *   log det       logdet = log det(1 + P)                        (Section 2, Eq. hamiltonian_alg)
+ *   Green's fn    G = (1 + P)^{-1}                                (Section 2, "sausage" inverse)
+ *   HMC force     F[t,x] = d logdet / d phi[t,x] = i (1 - [G_{t-1}]_{xx}),
+ *                 G_{t-1} = (1 + B_{t-1}...B_1 B_Nt...B_t)^{-1}  (Section 4, Eq. response_result)
+ * by the stabilised dense method of Section 7 (X D T representation, QR re-orthogonalisation
+ * every n_stab slices as proposed in Section 9, scale-separated assembly).
+ *
+ * Conventions shared by every entry point:
+ *   - All matrix/vector arguments inside fd_problem and all outputs are DEVICE pointers on the
+ *     context's device, owned by the caller, and must stay valid until the stream reaches the
+ *     end of the call.  Arrays of problems / of output pointers are HOST arrays, read during the
+ *     call only.
+ *   - Real matrices are float64 row-major (E and E^{-1} are symmetric, so row- and column-major
+ *     coincide).  Complex outputs are complex128 interleaved (re, im), row-major.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream).  The return code covers host-side validation and launch errors only.  Device-side
+ *     failures (non-finite values, zero pivots, a bounded wait that ran out) are recorded per
+ *     configuration and read back with fd_status().
+ *   - The library owns its workspace (checkpoints, per-configuration scratch, descriptor tables)
+ *     inside the context.  A call may grow it with cudaMalloc, which synchronises the device;
+ *     fd_reserve() sizes it ahead of time (required before stream capture).
+ *   - Every function returns FD_OK (0) or a negative FD_ERR_* code; fd_last_error() gives text.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef FD_H_
+#define FD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Largest spatial size handled (honeycomb L = 12 gives Nx = 288). */
+#define FD_NX_MAX 288
+
+enum {
+  FD_OK = 0,
+  FD_ERR_INVALID = -1,     /* bad argument: null pointer, size out of range, nt % n_stab != 0 */
+  FD_ERR_UNSUPPORTED = -2, /* valid request that this build does not implement */
+  FD_ERR_CUDA = -3,        /* a CUDA runtime call failed (text in fd_last_error) */
+  FD_ERR_NUMERIC = -4,     /* device: non-finite value or zero pivot in a configuration */
+  FD_ERR_TIMEOUT = -5      /* device: a bounded wait gave up (kernel returned early) */
+};
+
+/* Arithmetic of the slice products.  QR re-orthogonalisation, scale separation, assembly,
+ * boundary Green's functions and all outputs are FP64 in every mode. */
+enum {
+  FD_PREC_FP64 = 0,        /* everything in FP64 (DFMA) */
+  FD_PREC_MIXED_TF32 = 1,  /* slice GEMMs on tcgen05 tensor cores, TF32 operands, FP32 accumulate */
+  FD_PREC_MIXED_3XTF32 = 2 /* as above with split (hi + lo) TF32 operands, 3 MMAs per product */
+};
+
+typedef struct fd_ctx fd_ctx;
+
+/* One configuration.  All pointers are device pointers.
+ *   nx        spatial sites, 1 <= nx <= FD_NX_MAX
+ *   nt        time slices, nt >= 1
+ *   n_stab    slices between QR re-orthogonalisations, 1 <= n_stab <= nt, nt % n_stab == 0
+ *   expA      E = exp(delta*kappa*A), nx*nx float64 (symmetric)
+ *   expA_inv  E^{-1}, nx*nx float64 (symmetric); needed by fd_force, may be NULL otherwise
+ *   phi       nt*nx float64 row-major; row t-1 is the field of slice t */
+typedef struct {
+  int32_t nx;
+  int32_t nt;
+  int32_t n_stab;
+  int32_t reserved; /* must be 0 */
+  const double* expA;
+  const double* expA_inv;
+  const double* phi;
+} fd_problem;
+
+/* Create a context on CUDA device `device` (makes it current on the calling thread). */
+int fd_ctx_create(fd_ctx** out, int device);
+void fd_ctx_destroy(fd_ctx* ctx);
+const char* fd_last_error(const fd_ctx* ctx);
+
+/* Pre-size the workspace for up to `batch` configurations like `probs` with the given outputs
+ * (`what` = bitmask of FD_WANT_*), so that later calls of that shape allocate nothing. */
+enum { FD_WANT_LOGDET = 1, FD_WANT_GREEN = 2, FD_WANT_FORCE = 4 };
+int fd_reserve(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec);
+
+/* log det(1 + B_Nt...B_1) for `batch` configurations.
+ *   logdet  device, 2*batch float64: (re, im) per configuration; im wrapped to (-pi, pi]. */
+int fd_logdet(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, int prec,
+              void* stream);
+
+/* log det and the Green's function G = (1 + B_Nt...B_1)^{-1}.
+ *   G  host array of `batch` device pointers; G[c] receives nx*nx complex128, row-major. */
+int fd_green(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
+             int prec, void* stream);
+
+/* log det, (optionally) G, and the force F[t,x] = d logdet / d phi[t,x] (complex; for real
+ * fields Im F = 1/2 exactly on a bipartite lattice).  Forward pass with checkpoints of
+ * (X, D, T) every n_stab slices, then an adjoint backward sweep that recomputes the right
+ * products, forms the equal-time Green's function stably at each block boundary and wraps it
+ * through the block.
+ *   G  host array of device pointers or NULL (G not wanted)
+ *   F  host array of `batch` device pointers; F[c] receives nt*nx complex128, row-major
+ *      (row t-1 is slice t, like phi). */
+int fd_force(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
+             double* const* F, int prec, void* stream);
+
+/* Wait for `stream` and copy the per-configuration device status of the LAST call on this
+ * context into per_config_status[0..batch-1] (host): FD_OK, FD_ERR_NUMERIC or FD_ERR_TIMEOUT.
+ * Returns the worst code seen (FD_OK if all succeeded). */
+int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch);
+
+/* Number of kernel launches the last fd_logdet/fd_green/fd_force call issued. */
+int fd_last_launch_count(const fd_ctx* ctx);
+
+/* Measured FP64 FMA throughput of this device in GFLOP/s (a DFMA-bound loop over all SMs);
+ * used to state roofline fractions.  Synchronous. */
+int fd_measure_fp64_peak(fd_ctx* ctx, double* gflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FD_H_ */

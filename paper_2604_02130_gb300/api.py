@@ -1,0 +1,190 @@
+"""Python binding of the C ABI (include/fd.h).  Marshalling only: every step of the
+computation runs in libfd.so's CUDA kernels; torch provides device memory and streams.
+
+    ctx = Context(0)
+    batch = Batch(ctx, [(E, Einv, phi, n_stab), ...], want="force", prec="fp64")
+    out = batch.run()            # enqueues on the current torch stream
+    out.logdet, out.G, out.F     # complex128 tensors on the device
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
+
+import torch
+
+from . import _lib as L
+
+
+class FdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("fd error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """Owns an fd_ctx (workspace, descriptor tables) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = L.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("fd requires a CUDA device (there is no CPU path)")
+        torch.cuda.set_device(device)
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = self.lib.fd_ctx_create(ctypes.byref(h), device)
+        if rc != L.FD_OK:
+            raise FdError(rc, "fd_ctx_create failed")
+        self.h = h
+
+    def check(self, rc: int):
+        if rc != L.FD_OK:
+            raise FdError(rc, self.lib.fd_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fd_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, batch: int, stream=None) -> List[int]:
+        arr = (ctypes.c_int * max(1, batch))()
+        self.lib.fd_status(self.h, _stream_ptr(stream), arr, batch)
+        return [arr[i] for i in range(batch)]
+
+    def last_launch_count(self) -> int:
+        return self.lib.fd_last_launch_count(self.h)
+
+    def measure_fp64_peak(self) -> float:
+        g = ctypes.c_double()
+        self.check(self.lib.fd_measure_fp64_peak(self.h, ctypes.byref(g)))
+        return g.value
+
+
+@dataclass
+class Result:
+    logdet: torch.Tensor  # (batch,) complex128
+    G: Optional[List[torch.Tensor]]  # nx x nx complex128 each
+    F: Optional[List[torch.Tensor]]  # nt x nx complex128 each
+
+
+class Batch:
+    """A fixed batch of configurations with preallocated outputs; run() enqueues one call.
+
+    problems: sequence of (E, Einv, phi, n_stab) with E, Einv (nx, nx) float64 and phi (nt, nx)
+    float64 CUDA tensors (Einv may be None unless want == "force")."""
+
+    def __init__(self, ctx: Context, problems: Sequence[Tuple], want: str = "logdet",
+                 prec: str = "fp64"):
+        if want not in ("logdet", "green", "force", "force+green"):
+            raise ValueError(want)
+        self.ctx = ctx
+        self.want = want
+        self.prec = L.PRECISIONS[prec]
+        self.n = len(problems)
+        self._keep = []
+        arr = (L.fd_problem * max(1, self.n))()
+        dev = torch.device("cuda", ctx.device)
+        for c, (E, Einv, phi, n_stab) in enumerate(problems):
+            for t in (E, phi) + ((Einv,) if Einv is not None else ()):
+                if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                    raise ValueError("inputs must be contiguous float64 CUDA tensors")
+            nt, nx = phi.shape
+            arr[c].nx, arr[c].nt, arr[c].n_stab, arr[c].reserved = nx, nt, int(n_stab), 0
+            arr[c].expA = E.data_ptr()
+            arr[c].expA_inv = Einv.data_ptr() if Einv is not None else None
+            arr[c].phi = phi.data_ptr()
+            self._keep += [E, Einv, phi]
+        self.problems = arr
+        self.logdet_buf = torch.empty((self.n, 2), dtype=torch.float64, device=dev)
+        self.G = None
+        self.F = None
+        self._Gp = None
+        self._Fp = None
+        if want in ("green", "force+green"):
+            self.G = [torch.empty((p.nx, p.nx), dtype=torch.complex128, device=dev)
+                      for p in arr[:self.n]]
+            self._Gp = (ctypes.c_void_p * self.n)(*[g.data_ptr() for g in self.G])
+        if want.startswith("force"):
+            self.F = [torch.empty((p.nt, p.nx), dtype=torch.complex128, device=dev)
+                      for p in arr[:self.n]]
+            self._Fp = (ctypes.c_void_p * self.n)(*[f.data_ptr() for f in self.F])
+
+    def reserve(self):
+        what = {"logdet": 1, "green": 3, "force": 5, "force+green": 7}[self.want]
+        self.ctx.check(self.ctx.lib.fd_reserve(self.ctx.h, self.n, self.problems, what, self.prec))
+
+    def run(self, stream=None) -> Result:
+        lib, h = self.ctx.lib, self.ctx.h
+        s = _stream_ptr(stream)
+        ld = ctypes.c_void_p(self.logdet_buf.data_ptr())
+        if self.want == "logdet":
+            rc = lib.fd_logdet(h, self.n, self.problems, ld, self.prec, s)
+        elif self.want == "green":
+            rc = lib.fd_green(h, self.n, self.problems, ld, self._Gp, self.prec, s)
+        else:
+            rc = lib.fd_force(h, self.n, self.problems, ld, self._Gp, self._Fp, self.prec, s)
+        self.ctx.check(rc)
+        return Result(torch.view_as_complex(self.logdet_buf), self.G, self.F)
+
+    def status(self, stream=None) -> List[int]:
+        return self.ctx.status(self.n, stream)
+
+
+_default_ctx: Optional[Context] = None
+
+
+def default_context() -> Context:
+    global _default_ctx
+    if _default_ctx is None:
+        _default_ctx = Context(torch.cuda.current_device())
+    return _default_ctx
+
+
+def logdet(problems, prec: str = "fp64", ctx: Optional[Context] = None) -> torch.Tensor:
+    """log det(1 + B_Nt...B_1) for a batch, complex128 (batch,)."""
+    return Batch(ctx or default_context(), problems, "logdet", prec).run().logdet.clone()
+
+
+def green(problems, prec: str = "fp64", ctx: Optional[Context] = None):
+    r = Batch(ctx or default_context(), problems, "green", prec).run()
+    return r.logdet.clone(), r.G
+
+
+def force(problems, prec: str = "fp64", with_green: bool = False,
+          ctx: Optional[Context] = None):
+    r = Batch(ctx or default_context(), problems, "force+green" if with_green else "force",
+              prec).run()
+    return r.logdet.clone(), r.G, r.F
+
+
+class FermionLogDet(torch.autograd.Function):
+    """log det(1 + B_Nt...B_1) of one configuration as a differentiable function of phi.
+
+    forward(phi, E, Einv, n_stab, prec) -> complex128 scalar.  The backward pass uses the
+    adjoint force sweep (fd_force): with F = d logdet / d phi (complex, holomorphic in phi),
+    torch's convention for a real input gives grad_phi = Re(conj(grad_out) * F)."""
+
+    @staticmethod
+    def forward(ctx_, phi, E, Einv, n_stab, prec="fp64"):
+        c = default_context()
+        r = Batch(c, [(E, Einv, phi.detach().contiguous(), n_stab)], "force", prec).run()
+        ctx_.save_for_backward(r.F[0])
+        return r.logdet[0].clone()
+
+    @staticmethod
+    def backward(ctx_, grad_out):
+        (F,) = ctx_.saved_tensors
+        g = (grad_out.conj() * F).real
+        return g, None, None, None, None

@@ -1,0 +1,431 @@
+// fd_api.cu -- host runtime behind the C ABI of include/fd.h: context, validation, planning
+// (size classes, shared-memory placement, cost-sorted persistent queues), workspace and launches.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fd_kernels.h"
+
+struct fd_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int max_smem_optin = 0;
+  int smem_per_sm = 0;
+  std::string err;
+  char* scratch = nullptr;
+  size_t scratch_cap = 0;
+  fd::Desc* d_desc = nullptr;
+  size_t desc_cap = 0;
+  fd::Desc* h_desc = nullptr;  // pinned staging for the descriptor table
+  size_t h_desc_cap = 0;
+  int* d_queue = nullptr;
+  int queue_cap = 0;
+  int* d_status = nullptr;
+  int status_cap = 0;
+  cudaEvent_t staging_done = nullptr;
+  bool staging_pending = false;
+  int last_batch = 0;
+  int last_launches = 0;
+  int smem_attr = 0;
+};
+
+namespace {
+
+using fd::Desc;
+using fd::Layout;
+
+int fail(fd_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(fd_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, FD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define FD_CUDA(ctx, call)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+enum Kind { K_FWD = 0, K_FORCE = 1 };
+
+struct Group {
+  int kind;
+  int nx;
+  Layout L;
+  int grid;
+  std::vector<int> idx;  // user indices, cost-sorted (descending)
+  size_t desc_off;       // first descriptor of this group in the table
+  size_t scratch_off;    // byte offset of this group's slots
+};
+
+int threads_for(int n) {
+  if (n <= 12) return 32;
+  if (n <= 24) return 64;
+  if (n <= 40) return 128;
+  return 256;
+}
+
+long long round16(long long x) { return (x + 15) & ~15LL; }
+
+// Greedy placement: the buffers touched every slice first, then the per-block ones.
+Layout plan_layout(int n, int kind, int budget, int nthreads, int max_nt, int max_nstab_min) {
+  Layout L;
+  memset(&L, 0, sizeof(L));
+  L.nthreads = nthreads;
+  const long long cm = 16LL * n * n, rm = 8LL * n * n;
+  std::vector<std::pair<int, long long>> order;
+  if (kind == K_FWD) {
+    order = {{fd::B_E, rm}, {fd::B_X0, cm}, {fd::B_X1, cm}, {fd::B_T0, cm}, {fd::B_T1, cm}};
+  } else {
+    order = {{fd::B_E, rm},   {fd::B_X0, cm},  {fd::B_X1, cm},  {fd::B_EINV, rm},
+             {fd::B_GA, cm},  {fd::B_GB, cm},  {fd::B_GLO, cm}, {fd::B_GHI, cm},
+             {fd::B_T0, cm},  {fd::B_T1, cm}};
+  }
+  long long used = round16(fd::small_bytes(n)) + 16;  // small vectors + queue slot
+  long long gbytes = 0;
+  std::vector<std::pair<int, long long>> placed;
+  for (auto& b : order) {
+    if (used + b.second <= budget) {
+      L.in_smem[b.first] = 1;
+      placed.push_back({b.first, b.second});
+      used += round16(b.second);
+    } else {
+      L.in_smem[b.first] = 0;
+      if (b.first == fd::B_E || b.first == fd::B_EINV) {
+        L.off[b.first] = 0;  // read in place from the caller's input
+      } else {
+        L.off[b.first] = gbytes;
+        gbytes += round16(b.second);
+      }
+    }
+  }
+  long long o = 0;
+  for (auto& b : placed) {
+    L.off[b.first] = o;
+    o += round16(b.second);
+  }
+  L.small_off = (int)o;
+  L.smem_bytes = (int)(o + round16(fd::small_bytes(n)) + 16);
+  L.ws_bytes = round16(gbytes);
+  long long ck = 0;
+  if (kind == K_FORCE) {
+    // (nb - 1) checkpoints of X, T (n*n complex each) and log D (n doubles, padded)
+    long long stride = (2LL * n * n + (n + 1) / 2) * 16;
+    long long nb = max_nt / std::max(1, max_nstab_min);
+    ck = std::max(0LL, nb - 1) * stride;
+  }
+  L.slot_bytes = round16(L.ws_bytes + ck);
+  if (L.slot_bytes == 0) L.slot_bytes = 16;
+  return L;
+}
+
+int validate(fd_ctx* ctx, int batch, const fd_problem* probs, const void* logdet, int prec,
+             bool need_einv) {
+  if (!ctx) return FD_ERR_INVALID;
+  if (batch < 0) return fail(ctx, FD_ERR_INVALID, "batch < 0");
+  if (batch > 0 && (!probs || !logdet)) return fail(ctx, FD_ERR_INVALID, "null probs or logdet");
+  if (prec != FD_PREC_FP64 && prec != FD_PREC_MIXED_TF32 && prec != FD_PREC_MIXED_3XTF32)
+    return fail(ctx, FD_ERR_INVALID, "unknown precision %d", prec);
+  for (int c = 0; c < batch; ++c) {
+    const fd_problem& p = probs[c];
+    if (p.nx < 1 || p.nx > FD_NX_MAX)
+      return fail(ctx, FD_ERR_INVALID, "config %d: nx=%d outside [1,%d]", c, p.nx, FD_NX_MAX);
+    if (p.nt < 1) return fail(ctx, FD_ERR_INVALID, "config %d: nt=%d < 1", c, p.nt);
+    if (p.n_stab < 1 || p.n_stab > p.nt)
+      return fail(ctx, FD_ERR_INVALID, "config %d: n_stab=%d outside [1,nt]", c, p.n_stab);
+    if (p.nt % p.n_stab != 0)
+      return fail(ctx, FD_ERR_INVALID, "config %d: nt=%d not a multiple of n_stab=%d", c, p.nt,
+                  p.n_stab);
+    if (p.reserved != 0) return fail(ctx, FD_ERR_INVALID, "config %d: reserved != 0", c);
+    if (!p.expA || !p.phi) return fail(ctx, FD_ERR_INVALID, "config %d: null expA or phi", c);
+    if (need_einv && !p.expA_inv)
+      return fail(ctx, FD_ERR_INVALID, "config %d: fd_force needs expA_inv", c);
+  }
+  return FD_OK;
+}
+
+std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kind) {
+  std::vector<Group> groups;
+  std::vector<int> order(batch);
+  for (int c = 0; c < batch; ++c) order[c] = c;
+  // size classes by nx
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    if (probs[a].nx != probs[b].nx) return probs[a].nx > probs[b].nx;
+    if (probs[a].nt != probs[b].nt) return probs[a].nt > probs[b].nt;
+    return a < b;
+  });
+  size_t i = 0;
+  while (i < order.size()) {
+    Group g;
+    g.kind = kind;
+    g.nx = probs[order[i]].nx;
+    int max_nt = 0, min_ns = 1 << 30;
+    while (i < order.size() && probs[order[i]].nx == g.nx) {
+      g.idx.push_back(order[i]);
+      max_nt = std::max(max_nt, probs[order[i]].nt);
+      ++i;
+    }
+    // checkpoint count bound: max over the group of nt / n_stab
+    int max_nb = 0;
+    for (int c : g.idx) max_nb = std::max(max_nb, probs[c].nt / probs[c].n_stab);
+    min_ns = 1;
+    const int n = g.nx, nth = threads_for(n);
+    // try a budget that keeps several CTAs per SM, else the full opt-in budget
+    Layout full = plan_layout(n, kind, 1 << 30, nth, max_nb, min_ns);
+    int budget;
+    if (full.smem_bytes <= ctx->smem_per_sm / 4 - 1024)
+      budget = full.smem_bytes;
+    else if (full.smem_bytes <= ctx->smem_per_sm / 2 - 1024)
+      budget = full.smem_bytes;
+    else
+      budget = ctx->max_smem_optin;
+    g.L = plan_layout(n, kind, budget, nth, max_nb, min_ns);
+    int occ = fd::occupancy_fp64(kind == K_FORCE, nth, g.L.smem_bytes);
+    if (occ < 1) occ = 1;
+    g.grid = std::min<int>((int)g.idx.size(), ctx->num_sms * occ);
+    groups.push_back(g);
+  }
+  return groups;
+}
+
+int ensure(fd_ctx* ctx, size_t ndesc, size_t nstatus, size_t nqueue, size_t scratch_bytes) {
+  if (ndesc > ctx->desc_cap) {
+    if (ctx->d_desc) cudaFree(ctx->d_desc);
+    ctx->d_desc = nullptr;
+    size_t cap = std::max<size_t>(ndesc, 256);
+    FD_CUDA(ctx, cudaMalloc(&ctx->d_desc, cap * sizeof(Desc)));
+    ctx->desc_cap = cap;
+  }
+  if (ndesc > ctx->h_desc_cap) {
+    if (ctx->staging_pending) cudaEventSynchronize(ctx->staging_done);
+    ctx->staging_pending = false;
+    if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
+    ctx->h_desc = nullptr;
+    size_t cap = std::max<size_t>(ndesc, 256);
+    FD_CUDA(ctx, cudaMallocHost(&ctx->h_desc, cap * sizeof(Desc)));
+    ctx->h_desc_cap = cap;
+  }
+  if ((int)nstatus > ctx->status_cap) {
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    ctx->d_status = nullptr;
+    int cap = std::max<int>((int)nstatus, 256);
+    FD_CUDA(ctx, cudaMalloc(&ctx->d_status, cap * sizeof(int)));
+    ctx->status_cap = cap;
+  }
+  if ((int)nqueue > ctx->queue_cap) {
+    if (ctx->d_queue) cudaFree(ctx->d_queue);
+    ctx->d_queue = nullptr;
+    int cap = std::max<int>((int)nqueue, 64);
+    FD_CUDA(ctx, cudaMalloc(&ctx->d_queue, cap * sizeof(int)));
+    ctx->queue_cap = cap;
+  }
+  if (scratch_bytes > ctx->scratch_cap) {
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    FD_CUDA(ctx, cudaMalloc(&ctx->scratch, scratch_bytes));
+    ctx->scratch_cap = scratch_bytes;
+  }
+  return FD_OK;
+}
+
+size_t scratch_need(std::vector<Group>& groups) {
+  size_t off = 0;
+  for (auto& g : groups) {
+    g.scratch_off = off;
+    off += (size_t)g.grid * (size_t)g.L.slot_bytes;
+    off = (off + 255) & ~(size_t)255;
+  }
+  return off;
+}
+
+int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
+        double* const* F, int prec, void* stream_, int kind) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  ctx->last_launches = 0;
+  ctx->last_batch = batch;
+  if (batch == 0) return FD_OK;
+  if (prec != FD_PREC_FP64)
+    return fail(ctx, FD_ERR_UNSUPPORTED, "precision %d is not built yet", prec);
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  std::vector<Group> groups = plan(ctx, batch, probs, kind);
+  size_t need = scratch_need(groups);
+  int rc = ensure(ctx, (size_t)batch, (size_t)batch, groups.size(), need);
+  if (rc != FD_OK) return rc;
+  if (ctx->staging_pending) {
+    FD_CUDA(ctx, cudaEventSynchronize(ctx->staging_done));
+    ctx->staging_pending = false;
+  }
+  size_t k = 0;
+  for (auto& g : groups) {
+    g.desc_off = k;
+    for (int c : g.idx) {
+      const fd_problem& p = probs[c];
+      Desc d;
+      d.nx = p.nx;
+      d.nt = p.nt;
+      d.nstab = p.n_stab;
+      d.user_index = c;
+      d.E = p.expA;
+      d.Einv = p.expA_inv;
+      d.phi = p.phi;
+      d.logdet = logdet + 2 * (size_t)c;
+      d.G = G ? (double2*)G[c] : nullptr;
+      d.F = F ? (double2*)F[c] : nullptr;
+      ctx->h_desc[k++] = d;
+    }
+  }
+  FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(Desc) * batch,
+                               cudaMemcpyHostToDevice, stream));
+  FD_CUDA(ctx, cudaEventRecord(ctx->staging_done, stream));
+  ctx->staging_pending = true;
+  FD_CUDA(ctx, cudaMemsetAsync(ctx->d_queue, 0, sizeof(int) * groups.size(), stream));
+  FD_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * batch, stream));
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    Group& g = groups[gi];
+    if (g.L.smem_bytes > ctx->smem_attr) {
+      FD_CUDA(ctx, fd::set_smem_fp64(ctx->max_smem_optin));
+      ctx->smem_attr = ctx->max_smem_optin;
+    }
+    if (kind == K_FWD)
+      fd::launch_fwd_fp64(ctx->d_desc + g.desc_off, (int)g.idx.size(), ctx->d_queue + gi,
+                          ctx->d_status, ctx->scratch + g.scratch_off, g.L, g.grid, stream);
+    else
+      fd::launch_force_fp64(ctx->d_desc + g.desc_off, (int)g.idx.size(), ctx->d_queue + gi,
+                            ctx->d_status, ctx->scratch + g.scratch_off, g.L, g.grid, stream);
+    ctx->last_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+  }
+  return FD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fd_ctx_create(fd_ctx** out, int device) {
+  if (!out) return FD_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) return FD_ERR_CUDA;
+  if (device < 0 || device >= ndev) return FD_ERR_INVALID;
+  if (cudaSetDevice(device) != cudaSuccess) return FD_ERR_CUDA;
+  fd_ctx* ctx = new fd_ctx();
+  ctx->device = device;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  cudaDeviceGetAttribute(&ctx->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+  if (cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming) != cudaSuccess ||
+      fd::set_smem_fp64(ctx->max_smem_optin) != cudaSuccess) {
+    delete ctx;
+    return FD_ERR_CUDA;
+  }
+  ctx->smem_attr = ctx->max_smem_optin;
+  *out = ctx;
+  return FD_OK;
+}
+
+void fd_ctx_destroy(fd_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->staging_pending) cudaEventSynchronize(ctx->staging_done);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->d_desc) cudaFree(ctx->d_desc);
+  if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
+  if (ctx->d_queue) cudaFree(ctx->d_queue);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
+  delete ctx;
+}
+
+const char* fd_last_error(const fd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int fd_reserve(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec) {
+  double dummy;
+  int rc = validate(ctx, batch, probs, &dummy, prec, (what & FD_WANT_FORCE) != 0);
+  if (rc != FD_OK) return rc;
+  if (batch == 0) return FD_OK;
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  std::vector<Group> groups = plan(ctx, batch, probs, (what & FD_WANT_FORCE) ? K_FORCE : K_FWD);
+  size_t need = scratch_need(groups);
+  rc = ensure(ctx, (size_t)batch, (size_t)batch, groups.size(), need);
+  if (rc != FD_OK) return rc;
+  if (ctx->max_smem_optin > ctx->smem_attr) {
+    FD_CUDA(ctx, fd::set_smem_fp64(ctx->max_smem_optin));
+    ctx->smem_attr = ctx->max_smem_optin;
+  }
+  return FD_OK;
+}
+
+int fd_logdet(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, int prec,
+              void* stream) {
+  int rc = validate(ctx, batch, probs, logdet, prec, false);
+  if (rc != FD_OK) return rc;
+  return run(ctx, batch, probs, logdet, nullptr, nullptr, prec, stream, K_FWD);
+}
+
+int fd_green(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
+             int prec, void* stream) {
+  int rc = validate(ctx, batch, probs, logdet, prec, false);
+  if (rc != FD_OK) return rc;
+  if (batch > 0 && !G) return fail(ctx, FD_ERR_INVALID, "null G array");
+  for (int c = 0; c < batch; ++c)
+    if (!G[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null G", c);
+  return run(ctx, batch, probs, logdet, G, nullptr, prec, stream, K_FWD);
+}
+
+int fd_force(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
+             double* const* F, int prec, void* stream) {
+  int rc = validate(ctx, batch, probs, logdet, prec, true);
+  if (rc != FD_OK) return rc;
+  if (batch > 0 && !F) return fail(ctx, FD_ERR_INVALID, "null F array");
+  for (int c = 0; c < batch; ++c) {
+    if (!F[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null F", c);
+    if (G && !G[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null G", c);
+  }
+  return run(ctx, batch, probs, logdet, G, F, prec, stream, K_FORCE);
+}
+
+int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch) {
+  if (!ctx) return FD_ERR_INVALID;
+  if (batch < 0 || batch > ctx->last_batch)
+    return fail(ctx, FD_ERR_INVALID, "batch %d exceeds last call's %d", batch, ctx->last_batch);
+  if (batch > 0 && !per_config_status) return fail(ctx, FD_ERR_INVALID, "null status array");
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  FD_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+  if (batch == 0) return FD_OK;
+  std::vector<int> st(batch);
+  FD_CUDA(ctx, cudaMemcpy(st.data(), ctx->d_status, sizeof(int) * batch, cudaMemcpyDeviceToHost));
+  int worst = FD_OK;
+  for (int c = 0; c < batch; ++c) {
+    int code = st[c] == fd::ST_OK ? FD_OK : (st[c] == fd::ST_TIMEOUT ? FD_ERR_TIMEOUT : FD_ERR_NUMERIC);
+    per_config_status[c] = code;
+    if (code < worst) worst = code;
+  }
+  return worst;
+}
+
+int fd_last_launch_count(const fd_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+int fd_measure_fp64_peak(fd_ctx* ctx, double* gflops) {
+  if (!ctx || !gflops) return FD_ERR_INVALID;
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  FD_CUDA(ctx, fd::run_fp64_probe(ctx->num_sms * 8, 256, 4096, gflops, 0));
+  return FD_OK;
+}
+
+}  // extern "C"

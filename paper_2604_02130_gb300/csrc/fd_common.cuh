@@ -1,0 +1,92 @@
+// fd_common.cuh -- shared device-side definitions: complex helpers, the per-configuration
+// descriptor, buffer placement and status codes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fd.h"
+
+namespace fd {
+
+// ---------------------------------------------------------------- complex FP64 helpers
+struct cplx {
+  double re, im;
+};
+
+__device__ __forceinline__ cplx cx(double r, double i) { return cplx{r, i}; }
+__device__ __forceinline__ cplx operator+(cplx a, cplx b) { return cplx{a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cplx operator-(cplx a, cplx b) { return cplx{a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cplx operator*(cplx a, cplx b) {
+  return cplx{fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ cplx operator*(double s, cplx a) { return cplx{s * a.re, s * a.im}; }
+__device__ __forceinline__ cplx conj(cplx a) { return cplx{a.re, -a.im}; }
+__device__ __forceinline__ double abs2(cplx a) { return fma(a.re, a.re, a.im * a.im); }
+// conj(a) * b
+__device__ __forceinline__ cplx cmulc(cplx a, cplx b) {
+  return cplx{fma(a.re, b.re, a.im * b.im), fma(a.re, b.im, -a.im * b.re)};
+}
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  // scaled division (Smith-free but overflow-safe enough for O(1)..1e150 magnitudes)
+  double s = fmax(fabs(b.re), fabs(b.im));
+  double br = b.re / s, bi = b.im / s;
+  double d = fma(br, br, bi * bi);
+  return cplx{fma(a.re, br, a.im * bi) / (d * s), fma(a.im, br, -a.re * bi) / (d * s)};
+}
+__device__ __forceinline__ cplx ld(const double2* p) {
+  double2 v = *p;
+  return cplx{v.x, v.y};
+}
+__device__ __forceinline__ void st(double2* p, cplx v) { *p = make_double2(v.re, v.im); }
+
+// ---------------------------------------------------------------- descriptors
+// One configuration as the kernels see it (built on the host from fd_problem + outputs).
+struct Desc {
+  int nx, nt, nstab, user_index;
+  const double* E;     // nx*nx (symmetric)
+  const double* Einv;  // nx*nx or null
+  const double* phi;   // nt*nx
+  double* logdet;      // 2 doubles
+  double2* G;          // nx*nx row-major or null
+  double2* F;          // nt*nx row-major or null
+};
+
+// Where each working matrix lives: shared memory (offset in bytes from the dynamic smem base)
+// or the CTA's global scratch slot (offset in bytes from the slot base).  Each persistent CTA
+// owns one slot of `slot_bytes` and reuses it for every configuration it processes; the force
+// checkpoints follow the working buffers inside the slot.  Generic pointers let the same code
+// run on either memory.
+enum Buf {
+  B_E = 0,   // real nx*nx
+  B_EINV,    // real nx*nx
+  B_X0,      // complex nx*nx (column-major)
+  B_X1,
+  B_T0,
+  B_T1,
+  B_GLO,     // force only
+  B_GHI,
+  B_GA,
+  B_GB,
+  B_NBUF
+};
+
+struct Layout {
+  int nthreads;
+  int smem_bytes;              // dynamic shared memory per CTA
+  int small_off;               // offset (bytes, in smem) of the small-vector area
+  int in_smem[B_NBUF];         // 1 = shared memory
+  long long off[B_NBUF];       // byte offsets
+  long long ws_bytes;          // working buffers kept in global memory (bytes per slot)
+  long long slot_bytes;        // ws_bytes + checkpoints (bytes per slot)
+};
+
+__host__ __device__ __forceinline__ int small_bytes(int n) {
+  // ph 2n, rdiag n, vbuf 2n complex; 10 n doubles; red 64 doubles; perm, piv n ints; misc 32 ints
+  return 16 * 5 * n + 8 * 10 * n + 8 * 64 + 4 * 2 * n + 4 * 32;
+}
+
+// status codes written per configuration (device side)
+enum { ST_OK = 0, ST_NUMERIC = 1, ST_TIMEOUT = 2 };
+
+}  // namespace fd

@@ -1,0 +1,554 @@
+// fd_fp64.cuh -- CTA-level FP64 building blocks of the stabilised method (Section 7).
+//
+// Every routine is executed by all threads of one CTA on one configuration.  Matrices are
+// complex128 (double2), column-major with leading dimension n, addressed through generic
+// pointers so that the same code runs on shared-memory or global (L2-resident) buffers.
+// Contract: inputs are visible to every thread on entry (the caller synchronised), and each
+// routine ends with __syncthreads() so that its outputs are visible on return.
+#pragma once
+
+#include "fd_common.cuh"
+
+namespace fd {
+
+__device__ __forceinline__ int nthr() { return blockDim.x; }
+__device__ __forceinline__ int tid() { return threadIdx.x; }
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+__device__ __forceinline__ int nwarps() { return blockDim.x >> 5; }
+
+__device__ __forceinline__ int seg_width(int rows) {
+  int w = 1;
+  while (w < rows && w < 32) w <<= 1;
+  return w;
+}
+
+// xor-reduction inside aligned groups of W lanes (all 32 lanes must call it)
+__device__ __forceinline__ double seg_sum(double v, int W) {
+  for (int o = W >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- operand views
+struct RealMat {  // element (i,k) = p[i*rs + k*cs]
+  const double* p;
+  int rs, cs;
+  __device__ __forceinline__ double operator()(int i, int k) const { return p[i * rs + k * cs]; }
+};
+struct CMat {  // element (i,k) = p[i*rs + k*cs]
+  const double2* p;
+  int rs, cs;
+  __device__ __forceinline__ cplx operator()(int i, int k) const { return ld(p + i * rs + k * cs); }
+};
+struct CMatH {  // element (i,k) = conj(p[k*rs + i*cs]) : conjugate transpose of a stored matrix
+  const double2* p;
+  int rs, cs;
+  __device__ __forceinline__ cplx operator()(int i, int k) const {
+    return conj(ld(p + k * rs + i * cs));
+  }
+};
+
+__device__ __forceinline__ void mac(cplx& acc, double a, cplx b) {
+  acc.re = fma(a, b.re, acc.re);
+  acc.im = fma(a, b.im, acc.im);
+}
+__device__ __forceinline__ void mac(cplx& acc, cplx a, double b) {
+  acc.re = fma(a.re, b, acc.re);
+  acc.im = fma(a.im, b, acc.im);
+}
+__device__ __forceinline__ void mac(cplx& acc, cplx a, cplx b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+
+// Out(i,j) <- epi(i, j, sum_{k in [k_lo(i0), n)} A(i,k) B(k,j)), i,j in [0,n).
+// 2x2 register tiles; consecutive threads take consecutive row tiles.  If TRI, A is treated as
+// upper triangular (A(i,k) = 0 for k < i).  Out must not alias A or B.
+template <bool TRI, class AOp, class BOp, class Epi>
+__device__ void cta_gemm(int n, const AOp& A, const BOp& B, const Epi& epi) {
+  const int tm = (n + 1) >> 1;
+  const int ntiles = tm * tm;
+  for (int tile = tid(); tile < ntiles; tile += nthr()) {
+    const int i0 = (tile % tm) * 2, j0 = (tile / tm) * 2;
+    const int i1 = min(i0 + 1, n - 1), j1 = min(j0 + 1, n - 1);
+    cplx a00 = cx(0, 0), a01 = cx(0, 0), a10 = cx(0, 0), a11 = cx(0, 0);
+    int k = TRI ? i0 : 0;
+    if (TRI) {  // k = i0 contributes to row i0 only
+      auto a0 = A(i0, k);
+      mac(a00, a0, B(k, j0));
+      mac(a01, a0, B(k, j1));
+      ++k;
+    }
+#pragma unroll 2
+    for (; k < n; ++k) {
+      auto a0 = A(i0, k);
+      auto a1 = A(i1, k);
+      auto b0 = B(k, j0);
+      auto b1 = B(k, j1);
+      mac(a00, a0, b0);
+      mac(a01, a0, b1);
+      mac(a10, a1, b0);
+      mac(a11, a1, b1);
+    }
+    epi(i0, j0, a00);
+    if (j0 + 1 < n) epi(i0, j0 + 1, a01);
+    if (i0 + 1 < n) {
+      epi(i0 + 1, j0, a10);
+      if (j0 + 1 < n) epi(i0 + 1, j0 + 1, a11);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- small helpers
+__device__ __forceinline__ void cta_copy(int count, double2* dst, const double2* src) {
+  for (int e = tid(); e < count; e += nthr()) dst[e] = src[e];
+}
+__device__ __forceinline__ void cta_identity(int n, double2* A) {
+  for (int e = tid(); e < n * n; e += nthr()) {
+    int i = e % n, j = e / n;
+    A[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+__device__ __forceinline__ void cta_load_real(int count, double* dst, const double* src) {
+  for (int e = tid(); e < count; e += nthr()) dst[e] = src[e];
+}
+// phase vector e^{i s phi} of one slice (s = +1 or -1)
+__device__ __forceinline__ void cta_phase(int n, double2* ph, const double* phi_row, double s) {
+  for (int x = tid(); x < n; x += nthr()) {
+    double sn, cs;
+    sincos(phi_row[x], &sn, &cs);
+    ph[x] = make_double2(cs, s * sn);
+  }
+}
+// rows of A scaled by ph:  A(i,j) *= ph[i]
+__device__ __forceinline__ void cta_scale_rows(int n, double2* A, const double2* ph) {
+  for (int e = tid(); e < n * n; e += nthr()) {
+    int i = e % n;
+    st(A + e, ld(ph + i) * ld(A + e));
+  }
+}
+
+// Per-CTA small vectors (shared memory)
+struct Small {
+  double2* ph;     // 2n  phase of the current / next slice
+  double2* rdiag;  // n   diag R of the last QR
+  double2* vbuf;   // 2n  reflector copies (Q formation)
+  double* logD;    // n   log D of the left / forward product
+  double* logDR;   // n   log D of the right product (force)
+  double* logw;    // n   permuted weights during a QR
+  double* tau;     // n
+  double* key;     // n   pivot keys / row scales
+  double* sa;      // n   scale vectors
+  double* sb;      // n
+  double* sc;      // n
+  double* sd;      // n
+  int* perm;       // n
+  int* piv;        // n
+  int* misc;       // 32 ints: [0] status bits, [1] swap parity, [2] pivot index
+  double* red;     // 64 doubles: cross-warp reductions
+};
+
+__device__ __forceinline__ Small carve_small(char* base, int n) {
+  Small s;
+  char* p = base;
+  s.ph = (double2*)p;    p += 32 * n;
+  s.rdiag = (double2*)p; p += 16 * n;
+  s.vbuf = (double2*)p;  p += 32 * n;
+  s.logD = (double*)p;   p += 8 * n;
+  s.logDR = (double*)p;  p += 8 * n;
+  s.logw = (double*)p;   p += 8 * n;
+  s.tau = (double*)p;    p += 8 * n;
+  s.key = (double*)p;    p += 8 * n;
+  s.sa = (double*)p;     p += 8 * n;
+  s.sb = (double*)p;     p += 8 * n;
+  s.sc = (double*)p;     p += 8 * n;
+  s.sd = (double*)p;     p += 8 * n;
+  p += 8 * n;  // spare
+  s.red = (double*)p;    p += 8 * 64;
+  s.perm = (int*)p;      p += 4 * n;
+  s.piv = (int*)p;       p += 4 * n;
+  s.misc = (int*)p;
+  return s;
+}
+
+// ---------------------------------------------------------------- Householder helpers
+// Reflector for column k of A (rows k..n-1), computed by one segment of W lanes (sl = lane in
+// segment, all 32 lanes of the warp call this; only the owning segment's results are stored).
+// H = I - tau v v^H with v_k = 1, tau real = 2/(v^H v), H x = alpha e_k,
+// alpha = -(x_k/|x_k|) ||x||.  v (rows > k) overwrites A; rdiag[k] = alpha.
+__device__ __forceinline__ void seg_reflector(int n, int k, double2* A, int W, int sl, bool owner,
+                                              Small& s) {
+  double sig = 0.0;
+  if (owner)
+    for (int i = k + 1 + sl; i < n; i += W) sig += abs2(ld(A + i + k * n));
+  sig = seg_sum(sig, W);
+  if (!owner) return;
+  cplx x = ld(A + k + k * n);
+  if (k == n - 1) {
+    if (sl == 0) {
+      s.tau[k] = 0.0;
+      st(s.rdiag + k, x);
+    }
+    return;
+  }
+  double ax = sqrt(abs2(x));
+  double nrm = sqrt(fma(ax, ax, sig));
+  if (nrm == 0.0) {  // exactly zero column: singular product
+    if (sl == 0) {
+      s.tau[k] = 0.0;
+      st(s.rdiag + k, cx(0, 0));
+      atomicOr(&s.misc[0], 1);
+    }
+    return;
+  }
+  cplx ph = ax > 0.0 ? cx(x.re / ax, x.im / ax) : cx(1.0, 0.0);
+  cplx alpha = cx(-ph.re * nrm, -ph.im * nrm);
+  cplx c = x - alpha;  // |c| = |x_k| + nrm >= nrm > 0
+  double c2 = abs2(c);
+  cplx cinv = cx(c.re / c2, -c.im / c2);
+  for (int i = k + 1 + sl; i < n; i += W) st(A + i + k * n, ld(A + i + k * n) * cinv);
+  if (sl == 0) {
+    s.tau[k] = 2.0 / (1.0 + sig / c2);
+    st(s.rdiag + k, alpha);
+  }
+}
+
+// ---------------------------------------------------------------- QR re-orthogonalisation
+// One stabilisation step (Eqs. prod_2_mat_stab .. res_2_mat_stab with the QR every n_stab
+// slices of Section 9):  the current product is Xc diag(e^{logD}) Tc where Xc already carries
+// the latest slices.  Householder QR of Z = Xc diag(D) with the columns pre-sorted by
+// ||z_j|| = e^{logD_j} ||xc_j|| (pre-pivoting; the column scaling itself is never formed, since
+// a Householder QR is invariant under it: QR(Y D Pi) = Q R_Y (Pi^T D Pi)).
+// Result: Xn = Q, logD_k = log|R_kk| + logD_{pi(k)},
+//         Tn = diag(D')^{-1} R Pi^T Tc  with coefficients R'_kj e^{logw_j - logw_k} / |R'_kk|.
+__device__ void cta_reortho(int n, const double2* Xc, double2* Xn, const double2* Tc,
+                            double2* Tn, double* logD, Small& s) {
+  const int W0 = seg_width(n);
+  const int spw0 = 32 / W0;
+  const int lane = lane_id(), w = warp_id(), NW = nwarps();
+  // 1. pivot keys
+  for (int base = w * spw0; base < n; base += NW * spw0) {
+    int j = base + lane / W0;
+    int sl = lane % W0;
+    double a = 0.0;
+    if (j < n)
+      for (int i = sl; i < n; i += W0) a += abs2(ld(Xc + i + j * n));
+    a = seg_sum(a, W0);
+    if (j < n && sl == 0) {
+      double kk = logD[j] + 0.5 * log(a);
+      if (kk != kk) {  // NaN
+        kk = -INFINITY;
+        atomicOr(&s.misc[0], 1);
+      }
+      s.key[j] = kk;
+    }
+  }
+  __syncthreads();
+  // 2. rank sort, descending key, ties by index
+  for (int j = tid(); j < n; j += nthr()) {
+    double kj = s.key[j];
+    int r = 0;
+    for (int i = 0; i < n; ++i) {
+      double ki = s.key[i];
+      r += (ki > kj) || (ki == kj && i < j);
+    }
+    s.perm[r] = j;
+  }
+  __syncthreads();
+  // 3. gather columns
+  for (int e = tid(); e < n * n; e += nthr()) {
+    int i = e % n, k = e / n;
+    Xn[e] = Xc[i + s.perm[k] * n];
+  }
+  for (int k = tid(); k < n; k += nthr()) s.logw[k] = logD[s.perm[k]];
+  __syncthreads();
+  // 4. Householder factorisation, one barrier per column
+  if (w == 0) seg_reflector(n, 0, Xn, W0, lane % W0, lane < W0, s);
+  __syncthreads();
+  for (int k = 0; k < n - 1; ++k) {
+    const int rows = n - k;
+    const int W = seg_width(rows);
+    const int spw = 32 / W;
+    const int sl = lane % W;
+    const double tk = s.tau[k];
+    for (int base = k + 1 + w * spw; base < n; base += NW * spw) {
+      int j = base + lane / W;
+      bool act = j < n;
+      double sr = 0.0, si = 0.0;
+      if (act) {
+        for (int i = k + sl; i < n; i += W) {
+          cplx v = (i == k) ? cx(1.0, 0.0) : ld(Xn + i + k * n);
+          cplx a = ld(Xn + i + j * n);
+          cplx p = cmulc(v, a);
+          sr += p.re;
+          si += p.im;
+        }
+      }
+      sr = seg_sum(sr, W);
+      si = seg_sum(si, W);
+      if (act) {
+        cplx f = cx(tk * sr, tk * si);
+        for (int i = k + sl; i < n; i += W) {
+          cplx v = (i == k) ? cx(1.0, 0.0) : ld(Xn + i + k * n);
+          st(Xn + i + j * n, ld(Xn + i + j * n) - f * v);
+        }
+      }
+      // the segment that owns column k+1 (warp 0, segment 0, first round) makes its reflector
+      if (base == k + 1) {
+        __syncwarp();
+        seg_reflector(n, k + 1, Xn, W, sl, lane < W, s);
+      }
+    }
+    __syncthreads();
+  }
+  if (n == 1) {
+    // seg_reflector(k = n-1) already stored rdiag[0], tau[0]
+  }
+  // 5. new log D and the T-update coefficients (in place in the upper triangle)
+  for (int k = tid(); k < n; k += nthr()) {
+    double r = sqrt(abs2(ld(s.rdiag + k)));
+    if (!(r > 0.0)) atomicOr(&s.misc[0], 1);
+    logD[k] = log(r) + s.logw[k];
+  }
+  for (int e = tid(); e < n * n; e += nthr()) {
+    int k = e % n, j = e / n;
+    if (j < k) continue;
+    cplx rkk = ld(s.rdiag + k);
+    double r = sqrt(abs2(rkk));
+    cplx c;
+    if (j == k) {
+      c = cx(rkk.re / r, rkk.im / r);
+    } else {
+      cplx rkj = ld(Xn + e);
+      double ex = s.logw[j] - s.logw[k];
+      if (ex < 600.0) {
+        double f = exp(ex) / r;
+        c = f * rkj;
+      } else {
+        double m = sqrt(abs2(rkj));
+        if (m == 0.0) {
+          c = cx(0, 0);
+        } else {
+          double f = exp(log(m) - log(r) + ex) / m;
+          c = f * rkj;
+        }
+      }
+    }
+    st(Xn + e, c);
+  }
+  __syncthreads();
+  // 6. Tn = C (Pi^T Tc), C upper triangular
+  {
+    const double2* Tg = Tc;
+    const int* perm = s.perm;
+    struct CUp {
+      const double2* p;
+      int n;
+      __device__ __forceinline__ cplx operator()(int i, int k) const {
+        return k >= i ? ld(p + i + k * n) : cx(0, 0);
+      }
+    } Cop{Xn, n};
+    struct TP {
+      const double2* p;
+      const int* perm;
+      int n;
+      __device__ __forceinline__ cplx operator()(int k, int c) const {
+        return ld(p + perm[k] + c * n);
+      }
+    } Top{Tg, perm, n};
+    cta_gemm<true>(n, Cop, Top, [&](int i, int j, cplx v) { st(Tn + i + j * n, v); });
+  }
+  // 7. form Q in place: Q = H_0 H_1 ... H_{n-2}, accumulated backwards
+  for (int e = tid(); e < n * n; e += nthr()) {
+    int i = e % n, j = e / n;
+    if (i < j) Xn[e] = make_double2(0.0, 0.0);
+    if (i == n - 1 && j == n - 1) Xn[e] = make_double2(1.0, 0.0);
+  }
+  if (n >= 2)  // copy v_{n-2} (rows > n-2) to vbuf[(n-2)&1]
+    for (int i = n - 1 + tid(); i < n; i += nthr())
+      s.vbuf[((n - 2) & 1) * n + i] = Xn[i + (n - 2) * n];
+  __syncthreads();
+  for (int k = n - 2; k >= 0; --k) {
+    const int rows = n - k;
+    const int W = seg_width(rows);
+    const int spw = 32 / W;
+    const int sl = lane % W;
+    const double tk = s.tau[k];
+    const double2* vk = s.vbuf + (k & 1) * n;
+    for (int base = k + w * spw; base < n; base += NW * spw) {
+      int j = base + lane / W;
+      bool act = j < n && j > k;
+      double sr = 0.0, si = 0.0;
+      if (act)
+        for (int i = k + 1 + sl; i < n; i += W) {
+          cplx p = cmulc(ld(vk + i), ld(Xn + i + j * n));
+          sr += p.re;
+          si += p.im;
+        }
+      sr = seg_sum(sr, W);
+      si = seg_sum(si, W);
+      if (act) {
+        cplx f = cx(tk * sr, tk * si);
+        if (sl == 0) st(Xn + k + j * n, cx(-f.re, -f.im));
+        for (int i = k + 1 + sl; i < n; i += W) st(Xn + i + j * n, ld(Xn + i + j * n) - f * ld(vk + i));
+      }
+      if (j == k) {  // this segment sets column k and copies v_{k-1}
+        if (sl == 0) Xn[k + k * n] = make_double2(1.0 - tk, 0.0);
+        for (int i = k + 1 + sl; i < n; i += W) st(Xn + i + k * n, cx(-tk, 0.0) * ld(vk + i));
+        if (k >= 1)
+          for (int i = k + sl; i < n; i += W) s.vbuf[((k - 1) & 1) * n + i] = Xn[i + (k - 1) * n];
+      }
+    }
+    __syncthreads();
+  }
+  if (n == 1) {
+    if (tid() == 0) Xn[0] = make_double2(1.0, 0.0);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- LU with partial pivoting
+// Factor A in place (A = P^T L U, unit L), applying the same row operations to the n columns of
+// Bm (so that Bm <- L^{-1} P Bm), then back-substitute Bm <- U^{-1} Bm.  On return Bm holds
+// A^{-1} Bm_in and *logdet_out = log det A (principal logs of the pivots + i pi * swaps).
+__device__ void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, double* logdet_re,
+                             double* logdet_im) {
+  const int lane = lane_id(), w = warp_id();
+  if (tid() == 0) s.misc[1] = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (w == 0) {
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + lane; i < n; i += 32) {
+        double m = abs2(ld(A + i + k * n));
+        if (m > best) {
+          best = m;
+          bi = i;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      const int p = bi;
+      if (p != k) {
+        for (int j = lane; j < n; j += 32) {
+          double2 t = A[k + j * n];
+          A[k + j * n] = A[p + j * n];
+          A[p + j * n] = t;
+          t = Bm[k + j * n];
+          Bm[k + j * n] = Bm[p + j * n];
+          Bm[p + j * n] = t;
+        }
+        if (lane == 0) s.misc[1] ^= 1;
+      }
+      __syncwarp();
+      cplx piv = ld(A + k + k * n);
+      if (!(abs2(piv) > 0.0)) {
+        if (lane == 0) atomicOr(&s.misc[0], 1);
+        piv = cx(1e-300, 0.0);
+      }
+      double p2 = abs2(piv);
+      cplx pinv = cx(piv.re / p2, -piv.im / p2);
+      for (int i = k + 1 + lane; i < n; i += 32) st(A + i + k * n, ld(A + i + k * n) * pinv);
+    }
+    __syncthreads();
+    // trailing update of A (columns k+1..n-1) and of all columns of Bm, rows k+1..n-1
+    const int m = n - k - 1;
+    const int cols = m + n;
+    for (int e = tid(); e < m * cols; e += nthr()) {
+      int i = k + 1 + e % m;
+      int c = e / m;
+      cplx l = ld(A + i + k * n);
+      if (c < m) {
+        int j = k + 1 + c;
+        st(A + i + j * n, ld(A + i + j * n) - l * ld(A + k + j * n));
+      } else {
+        int j = c - m;
+        st(Bm + i + j * n, ld(Bm + i + j * n) - l * ld(Bm + k + j * n));
+      }
+    }
+    __syncthreads();
+  }
+  // log det A
+  if (w == 0) {
+    double lr = 0.0, li = 0.0;
+    for (int k = lane; k < n; k += 32) {
+      cplx u = ld(A + k + k * n);
+      lr += 0.5 * log(abs2(u));
+      li += atan2(u.im, u.re);
+    }
+    lr = seg_sum(lr, 32);
+    li = seg_sum(li, 32);
+    if (lane == 0) {
+      *logdet_re = lr;
+      *logdet_im = li + (s.misc[1] ? 3.14159265358979323846 : 0.0);
+    }
+  }
+  // back substitution U X = Bm
+  for (int k = n - 1; k >= 0; --k) {
+    for (int j = tid(); j < n; j += nthr()) {
+      cplx u = ld(A + k + k * n);
+      st(Bm + k + j * n, cdiv(ld(Bm + k + j * n), u));
+    }
+    __syncthreads();
+    for (int e = tid(); e < k * n; e += nthr()) {
+      int i = e % k, j = e / k;
+      st(Bm + i + j * n, ld(Bm + i + j * n) - ld(A + i + k * n) * ld(Bm + k + j * n));
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- assembly (Section 7)
+// With D = D_b D_s, D_b = max(D,1), D_s = min(D,1):
+//   1 + X D T = X D_b C,  C = D_b^{-1} X^H + D_s T,
+//   log det(1 + X D T) = log det X + sum log D_b + log det C,  G = C^{-1} D_b^{-1} X^H.
+// X is the Q of the last QR (product of n-1 reflections): det X = (-1)^{n-1}.
+// Cbuf and Gbuf are scratch; on return Gbuf holds G (column-major).
+__device__ void cta_assemble(int n, const double2* X, const double2* T, const double* logD,
+                             double2* Cbuf, double2* Gbuf, Small& s, double* ld_re,
+                             double* ld_im) {
+  for (int e = tid(); e < n * n; e += nthr()) {
+    int i = e % n, j = e / n;
+    double lb = fmax(logD[i], 0.0);
+    double ls = fmin(logD[i], 0.0);
+    double ib = exp(-lb), ds = exp(ls);
+    cplx xh = conj(ld(X + j + i * n));
+    cplx r = ib * xh;
+    st(Gbuf + e, r);
+    st(Cbuf + e, r + ds * ld(T + e));
+  }
+  __syncthreads();
+  double cre = 0.0, cim = 0.0;
+  cta_lu_solve(n, Cbuf, Gbuf, s, s.red + 0, s.red + 1);
+  if (warp_id() == 0) {
+    double sb = 0.0;
+    for (int k = lane_id(); k < n; k += 32) sb += fmax(logD[k], 0.0);
+    sb = seg_sum(sb, 32);
+    if (lane_id() == 0) {
+      cre = s.red[0] + sb;
+      cim = s.red[1] + ((n - 1) & 1 ? 3.14159265358979323846 : 0.0);
+      *ld_re = cre;
+      *ld_im = cim;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double wrap_pi(double x) {
+  const double pi = 3.14159265358979323846;
+  double y = remainder(x, 2.0 * pi);  // (-pi, pi]
+  if (y <= -pi) y += 2.0 * pi;
+  return y;
+}
+
+}  // namespace fd

@@ -1,0 +1,47 @@
+// fd_probe.cu -- FP64 FMA throughput probe (the roofline denominator of the FP64 pipe).
+//
+// Every thread runs 8 independent chains of dependent DFMAs; the result is written so the
+// compiler cannot drop the work.  GFLOP/s = 2 * grid * threads * iters * 8 / time.
+#include "fd_kernels.h"
+
+namespace fd {
+
+__global__ void k_fp64_probe(int iters, double* sink) {
+  double a0 = threadIdx.x * 1e-9, a1 = a0 + 1e-10, a2 = a0 + 2e-10, a3 = a0 + 3e-10;
+  double a4 = a0 + 4e-10, a5 = a0 + 5e-10, a6 = a0 + 6e-10, a7 = a0 + 7e-10;
+  const double m = 0.9999999, c = 1e-12;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+      a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+    }
+  }
+  double s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == 12345.678) sink[threadIdx.x] = s;  // practically never; keeps the chains live
+}
+
+cudaError_t run_fp64_probe(int grid, int threads, int iters, double* out, cudaStream_t stream) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double* sink = nullptr;
+  cudaError_t err = cudaMalloc(&sink, sizeof(double) * threads);
+  if (err != cudaSuccess) return err;
+  k_fp64_probe<<<grid, threads, 0, stream>>>(iters / 8 + 1, sink);  // warm-up
+  cudaEventRecord(e0, stream);
+  k_fp64_probe<<<grid, threads, 0, stream>>>(iters, sink);
+  cudaEventRecord(e1, stream);
+  err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaFree(sink);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return err;
+  double flops = 2.0 * grid * threads * (double)iters * 16.0 * 8.0;
+  *out = flops / (ms * 1e-3) / 1e9;
+  return cudaGetLastError();
+}
+
+}  // namespace fd

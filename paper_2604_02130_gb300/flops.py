@@ -1,0 +1,37 @@
+"""Algorithmic operation counts of the stabilised method (real flops; a complex multiply-add
+counts 8, a real x complex multiply-add 4).  Padding and repeated work are not counted; the
+same counts are used for every path (CPU oracle, FP64 GPU, mixed GPU).
+
+Per configuration with n = Nx, blocks nb = Nt / n_stab:
+  slice products  (Section 7 products, Section 9 blocking):  4 n^3 per slice  (E real)
+  QR re-orthogonalisation per block: factor 16/3 n^3 + form Q 16/3 n^3 + T update 4 n^3
+  assembly (Section 7 steps 4-6, scale separated): LU 8/3 n^3 + solve 8 n^3
+  force (Section 4 response, Section 5.3 pre/suffix): right products 4 n^3 per slice,
+    wraps 8 n^3 per slice, one QR (44/3 n^3) and one boundary Green's function
+    (2 GEMMs 16 n^3 + LU 8/3 + solve 8 + product 8 = 104/3 n^3) per block.
+"""
+from __future__ import annotations
+
+
+def fwd_flops(nx: int, nt: int, n_stab: int) -> dict:
+    n3 = float(nx) ** 3
+    nb = nt // n_stab
+    slices = 4.0 * n3 * nt
+    qr = (44.0 / 3.0) * n3 * nb
+    asm = (32.0 / 3.0) * n3
+    return {"slices": slices, "qr": qr, "assembly": asm, "total": slices + qr + asm}
+
+
+def force_flops(nx: int, nt: int, n_stab: int) -> dict:
+    """Forward pass (with checkpoints) plus the adjoint sweep."""
+    f = fwd_flops(nx, nt, n_stab)
+    n3 = float(nx) ** 3
+    nb = nt // n_stab
+    right = 4.0 * n3 * nt
+    wraps = 8.0 * n3 * (nt - nb)
+    qr = (44.0 / 3.0) * n3 * nb
+    boundary = (104.0 / 3.0) * n3 * nb
+    bwd = right + wraps + qr + boundary
+    return {"forward": f["total"], "backward": bwd, "total": f["total"] + bwd,
+            "slices_and_wraps": f["slices"] + right + wraps,
+            "per_block_fp64": f["qr"] + f["assembly"] + qr + boundary}

@@ -1,0 +1,76 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, and exports exactly the
+functions include/fd.h declares, with the ctypes signatures the binding uses.  No compute calls
+(there is no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fd_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_02130_gb300 import build
+
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_api():
+    names = _declared()
+    for n in ("fd_ctx_create", "fd_ctx_destroy", "fd_logdet", "fd_green", "fd_force",
+              "fd_status", "fd_last_error", "fd_reserve"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_signatures_cover_header():
+    from paper_2604_02130_gb300 import _lib
+
+    bound = {name for name, _, _ in _lib.SIGNATURES}
+    assert bound == set(_declared())
+
+
+def test_problem_struct_layout():
+    from paper_2604_02130_gb300 import _lib
+
+    assert ctypes.sizeof(_lib.fd_problem) == 40
+    assert _lib.fd_problem.expA.offset == 16
+
+
+def test_ctx_create_without_gpu_fails_cleanly(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    lib.fd_ctx_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
+    rc = lib.fd_ctx_create(ctypes.byref(h), 0)
+    assert rc == -3 and not h.value  # FD_ERR_CUDA, no context
+
+
+def test_null_context_is_rejected(lib):
+    lib.fd_logdet.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_int, ctypes.c_void_p]
+    assert lib.fd_logdet(None, 1, None, None, 0, None) == -1
+
+
+def test_flop_counts():
+    from paper_2604_02130_gb300 import force_flops, fwd_flops
+
+    f = fwd_flops(72, 512, 16)
+    assert abs(f["slices"] - 4 * 72 ** 3 * 512) < 1
+    g = force_flops(72, 256, 8)
+    assert g["total"] > fwd_flops(72, 256, 8)["total"]
