@@ -1,0 +1,388 @@
+"""Benchmark of the batched stabilised fermion determinant on GB300.
+
+One step = log det + G + force (forward pass with checkpoints, adjoint sweep) for one batch of
+configurations.  Default workload: 256 configurations of the honeycomb L = 3 lattice (Nx = 18),
+beta = 8, Nt = 64, U = 3, n_stab = 8.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|tf32|3xtf32]
+                    [--workload batch18|cold72|force72|tiny8] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  `value` is configurations per second over all ranks with the
+inputs resident on the device; `e2e` is the same metric through the public API with the inputs
+copied from pinned host memory and the results read back inside the timed region.
+The reference arm (--impl reference) times the CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+FLUSH_BYTES = 4 * L2_BYTES
+
+WORKLOAD_TEXT = {
+    "batch18": "honeycomb L=3 (Nx=18), kappa=1, beta=8, Nt=64, U=3, phi~N(0,delta*U), n_stab=8, "
+               "256 configs; log det + G + force",
+    "cold72": "honeycomb L=6 (Nx=72), beta=64, Nt=512, U=3.5, n_stab=16, 64 configs; "
+              "log det + G + force",
+    "force72": "honeycomb L=6 (Nx=72), beta=32, Nt=256, U=3, n_stab=8, 32 configs; "
+               "log det + G + force",
+    "tiny8": "honeycomb L=2 (Nx=8), beta=2, Nt=16, U=2, n_stab=4, 1 config; log det + G + force",
+}
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+def _oracle_worker(args):
+    """One configuration through the CPU oracle: stabilised log det and G, and the force."""
+    name, c = args
+    import fd_inputs as fi
+    from oracle import force as oforce
+    from oracle import stable
+
+    p = fi.workload(name, batch=1, first=c)[0]
+    t0 = time.perf_counter()
+    ld, G = stable.logdet_green(p.E, p.phi, p.n_stab)
+    F = oforce.force(p.E, p.phi, p.n_stab)
+    return c, ld, G, F, time.perf_counter() - t0
+
+
+def _pool(cores):
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    pool = mp.get_context("spawn").Pool(cores)
+    for k, v in old.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    return pool
+
+
+def oracle_sample(pool, name, configs):
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_worker, [(name, c) for c in configs])
+    return res, time.perf_counter() - t0
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=parts[3],
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, label in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                               ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(label)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2604_02130_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, workload, prec):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        db = json.load(open(path))
+        e = db.get("%s|%s|%s" % (kernel, workload, prec))
+        if e and e.get("source_hash") == _kernel_source_hash():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        return None
+    return None
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import fd_inputs as fi
+
+    name = args.workload
+    batch = len(fi.workload(name, batch=None)) if name != "tiny8" else 1
+    cores = os.cpu_count() or 1
+    pool = _pool(cores)
+    sample = list(range(min(batch, 8 * cores)))
+    for _ in range(args.warmup):
+        oracle_sample(pool, name, sample[:cores])
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_sample(pool, name, sample)
+        times.append(dt)
+    pool.close()
+    total = sum(times)
+    value = len(sample) * args.steps / total
+    line = {
+        "impl": "reference", "metric": "configs/s (log det + G + force)", "value": value,
+        "unit": "configs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[name], "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "configs/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d of the %d configurations per step, one per process"
+                                   % (len(sample), batch)},
+        "e2e": {"value": value, "unit": "configs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    ws, rank, local = _dist()
+    import numpy as np
+
+    import fd_inputs as fi
+
+    name = args.workload
+    w_batch = 1 if name == "tiny8" else fi.WORKLOADS[name]["batch"]
+    cores = os.cpu_count() or 1
+    pool = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        pool = _pool(cores)  # spawned before the first CUDA call
+    import torch
+
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2604_02130_gb300 import api, force_flops
+
+    dev = torch.device("cuda", local)
+    probs = fi.workload(name, batch=w_batch, first=rank * w_batch)
+    nx, nt = probs[0].nx, probs[0].nt
+    # inputs resident on the device: one phi buffer for the batch; E, E^{-1} shared
+    phi_host = torch.from_numpy(np.stack([p.phi for p in probs])).pin_memory()
+    phi_dev = phi_host.to(dev)
+    E = torch.from_numpy(probs[0].E).to(dev)
+    Einv = torch.from_numpy(probs[0].Einv).to(dev)
+    ctx = api.Context(local)
+    batch = api.Batch(ctx, [(E, Einv, phi_dev[c], p.n_stab) for c, p in enumerate(probs)],
+                      "force+green", args.prec)
+    batch.reserve()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        batch.run()
+    barrier()
+    assert all(s == 0 for s in batch.status()), "device status not OK"
+
+    # ---- device-resident timing: per-step events, L2 flushed between steps
+    ctx.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kernel_ms = []
+    launches = 0
+    barrier()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            batch.run()
+            ev[k][1].record(stream)
+            launches += ctx.last_launch_count()
+            kernel_ms.append(sum(ctx.last_kernel_ms()))
+        barrier()
+    clocks = clk.summary()
+    ctx.set_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n_total = w_batch * ws
+    value = n_total * args.steps / (total_ms * 1e-3)
+
+    # ---- end to end through the public API: pinned host inputs in, results out
+    ld_host = torch.empty((w_batch, 2), dtype=torch.float64).pin_memory()
+    G_host = torch.empty(batch.G_flat.shape, dtype=torch.complex128).pin_memory()
+    F_host = torch.empty(batch.F_flat.shape, dtype=torch.complex128).pin_memory()
+    h2d = phi_host.numel() * 8
+    d2h = ld_host.numel() * 8 + G_host.numel() * 16 + F_host.numel() * 16
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        phi_dev.copy_(phi_host, non_blocking=True)
+        batch.run()
+        ld_host.copy_(batch.logdet_buf, non_blocking=True)
+        G_host.copy_(batch.G_flat, non_blocking=True)
+        F_host.copy_(batch.F_flat, non_blocking=True)
+        ev2[k][1].record(stream)
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": n_total * args.steps / (e2e_ms * 1e-3), "unit": "configs/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (the force kernel: the only launch of the step)
+    fl = force_flops(nx, nt, probs[0].n_stab)
+    fl_launch = fl["total"] * w_batch
+    k_ms = statistics.mean(kernel_ms)
+    peak_gflops = ctx.measure_fp64_peak()
+    achieved = fl_launch / (k_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_gflops / 1e3, "unit": "TFLOP/s",
+            "frac": achieved / (peak_gflops / 1e3),
+            "traffic": _traffic("k_force_fp64", name, args.prec),
+            "kernel": "k_force_fp64", "kernel_ms": k_ms,
+            "peak_source": "measured FP64 DFMA probe (fd_measure_fp64_peak), same run"}
+
+    # ---- CPU oracle on a bounded sample, and the error of the GPU results on that sample
+    cpu = None
+    err = None
+    if pool is not None:
+        sample = list(range(min(w_batch, 8 * cores)))
+        res, dt = oracle_sample(pool, name, sample)
+        pool.close()
+        cpu = {"value": len(sample) / dt, "unit": "configs/s", "cores": cores, "kind": "oracle",
+               "sample": "%d of the %d configurations (log det + G + force), one per process"
+                         % (len(sample), w_batch)}
+        ld = batch.logdet_buf.cpu().numpy()
+        e_ld = e_g = e_f = 0.0
+        for c, ldr, Gr, Fr, _ in res:
+            g = complex(ld[c, 0], ld[c, 1])
+            dim = abs(np.angle(np.exp(1j * (g.imag - ldr.imag))))
+            e_ld = max(e_ld, max(abs(g.real - ldr.real), dim) / abs(ldr))
+            e_g = max(e_g, float(np.abs(batch.G[c].cpu().numpy() - Gr).max()))
+            e_f = max(e_f, float(np.abs(batch.F[c].cpu().numpy() - Fr).max()))
+        err = {"logdet_rel": e_ld, "G_abs": e_g, "F_abs": e_f, "configs_checked": len(res)}
+
+    line = {
+        "metric": "configs/s (log det + G + force)",
+        "value": value,
+        "unit": "configs/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": max(3, args.warmup),
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32+f64", "3xtf32": "3xtf32+f64"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[name], "prec": args.prec,
+                   "l2": "flushed between timed steps (%d MB write)" % (FLUSH_BYTES >> 20)},
+        "tflops": fl["total"] * n_total * args.steps / (total_ms * 1e-3) / 1e12,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "error_vs_oracle": err,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--prec", choices=("fp64", "tf32", "3xtf32"), default="fp64")
+    ap.add_argument("--workload", choices=tuple(WORKLOAD_TEXT), default="batch18")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

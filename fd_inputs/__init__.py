@@ -171,8 +171,9 @@ def _uneven(batch: int = 512, n_stab: int = 16) -> List[Problem]:
 
 
 def workload(name: str, batch: int | None = None, n_stab: int | None = None,
-             zero_field: bool = False) -> List[Problem]:
-    """The configurations of a named workload (optionally truncated to ``batch``)."""
+             zero_field: bool = False, first: int = 0) -> List[Problem]:
+    """The configurations of a named workload (optionally ``batch`` of them, starting at
+    configuration index ``first``; shards of a multi-GPU run use disjoint index ranges)."""
     if name == "uneven512":
         return _uneven(batch or 512, n_stab or 16)
     w = WORKLOADS[name]
@@ -180,4 +181,4 @@ def workload(name: str, batch: int | None = None, n_stab: int | None = None,
     ns = w["n_stab"] if n_stab is None else n_stab
     seed = 1000 + w["index"]
     return [make_problem(w["L"], w["nt"], w["beta"], w["U"], ns, seed, c, zero_field=zero_field)
-            for c in range(b)]
+            for c in range(first, first + b)]

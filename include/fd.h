@@ -118,6 +118,13 @@ int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch);
 /* Number of kernel launches the last fd_logdet/fd_green/fd_force call issued. */
 int fd_last_launch_count(const fd_ctx* ctx);
 
+/* Per-launch timing.  With timing on, every kernel launch of a call is bracketed by CUDA events
+ * recorded on the call's stream.  fd_last_kernel_ms waits for them and writes the durations (ms)
+ * of the last call's launches, in launch order, to ms[0..max-1]; it returns how many it wrote
+ * (>= 0) or a negative FD_ERR_* code. */
+int fd_set_timing(fd_ctx* ctx, int on);
+int fd_last_kernel_ms(fd_ctx* ctx, double* ms, int max);
+
 /* Measured FP64 FMA throughput of this device in GFLOP/s (a DFMA-bound loop over all SMs);
  * used to state roofline fractions.  Synchronous. */
 int fd_measure_fp64_peak(fd_ctx* ctx, double* gflops);

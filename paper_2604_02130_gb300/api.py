@@ -66,6 +66,16 @@ class Context:
     def last_launch_count(self) -> int:
         return self.lib.fd_last_launch_count(self.h)
 
+    def set_timing(self, on: bool):
+        self.check(self.lib.fd_set_timing(self.h, 1 if on else 0))
+
+    def last_kernel_ms(self, max_launches: int = 64) -> List[float]:
+        arr = (ctypes.c_double * max_launches)()
+        n = self.lib.fd_last_kernel_ms(self.h, arr, max_launches)
+        if n < 0:
+            self.check(n)
+        return [arr[i] for i in range(n)]
+
     def measure_fp64_peak(self) -> float:
         g = ctypes.c_double()
         self.check(self.lib.fd_measure_fp64_peak(self.h, ctypes.byref(g)))
@@ -112,14 +122,25 @@ class Batch:
         self.F = None
         self._Gp = None
         self._Fp = None
+        # outputs live in one flat buffer each (one host copy fetches them all)
+        self.G_flat = None
+        self.F_flat = None
         if want in ("green", "force+green"):
-            self.G = [torch.empty((p.nx, p.nx), dtype=torch.complex128, device=dev)
-                      for p in arr[:self.n]]
+            self.G_flat, self.G = self._flat(dev, [(p.nx, p.nx) for p in arr[:self.n]])
             self._Gp = (ctypes.c_void_p * self.n)(*[g.data_ptr() for g in self.G])
         if want.startswith("force"):
-            self.F = [torch.empty((p.nt, p.nx), dtype=torch.complex128, device=dev)
-                      for p in arr[:self.n]]
+            self.F_flat, self.F = self._flat(dev, [(p.nt, p.nx) for p in arr[:self.n]])
             self._Fp = (ctypes.c_void_p * self.n)(*[f.data_ptr() for f in self.F])
+
+    @staticmethod
+    def _flat(dev, shapes):
+        total = sum(a * b for a, b in shapes)
+        flat = torch.empty(max(1, total), dtype=torch.complex128, device=dev)
+        views, o = [], 0
+        for a, b in shapes:
+            views.append(flat[o:o + a * b].view(a, b))
+            o += a * b
+        return flat, views
 
     def reserve(self):
         what = {"logdet": 1, "green": 3, "force": 5, "force+green": 7}[self.want]

@@ -30,6 +30,10 @@ struct fd_ctx {
   int last_batch = 0;
   int last_launches = 0;
   int smem_attr = 0;
+  // optional per-launch timing (events around every kernel launch of a call)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;  // pairs (start, stop)
+  int ev_used = 0;
 };
 
 namespace {
@@ -293,12 +297,21 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double*
   ctx->staging_pending = true;
   FD_CUDA(ctx, cudaMemsetAsync(ctx->d_queue, 0, sizeof(int) * groups.size(), stream));
   FD_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * batch, stream));
+  if (ctx->timing) {
+    while (ctx->ev.size() < 2 * groups.size()) {
+      cudaEvent_t e;
+      FD_CUDA(ctx, cudaEventCreate(&e));
+      ctx->ev.push_back(e);
+    }
+    ctx->ev_used = 2 * (int)groups.size();
+  }
   for (size_t gi = 0; gi < groups.size(); ++gi) {
     Group& g = groups[gi];
     if (g.L.smem_bytes > ctx->smem_attr) {
       FD_CUDA(ctx, fd::set_smem_fp64(ctx->max_smem_optin));
       ctx->smem_attr = ctx->max_smem_optin;
     }
+    if (ctx->timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * gi], stream));
     if (kind == K_FWD)
       fd::launch_fwd_fp64(ctx->d_desc + g.desc_off, (int)g.idx.size(), ctx->d_queue + gi,
                           ctx->d_status, ctx->scratch + g.scratch_off, g.L, g.grid, stream);
@@ -308,6 +321,7 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double*
     ctx->last_launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    if (ctx->timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * gi + 1], stream));
   }
   return FD_OK;
 }
@@ -349,6 +363,7 @@ void fd_ctx_destroy(fd_ctx* ctx) {
   if (ctx->d_queue) cudaFree(ctx->d_queue);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
+  for (auto e : ctx->ev) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -420,6 +435,26 @@ int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch) {
 }
 
 int fd_last_launch_count(const fd_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+int fd_set_timing(fd_ctx* ctx, int on) {
+  if (!ctx) return FD_ERR_INVALID;
+  ctx->timing = on != 0;
+  ctx->ev_used = 0;
+  return FD_OK;
+}
+
+int fd_last_kernel_ms(fd_ctx* ctx, double* ms, int max) {
+  if (!ctx || (max > 0 && !ms)) return FD_ERR_INVALID;
+  if (!ctx->timing) return fail(ctx, FD_ERR_INVALID, "timing is off (fd_set_timing)");
+  int n = std::min(max, ctx->ev_used / 2);
+  for (int i = 0; i < n; ++i) {
+    FD_CUDA(ctx, cudaEventSynchronize(ctx->ev[2 * i + 1]));
+    float t = 0.f;
+    FD_CUDA(ctx, cudaEventElapsedTime(&t, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
+    ms[i] = t;
+  }
+  return n;
+}
 
 int fd_measure_fp64_peak(fd_ctx* ctx, double* gflops) {
   if (!ctx || !gflops) return FD_ERR_INVALID;
