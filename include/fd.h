@@ -49,7 +49,8 @@ enum {
   FD_ERR_UNSUPPORTED = -2, /* valid request that this build does not implement */
   FD_ERR_CUDA = -3,        /* a CUDA runtime call failed (text in fd_last_error) */
   FD_ERR_NUMERIC = -4,     /* device: non-finite value or zero pivot in a configuration */
-  FD_ERR_TIMEOUT = -5      /* device: a bounded wait gave up (kernel returned early) */
+  FD_ERR_TIMEOUT = -5,     /* device: a bounded wait gave up (kernel returned early) */
+  FD_ERR_TOO_LARGE = -6    /* request exceeds a fixed capacity (fd_logdet_noalloc limits) */
 };
 
 /* Arithmetic of the slice products.  QR re-orthogonalisation, scale separation, assembly,
@@ -128,6 +129,36 @@ int fd_last_kernel_ms(fd_ctx* ctx, double* ms, int max);
 /* Measured FP64 FMA throughput of this device in GFLOP/s (a DFMA-bound loop over all SMs);
  * used to state roofline fractions.  Synchronous. */
 int fd_measure_fp64_peak(fd_ctx* ctx, double* gflops);
+
+/* ---------------------------------------------------------------------------------------
+ * fd_logdet_noalloc: log det (and optionally G) without any memory allocation.
+ * The paper has no counterpart; this entry point exists for callers that cannot allocate
+ * device memory -- e.g. a host framework that owns every device allocation through its own
+ * pool, a real-time loop whose memory budget is fixed at start-up, or a pipeline step that must
+ * not suffer the implicit device-wide synchronisation of cudaMalloc/cudaFree.  It needs no
+ * fd_ctx and never calls cudaMalloc, cudaFree or any allocating library routine.
+ *
+ * Working memory: one file-scope device array of 12 MiB inside libfd.so, held on every GPU that
+ * loads the library until the process exits and shared by every call on that GPU.  Nothing in
+ * it has to start at zero (each call writes every scratch entry before reading it), but it keeps
+ * the last call's contents, so calls whose kernels overlap on the GPU race with each other:
+ * issue them on one stream, or order them with events.
+ *
+ * Limits: batch <= FD_NOALLOC_MAX_BATCH, nx <= FD_NOALLOC_MAX_NX; larger requests return
+ * FD_ERR_TOO_LARGE and launch nothing.  FP64 arithmetic only (the FD_PREC_FP64 path).
+ * The first call on a device performs a one-time set-up on the current device (it looks up
+ * the device address of the array and sets the kernel's shared-memory limit); make that first
+ * call before any stream capture.
+ *   probs   host array of `batch` problems (device pointers inside, as for fd_logdet)
+ *   logdet  device, 2*batch float64 (re, im); G: NULL or host array of device pointers
+ *           (nx*nx complex128, row-major); status: NULL or device int[batch] receiving 0 (ok)
+ *           or 1 (non-finite value / zero pivot) per configuration.
+ * Runs on the current device, asynchronously on `stream`.  Returns FD_OK, FD_ERR_INVALID,
+ * FD_ERR_TOO_LARGE, FD_ERR_UNSUPPORTED (device index >= 64) or FD_ERR_CUDA. */
+#define FD_NOALLOC_MAX_BATCH 64
+#define FD_NOALLOC_MAX_NX 72
+int fd_logdet_noalloc(int batch, const fd_problem* probs, double* logdet, double* const* G,
+                      int* status, void* stream);
 
 #ifdef __cplusplus
 }

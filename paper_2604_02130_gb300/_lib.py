@@ -13,6 +13,9 @@ FD_ERR_UNSUPPORTED = -2
 FD_ERR_CUDA = -3
 FD_ERR_NUMERIC = -4
 FD_ERR_TIMEOUT = -5
+FD_ERR_TOO_LARGE = -6
+FD_NOALLOC_MAX_BATCH = 64
+FD_NOALLOC_MAX_NX = 72
 
 FD_PREC_FP64 = 0
 FD_PREC_MIXED_TF32 = 1
@@ -55,6 +58,7 @@ SIGNATURES = [
     ("fd_measure_fp64_peak", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
     ("fd_set_timing", _I, [_VP, _I]),
     ("fd_last_kernel_ms", _I, [_VP, ctypes.POINTER(ctypes.c_double), _I]),
+    ("fd_logdet_noalloc", _I, [_I, _PP, _VP, _VP, _VP, _VP]),
 ]
 
 _lib = None

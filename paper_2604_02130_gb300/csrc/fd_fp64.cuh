@@ -224,7 +224,7 @@ __device__ __forceinline__ void seg_reflector(int n, int k, double2* A, int W, i
 // a Householder QR is invariant under it: QR(Y D Pi) = Q R_Y (Pi^T D Pi)).
 // Result: Xn = Q, logD_k = log|R_kk| + logD_{pi(k)},
 //         Tn = diag(D')^{-1} R Pi^T Tc  with coefficients R'_kj e^{logw_j - logw_k} / |R'_kk|.
-__device__ void cta_reortho(int n, const double2* Xc, double2* Xn, const double2* Tc,
+__device__ inline void cta_reortho(int n, const double2* Xc, double2* Xn, const double2* Tc,
                             double2* Tn, double* logD, Small& s) {
   const int W0 = seg_width(n);
   const int spw0 = 32 / W0;
@@ -414,7 +414,7 @@ __device__ void cta_reortho(int n, const double2* Xc, double2* Xn, const double2
 // Factor A in place (A = P^T L U, unit L), applying the same row operations to the n columns of
 // Bm (so that Bm <- L^{-1} P Bm), then back-substitute Bm <- U^{-1} Bm.  On return Bm holds
 // A^{-1} Bm_in and *logdet_out = log det A (principal logs of the pivots + i pi * swaps).
-__device__ void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, double* logdet_re,
+__device__ inline void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, double* logdet_re,
                              double* logdet_im) {
   const int lane = lane_id(), w = warp_id();
   if (tid() == 0) s.misc[1] = 0;
@@ -514,7 +514,7 @@ __device__ void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, double* l
 //   log det(1 + X D T) = log det X + sum log D_b + log det C,  G = C^{-1} D_b^{-1} X^H.
 // X is the Q of the last QR (product of n-1 reflections): det X = (-1)^{n-1}.
 // Cbuf and Gbuf are scratch; on return Gbuf holds G (column-major).
-__device__ void cta_assemble(int n, const double2* X, const double2* T, const double* logD,
+__device__ inline void cta_assemble(int n, const double2* X, const double2* T, const double* logD,
                              double2* Cbuf, double2* Gbuf, Small& s, double* ld_re,
                              double* ld_im) {
   for (int e = tid(); e < n * n; e += nthr()) {
