@@ -68,7 +68,9 @@ enum Kind { K_FWD = 0, K_FORCE = 1 };
 struct Group {
   int kind;
   int nx;
+  int mixed;   // 1: tcgen05 slice path (ML), 0: FP64 path (L)
   Layout L;
+  fd::MLayout ML;
   int grid;
   std::vector<int> idx;  // user indices, cost-sorted (descending)
   size_t desc_off;       // first descriptor of this group in the table
@@ -136,6 +138,108 @@ Layout plan_layout(int n, int kind, int budget, int nthreads, int max_nt, int ma
   return L;
 }
 
+// Mixed path: A = E and B = the product in shared memory (K-major TF32), then the FP64
+// result Xc (aliasing B when it fits), the QR output Xn, small vectors; T and whatever did not
+// fit in the CTA's scratch slot.  Returns smem_bytes = 0 if A and B alone do not fit.
+fd::MLayout plan_mixed(int n, int kind, bool three, int budget, int smem_per_sm, int max_nb) {
+  fd::MLayout M;
+  memset(&M, 0, sizeof(M));
+  M.n = n;
+  M.Np = (n + 7) & ~7;
+  M.Kp = M.Np;
+  M.N = 2 * M.Np;
+  M.three = three ? 1 : 0;
+  int need = M.Np + ((M.Np + 15) & ~15);
+  M.tmem_cols = 32;
+  while (M.tmem_cols < need) M.tmem_cols <<= 1;
+  M.nthreads = n <= 40 ? 128 : 256;
+  const long long a_bytes = (long long)M.Np * M.Kp * 4;
+  const long long b_one = (long long)M.N * M.Kp * 4;
+  const long long b_bytes = b_one * (three ? 2 : 1);
+  const long long cm = 16LL * n * n;
+  long long o = 0;
+  M.a_hi = 0;
+  o = round16(a_bytes);
+  if (three) {
+    M.a_lo = (int)o;
+    o += round16(a_bytes);
+  } else {
+    M.a_lo = -1;
+  }
+  M.a2_hi = M.a2_lo = -1;
+  if (kind == K_FORCE) {  // E^{-1} for the wraps
+    M.a2_hi = (int)o;
+    o += round16(a_bytes);
+    if (three) {
+      M.a2_lo = (int)o;
+      o += round16(a_bytes);
+    }
+  }
+  const long long last_a = kind == K_FORCE ? (three ? M.a2_lo : M.a2_hi) : (three ? M.a_lo : M.a_hi);
+  o = (o + 127) & ~127LL;
+  M.b_hi = (int)o;
+  M.b_lo = three ? (int)(o + round16(b_one)) : -1;
+  long long breg = round16(b_bytes);
+  const long long fixed = round16(fd::small_bytes(n)) + 64;
+  long long g = 0;  // scratch-slot bytes
+  // Xn first (the QR works in place on it), then Xc
+  const bool xn_fits = o + breg + cm + fixed <= budget;
+  const bool xc_alias = cm <= breg || (xn_fits ? o + std::max(breg, cm) + cm + fixed <= budget
+                                               : o + std::max(breg, cm) + fixed <= budget);
+  if (xc_alias) {
+    breg = std::max(breg, round16(cm));
+    M.xc_smem = 1;
+    M.xc_off = M.b_hi;
+  } else {
+    M.xc_smem = 0;
+    M.xc_off = g;
+    g += round16(cm);
+  }
+  o += breg;
+  if (o + cm + fixed <= budget) {
+    M.xn_smem = 1;
+    M.xn_off = o;
+    o += round16(cm);
+  } else {
+    M.xn_smem = 0;
+    M.xn_off = g;
+    g += round16(cm);
+  }
+  M.small_off = (int)o;
+  o += round16(fd::small_bytes(n));
+  M.bar_off = (int)o;
+  o += 64;
+  // the MMA reads 128 rows of A: keep that footprint inside the allocation
+  long long foot = last_a + 128LL * M.Kp * 4;
+  if (o < foot) o = foot;
+  M.smem_bytes = (int)((o + 127) & ~127LL);
+  // co-resident CTAs must fit the SM's 512 TMEM columns: size the request so that the
+  // shared-memory occupancy limit enforces that
+  const int max_ctas = 512 / M.tmem_cols;
+  const int floor_bytes = smem_per_sm / (max_ctas + 1) + 1024;
+  if (M.smem_bytes < floor_bytes) M.smem_bytes = (floor_bytes + 127) & ~127;
+  if (M.smem_bytes > budget || M.Np > 128) {
+    M.smem_bytes = 0;
+    return M;
+  }
+  M.t0_off = g;
+  g += round16(cm);
+  M.t1_off = g;
+  g += round16(cm);
+  if (kind == K_FORCE) {
+    for (int i = 0; i < 4; ++i) {
+      M.g_off[i] = g;
+      g += round16(cm);
+    }
+  }
+  M.ws_bytes = round16(g);
+  long long ck = 0;
+  if (kind == K_FORCE) ck = std::max(0, max_nb - 1) * (2LL * n * n + (n + 1) / 2) * 16;
+  M.slot_bytes = round16(M.ws_bytes + ck);
+  if (M.slot_bytes == 0) M.slot_bytes = 16;
+  return M;
+}
+
 int validate(fd_ctx* ctx, int batch, const fd_problem* probs, const void* logdet, int prec,
              bool need_einv) {
   if (!ctx) return FD_ERR_INVALID;
@@ -161,7 +265,7 @@ int validate(fd_ctx* ctx, int batch, const fd_problem* probs, const void* logdet
   return FD_OK;
 }
 
-std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kind) {
+std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kind, int prec) {
   std::vector<Group> groups;
   std::vector<int> order(batch);
   for (int c = 0; c < batch; ++c) order[c] = c;
@@ -187,6 +291,22 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
     for (int c : g.idx) max_nb = std::max(max_nb, probs[c].nt / probs[c].n_stab);
     min_ns = 1;
     const int n = g.nx, nth = threads_for(n);
+    g.mixed = 0;
+    if (prec != FD_PREC_FP64) {
+      fd::MLayout M = plan_mixed(n, kind, prec == FD_PREC_MIXED_3XTF32, ctx->max_smem_optin,
+                                 ctx->smem_per_sm, max_nb);
+      if (M.smem_bytes > 0) {
+        g.mixed = 1;
+        g.ML = M;
+        memset(&g.L, 0, sizeof(g.L));
+        int occ = fd::occupancy_mixed(kind == K_FORCE, M.nthreads, M.smem_bytes);
+        occ = std::max(1, std::min(occ, 512 / M.tmem_cols));
+        g.grid = std::min<int>((int)g.idx.size(), ctx->num_sms * occ);
+        g.L.slot_bytes = M.slot_bytes;
+        groups.push_back(g);
+        continue;
+      }
+    }
     // try a budget that keeps several CTAs per SM, else the full opt-in budget
     Layout full = plan_layout(n, kind, 1 << 30, nth, max_nb, min_ns);
     int budget;
@@ -261,10 +381,12 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double*
   ctx->last_launches = 0;
   ctx->last_batch = batch;
   if (batch == 0) return FD_OK;
-  if (prec != FD_PREC_FP64)
-    return fail(ctx, FD_ERR_UNSUPPORTED, "precision %d is not built yet", prec);
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
-  std::vector<Group> groups = plan(ctx, batch, probs, kind);
+  std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
+  for (auto& g : groups)
+    if (prec != FD_PREC_FP64 && !g.mixed)
+      return fail(ctx, FD_ERR_UNSUPPORTED,
+                  "nx=%d does not fit the mixed-precision kernel (nx <= 128, shared memory)", g.nx);
   size_t need = scratch_need(groups);
   int rc = ensure(ctx, (size_t)batch, (size_t)batch, groups.size(), need);
   if (rc != FD_OK) return rc;
@@ -296,7 +418,7 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double*
   FD_CUDA(ctx, cudaEventRecord(ctx->staging_done, stream));
   ctx->staging_pending = true;
   FD_CUDA(ctx, cudaMemsetAsync(ctx->d_queue, 0, sizeof(int) * groups.size(), stream));
-  FD_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * batch, stream));
+  FD_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0xFF, sizeof(int) * batch, stream));  // pending
   if (ctx->timing) {
     while (ctx->ev.size() < 2 * groups.size()) {
       cudaEvent_t e;
@@ -312,7 +434,13 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double*
       ctx->smem_attr = ctx->max_smem_optin;
     }
     if (ctx->timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * gi], stream));
-    if (kind == K_FWD)
+    if (g.mixed && kind == K_FORCE)
+      fd::launch_force_mixed(ctx->d_desc + g.desc_off, (int)g.idx.size(), ctx->d_queue + gi,
+                             ctx->d_status, ctx->scratch + g.scratch_off, g.ML, g.grid, stream);
+    else if (g.mixed)
+      fd::launch_fwd_mixed(ctx->d_desc + g.desc_off, (int)g.idx.size(), ctx->d_queue + gi,
+                           ctx->d_status, ctx->scratch + g.scratch_off, g.ML, g.grid, stream);
+    else if (kind == K_FWD)
       fd::launch_fwd_fp64(ctx->d_desc + g.desc_off, (int)g.idx.size(), ctx->d_queue + gi,
                           ctx->d_status, ctx->scratch + g.scratch_off, g.L, g.grid, stream);
     else
@@ -344,7 +472,8 @@ int fd_ctx_create(fd_ctx** out, int device) {
   cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   cudaDeviceGetAttribute(&ctx->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
   if (cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming) != cudaSuccess ||
-      fd::set_smem_fp64(ctx->max_smem_optin) != cudaSuccess) {
+      fd::set_smem_fp64(ctx->max_smem_optin) != cudaSuccess ||
+      fd::set_smem_mixed(ctx->max_smem_optin) != cudaSuccess) {
     delete ctx;
     return FD_ERR_CUDA;
   }
@@ -375,7 +504,8 @@ int fd_reserve(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int pr
   if (rc != FD_OK) return rc;
   if (batch == 0) return FD_OK;
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
-  std::vector<Group> groups = plan(ctx, batch, probs, (what & FD_WANT_FORCE) ? K_FORCE : K_FWD);
+  std::vector<Group> groups =
+      plan(ctx, batch, probs, (what & FD_WANT_FORCE) ? K_FORCE : K_FWD, prec);
   size_t need = scratch_need(groups);
   rc = ensure(ctx, (size_t)batch, (size_t)batch, groups.size(), need);
   if (rc != FD_OK) return rc;
@@ -427,7 +557,9 @@ int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch) {
   FD_CUDA(ctx, cudaMemcpy(st.data(), ctx->d_status, sizeof(int) * batch, cudaMemcpyDeviceToHost));
   int worst = FD_OK;
   for (int c = 0; c < batch; ++c) {
-    int code = st[c] == fd::ST_OK ? FD_OK : (st[c] == fd::ST_TIMEOUT ? FD_ERR_TIMEOUT : FD_ERR_NUMERIC);
+    int code = st[c] == fd::ST_OK ? FD_OK
+               : (st[c] == fd::ST_TIMEOUT || st[c] == fd::ST_PENDING) ? FD_ERR_TIMEOUT
+                                                                      : FD_ERR_NUMERIC;
     per_config_status[c] = code;
     if (code < worst) worst = code;
   }

@@ -86,7 +86,30 @@ __host__ __device__ __forceinline__ int small_bytes(int n) {
   return 16 * 5 * n + 8 * 10 * n + 8 * 64 + 4 * 2 * n + 4 * 32;
 }
 
-// status codes written per configuration (device side)
-enum { ST_OK = 0, ST_NUMERIC = 1, ST_TIMEOUT = 2 };
+// Layout of the mixed-precision kernels (slice GEMMs on tcgen05).  Byte offsets into dynamic
+// shared memory unless stated otherwise.  Operands use the K-major no-swizzle layout of
+// fd_tc.cuh: A = E (Np rows x Kp, TF32), B = the current product (2*Np rows: Re then Im, x Kp).
+struct MLayout {
+  int nthreads;
+  int smem_bytes;
+  int n, Np, Kp, N;      // N = 2*Np MMA columns; Kp = Np
+  int tmem_cols;
+  int three;             // 1 = split TF32 (hi + lo, 3 MMAs per K step)
+  int a_hi, a_lo;        // A operand(s): E
+  int a2_hi, a2_lo;      // force only: E^{-1}
+  int b_hi, b_lo;        // B operand(s); the region also hosts the FP64 block result Xc
+  int xc_smem, xn_smem;  // 1 = shared memory, 0 = CTA scratch slot
+  long long xc_off, xn_off;
+  long long t0_off, t1_off;  // T buffers, always in the scratch slot
+  int small_off;
+  int bar_off;           // mbarrier (8 B), TMEM address (4 B), queue slot (4 B)
+  long long slot_bytes;
+  // force only
+  long long g_off[4];    // G_lo, G_hi, G_a, G_b (scratch slot, complex128 n*n each)
+  long long ws_bytes;    // slot bytes before the checkpoints
+};
+
+// status codes written per configuration (device side); the host pre-fills ST_PENDING
+enum { ST_OK = 0, ST_NUMERIC = 1, ST_TIMEOUT = 2, ST_PENDING = -1 };
 
 }  // namespace fd

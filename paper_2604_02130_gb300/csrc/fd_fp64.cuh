@@ -544,6 +544,67 @@ __device__ inline void cta_assemble(int n, const double2* X, const double2* T, c
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- force building blocks
+// Equal-time Green's function at a block boundary (Section 7 steps 7-9 with t1 = t2, combined
+// with the stabilised pre-/suffix products of Section 5.3):
+//   L = X_L diag(D_L) T_L = B_t...B_1,   R = (X_R diag(D_R) T_R)^H = B_Nt...B_{t+1},
+//   1 + L R = X_L D_Lb [ D_Lb^{-1} X_L^H X_R D_Rb^{-1} + D_Ls T_L T_R^H D_Rs ] D_Rb X_R^H,
+//   G_t = X_R D_Rb^{-1} M^{-1} D_Lb^{-1} X_L^H.
+// identity_left: L = 1 (t = 0).  Scratch: Mb, Wb.  Result in Gout.
+__device__ inline void boundary_green(int n, bool identity_left, const double2* XL, const double2* TL,
+                               const double* logDL, const double2* XR, const double2* TR,
+                               const double* logDR, double2* Mb, double2* Wb, double2* Gout,
+                               Small& s) {
+  for (int k = tid(); k < n; k += nthr()) {
+    double lL = identity_left ? 0.0 : logDL[k];
+    double lR = logDR[k];
+    s.sa[k] = exp(-fmax(lL, 0.0));
+    s.sc[k] = exp(fmin(lL, 0.0));
+    s.sb[k] = exp(-fmax(lR, 0.0));
+    s.sd[k] = exp(fmin(lR, 0.0));
+  }
+  __syncthreads();
+  const double *a = s.sa, *b = s.sb, *c = s.sc, *dd = s.sd;
+  if (identity_left) {
+    // M = X_R D_Rb^{-1} + T_R^H D_Rs ;  RHS = 1
+    for (int e = tid(); e < n * n; e += nthr()) {
+      int i = e % n, j = e / n;
+      cplx m = b[j] * ld(XR + e) + dd[j] * conj(ld(TR + j + i * n));
+      st(Mb + e, m);
+      Wb[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+  } else {
+    cta_gemm<false>(n, CMatH{XL, 1, n}, CMat{XR, 1, n},
+                    [&](int i, int j, cplx v) { st(Mb + i + j * n, (a[i] * b[j]) * v); });
+    cta_gemm<false>(n, CMat{TL, 1, n}, CMatH{TR, 1, n}, [&](int i, int j, cplx v) {
+      st(Mb + i + j * n, ld(Mb + i + j * n) + (c[i] * dd[j]) * v);
+    });
+    for (int e = tid(); e < n * n; e += nthr()) {
+      int i = e % n, j = e / n;
+      st(Wb + e, a[i] * conj(ld(XL + j + i * n)));
+    }
+    __syncthreads();
+  }
+  cta_lu_solve(n, Mb, Wb, s, s.red + 4, s.red + 5);
+  // Gout = X_R diag(b) W
+  struct BW {
+    const double2* p;
+    const double* b;
+    int n;
+    __device__ __forceinline__ cplx operator()(int k, int j) const { return b[k] * ld(p + k + j * n); }
+  } Bop{Wb, b, n};
+  cta_gemm<false>(n, CMat{XR, 1, n}, Bop, [&](int i, int j, cplx v) { st(Gout + i + j * n, v); });
+}
+
+__device__ __forceinline__ void emit_force_row(int n, const double2* G, double2* Frow) {
+  // F[t,x] = i (1 - G_xx) = (Im G_xx, 1 - Re G_xx)
+  for (int x = tid(); x < n; x += nthr()) {
+    double2 g = G[x + x * n];
+    Frow[x] = make_double2(g.y, 1.0 - g.x);
+  }
+}
+
 __device__ __forceinline__ double wrap_pi(double x) {
   const double pi = 3.14159265358979323846;
   double y = remainder(x, 2.0 * pi);  // (-pi, pi]

@@ -13,6 +13,14 @@ void launch_force_fp64(const Desc* descs, int ndesc, int* queue, int* status, ch
 cudaError_t set_smem_fp64(int bytes);
 int occupancy_fp64(bool force, int nthreads, int smem_bytes);
 
+// mixed path (tcgen05 slice GEMMs)
+void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
+                      const MLayout& L, int grid, cudaStream_t stream);
+void launch_force_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
+                        const MLayout& L, int grid, cudaStream_t stream);
+cudaError_t set_smem_mixed(int bytes);
+int occupancy_mixed(bool force, int nthreads, int smem_bytes);
+
 // FP64 throughput probe
 cudaError_t run_fp64_probe(int grid, int threads, int iters, double* out, cudaStream_t stream);
 

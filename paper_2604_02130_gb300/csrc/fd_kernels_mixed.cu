@@ -1,0 +1,488 @@
+// fd_kernels_mixed.cu -- mixed-precision path: the slice products X <- E diag(e^{i phi_t}) X run
+// on the tcgen05 tensor cores (TF32 operands, FP32 accumulation in TMEM), the QR
+// re-orthogonalisation every n_stab slices, the scale separation and the assembly stay FP64
+// (the same CTA routines as the FP64 path).
+//
+// Per slice one CTA issues, from a single thread, ceil(Nx/8) MMAs of shape 128 x 2Np x 8
+// (x3 for split TF32):  D[i, j] = sum_k E[i, k] Y[k, j], with A = E (rows i, K-major) and
+// B = Y stored as 2Np rows (Re Y[:, j], then Im Y[:, j]) with K = the row index of Y, so the
+// accumulator holds row i of Re and Im of the product in TMEM lane i.  The epilogue reads each
+// lane's row, multiplies it by the next slice's phase e^{i phi_{t+1, i}} (the diagonal factor of
+// the next slice, fused here) and writes it back as the next B operand.  After the last slice of
+// a block the FP32 result is widened to FP64 for the QR.
+#include "fd_fp64.cuh"
+#include "fd_kernels.h"
+#include "fd_tc.cuh"
+
+namespace fd {
+
+// mbarrier waits give up after about one second at ~2 GHz
+#define FD_WAIT_CYCLES (2LL * 1000 * 1000 * 1000)
+
+struct MixedSmem {
+  float* a_hi;
+  float* a_lo;
+  float* b_hi;
+  float* b_lo;
+  double2* Xc;
+  double2* Xn;
+  uint64_t* mbar;
+  uint32_t* taddr;
+  int* qslot;
+};
+
+__device__ __forceinline__ MixedSmem mixed_smem(char* smem, char* slot, const MLayout& L) {
+  MixedSmem m;
+  m.a_hi = (float*)(smem + L.a_hi);
+  m.a_lo = L.three ? (float*)(smem + L.a_lo) : nullptr;
+  m.b_hi = (float*)(smem + L.b_hi);
+  m.b_lo = L.three ? (float*)(smem + L.b_lo) : nullptr;
+  m.Xc = L.xc_smem ? (double2*)(smem + L.xc_off) : (double2*)(slot + L.xc_off);
+  m.Xn = L.xn_smem ? (double2*)(smem + L.xn_off) : (double2*)(slot + L.xn_off);
+  m.mbar = (uint64_t*)(smem + L.bar_off);
+  m.taddr = (uint32_t*)(smem + L.bar_off + 8);
+  m.qslot = (int*)(smem + L.bar_off + 12);
+  return m;
+}
+
+// A operand: E (n x n FP64, symmetric) -> TF32 (hi, and lo = E - hi for the split mode), zero
+// padded to Np x Kp.
+__device__ void fill_a(const MLayout& L, float* a_hi, float* a_lo, const double* E) {
+  const int n = L.n, Np = L.Np, Kp = L.Kp;
+  for (int e = tid(); e < Np * Kp; e += nthr()) {
+    int r = e / Kp, k = e % Kp;
+    double v = (r < n && k < n) ? E[r * n + k] : 0.0;
+    float f = (float)v;
+    float hi = tc::to_tf32(f);
+    uint32_t o = tc::kmaj_off(r, k, Kp) >> 2;
+    a_hi[o] = hi;
+    if (L.three) a_lo[o] = tc::to_tf32(f - hi);
+  }
+}
+
+// One slice GEMM on the tensor core: issue (single thread), commit, bounded wait.
+// Returns false on a timeout (uniform across the CTA).
+__device__ bool mma_ab(const MLayout& L, const MixedSmem& m, const float* a_hi, const float* a_lo,
+                       uint32_t tbase, uint32_t& phase) {
+  tc::fence_proxy_async();
+  __syncthreads();
+  if (tid() == 0) {
+    tc::fence_after();
+    const uint32_t idesc = tc::idesc_tf32(128, L.N);
+    const uint32_t sbo = (uint32_t)(L.Kp / 4) * 128u;
+    const uint32_t ah = tc::smem_u32(a_hi), bh = tc::smem_u32(m.b_hi);
+    const uint32_t al = L.three ? tc::smem_u32(a_lo) : 0u, bl = L.three ? tc::smem_u32(m.b_lo) : 0u;
+    for (int s = 0; s < L.Kp / 8; ++s) {
+      const uint32_t o = 256u * s;
+      tc::mma_tf32(tbase, tc::make_desc(ah + o, 128, sbo), tc::make_desc(bh + o, 128, sbo), idesc,
+                   s > 0);
+      if (L.three) {
+        tc::mma_tf32(tbase, tc::make_desc(ah + o, 128, sbo), tc::make_desc(bl + o, 128, sbo),
+                     idesc, 1);
+        tc::mma_tf32(tbase, tc::make_desc(al + o, 128, sbo), tc::make_desc(bh + o, 128, sbo),
+                     idesc, 1);
+      }
+    }
+    tc::mma_commit(m.mbar);
+  }
+  bool ok = tc::mbar_wait(m.mbar, phase, FD_WAIT_CYCLES);
+  phase ^= 1u;
+  int bad = __syncthreads_or(!ok);
+  tc::fence_after();
+  return bad == 0;
+}
+__device__ __forceinline__ bool slice_mma(const MLayout& L, const MixedSmem& m, uint32_t tbase,
+                                          uint32_t& phase) {
+  return mma_ab(L, m, m.a_hi, m.a_lo, tbase, phase);
+}
+
+// Scale factor per row or column: p[x] (or its conjugate), or 1 when p == nullptr.  FP32: the
+// epilogue and the operand fills work at the precision of the TF32 operands they produce (the
+// FP64 pipe of this GPU is 1/64 of the FP32 rate).
+struct Scale {
+  const float2* p;
+  bool cj;
+  __device__ __forceinline__ float2 at(int x) const {
+    if (!p) return make_float2(1.f, 0.f);
+    float2 v = p[x];
+    return cj ? make_float2(v.x, -v.y) : v;
+  }
+};
+__device__ __forceinline__ float2 cmul32(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// phase vector e^{i s phi} of one slice in FP32
+__device__ __forceinline__ void cta_phase32(int n, float2* ph, const double* phi_row, float s) {
+  for (int x = tid(); x < n; x += nthr()) {
+    float sn, cs;
+    sincosf((float)phi_row[x], &sn, &cs);
+    ph[x] = make_float2(cs, s * sn);
+  }
+}
+
+enum EpiMode { TO_B_K = 0, TO_B_N = 1, TO_FP64 = 2, NONE = 3 };
+
+__device__ __forceinline__ void put_b(const MLayout& L, const MixedSmem& m, int row, int k,
+                                      float v) {
+  float hi = tc::to_tf32(v);
+  uint32_t o = tc::kmaj_off(row, k, L.Kp) >> 2;
+  m.b_hi[o] = hi;
+  if (L.three) m.b_lo[o] = tc::to_tf32(v - hi);
+}
+
+// Epilogue of one MMA.  TMEM lane l (< n) holds v(l, c) = D[l, c] + i D[l, Np + c], c < n.
+//   TO_B_K : B(n = c, k = l) = rs(l) v cs(c)   (the lane indexes K: slices, right products)
+//   TO_B_N : B(n = l, k = c) = rs(l) v cs(c)   (the lane indexes N: wraps)
+//   TO_FP64: out[l + c n]    = rs(l) v cs(c)   (column-major FP64)
+// diag (optional): diag[l] = (Im v(l,l), 1 - Re v(l,l)), a force row F = i (1 - G_ll).
+template <int MODE>
+__device__ void epilogue(const MLayout& L, const MixedSmem& m, uint32_t tbase, Scale rs,
+                         Scale cs, double2* out, double2* diag) {
+  const int n = L.n, Np = L.Np;
+  const int w = warp_id(), nw = nwarps();
+  const int quad = w & 3;
+  const int half = w >> 2;
+  const int nhalf = nw > 4 ? 2 : 1;
+  const int l = quad * 32 + lane_id();
+  if (quad * 32 < n) {
+    const uint32_t lane_base = tbase + ((uint32_t)(quad * 32) << 16);
+    const int nchunk = (Np + 15) / 16;
+    const float2 r = l < n ? rs.at(l) : make_float2(1.f, 0.f);
+    for (int c = half; c < nchunk; c += nhalf) {
+      float re[16], im[16];
+      tc::tmem_ld16(lane_base + (uint32_t)(c * 16), re);
+      tc::tmem_ld16(lane_base + (uint32_t)(Np + c * 16), im);
+      if (l < n) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int j = c * 16 + u;
+          if (j < n) {
+            const float2 v = make_float2(re[u], im[u]);
+            if (diag && j == l) diag[l] = make_double2((double)v.y, 1.0 - (double)v.x);
+            if (MODE == NONE) continue;
+            const float2 y = cmul32(cmul32(r, v), cs.at(j));
+            if (MODE == TO_B_K) {
+              put_b(L, m, j, l, y.x);
+              put_b(L, m, Np + j, l, y.y);
+            } else if (MODE == TO_B_N) {
+              put_b(L, m, l, j, y.x);
+              put_b(L, m, Np + l, j, y.y);
+            } else {
+              out[l + j * n] = make_double2((double)y.x, (double)y.y);
+            }
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+}
+
+// B operand from an FP64 column-major matrix G (identity if G == nullptr):
+// B(n = j, k = i) = rs(i) G[i, j] cs(j).
+__device__ void fill_b2(const MLayout& L, const MixedSmem& m, const double2* G, Scale rs,
+                        Scale cs) {
+  const int n = L.n, Np = L.Np, Kp = L.Kp;
+  for (int e = tid(); e < 2 * Np * Kp; e += nthr()) {
+    int k = e % Kp, row = e / Kp;
+    int j = row < Np ? row : row - Np;
+    float v = 0.f;
+    if (j < n && k < n) {
+      float2 x;
+      if (G) {
+        double2 g = G[k + j * n];
+        x = make_float2((float)g.x, (float)g.y);
+      } else {
+        x = make_float2(k == j ? 1.f : 0.f, 0.f);
+      }
+      float2 y = cmul32(cmul32(rs.at(k), x), cs.at(j));
+      v = row < Np ? y.x : y.y;
+    }
+    put_b(L, m, row, k, v);
+  }
+}
+
+__device__ __forceinline__ void slice_epilogue(const MLayout& L, const MixedSmem& m,
+                                               uint32_t tbase, const float2* ph, bool to_b) {
+  if (to_b)
+    epilogue<TO_B_K>(L, m, tbase, Scale{ph, false}, Scale{nullptr, false}, nullptr, nullptr);
+  else
+    epilogue<TO_FP64>(L, m, tbase, Scale{nullptr, false}, Scale{nullptr, false}, m.Xc, nullptr);
+}
+
+__device__ __forceinline__ int grab_m(int* queue, int* slot) {
+  __syncthreads();
+  if (threadIdx.x == 0) *slot = atomicAdd(queue, 1);
+  __syncthreads();
+  return *slot;
+}
+
+// ------------------------------------------------------------------ log det and G
+__global__ void __launch_bounds__(256) k_fwd_mixed(const Desc* __restrict__ descs, int ndesc,
+                                                    int* queue, int* status, char* scratch,
+                                                    MLayout L) {
+  extern __shared__ __align__(128) char smem[];
+  char* slot = scratch + (size_t)blockIdx.x * L.slot_bytes;
+  MixedSmem m = mixed_smem(smem, slot, L);
+  if (warp_id() == 0) tc::tmem_alloc(m.taddr, (uint32_t)L.tmem_cols);
+  if (tid() == 0) tc::mbar_init(m.mbar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *m.taddr;
+  uint32_t phase = 0;
+  const int n = L.n;
+  double2* T = (double2*)(slot + L.t0_off);
+  double2* To = (double2*)(slot + L.t1_off);
+  for (;;) {
+    int c = grab_m(queue, m.qslot);
+    if (c >= ndesc) break;
+    const Desc d = descs[c];
+    Small s = carve_small(smem + L.small_off, n);
+    float2* pf = (float2*)s.ph;  // FP32 phases: two halves of n
+    if (tid() == 0) s.misc[0] = 0;
+    fill_a(L, m.a_hi, m.a_lo, d.E);
+    cta_identity(n, T);
+    for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
+    bool ok = true;
+    for (int b = 0; b < d.nt && ok; b += d.nstab) {
+      cta_phase32(n, pf, d.phi + (size_t)b * n, 1.f);
+      __syncthreads();
+      fill_b2(L, m, b == 0 ? nullptr : m.Xn, Scale{pf, false}, Scale{nullptr, false});
+      for (int t = b; t < b + d.nstab; ++t) {
+        const bool last = t + 1 == b + d.nstab;
+        float2* phn = pf + ((t - b + 1) & 1) * n;
+        if (!last) cta_phase32(n, phn, d.phi + (size_t)(t + 1) * n, 1.f);
+        if (!slice_mma(L, m, tbase, phase)) {
+          ok = false;
+          break;
+        }
+        slice_epilogue(L, m, tbase, phn, !last);
+      }
+      if (!ok) break;
+      cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
+      double2* t2 = T; T = To; To = t2;
+    }
+    if (!ok) {
+      if (tid() == 0) status[d.user_index] = ST_TIMEOUT;
+      break;
+    }
+    cta_assemble(n, m.Xn, T, s.logD, m.Xc, To, s, s.red + 2, s.red + 3);
+    const double re = s.red[2], im = wrap_pi(s.red[3]);
+    if (tid() == 0) {
+      d.logdet[0] = re;
+      d.logdet[1] = im;
+      status[d.user_index] = (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK;
+    }
+    if (d.G)
+      for (int e = tid(); e < n * n; e += nthr()) d.G[e] = To[(e / n) + (e % n) * n];
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp_id() == 0) tc::tmem_dealloc(tbase, (uint32_t)L.tmem_cols);
+}
+
+// ------------------------------------------------------------------ force (mixed)
+// Forward pass as k_fwd_mixed plus FP64 checkpoints; adjoint sweep with the right products
+// X_R <- diag(e^{-i phi_s}) E X_R on the tensor core (the conjugate phase applied in the
+// epilogue), FP64 QR and boundary Green's function, and the wraps inside a block on the tensor
+// core as two MMAs each:
+//   forward  G_s     = E [D_s G_{s-1} D_s^*] E^{-1}:  MMA(A = E, B = D G D^*) gives
+//            W = E (D G D^*) with lane = row; written lane-as-N it is the B operand of
+//            MMA(A = E^{-1}), whose result E^{-1} W^T = G_s^T leaves column m of G_s in lane m.
+//   backward G_{q-1} = D_q^* [E^{-1} G_q E] D_q: MMA(A = E^{-1}, B = G_q), then MMA(A = E,
+//            B = (E^{-1} G_q)^T) leaves column m of E^{-1} G_q E in lane m.
+// The diagonal (the force row) is read straight out of the second accumulator; the phases of
+// the next wrap are applied while writing the next B operand.
+__global__ void __launch_bounds__(256) k_force_mixed(const Desc* __restrict__ descs, int ndesc,
+                                                      int* queue, int* status, char* scratch,
+                                                      MLayout L) {
+  extern __shared__ __align__(128) char smem[];
+  char* slot = scratch + (size_t)blockIdx.x * L.slot_bytes;
+  MixedSmem m = mixed_smem(smem, slot, L);
+  float* e2_hi = (float*)(smem + L.a2_hi);
+  float* e2_lo = L.three ? (float*)(smem + L.a2_lo) : nullptr;
+  if (warp_id() == 0) tc::tmem_alloc(m.taddr, (uint32_t)L.tmem_cols);
+  if (tid() == 0) tc::mbar_init(m.mbar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *m.taddr;
+  uint32_t phase = 0;
+  const int n = L.n;
+  double2* T = (double2*)(slot + L.t0_off);
+  double2* To = (double2*)(slot + L.t1_off);
+  double2* Glo = (double2*)(slot + L.g_off[0]);
+  double2* Ghi = (double2*)(slot + L.g_off[1]);
+  double2* Ga = (double2*)(slot + L.g_off[2]);
+  double2* Gb = (double2*)(slot + L.g_off[3]);
+  double2* ckbase = (double2*)(slot + L.ws_bytes);
+  const Scale one{nullptr, false};
+  for (;;) {
+    int c = grab_m(queue, m.qslot);
+    if (c >= ndesc) break;
+    const Desc d = descs[c];
+    const int ns = d.nstab, nb = d.nt / d.nstab;
+    const size_t ck_stride = (size_t)2 * n * n + (n + 1) / 2;
+    auto ckX = [&](int b) { return ckbase + (size_t)(b - 1) * ck_stride; };
+    auto ckT = [&](int b) { return ckbase + (size_t)(b - 1) * ck_stride + (size_t)n * n; };
+    auto ckD = [&](int b) {
+      return (double*)(ckbase + (size_t)(b - 1) * ck_stride + (size_t)2 * n * n);
+    };
+    Small s = carve_small(smem + L.small_off, n);
+    float2* pf = (float2*)s.ph;  // FP32 phases: two halves of n
+    if (tid() == 0) s.misc[0] = 0;
+    fill_a(L, m.a_hi, m.a_lo, d.E);
+    fill_a(L, e2_hi, e2_lo, d.Einv);
+    cta_identity(n, T);
+    for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
+    bool ok = true;
+    // ---- forward pass with checkpoints
+    for (int b = 1; b <= nb && ok; ++b) {
+      const int t0 = (b - 1) * ns;
+      cta_phase32(n, pf, d.phi + (size_t)t0 * n, 1.f);
+      __syncthreads();
+      fill_b2(L, m, b == 1 ? nullptr : m.Xn, Scale{pf, false}, one);
+      for (int t = t0; t < t0 + ns; ++t) {
+        const bool last = t + 1 == t0 + ns;
+        float2* phn = pf + ((t - t0 + 1) & 1) * n;
+        if (!last) cta_phase32(n, phn, d.phi + (size_t)(t + 1) * n, 1.f);
+        if (!slice_mma(L, m, tbase, phase)) { ok = false; break; }
+        slice_epilogue(L, m, tbase, phn, !last);
+      }
+      if (!ok) break;
+      cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
+      double2* t2 = T; T = To; To = t2;
+      if (b < nb) {
+        cta_copy(n * n, ckX(b), m.Xn);
+        cta_copy(n * n, ckT(b), T);
+        for (int k = tid(); k < n; k += nthr()) ckD(b)[k] = s.logD[k];
+        __syncthreads();
+      }
+    }
+    if (!ok) {
+      if (tid() == 0) status[d.user_index] = ST_TIMEOUT;
+      break;
+    }
+    cta_assemble(n, m.Xn, T, s.logD, m.Xc, Ghi, s, s.red + 2, s.red + 3);
+    const double re = s.red[2], im = wrap_pi(s.red[3]);
+    if (tid() == 0) {
+      d.logdet[0] = re;
+      d.logdet[1] = im;
+    }
+    if (d.G)
+      for (int e = tid(); e < n * n; e += nthr()) d.G[e] = Ghi[(e / n) + (e % n) * n];
+    // ---- adjoint sweep
+    cta_identity(n, T);
+    for (int k = tid(); k < n; k += nthr()) s.logDR[k] = 0.0;
+    __syncthreads();
+    const int h = (ns - 1) / 2;
+    for (int b = nb; b >= 1 && ok; --b) {
+      const int t0 = (b - 1) * ns;
+      // right product: X_R <- diag(e^{-i phi_t}) E X_R, t = b*ns-1 .. t0 (rows of phi)
+      fill_b2(L, m, b == nb ? nullptr : m.Xn, one, one);
+      for (int t = b * ns - 1; t >= t0; --t) {
+        const bool last = t == t0;
+        cta_phase32(n, pf, d.phi + (size_t)t * n, -1.f);
+        if (!slice_mma(L, m, tbase, phase)) { ok = false; break; }
+        if (last)
+          epilogue<TO_FP64>(L, m, tbase, Scale{pf, false}, one, m.Xc, nullptr);
+        else
+          epilogue<TO_B_K>(L, m, tbase, Scale{pf, false}, one, nullptr, nullptr);
+      }
+      if (!ok) break;
+      cta_reortho(n, m.Xc, m.Xn, T, To, s.logDR, s);
+      double2* t2 = T; T = To; To = t2;
+      if (b == 1)
+        boundary_green(n, true, nullptr, nullptr, nullptr, m.Xn, T, s.logDR, Ga, Gb, Glo, s);
+      else
+        boundary_green(n, false, ckX(b - 1), ckT(b - 1), ckD(b - 1), m.Xn, T, s.logDR, Ga, Gb,
+                       Glo, s);
+      emit_force_row(n, Glo, d.F + (size_t)t0 * n);
+      // forward wraps from G_{t0}: G_{t0+j}, j = 1..h; slice t0+j uses phi row t0+j-1
+      for (int j = 1; j <= h && ok; ++j) {
+        float2* ph = pf + ((j & 1) ? n : 0);
+        cta_phase32(n, ph, d.phi + (size_t)(t0 + j - 1) * n, 1.f);
+        if (j == 1) {
+          __syncthreads();
+          fill_b2(L, m, Glo, Scale{ph, false}, Scale{ph, true});
+        }
+        if (!mma_ab(L, m, m.a_hi, m.a_lo, tbase, phase)) { ok = false; break; }
+        epilogue<TO_B_N>(L, m, tbase, one, one, nullptr, nullptr);
+        // the next wrap's phase (slice t0+j+1, phi row t0+j) is applied while writing B
+        float2* phn = pf + ((j & 1) ? 0 : n);
+        const bool more = j < h;
+        if (more) cta_phase32(n, phn, d.phi + (size_t)(t0 + j) * n, 1.f);
+        if (!mma_ab(L, m, e2_hi, e2_lo, tbase, phase)) { ok = false; break; }
+        if (more)
+          epilogue<TO_B_N>(L, m, tbase, Scale{phn, true}, Scale{phn, false}, nullptr,
+                           d.F + (size_t)(t0 + j) * n);
+        else
+          epilogue<NONE>(L, m, tbase, one, one, nullptr, d.F + (size_t)(t0 + j) * n);
+      }
+      // backward wraps from G_{b*ns}: G_{q-1}, q = b*ns .. t0+h+2; slice q uses phi row q-1
+      bool first = true;
+      for (int q = b * ns; q >= t0 + h + 2 && ok; --q) {
+        float2* ph = pf + ((q & 1) ? n : 0);
+        cta_phase32(n, ph, d.phi + (size_t)(q - 1) * n, 1.f);
+        if (first) {
+          __syncthreads();
+          fill_b2(L, m, Ghi, one, one);
+          first = false;
+        }
+        if (!mma_ab(L, m, e2_hi, e2_lo, tbase, phase)) { ok = false; break; }
+        epilogue<TO_B_N>(L, m, tbase, one, one, nullptr, nullptr);
+        if (!mma_ab(L, m, m.a_hi, m.a_lo, tbase, phase)) { ok = false; break; }
+        // lane m holds column m of E^{-1} G_q E; G_{q-1} = D^* (.) D has the same diagonal.
+        // Next B: B(n = m, k = i) = G_{q-1}[i, m] = conj(ph_i) X[i, m] ph_m
+        const bool more = q - 1 >= t0 + h + 2;
+        if (more)
+          epilogue<TO_B_N>(L, m, tbase, Scale{ph, false}, Scale{ph, true}, nullptr,
+                           d.F + (size_t)(q - 1) * n);
+        else
+          epilogue<NONE>(L, m, tbase, one, one, nullptr, d.F + (size_t)(q - 1) * n);
+      }
+      double2* tg = Ghi; Ghi = Glo; Glo = tg;
+    }
+    if (!ok) {
+      if (tid() == 0) status[d.user_index] = ST_TIMEOUT;
+      break;
+    }
+    if (tid() == 0)
+      status[d.user_index] = (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK;
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp_id() == 0) tc::tmem_dealloc(tbase, (uint32_t)L.tmem_cols);
+}
+
+void launch_force_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
+                        const MLayout& L, int grid, cudaStream_t stream) {
+  k_force_mixed<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status,
+                                                             scratch, L);
+}
+
+void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
+                      const MLayout& L, int grid, cudaStream_t stream) {
+  k_fwd_mixed<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch,
+                                                           L);
+}
+cudaError_t set_smem_mixed(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_force_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+int occupancy_mixed(bool force, int nthreads, int smem_bytes) {
+  int nb = 0;
+  if (force)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_mixed, nthreads, smem_bytes);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_mixed, nthreads, smem_bytes);
+  return nb;
+}
+
+}  // namespace fd

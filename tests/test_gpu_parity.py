@@ -204,3 +204,68 @@ def test_host_validation(ctx):
     # empty batch is a no-op
     r = api.Batch(ctx, [], "logdet").run()
     assert r.logdet.numel() == 0
+
+
+# ------------------------------------------------------------------ mixed precision
+from gpu_helpers import MIXED_TOL, g_scaled_err  # noqa: E402
+
+MIXED_CASES = [  # L, nt, beta, U, n_stab
+    (2, 16, 2.0, 2.0, 4),
+    (3, 64, 8.0, 3.0, 8),
+    (4, 32, 4.0, 3.0, 8),
+    (5, 32, 4.0, 3.0, 16),
+    (6, 64, 8.0, 3.0, 16),
+]
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "tf32"])
+@pytest.mark.parametrize("L,nt,beta,U,n_stab", MIXED_CASES)
+def test_mixed_logdet_green(ctx, prec, L, nt, beta, U, n_stab):
+    probs = [fi.make_problem(L, nt, beta, U, n_stab, 55, c) for c in range(3)]
+    ld, G, _ = _run(ctx, probs, "green", prec)
+    tol = MIXED_TOL[prec]
+    for c, p in enumerate(probs):
+        ref_ld, ref_G = stable.logdet_green(p.E, p.phi, n_stab)
+        assert logdet_err(complex(ld[c]), ref_ld) * max(1.0, abs(ref_ld)) / abs(ref_ld) \
+            <= tol["logdet_rel"]
+        assert g_scaled_err(G[c], ref_G) <= tol["G_scaled"]
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "tf32"])
+def test_mixed_cold72_sampled(ctx, prec):
+    probs = fi.workload("cold72", batch=8)
+    ld, G, _ = _run(ctx, probs, "green", prec)
+    tol = MIXED_TOL[prec]
+    for c in (0, 5):
+        p = probs[c]
+        ref_ld, ref_G = stable.logdet_green(p.E, p.phi, p.n_stab)
+        assert logdet_err(complex(ld[c]), ref_ld) * max(1.0, abs(ref_ld)) / abs(ref_ld) \
+            <= tol["logdet_rel"]
+        assert g_scaled_err(G[c], ref_G) <= tol["G_scaled"]
+
+
+def test_mixed_rejects_oversize(ctx):
+    from paper_2604_02130_gb300 import _lib as L
+    from paper_2604_02130_gb300 import api
+
+    probs = [fi.make_problem(12, 16, 1.0, 3.0, 16, 1, 0)]  # Nx = 288 > 128
+    with pytest.raises(api.FdError) as e:
+        api.Batch(ctx, to_dev(probs), "logdet", "tf32").run()
+    assert e.value.code == L.FD_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "tf32"])
+@pytest.mark.parametrize("L,nt,beta,U,n_stab", [(2, 16, 2.0, 2.0, 4), (3, 64, 8.0, 3.0, 8),
+                                                (4, 32, 4.0, 3.0, 8), (6, 32, 4.0, 3.0, 8)])
+def test_mixed_force(ctx, prec, L, nt, beta, U, n_stab):
+    probs = [fi.make_problem(L, nt, beta, U, n_stab, 56, c) for c in range(2)]
+    ld, G, F = _run(ctx, probs, "force+green", prec)
+    tol = MIXED_TOL[prec]
+    for c, p in enumerate(probs):
+        ref_ld, ref_G = stable.logdet_green(p.E, p.phi, n_stab)
+        assert logdet_err(complex(ld[c]), ref_ld) * max(1.0, abs(ref_ld)) / abs(ref_ld) \
+            <= tol["logdet_rel"]
+        assert g_scaled_err(G[c], ref_G) <= tol["G_scaled"]
+        ref_F = oforce.force(p.E, p.phi, n_stab)
+        scale = max(1.0, float(np.abs(ref_F).max())) ** 2
+        assert float(np.abs(F[c] - ref_F).max()) / scale <= tol["F_scaled"]
