@@ -119,6 +119,16 @@ int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch);
 /* Number of kernel launches the last fd_logdet/fd_green/fd_force call issued. */
 int fd_last_launch_count(const fd_ctx* ctx);
 
+/* The launch plan a call with these arguments would use, without launching anything: one
+ * record of 8 ints per launch (size class) in info[8*g .. 8*g+7]:
+ *   nx, kernel (0 FP64 log det/G, 1 FP64 force, 2 mixed log det/G, 3 mixed force),
+ *   threads per CTA, dynamic shared memory bytes, grid (persistent CTAs), resident CTAs per SM,
+ *   scratch KiB per CTA, configurations in the class.
+ * Returns the number of launches (>= 0, records beyond max_groups are not written) or a
+ * negative FD_ERR_* code.  Synchronous, host only (queries the device's occupancy limits). */
+int fd_plan_query(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec, int* info,
+                  int max_groups);
+
 /* Per-launch timing.  With timing on, every kernel launch of a call is bracketed by CUDA events
  * recorded on the call's stream.  fd_last_kernel_ms waits for them and writes the durations (ms)
  * of the last call's launches, in launch order, to ms[0..max-1]; it returns how many it wrote

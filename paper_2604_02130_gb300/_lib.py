@@ -59,6 +59,7 @@ SIGNATURES = [
     ("fd_set_timing", _I, [_VP, _I]),
     ("fd_last_kernel_ms", _I, [_VP, ctypes.POINTER(ctypes.c_double), _I]),
     ("fd_logdet_noalloc", _I, [_I, _PP, _VP, _VP, _VP, _VP]),
+    ("fd_plan_query", _I, [_VP, _I, _PP, _I, _I, ctypes.POINTER(_I), _I]),
 ]
 
 _lib = None

@@ -142,6 +142,16 @@ class Batch:
             o += a * b
         return flat, views
 
+    def plan(self) -> List[dict]:
+        """The launch plan of this batch (one dict per size class), see fd_plan_query."""
+        what = {"logdet": 1, "green": 3, "force": 5, "force+green": 7}[self.want]
+        info = (ctypes.c_int * (8 * 64))()
+        n = self.ctx.lib.fd_plan_query(self.ctx.h, self.n, self.problems, what, self.prec, info, 64)
+        if n < 0:
+            self.ctx.check(n)
+        keys = ("nx", "kernel", "threads", "smem", "grid", "ctas_per_sm", "scratch_kib", "configs")
+        return [dict(zip(keys, info[8 * g:8 * g + 8])) for g in range(min(n, 64))]
+
     def reserve(self):
         what = {"logdet": 1, "green": 3, "force": 5, "force+green": 7}[self.want]
         self.ctx.check(self.ctx.lib.fd_reserve(self.ctx.h, self.n, self.problems, what, self.prec))

@@ -72,19 +72,45 @@ struct Group {
   Layout L;
   fd::MLayout ML;
   int grid;
+  int occ;     // resident CTAs per SM assumed by the plan
   std::vector<int> idx;  // user indices, cost-sorted (descending)
   size_t desc_off;       // first descriptor of this group in the table
   size_t scratch_off;    // byte offset of this group's slots
 };
 
+// Threads per CTA.  The FP64 pipe of this GPU (about 2 DFMA/clk/SM, spread over the four SM
+// sub-partitions) is only kept busy when every sub-partition has warps issuing FP64 work, so even
+// small matrices get 4-8 warps; the CTA routines spread their element loops over all of them.
 int threads_for(int n) {
-  if (n <= 12) return 32;
-  if (n <= 24) return 64;
-  if (n <= 40) return 128;
+  if (n <= 12) return 128;
   return 256;
 }
 
 long long round16(long long x) { return (x + 15) & ~15LL; }
+
+// Resident CTAs per SM for a kernel: the runtime's occupancy calculator, cross-checked by a
+// direct count from the kernel's registers and shared memory (the smaller wins; 1 at least).
+int resident_ctas(fd_ctx* ctx, bool mixed, bool force, int nthreads, int smem_bytes) {
+  int api = mixed ? fd::occupancy_mixed(force, nthreads, smem_bytes)
+                  : fd::occupancy_fp64(force, nthreads, smem_bytes);
+  cudaFuncAttributes fa;
+  cudaError_t e = mixed ? fd::attrs_mixed(force, &fa) : fd::attrs_fp64(force, &fa);
+  int manual = 1;
+  if (e == cudaSuccess) {
+    const int warps = (nthreads + 31) / 32;
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_warp > 0 ? 65536 / (regs_warp * warps) : 32;
+    const int per_cta = smem_bytes + (int)fa.sharedSizeBytes + 1024;
+    const int by_smem = per_cta > 0 ? (ctx->smem_per_sm + 1024) / per_cta : 32;
+    const int by_thr = 2048 / (warps * 32);
+    manual = std::max(1, std::min(std::min(by_regs, by_smem), std::min(by_thr, 32)));
+  }
+  // The runtime calculator reports 1 resident CTA for the tcgen05 kernels even where registers,
+  // shared memory and threads allow more (ncu's launch statistics agree with the direct count);
+  // those kernels use the direct count, bounded by the TMEM columns by the caller.
+  if (api <= 0 || mixed) return manual;
+  return std::max(1, std::min(api, manual));
+}
 
 // Greedy placement: the buffers touched every slice first, then the per-block ones.
 Layout plan_layout(int n, int kind, int budget, int nthreads, int max_nt, int max_nstab_min) {
@@ -152,8 +178,9 @@ fd::MLayout plan_mixed(int n, int kind, bool three, int budget, int smem_per_sm,
   int need = M.Np + ((M.Np + 15) & ~15);
   M.tmem_cols = 32;
   while (M.tmem_cols < need) M.tmem_cols <<= 1;
-  M.nthreads = n <= 40 ? 128 : 256;
-  const long long a_bytes = (long long)M.Np * M.Kp * 4;
+  M.nthreads = n <= 12 ? 128 : 256;
+  M.perm = n <= 64 ? 1 : 0;
+  const long long a_bytes = (long long)(M.perm ? 128 : M.Np) * M.Kp * 4;
   const long long b_one = (long long)M.N * M.Kp * 4;
   const long long b_bytes = b_one * (three ? 2 : 1);
   const long long cm = 16LL * n * n;
@@ -205,6 +232,22 @@ fd::MLayout plan_mixed(int n, int kind, bool three, int budget, int smem_per_sm,
     M.xn_off = g;
     g += round16(cm);
   }
+  // T pair, then (force) the four G buffers: shared memory when they fit
+  M.t_smem = o + 2 * round16(cm) + fixed <= budget ? 1 : 0;
+  if (M.t_smem) {
+    M.t0_off = o;
+    o += round16(cm);
+    M.t1_off = o;
+    o += round16(cm);
+  }
+  M.g_smem = 0;
+  if (kind == K_FORCE && o + 4 * round16(cm) + fixed <= budget) {
+    M.g_smem = 1;
+    for (int i = 0; i < 4; ++i) {
+      M.g_off[i] = o;
+      o += round16(cm);
+    }
+  }
   M.small_off = (int)o;
   o += round16(fd::small_bytes(n));
   M.bar_off = (int)o;
@@ -222,11 +265,13 @@ fd::MLayout plan_mixed(int n, int kind, bool three, int budget, int smem_per_sm,
     M.smem_bytes = 0;
     return M;
   }
-  M.t0_off = g;
-  g += round16(cm);
-  M.t1_off = g;
-  g += round16(cm);
-  if (kind == K_FORCE) {
+  if (!M.t_smem) {
+    M.t0_off = g;
+    g += round16(cm);
+    M.t1_off = g;
+    g += round16(cm);
+  }
+  if (kind == K_FORCE && !M.g_smem) {
     for (int i = 0; i < 4; ++i) {
       M.g_off[i] = g;
       g += round16(cm);
@@ -299,8 +344,9 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
         g.mixed = 1;
         g.ML = M;
         memset(&g.L, 0, sizeof(g.L));
-        int occ = fd::occupancy_mixed(kind == K_FORCE, M.nthreads, M.smem_bytes);
+        int occ = resident_ctas(ctx, true, kind == K_FORCE, M.nthreads, M.smem_bytes);
         occ = std::max(1, std::min(occ, 512 / M.tmem_cols));
+        g.occ = occ;
         g.grid = std::min<int>((int)g.idx.size(), ctx->num_sms * occ);
         g.L.slot_bytes = M.slot_bytes;
         groups.push_back(g);
@@ -317,8 +363,8 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
     else
       budget = ctx->max_smem_optin;
     g.L = plan_layout(n, kind, budget, nth, max_nb, min_ns);
-    int occ = fd::occupancy_fp64(kind == K_FORCE, nth, g.L.smem_bytes);
-    if (occ < 1) occ = 1;
+    int occ = resident_ctas(ctx, false, kind == K_FORCE, nth, g.L.smem_bytes);
+    g.occ = occ;
     g.grid = std::min<int>((int)g.idx.size(), ctx->num_sms * occ);
     groups.push_back(g);
   }
@@ -567,6 +613,31 @@ int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch) {
 }
 
 int fd_last_launch_count(const fd_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+int fd_plan_query(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec, int* info,
+                  int max_groups) {
+  double dummy;
+  int rc = validate(ctx, batch, probs, &dummy, prec, (what & FD_WANT_FORCE) != 0);
+  if (rc != FD_OK) return rc;
+  if (max_groups > 0 && !info) return fail(ctx, FD_ERR_INVALID, "null info");
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int kind = (what & FD_WANT_FORCE) ? K_FORCE : K_FWD;
+  std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
+  int k = 0;
+  for (auto& g : groups) {
+    if (k >= max_groups) break;
+    int* o = info + 8 * k++;
+    o[0] = g.nx;
+    o[1] = (g.mixed ? 2 : 0) + (kind == K_FORCE ? 1 : 0);
+    o[2] = g.mixed ? g.ML.nthreads : g.L.nthreads;
+    o[3] = g.mixed ? g.ML.smem_bytes : g.L.smem_bytes;
+    o[4] = g.grid;
+    o[5] = g.occ;
+    o[6] = (int)((g.mixed ? g.ML.slot_bytes : g.L.slot_bytes) >> 10);
+    o[7] = (int)g.idx.size();
+  }
+  return (int)groups.size();
+}
 
 int fd_set_timing(fd_ctx* ctx, int on) {
   if (!ctx) return FD_ERR_INVALID;

@@ -95,17 +95,20 @@ struct MLayout {
   int n, Np, Kp, N;      // N = 2*Np MMA columns; Kp = Np
   int tmem_cols;
   int three;             // 1 = split TF32 (hi + lo, 3 MMAs per K step)
+  int perm;              // 1 = matrix row i sits in accumulator lane 32*(i%4) + i/4 (spreads
+                         //     small matrices over all four TMEM lane quarters / warps)
   int a_hi, a_lo;        // A operand(s): E
   int a2_hi, a2_lo;      // force only: E^{-1}
   int b_hi, b_lo;        // B operand(s); the region also hosts the FP64 block result Xc
   int xc_smem, xn_smem;  // 1 = shared memory, 0 = CTA scratch slot
   long long xc_off, xn_off;
-  long long t0_off, t1_off;  // T buffers, always in the scratch slot
+  int t_smem, g_smem;        // 1 = T pair / force G buffers in shared memory
+  long long t0_off, t1_off;  // T buffers (shared memory or scratch slot)
   int small_off;
   int bar_off;           // mbarrier (8 B), TMEM address (4 B), queue slot (4 B)
   long long slot_bytes;
   // force only
-  long long g_off[4];    // G_lo, G_hi, G_a, G_b (scratch slot, complex128 n*n each)
+  long long g_off[4];    // G_lo, G_hi, G_a, G_b (complex128 n*n each)
   long long ws_bytes;    // slot bytes before the checkpoints
 };
 

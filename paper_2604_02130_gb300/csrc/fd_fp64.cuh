@@ -63,42 +63,58 @@ __device__ __forceinline__ void mac(cplx& acc, cplx a, cplx b) {
   acc.im = fma(a.im, b.re, acc.im);
 }
 
-// Out(i,j) <- epi(i, j, sum_{k in [k_lo(i0), n)} A(i,k) B(k,j)), i,j in [0,n).
-// 2x2 register tiles; consecutive threads take consecutive row tiles.  If TRI, A is treated as
-// upper triangular (A(i,k) = 0 for k < i).  Out must not alias A or B.
-template <bool TRI, class AOp, class BOp, class Epi>
-__device__ void cta_gemm(int n, const AOp& A, const BOp& B, const Epi& epi) {
-  const int tm = (n + 1) >> 1;
-  const int ntiles = tm * tm;
+// Out(i,j) <- epi(i, j, sum_k A(i,k) B(k,j)), i,j in [0,n), with TM x TN register tiles;
+// consecutive threads take consecutive row tiles.  If TRI, A is upper triangular (A(i,k) = 0 for
+// k < i; its first TM - 1 columns are masked explicitly).  Out must not alias A or B.
+template <int TM, int TN, bool TRI, class AOp, class BOp, class Epi>
+__device__ __forceinline__ void gemm_tiles(int n, const AOp& A, const BOp& B, const Epi& epi) {
+  const int tm = (n + TM - 1) / TM, tn = (n + TN - 1) / TN;
+  const int ntiles = tm * tn;
   for (int tile = tid(); tile < ntiles; tile += nthr()) {
-    const int i0 = (tile % tm) * 2, j0 = (tile / tm) * 2;
-    const int i1 = min(i0 + 1, n - 1), j1 = min(j0 + 1, n - 1);
-    cplx a00 = cx(0, 0), a01 = cx(0, 0), a10 = cx(0, 0), a11 = cx(0, 0);
+    const int i0 = (tile % tm) * TM, j0 = (tile / tm) * TN;
+    int ii[TM], jj[TN];
+#pragma unroll
+    for (int a = 0; a < TM; ++a) ii[a] = min(i0 + a, n - 1);
+#pragma unroll
+    for (int b = 0; b < TN; ++b) jj[b] = min(j0 + b, n - 1);
+    cplx acc[TM][TN];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) acc[a][b] = cx(0, 0);
     int k = TRI ? i0 : 0;
-    if (TRI) {  // k = i0 contributes to row i0 only
-      auto a0 = A(i0, k);
-      mac(a00, a0, B(k, j0));
-      mac(a01, a0, B(k, j1));
-      ++k;
-    }
 #pragma unroll 2
     for (; k < n; ++k) {
-      auto a0 = A(i0, k);
-      auto a1 = A(i1, k);
-      auto b0 = B(k, j0);
-      auto b1 = B(k, j1);
-      mac(a00, a0, b0);
-      mac(a01, a0, b1);
-      mac(a10, a1, b0);
-      mac(a11, a1, b1);
+      decltype(A(0, 0)) av[TM];
+      decltype(B(0, 0)) bv[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a) av[a] = A(ii[a], k);
+#pragma unroll
+      for (int b = 0; b < TN; ++b) bv[b] = B(k, jj[b]);
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) mac(acc[a][b], av[a], bv[b]);
     }
-    epi(i0, j0, a00);
-    if (j0 + 1 < n) epi(i0, j0 + 1, a01);
-    if (i0 + 1 < n) {
-      epi(i0 + 1, j0, a10);
-      if (j0 + 1 < n) epi(i0 + 1, j0 + 1, a11);
-    }
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b)
+        if (i0 + a < n && j0 + b < n) epi(i0 + a, j0 + b, acc[a][b]);
   }
+}
+
+// CTA GEMM: picks the largest register tile that still gives every thread at least one tile
+// (small matrices use 1x1 tiles so that all warps -- and all four FP64 pipes of the SM -- work).
+template <bool TRI, class AOp, class BOp, class Epi>
+__device__ void cta_gemm(int n, const AOp& A, const BOp& B, const Epi& epi) {
+  const int t2 = ((n + 1) >> 1) * ((n + 1) >> 1);
+  if (t2 >= nthr())
+    gemm_tiles<2, 2, TRI>(n, A, B, epi);
+  else if (((n + 1) >> 1) * n >= nthr())
+    gemm_tiles<1, 2, TRI>(n, A, B, epi);
+  else
+    gemm_tiles<1, 1, TRI>(n, A, B, epi);
   __syncthreads();
 }
 

@@ -11,7 +11,8 @@ void launch_fwd_fp64(const Desc* descs, int ndesc, int* queue, int* status, char
 void launch_force_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                        const Layout& L, int grid, cudaStream_t stream);
 cudaError_t set_smem_fp64(int bytes);
-int occupancy_fp64(bool force, int nthreads, int smem_bytes);
+int occupancy_fp64(bool force, int nthreads, int smem_bytes);  // -1 on error
+cudaError_t attrs_fp64(bool force, cudaFuncAttributes* a);
 
 // mixed path (tcgen05 slice GEMMs)
 void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
@@ -19,7 +20,8 @@ void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, cha
 void launch_force_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                         const MLayout& L, int grid, cudaStream_t stream);
 cudaError_t set_smem_mixed(int bytes);
-int occupancy_mixed(bool force, int nthreads, int smem_bytes);
+int occupancy_mixed(bool force, int nthreads, int smem_bytes);  // -1 on error
+cudaError_t attrs_mixed(bool force, cudaFuncAttributes* a);
 
 // FP64 throughput probe
 cudaError_t run_fp64_probe(int grid, int threads, int iters, double* out, cudaStream_t stream);

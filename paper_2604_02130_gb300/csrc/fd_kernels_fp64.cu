@@ -280,16 +280,25 @@ void launch_force_fp64(const Desc* descs, int ndesc, int* queue, int* status, ch
 }
 int occupancy_fp64(bool force, int nthreads, int smem_bytes) {
   int nb = 0;
+  cudaError_t e;
   if (force)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_fp64, nthreads, smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_fp64, nthreads, smem_bytes);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_fp64, nthreads, smem_bytes);
-  return nb;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_fp64, nthreads, smem_bytes);
+  return e == cudaSuccess ? nb : -1;
 }
 cudaError_t set_smem_fp64(int bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_force_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  for (const void* k : {(const void*)k_fwd_fp64, (const void*)k_force_fp64}) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+cudaError_t attrs_fp64(bool force, cudaFuncAttributes* a) {
+  return cudaFuncGetAttributes(a, force ? (const void*)k_force_fp64 : (const void*)k_fwd_fp64);
 }
 
 }  // namespace fd

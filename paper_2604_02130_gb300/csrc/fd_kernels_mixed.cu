@@ -47,11 +47,21 @@ __device__ __forceinline__ MixedSmem mixed_smem(char* smem, char* slot, const ML
 
 // A operand: E (n x n FP64, symmetric) -> TF32 (hi, and lo = E - hi for the split mode), zero
 // padded to Np x Kp.
+// Accumulator lane of matrix row i, and back.
+__device__ __forceinline__ int lane_of_row(const MLayout& L, int i) {
+  return L.perm ? 32 * (i & 3) + (i >> 2) : i;
+}
+__device__ __forceinline__ int row_of_lane(const MLayout& L, int l) {
+  return L.perm ? 4 * (l & 31) + (l >> 5) : l;
+}
+
 __device__ void fill_a(const MLayout& L, float* a_hi, float* a_lo, const double* E) {
-  const int n = L.n, Np = L.Np, Kp = L.Kp;
-  for (int e = tid(); e < Np * Kp; e += nthr()) {
+  const int n = L.n, Kp = L.Kp;
+  const int rows = L.perm ? 128 : L.Np;
+  for (int e = tid(); e < rows * Kp; e += nthr()) {
     int r = e / Kp, k = e % Kp;
-    double v = (r < n && k < n) ? E[r * n + k] : 0.0;
+    int i = row_of_lane(L, r);
+    double v = (i < n && k < n) ? E[i * n + k] : 0.0;
     float f = (float)v;
     float hi = tc::to_tf32(f);
     uint32_t o = tc::kmaj_off(r, k, Kp) >> 2;
@@ -143,8 +153,9 @@ __device__ void epilogue(const MLayout& L, const MixedSmem& m, uint32_t tbase, S
   const int quad = w & 3;
   const int half = w >> 2;
   const int nhalf = nw > 4 ? 2 : 1;
-  const int l = quad * 32 + lane_id();
-  if (quad * 32 < n) {
+  const int l = row_of_lane(L, quad * 32 + lane_id());  // matrix row held by this thread
+  const int first_row = row_of_lane(L, quad * 32);
+  if (first_row < n) {
     const uint32_t lane_base = tbase + ((uint32_t)(quad * 32) << 16);
     const int nchunk = (Np + 15) / 16;
     const float2 r = l < n ? rs.at(l) : make_float2(1.f, 0.f);
@@ -233,8 +244,8 @@ __global__ void __launch_bounds__(256) k_fwd_mixed(const Desc* __restrict__ desc
   const uint32_t tbase = *m.taddr;
   uint32_t phase = 0;
   const int n = L.n;
-  double2* T = (double2*)(slot + L.t0_off);
-  double2* To = (double2*)(slot + L.t1_off);
+  double2* T = (double2*)((L.t_smem ? smem : slot) + L.t0_off);
+  double2* To = (double2*)((L.t_smem ? smem : slot) + L.t1_off);
   for (;;) {
     int c = grab_m(queue, m.qslot);
     if (c >= ndesc) break;
@@ -312,12 +323,13 @@ __global__ void __launch_bounds__(256) k_force_mixed(const Desc* __restrict__ de
   const uint32_t tbase = *m.taddr;
   uint32_t phase = 0;
   const int n = L.n;
-  double2* T = (double2*)(slot + L.t0_off);
-  double2* To = (double2*)(slot + L.t1_off);
-  double2* Glo = (double2*)(slot + L.g_off[0]);
-  double2* Ghi = (double2*)(slot + L.g_off[1]);
-  double2* Ga = (double2*)(slot + L.g_off[2]);
-  double2* Gb = (double2*)(slot + L.g_off[3]);
+  double2* T = (double2*)((L.t_smem ? smem : slot) + L.t0_off);
+  double2* To = (double2*)((L.t_smem ? smem : slot) + L.t1_off);
+  char* gb = L.g_smem ? smem : slot;
+  double2* Glo = (double2*)(gb + L.g_off[0]);
+  double2* Ghi = (double2*)(gb + L.g_off[1]);
+  double2* Ga = (double2*)(gb + L.g_off[2]);
+  double2* Gb = (double2*)(gb + L.g_off[3]);
   double2* ckbase = (double2*)(slot + L.ws_bytes);
   const Scale one{nullptr, false};
   for (;;) {
@@ -471,18 +483,26 @@ void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, cha
                                                            L);
 }
 cudaError_t set_smem_mixed(int bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_force_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  for (const void* k : {(const void*)k_fwd_mixed, (const void*)k_force_mixed}) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+cudaError_t attrs_mixed(bool force, cudaFuncAttributes* a) {
+  return cudaFuncGetAttributes(a, force ? (const void*)k_force_mixed : (const void*)k_fwd_mixed);
 }
 int occupancy_mixed(bool force, int nthreads, int smem_bytes) {
   int nb = 0;
+  cudaError_t e;
   if (force)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_mixed, nthreads, smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_mixed, nthreads, smem_bytes);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_mixed, nthreads, smem_bytes);
-  return nb;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_mixed, nthreads, smem_bytes);
+  return e == cudaSuccess ? nb : -1;
 }
 
 }  // namespace fd
