@@ -4,9 +4,11 @@ One step = log det + G + force (forward pass with checkpoints, adjoint sweep) fo
 configurations.  Default workload: 256 configurations of the honeycomb L = 3 lattice (Nx = 18),
 beta = 8, Nt = 64, U = 3, n_stab = 8.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|tf32|3xtf32]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec 3xtf32|tf32|fp64]
                     [--workload batch18|cold72|force72|tiny8] [--impl ours|reference]
 
+The headline is the mixed-precision path (slice products on tensor cores, FP64 QR/assembly);
+the plain FP64 path is measured on the same inputs and reported beside it (`fp64_path`).
 Prints ONE JSON line (rank 0).  `value` is configurations per second over all ranks with the
 inputs resident on the device; `e2e` is the same metric through the public API with the inputs
 copied from pinned host memory and the results read back inside the timed region.
@@ -206,6 +208,67 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our arm
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _tensor_flops(nx, nt, n_stab):
+    """Flops of the steps the mixed path runs on tensor cores: slice products and right products
+    (4 Nx^3 each per slice) and the in-block wraps (8 Nx^3 each)."""
+    n3 = float(nx) ** 3
+    nb = nt // n_stab
+    return 4 * n3 * nt * 2 + 8 * n3 * (nt - nb)
+
+
+def _time_batch(batch, ctx, steps, flush, stream, barrier, sample_clocks, gpu):
+    import torch
+
+    ctx.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    kernel_ms, launches = [], 0
+    barrier()
+    clk = ClockSampler(gpu) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    try:
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            batch.run()
+            ev[k][1].record(stream)
+            launches += ctx.last_launch_count()
+            kernel_ms.append(sum(ctx.last_kernel_ms()))
+        barrier()
+    finally:
+        if clk:
+            clk.__exit__()
+    ctx.set_timing(False)
+    return {"total_ms": sum(a.elapsed_time(b) for a, b in ev), "kernel_ms": kernel_ms,
+            "launches": launches, "clocks": clk.summary() if clk else None}
+
+
+def _errors(batch, res):
+    import numpy as np
+
+    ld = batch.logdet_buf.cpu().numpy()
+    e_ld = e_g = e_f = 0.0
+    for c, ldr, Gr, Fr, _ in res:
+        g = complex(ld[c, 0], ld[c, 1])
+        dim = abs(np.angle(np.exp(1j * (g.imag - ldr.imag))))
+        e_ld = max(e_ld, max(abs(g.real - ldr.real), dim) / abs(ldr))
+        sg = max(1.0, float(np.abs(Gr).max())) ** 2
+        e_g = max(e_g, float(np.abs(batch.G[c].cpu().numpy() - Gr).max()) / sg)
+        sf = max(1.0, float(np.abs(Fr).max())) ** 2
+        e_f = max(e_f, float(np.abs(batch.F[c].cpu().numpy() - Fr).max()) / sf)
+    return {"logdet_rel": e_ld, "G_abs_over_maxG2": e_g, "F_abs_over_maxF2": e_f,
+            "configs_checked": len(res)}
+
+
 def run_ours(args):
     ws, rank, local = _dist()
     import numpy as np
@@ -229,16 +292,13 @@ def run_ours(args):
 
     dev = torch.device("cuda", local)
     probs = fi.workload(name, batch=w_batch, first=rank * w_batch)
-    nx, nt = probs[0].nx, probs[0].nt
+    nx, nt, ns = probs[0].nx, probs[0].nt, probs[0].n_stab
     # inputs resident on the device: one phi buffer for the batch; E, E^{-1} shared
     phi_host = torch.from_numpy(np.stack([p.phi for p in probs])).pin_memory()
     phi_dev = phi_host.to(dev)
     E = torch.from_numpy(probs[0].E).to(dev)
     Einv = torch.from_numpy(probs[0].Einv).to(dev)
     ctx = api.Context(local)
-    batch = api.Batch(ctx, [(E, Einv, phi_dev[c], p.n_stab) for c, p in enumerate(probs)],
-                      "force+green", args.prec)
-    batch.reserve()
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -247,36 +307,33 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(max(3, args.warmup)):
-        batch.run()
-    barrier()
-    assert all(s == 0 for s in batch.status()), "device status not OK"
-
-    # ---- device-resident timing: per-step events, L2 flushed between steps
-    ctx.set_timing(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    kernel_ms = []
-    launches = 0
-    barrier()
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            batch.run()
-            ev[k][1].record(stream)
-            launches += ctx.last_launch_count()
-            kernel_ms.append(sum(ctx.last_kernel_ms()))
+    def make(prec):
+        b = api.Batch(ctx, [(E, Einv, phi_dev[c], p.n_stab) for c, p in enumerate(probs)],
+                      "force+green", prec)
+        b.reserve()
+        for _ in range(max(3, args.warmup)):
+            b.run()
         barrier()
-    clocks = clk.summary()
-    ctx.set_timing(False)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        assert all(s == 0 for s in b.status()), "device status not OK"
+        return b
+
+    def allmax(x):
+        if ws > 1:
+            t = torch.tensor([x], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
     n_total = w_batch * ws
+    fl = force_flops(nx, nt, ns)
+    fl_tensor = _tensor_flops(nx, nt, ns)
+    fl_fp64_mixed = fl["total"] - fl_tensor
+
+    # ---- headline path: device-resident timing, L2 flushed between steps
+    batch = make(args.prec)
+    plan = batch.plan()
+    head = _time_batch(batch, ctx, args.steps, flush, stream, barrier, True, local)
+    total_ms = allmax(head["total_ms"])
     value = n_total * args.steps / (total_ms * 1e-3)
 
     # ---- end to end through the public API: pinned host inputs in, results out
@@ -298,31 +355,51 @@ def run_ours(args):
         F_host.copy_(batch.F_flat, non_blocking=True)
         ev2[k][1].record(stream)
     barrier()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = allmax(sum(a.elapsed_time(b) for a, b in ev2))
     e2e = {"value": n_total * args.steps / (e2e_ms * 1e-3), "unit": "configs/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    launches = head["launches"]
+
+    # ---- the plain FP64 path on the same inputs, reported beside the headline
+    fp64 = None
+    b64 = None
+    if args.prec != "fp64" and not args.no_fp64_path:
+        b64 = make("fp64")
+        r64 = _time_batch(b64, ctx, max(3, args.steps // 2), flush, stream, barrier, False, local)
+        ms64 = allmax(r64["total_ms"]) / max(3, args.steps // 2)
+        fp64 = {"value": n_total / (ms64 * 1e-3), "unit": "configs/s", "ms_per_step": ms64,
+                "tflops": fl["total"] * n_total / (ms64 * 1e-3) / 1e12,
+                "kernel_ms": statistics.mean(r64["kernel_ms"])}
 
     if rank != 0:
         torch.distributed.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel (the force kernel: the only launch of the step)
-    fl = force_flops(nx, nt, probs[0].n_stab)
-    fl_launch = fl["total"] * w_batch
-    k_ms = statistics.mean(kernel_ms)
-    peak_gflops = ctx.measure_fp64_peak()
-    achieved = fl_launch / (k_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_gflops / 1e3, "unit": "TFLOP/s",
-            "frac": achieved / (peak_gflops / 1e3),
-            "traffic": _traffic("k_force_fp64", name, args.prec),
-            "kernel": "k_force_fp64", "kernel_ms": k_ms,
-            "peak_source": "measured FP64 DFMA probe (fd_measure_fp64_peak), same run"}
+    # ---- roofline of the dominant kernel (the force kernel is the step's only launch)
+    peaks, peak_src = _measured_peaks()
+    peak_fp64 = ctx.measure_fp64_peak() / 1e3
+    k_ms = statistics.mean(head["kernel_ms"])
+    mixed = args.prec != "fp64"
+    kname = "k_force_mixed" if mixed else "k_force_fp64"
+    fp64_work = (fl_fp64_mixed if mixed else fl["total"]) * w_batch
+    achieved = fp64_work / (k_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+            "frac": achieved / peak_fp64, "traffic": _traffic(kname, name, args.prec),
+            "kernel": kname, "kernel_ms": k_ms,
+            "what": "FP64 algorithmic work of the kernel (QR, boundary G, assembly%s) per launch "
+                    "over its CUDA-event duration" % ("" if mixed else ", slices, wraps"),
+            "peak_source": "FP64 DFMA probe over all SMs in this run (fd_measure_fp64_peak)"}
+    if mixed:
+        tf32_peak = peaks["bf16_tflops"] / 2.0
+        t_ach = fl_tensor * w_batch / (k_ms * 1e-3) / 1e12
+        roof["tensor"] = {"achieved": t_ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                          "frac": t_ach / tf32_peak,
+                          "what": "tensor-core work (slice and right products, wraps; one "
+                                  "product counted once, not x3 for split TF32)",
+                          "peak_source": "%s bf16 dense x 1/2 (TF32:BF16 nominal ratio)"
+                                         % peak_src}
 
-    # ---- CPU oracle on a bounded sample, and the error of the GPU results on that sample
+    # ---- CPU oracle on a bounded sample, and the errors of the GPU results on that sample
     cpu = None
     err = None
     if pool is not None:
@@ -332,15 +409,9 @@ def run_ours(args):
         cpu = {"value": len(sample) / dt, "unit": "configs/s", "cores": cores, "kind": "oracle",
                "sample": "%d of the %d configurations (log det + G + force), one per process"
                          % (len(sample), w_batch)}
-        ld = batch.logdet_buf.cpu().numpy()
-        e_ld = e_g = e_f = 0.0
-        for c, ldr, Gr, Fr, _ in res:
-            g = complex(ld[c, 0], ld[c, 1])
-            dim = abs(np.angle(np.exp(1j * (g.imag - ldr.imag))))
-            e_ld = max(e_ld, max(abs(g.real - ldr.real), dim) / abs(ldr))
-            e_g = max(e_g, float(np.abs(batch.G[c].cpu().numpy() - Gr).max()))
-            e_f = max(e_f, float(np.abs(batch.F[c].cpu().numpy() - Fr).max()))
-        err = {"logdet_rel": e_ld, "G_abs": e_g, "F_abs": e_f, "configs_checked": len(res)}
+        err = {args.prec: _errors(batch, res)}
+        if b64 is not None:
+            err["fp64"] = _errors(b64, res)
 
     line = {
         "metric": "configs/s (log det + G + force)",
@@ -355,14 +426,15 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32+f64", "3xtf32": "3xtf32+f64"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[name], "prec": args.prec,
+        "config": {"workload": WORKLOAD_TEXT[name], "prec": args.prec, "plan": plan,
                    "l2": "flushed between timed steps (%d MB write)" % (FLUSH_BYTES >> 20)},
         "tflops": fl["total"] * n_total * args.steps / (total_ms * 1e-3) / 1e12,
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roof,
-        "clocks": clocks,
+        "clocks": head["clocks"],
         "cpu_baseline": cpu,
+        "fp64_path": fp64,
         "error_vs_oracle": err,
     }
     print(json.dumps(line), flush=True)
@@ -375,9 +447,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--prec", choices=("fp64", "tf32", "3xtf32"), default="fp64")
+    ap.add_argument("--prec", choices=("fp64", "tf32", "3xtf32"), default="3xtf32")
     ap.add_argument("--workload", choices=tuple(WORKLOAD_TEXT), default="batch18")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true",
+                    help="skip the FP64-path measurement reported beside the mixed path")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

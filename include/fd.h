@@ -54,7 +54,9 @@ enum {
 };
 
 /* Arithmetic of the slice products.  QR re-orthogonalisation, scale separation, assembly,
- * boundary Green's functions and all outputs are FP64 in every mode. */
+ * boundary Green's functions and all outputs are FP64 in every mode.  The mixed modes apply to
+ * configurations with nx <= 128 (one tensor-core tile: M = 128 rows, N = 2*nx <= 256 TMEM
+ * columns); larger nx in the same call run on the FP64 kernels (see fd_plan_query). */
 enum {
   FD_PREC_FP64 = 0,        /* everything in FP64 (DFMA) */
   FD_PREC_MIXED_TF32 = 1,  /* slice GEMMs on tcgen05 tensor cores, TF32 operands, FP32 accumulate */

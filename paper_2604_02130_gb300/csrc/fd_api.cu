@@ -428,11 +428,9 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double*
   ctx->last_batch = batch;
   if (batch == 0) return FD_OK;
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  // Mixed precision applies to the size classes that fit the tensor-core kernels (nx <= 128 and
+  // its operands in shared memory); larger classes run the FP64 kernels (fd_plan_query says so).
   std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
-  for (auto& g : groups)
-    if (prec != FD_PREC_FP64 && !g.mixed)
-      return fail(ctx, FD_ERR_UNSUPPORTED,
-                  "nx=%d does not fit the mixed-precision kernel (nx <= 128, shared memory)", g.nx);
   size_t need = scratch_need(groups);
   int rc = ensure(ctx, (size_t)batch, (size_t)batch, groups.size(), need);
   if (rc != FD_OK) return rc;

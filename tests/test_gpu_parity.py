@@ -244,14 +244,20 @@ def test_mixed_cold72_sampled(ctx, prec):
         assert g_scaled_err(G[c], ref_G) <= tol["G_scaled"]
 
 
-def test_mixed_rejects_oversize(ctx):
-    from paper_2604_02130_gb300 import _lib as L
+def test_mixed_oversize_class_runs_fp64(ctx):
+    # Nx = 288 exceeds one tensor-core tile: that size class runs on the FP64 kernel, the
+    # Nx = 18 class of the same call on the tensor cores
     from paper_2604_02130_gb300 import api
 
-    probs = [fi.make_problem(12, 16, 1.0, 3.0, 16, 1, 0)]  # Nx = 288 > 128
-    with pytest.raises(api.FdError) as e:
-        api.Batch(ctx, to_dev(probs), "logdet", "tf32").run()
-    assert e.value.code == L.FD_ERR_UNSUPPORTED
+    probs = [fi.make_problem(12, 16, 1.0, 3.0, 16, 1, 0), fi.make_problem(3, 16, 1.0, 3.0, 8, 1, 1)]
+    b = api.Batch(ctx, to_dev(probs), "green", "3xtf32")
+    kinds = {g["nx"]: g["kernel"] for g in b.plan()}
+    assert kinds == {288: 0, 18: 2}
+    ld, G, _ = _run(ctx, probs, "green", "3xtf32")
+    p = probs[0]
+    ref_ld, ref_G = stable.logdet_green(p.E, p.phi, p.n_stab)
+    assert logdet_err(complex(ld[0]), ref_ld) <= LOGDET_RTOL_FP64
+    assert np.abs(G[0] - ref_G).max() <= G_ATOL_FP64
 
 
 @pytest.mark.parametrize("prec", ["3xtf32", "tf32"])
