@@ -288,10 +288,11 @@ def run_ours(args):
 
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    from paper_2604_02130_gb300 import api, force_flops
+    from paper_2604_02130_gb300 import api, force_flops, shard
 
     dev = torch.device("cuda", local)
-    probs = fi.workload(name, batch=w_batch, first=rank * w_batch)
+    mine = shard.shard_range(rank, w_batch)  # disjoint configuration indices per rank
+    probs = fi.workload(name, batch=w_batch, first=mine.start)
     nx, nt, ns = probs[0].nx, probs[0].nt, probs[0].n_stab
     # inputs resident on the device: one phi buffer for the batch; E, E^{-1} shared
     phi_host = torch.from_numpy(np.stack([p.phi for p in probs])).pin_memory()
@@ -318,11 +319,7 @@ def run_ours(args):
         return b
 
     def allmax(x):
-        if ws > 1:
-            t = torch.tensor([x], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            return float(t.item())
-        return x
+        return shard.max_over_ranks(x, dev)
 
     n_total = w_batch * ws
     fl = force_flops(nx, nt, ns)
@@ -334,7 +331,7 @@ def run_ours(args):
     plan = batch.plan()
     head = _time_batch(batch, ctx, args.steps, flush, stream, barrier, True, local)
     total_ms = allmax(head["total_ms"])
-    value = n_total * args.steps / (total_ms * 1e-3)
+    value = shard.aggregate_rate(w_batch, ws, args.steps, total_ms)
 
     # ---- end to end through the public API: pinned host inputs in, results out
     ld_host = torch.empty((w_batch, 2), dtype=torch.float64).pin_memory()

@@ -121,6 +121,37 @@ int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch);
 /* Number of kernel launches the last fd_logdet/fd_green/fd_force call issued. */
 int fd_last_launch_count(const fd_ctx* ctx);
 
+/* Autotuner.  fd_tune times every size class of this batch with 128 and 256 threads per CTA
+ * (`reps` timed runs each after a warm-up, FP64 or mixed as `prec` says) and keeps the faster
+ * choice in the context's plan cache, which later plans (calls, graphs, fd_plan_query) use.
+ * Synchronous; allocates and frees its own trial outputs.
+ * fd_tune_nstab picks, for one configuration, the largest QR interval among `candidates`
+ * (each must divide nt) whose log det at precision `prec` stays within `rel_budget`
+ * (|d Re|, |d Im mod 2pi| over max(1, |logdet|)) of an FP64 run with the smallest candidate;
+ * *best = 0 if none does.  The Section 9 proposal of stabilising every beta_0/delta slices with
+ * beta_0 ~ 10 is the regime this explores.  Synchronous.
+ * fd_tune_save / fd_tune_load write / read the plan cache as a JSON list (one object per size
+ * class: gpu, kind, mixed, three, nx, threads); load returns the number of entries read. */
+int fd_tune(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec, int reps);
+int fd_tune_nstab(fd_ctx* ctx, const fd_problem* prob, const int* candidates, int ncand,
+                  double rel_budget, int prec, int* best);
+int fd_tune_save(fd_ctx* ctx, const char* path);
+int fd_tune_load(fd_ctx* ctx, const char* path);
+
+/* CUDA-graph batching.  fd_graph_create plans the call fd_force (F != NULL) or fd_green /
+ * fd_logdet (F == NULL; G may be NULL) would make for this batch, gives it its own descriptor
+ * table, queues, status words and scratch, and captures it -- the queue/status resets and one
+ * persistent kernel per size class, the classes as parallel branches -- into an executable
+ * graph.  fd_graph_launch replays it on `stream`: one cudaGraphLaunch, no host work.  Every
+ * replay reads the inputs and writes the outputs through the pointers given at creation, so
+ * callers update phi (and E) in place between replays.  fd_status after a replay reports that
+ * replay.  fd_graph_destroy synchronises the device and frees the graph's memory.
+ * The graph owns its memory; it stays valid across other calls on the context. */
+int fd_graph_create(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet,
+                    double* const* G, double* const* F, int prec, void** graph);
+int fd_graph_launch(fd_ctx* ctx, void* graph, void* stream);
+int fd_graph_destroy(fd_ctx* ctx, void* graph);
+
 /* The launch plan a call with these arguments would use, without launching anything: one
  * record of 8 ints per launch (size class) in info[8*g .. 8*g+7]:
  *   nx, kernel (0 FP64 log det/G, 1 FP64 force, 2 mixed log det/G, 3 mixed force),

@@ -60,6 +60,14 @@ SIGNATURES = [
     ("fd_last_kernel_ms", _I, [_VP, ctypes.POINTER(ctypes.c_double), _I]),
     ("fd_logdet_noalloc", _I, [_I, _PP, _VP, _VP, _VP, _VP]),
     ("fd_plan_query", _I, [_VP, _I, _PP, _I, _I, ctypes.POINTER(_I), _I]),
+    ("fd_graph_create", _I, [_VP, _I, _PP, _VP, _VP, _VP, _I, ctypes.POINTER(_VP)]),
+    ("fd_graph_launch", _I, [_VP, _VP, _VP]),
+    ("fd_graph_destroy", _I, [_VP, _VP]),
+    ("fd_tune", _I, [_VP, _I, _PP, _I, _I, _I]),
+    ("fd_tune_nstab", _I, [_VP, _PP, ctypes.POINTER(_I), _I, ctypes.c_double, _I,
+                           ctypes.POINTER(_I)]),
+    ("fd_tune_save", _I, [_VP, ctypes.c_char_p]),
+    ("fd_tune_load", _I, [_VP, ctypes.c_char_p]),
 ]
 
 _lib = None

@@ -76,6 +76,27 @@ class Context:
             self.check(n)
         return [arr[i] for i in range(n)]
 
+    def tune_nstab(self, problem: Tuple, candidates: Sequence[int], rel_budget: float,
+                   prec: str = "3xtf32") -> int:
+        """Largest QR interval among candidates within rel_budget of FP64 (fd_tune_nstab)."""
+        E, Einv, phi, _ = problem
+        p = L.fd_problem(phi.shape[1], phi.shape[0], int(candidates[0]), 0, E.data_ptr(),
+                         Einv.data_ptr() if Einv is not None else None, phi.data_ptr())
+        cand = (ctypes.c_int * len(candidates))(*candidates)
+        best = ctypes.c_int()
+        self.check(self.lib.fd_tune_nstab(self.h, ctypes.byref(p), cand, len(candidates),
+                                          rel_budget, L.PRECISIONS[prec], ctypes.byref(best)))
+        return best.value
+
+    def tune_save(self, path: str):
+        self.check(self.lib.fd_tune_save(self.h, path.encode()))
+
+    def tune_load(self, path: str) -> int:
+        n = self.lib.fd_tune_load(self.h, path.encode())
+        if n < 0:
+            self.check(n)
+        return n
+
     def measure_fp64_peak(self) -> float:
         g = ctypes.c_double()
         self.check(self.lib.fd_measure_fp64_peak(self.h, ctypes.byref(g)))
@@ -171,6 +192,51 @@ class Batch:
 
     def status(self, stream=None) -> List[int]:
         return self.ctx.status(self.n, stream)
+
+    def tune(self, reps: int = 2):
+        """Time 128 vs 256 threads per CTA for every size class of this batch (fd_tune)."""
+        what = {"logdet": 1, "green": 3, "force": 5, "force+green": 7}[self.want]
+        self.ctx.check(self.ctx.lib.fd_tune(self.ctx.h, self.n, self.problems, what, self.prec,
+                                            reps))
+
+    def graph(self) -> "BatchGraph":
+        """Capture this batch's call into a CUDA graph (fd_graph_create)."""
+        return BatchGraph(self)
+
+
+class BatchGraph:
+    """A captured fd_* call over a Batch; launch() replays it with one cudaGraphLaunch.
+    Inputs are read and outputs written through the Batch's tensors (update phi in place)."""
+
+    def __init__(self, batch: Batch):
+        self.batch = batch
+        ctx = batch.ctx
+        h = ctypes.c_void_p()
+        ld = ctypes.c_void_p(batch.logdet_buf.data_ptr())
+        F = batch._Fp if batch.want.startswith("force") else None
+        ctx.check(ctx.lib.fd_graph_create(ctx.h, batch.n, batch.problems, ld, batch._Gp, F,
+                                          batch.prec, ctypes.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None) -> Result:
+        ctx = self.batch.ctx
+        ctx.check(ctx.lib.fd_graph_launch(ctx.h, self.h, _stream_ptr(stream)))
+        b = self.batch
+        return Result(torch.view_as_complex(b.logdet_buf), b.G, b.F)
+
+    def status(self, stream=None) -> List[int]:
+        return self.batch.ctx.status(self.batch.n, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.batch.ctx.lib.fd_graph_destroy(self.batch.ctx.h, self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _default_ctx: Optional[Context] = None

@@ -1,6 +1,7 @@
 // fd_api.cu -- host runtime behind the C ABI of include/fd.h: context, validation, planning
 // (size classes, shared-memory placement, cost-sorted persistent queues), workspace and launches.
 #include <algorithm>
+#include <map>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -30,6 +31,13 @@ struct fd_ctx {
   int last_batch = 0;
   int last_launches = 0;
   int smem_attr = 0;
+  // side streams and events for concurrent size classes
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  int* last_status = nullptr;  // status array of the last graph launch (null: ctx's own)
+  // autotuner plan cache: (kind, mixed, three, nx) -> threads per CTA
+  std::map<long long, int> tuned;
   // optional per-launch timing (events around every kernel launch of a call)
   bool timing = false;
   std::vector<cudaEvent_t> ev;  // pairs (start, stop)
@@ -110,6 +118,10 @@ int resident_ctas(fd_ctx* ctx, bool mixed, bool force, int nthreads, int smem_by
   // those kernels use the direct count, bounded by the TMEM columns by the caller.
   if (api <= 0 || mixed) return manual;
   return std::max(1, std::min(api, manual));
+}
+
+long long tune_key(int kind, int mixed, int three, int nx) {
+  return ((long long)kind << 40) | ((long long)mixed << 36) | ((long long)three << 32) | nx;
 }
 
 // Greedy placement: the buffers touched every slice first, then the per-block ones.
@@ -335,11 +347,18 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
     int max_nb = 0;
     for (int c : g.idx) max_nb = std::max(max_nb, probs[c].nt / probs[c].n_stab);
     min_ns = 1;
-    const int n = g.nx, nth = threads_for(n);
+    const int n = g.nx;
+    int nth = threads_for(n);
+    {
+      auto it = ctx->tuned.find(tune_key(kind, 0, 0, n));
+      if (it != ctx->tuned.end()) nth = it->second;
+    }
     g.mixed = 0;
     if (prec != FD_PREC_FP64) {
-      fd::MLayout M = plan_mixed(n, kind, prec == FD_PREC_MIXED_3XTF32, ctx->max_smem_optin,
-                                 ctx->smem_per_sm, max_nb);
+      const bool three = prec == FD_PREC_MIXED_3XTF32;
+      fd::MLayout M = plan_mixed(n, kind, three, ctx->max_smem_optin, ctx->smem_per_sm, max_nb);
+      auto it = ctx->tuned.find(tune_key(kind, 1, three ? 1 : 0, n));
+      if (it != ctx->tuned.end()) M.nthreads = it->second;
       if (M.smem_bytes > 0) {
         g.mixed = 1;
         g.ML = M;
@@ -421,23 +440,8 @@ size_t scratch_need(std::vector<Group>& groups) {
   return off;
 }
 
-int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
-        double* const* F, int prec, void* stream_, int kind) {
-  cudaStream_t stream = (cudaStream_t)stream_;
-  ctx->last_launches = 0;
-  ctx->last_batch = batch;
-  if (batch == 0) return FD_OK;
-  FD_CUDA(ctx, cudaSetDevice(ctx->device));
-  // Mixed precision applies to the size classes that fit the tensor-core kernels (nx <= 128 and
-  // its operands in shared memory); larger classes run the FP64 kernels (fd_plan_query says so).
-  std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
-  size_t need = scratch_need(groups);
-  int rc = ensure(ctx, (size_t)batch, (size_t)batch, groups.size(), need);
-  if (rc != FD_OK) return rc;
-  if (ctx->staging_pending) {
-    FD_CUDA(ctx, cudaEventSynchronize(ctx->staging_done));
-    ctx->staging_pending = false;
-  }
+void build_descs(std::vector<Group>& groups, const fd_problem* probs, double* logdet,
+                 double* const* G, double* const* F, Desc* out) {
   size_t k = 0;
   for (auto& g : groups) {
     g.desc_off = k;
@@ -454,16 +458,33 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double*
       d.logdet = logdet + 2 * (size_t)c;
       d.G = G ? (double2*)G[c] : nullptr;
       d.F = F ? (double2*)F[c] : nullptr;
-      ctx->h_desc[k++] = d;
+      out[k++] = d;
     }
   }
-  FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(Desc) * batch,
-                               cudaMemcpyHostToDevice, stream));
-  FD_CUDA(ctx, cudaEventRecord(ctx->staging_done, stream));
-  ctx->staging_pending = true;
-  FD_CUDA(ctx, cudaMemsetAsync(ctx->d_queue, 0, sizeof(int) * groups.size(), stream));
-  FD_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0xFF, sizeof(int) * batch, stream));  // pending
-  if (ctx->timing) {
+}
+
+// Side streams for running several size classes concurrently (fork/join with events; the same
+// pattern is recorded into CUDA graphs as parallel branches).
+int ensure_side(fd_ctx* ctx, size_t n) {
+  while (ctx->side.size() < n) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    FD_CUDA(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    FD_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->side.push_back(s);
+    ctx->join.push_back(e);
+  }
+  if (!ctx->fork) FD_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
+  return FD_OK;
+}
+
+// Enqueue one call: reset the queues and the status words, then one persistent kernel per size
+// class -- on `stream` itself for a single class, else forked onto side streams and joined back.
+int enqueue(fd_ctx* ctx, std::vector<Group>& groups, int kind, Desc* d_desc, int* d_queue,
+            int* d_status, char* scratch, int batch, cudaStream_t stream, bool timing) {
+  FD_CUDA(ctx, cudaMemsetAsync(d_queue, 0, sizeof(int) * groups.size(), stream));
+  FD_CUDA(ctx, cudaMemsetAsync(d_status, 0xFF, sizeof(int) * batch, stream));  // pending
+  if (timing) {
     while (ctx->ev.size() < 2 * groups.size()) {
       cudaEvent_t e;
       FD_CUDA(ctx, cudaEventCreate(&e));
@@ -471,31 +492,93 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double*
     }
     ctx->ev_used = 2 * (int)groups.size();
   }
+  const bool fork = groups.size() > 1;
+  const size_t nside = std::min<size_t>(groups.size(), 8);
+  if (fork) {
+    int rc = ensure_side(ctx, nside);
+    if (rc != FD_OK) return rc;
+    FD_CUDA(ctx, cudaEventRecord(ctx->fork, stream));
+    for (size_t i = 0; i < nside; ++i) FD_CUDA(ctx, cudaStreamWaitEvent(ctx->side[i], ctx->fork, 0));
+  }
   for (size_t gi = 0; gi < groups.size(); ++gi) {
     Group& g = groups[gi];
-    if (g.L.smem_bytes > ctx->smem_attr) {
-      FD_CUDA(ctx, fd::set_smem_fp64(ctx->max_smem_optin));
-      ctx->smem_attr = ctx->max_smem_optin;
-    }
-    if (ctx->timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * gi], stream));
+    cudaStream_t s = fork ? ctx->side[gi % nside] : stream;
+    if (timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * gi], s));
     if (g.mixed && kind == K_FORCE)
-      fd::launch_force_mixed(ctx->d_desc + g.desc_off, (int)g.idx.size(), ctx->d_queue + gi,
-                             ctx->d_status, ctx->scratch + g.scratch_off, g.ML, g.grid, stream);
+      fd::launch_force_mixed(d_desc + g.desc_off, (int)g.idx.size(), d_queue + gi, d_status,
+                             scratch + g.scratch_off, g.ML, g.grid, s);
     else if (g.mixed)
-      fd::launch_fwd_mixed(ctx->d_desc + g.desc_off, (int)g.idx.size(), ctx->d_queue + gi,
-                           ctx->d_status, ctx->scratch + g.scratch_off, g.ML, g.grid, stream);
+      fd::launch_fwd_mixed(d_desc + g.desc_off, (int)g.idx.size(), d_queue + gi, d_status,
+                           scratch + g.scratch_off, g.ML, g.grid, s);
     else if (kind == K_FWD)
-      fd::launch_fwd_fp64(ctx->d_desc + g.desc_off, (int)g.idx.size(), ctx->d_queue + gi,
-                          ctx->d_status, ctx->scratch + g.scratch_off, g.L, g.grid, stream);
+      fd::launch_fwd_fp64(d_desc + g.desc_off, (int)g.idx.size(), d_queue + gi, d_status,
+                          scratch + g.scratch_off, g.L, g.grid, s);
     else
-      fd::launch_force_fp64(ctx->d_desc + g.desc_off, (int)g.idx.size(), ctx->d_queue + gi,
-                            ctx->d_status, ctx->scratch + g.scratch_off, g.L, g.grid, stream);
+      fd::launch_force_fp64(d_desc + g.desc_off, (int)g.idx.size(), d_queue + gi, d_status,
+                            scratch + g.scratch_off, g.L, g.grid, s);
     ctx->last_launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
-    if (ctx->timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * gi + 1], stream));
+    if (timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * gi + 1], s));
+  }
+  if (fork) {
+    for (size_t i = 0; i < nside; ++i) {
+      FD_CUDA(ctx, cudaEventRecord(ctx->join[i], ctx->side[i]));
+      FD_CUDA(ctx, cudaStreamWaitEvent(stream, ctx->join[i], 0));
+    }
   }
   return FD_OK;
+}
+
+int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
+        double* const* F, int prec, void* stream_, int kind) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  ctx->last_launches = 0;
+  ctx->last_batch = batch;
+  ctx->last_status = nullptr;
+  if (batch == 0) return FD_OK;
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  // Mixed precision applies to the size classes that fit the tensor-core kernels (nx <= 128 and
+  // its operands in shared memory); larger classes run the FP64 kernels (fd_plan_query says so).
+  std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
+  size_t need = scratch_need(groups);
+  int rc = ensure(ctx, (size_t)batch, (size_t)batch, groups.size(), need);
+  if (rc != FD_OK) return rc;
+  if (ctx->staging_pending) {
+    FD_CUDA(ctx, cudaEventSynchronize(ctx->staging_done));
+    ctx->staging_pending = false;
+  }
+  build_descs(groups, probs, logdet, G, F, ctx->h_desc);
+  FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(Desc) * batch,
+                               cudaMemcpyHostToDevice, stream));
+  FD_CUDA(ctx, cudaEventRecord(ctx->staging_done, stream));
+  ctx->staging_pending = true;
+  return enqueue(ctx, groups, kind, ctx->d_desc, ctx->d_queue, ctx->d_status, ctx->scratch,
+                 batch, stream, ctx->timing);
+}
+
+// A captured call: its own descriptor table, queues, status words and scratch (so later calls
+// on the context cannot move memory the graph uses), replayed with one cudaGraphLaunch.
+struct GraphObj {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  Desc* d_desc = nullptr;
+  int* d_queue = nullptr;
+  int* d_status = nullptr;
+  char* scratch = nullptr;
+  int batch = 0;
+  int launches = 0;
+};
+
+void graph_free(GraphObj* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->d_desc) cudaFree(g->d_desc);
+  if (g->d_queue) cudaFree(g->d_queue);
+  if (g->d_status) cudaFree(g->d_status);
+  if (g->scratch) cudaFree(g->scratch);
+  delete g;
 }
 
 }  // namespace
@@ -537,6 +620,9 @@ void fd_ctx_destroy(fd_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
   for (auto e : ctx->ev) cudaEventDestroy(e);
+  for (auto s : ctx->side) cudaStreamDestroy(s);
+  for (auto e : ctx->join) cudaEventDestroy(e);
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
   delete ctx;
 }
 
@@ -598,7 +684,8 @@ int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch) {
   FD_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));
   if (batch == 0) return FD_OK;
   std::vector<int> st(batch);
-  FD_CUDA(ctx, cudaMemcpy(st.data(), ctx->d_status, sizeof(int) * batch, cudaMemcpyDeviceToHost));
+  FD_CUDA(ctx, cudaMemcpy(st.data(), ctx->last_status ? ctx->last_status : ctx->d_status,
+                          sizeof(int) * batch, cudaMemcpyDeviceToHost));
   int worst = FD_OK;
   for (int c = 0; c < batch; ++c) {
     int code = st[c] == fd::ST_OK ? FD_OK
@@ -611,6 +698,242 @@ int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch) {
 }
 
 int fd_last_launch_count(const fd_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+int fd_graph_create(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet,
+                    double* const* G, double* const* F, int prec, void** graph) {
+  if (!graph) return fail(ctx, FD_ERR_INVALID, "null graph handle");
+  *graph = nullptr;
+  const bool force = F != nullptr;
+  int rc = validate(ctx, batch, probs, logdet, prec, force);
+  if (rc != FD_OK) return rc;
+  if (batch < 1) return fail(ctx, FD_ERR_INVALID, "a graph needs batch >= 1");
+  for (int c = 0; c < batch; ++c)
+    if ((G && !G[c]) || (F && !F[c])) return fail(ctx, FD_ERR_INVALID, "config %d: null output", c);
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int kind = force ? K_FORCE : K_FWD;
+  std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
+  GraphObj* g = new GraphObj();
+  g->batch = batch;
+  std::vector<Desc> h(batch);
+  build_descs(groups, probs, logdet, G, F, h.data());
+  size_t need = scratch_need(groups);
+  cudaStream_t cs = nullptr;
+  int saved_launches = ctx->last_launches;
+  auto bail = [&](int code) {
+    if (cs) cudaStreamDestroy(cs);
+    graph_free(g);
+    ctx->last_launches = saved_launches;
+    return code;
+  };
+#define FD_G(call)                                                do {                                                              cudaError_t e_ = (call);                                        if (e_ != cudaSuccess) return bail(cuda_fail(ctx, e_, #call));   } while (0)
+  FD_G(cudaMalloc(&g->d_desc, sizeof(Desc) * batch));
+  FD_G(cudaMalloc(&g->d_queue, sizeof(int) * groups.size()));
+  FD_G(cudaMalloc(&g->d_status, sizeof(int) * batch));
+  FD_G(cudaMalloc(&g->scratch, std::max<size_t>(need, 256)));
+  FD_G(cudaMemcpy(g->d_desc, h.data(), sizeof(Desc) * batch, cudaMemcpyHostToDevice));
+  FD_G(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  rc = ensure_side(ctx, std::min<size_t>(groups.size(), 8));
+  if (rc != FD_OK) return bail(rc);
+  FD_G(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  ctx->last_launches = 0;
+  rc = enqueue(ctx, groups, kind, g->d_desc, g->d_queue, g->d_status, g->scratch, batch, cs, false);
+  cudaGraph_t captured = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+  g->graph = captured;
+  if (rc != FD_OK) return bail(rc);
+  if (ce != cudaSuccess) return bail(cuda_fail(ctx, ce, "cudaStreamEndCapture"));
+  g->launches = ctx->last_launches;
+  FD_G(cudaGraphInstantiate(&g->exec, g->graph, 0));
+  cudaStreamDestroy(cs);
+  cs = nullptr;
+#undef FD_G
+  ctx->last_launches = saved_launches;
+  *graph = g;
+  return FD_OK;
+}
+
+int fd_graph_launch(fd_ctx* ctx, void* graph, void* stream) {
+  if (!ctx || !graph) return FD_ERR_INVALID;
+  GraphObj* g = (GraphObj*)graph;
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  FD_CUDA(ctx, cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+  ctx->last_batch = g->batch;
+  ctx->last_launches = g->launches;
+  ctx->last_status = g->d_status;
+  return FD_OK;
+}
+
+int fd_graph_destroy(fd_ctx* ctx, void* graph) {
+  if (!ctx) return FD_ERR_INVALID;
+  if (!graph) return FD_OK;
+  GraphObj* g = (GraphObj*)graph;
+  if (ctx->last_status == g->d_status) ctx->last_status = nullptr;
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  FD_CUDA(ctx, cudaDeviceSynchronize());
+  graph_free(g);
+  return FD_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+int fd_tune(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec, int reps) {
+  double dummy;
+  const bool force = (what & FD_WANT_FORCE) != 0;
+  int rc = validate(ctx, batch, probs, &dummy, prec, force);
+  if (rc != FD_OK) return rc;
+  if (batch == 0) return FD_OK;
+  if (reps < 1) reps = 2;
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int kind = force ? K_FORCE : K_FWD;
+  // outputs for the trial runs
+  size_t g_elems = 0, f_elems = 0;
+  for (int c = 0; c < batch; ++c) {
+    g_elems += (size_t)probs[c].nx * probs[c].nx;
+    f_elems += (size_t)probs[c].nt * probs[c].nx;
+  }
+  double *d_ld = nullptr, *d_g = nullptr, *d_f = nullptr;
+  FD_CUDA(ctx, cudaMalloc(&d_ld, sizeof(double) * 2 * batch));
+  FD_CUDA(ctx, cudaMalloc(&d_g, sizeof(double) * 2 * g_elems));
+  if (force) FD_CUDA(ctx, cudaMalloc(&d_f, sizeof(double) * 2 * f_elems));
+  std::vector<double*> Gp(batch), Fp(batch);
+  size_t og = 0, of = 0;
+  for (int c = 0; c < batch; ++c) {
+    Gp[c] = d_g + 2 * og;
+    og += (size_t)probs[c].nx * probs[c].nx;
+    Fp[c] = force ? d_f + 2 * of : nullptr;
+    of += (size_t)probs[c].nt * probs[c].nx;
+  }
+  std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int result = FD_OK;
+  for (auto& g : groups) {
+    std::vector<fd_problem> sub;
+    std::vector<double*> sg, sf;
+    for (int c : g.idx) {
+      sub.push_back(probs[c]);
+      sg.push_back(Gp[c]);
+      sf.push_back(Fp[c]);
+    }
+    const int three = prec == FD_PREC_MIXED_3XTF32 ? 1 : 0;
+    const long long key = tune_key(kind, g.mixed, g.mixed ? three : 0, g.nx);
+    float best = 1e30f;
+    int best_t = 0;
+    for (int nth : {128, 256}) {
+      ctx->tuned[key] = nth;
+      float tot = 0.f;
+      for (int r = 0; r <= reps; ++r) {  // first run is a warm-up
+        cudaEventRecord(e0, 0);
+        int rr = run(ctx, (int)sub.size(), sub.data(), d_ld, sg.data(), force ? sf.data() : nullptr,
+                     prec, nullptr, kind);
+        cudaEventRecord(e1, 0);
+        if (rr != FD_OK) { result = rr; break; }
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) tot += ms;
+      }
+      if (result != FD_OK) break;
+      if (tot < best) {
+        best = tot;
+        best_t = nth;
+      }
+    }
+    if (result != FD_OK) break;
+    ctx->tuned[key] = best_t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaDeviceSynchronize();
+  cudaFree(d_ld);
+  cudaFree(d_g);
+  if (d_f) cudaFree(d_f);
+  return result;
+}
+
+int fd_tune_nstab(fd_ctx* ctx, const fd_problem* prob, const int* candidates, int ncand,
+                  double rel_budget, int prec, int* best) {
+  if (!ctx || !prob || !candidates || ncand < 1 || !best) return FD_ERR_INVALID;
+  *best = 0;
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  int nmin = 1 << 30;
+  for (int i = 0; i < ncand; ++i) {
+    if (candidates[i] < 1 || prob->nt % candidates[i] != 0)
+      return fail(ctx, FD_ERR_INVALID, "candidate n_stab=%d does not divide nt=%d",
+                  candidates[i], prob->nt);
+    nmin = std::min(nmin, candidates[i]);
+  }
+  double* d_ld = nullptr;
+  FD_CUDA(ctx, cudaMalloc(&d_ld, sizeof(double) * 2));
+  // reference: FP64 with the smallest candidate interval
+  fd_problem p = *prob;
+  p.n_stab = nmin;
+  int rc = run(ctx, 1, &p, d_ld, nullptr, nullptr, FD_PREC_FP64, nullptr, K_FWD);
+  double ref[2] = {0, 0};
+  if (rc == FD_OK) {
+    cudaDeviceSynchronize();
+    cudaMemcpy(ref, d_ld, sizeof(ref), cudaMemcpyDeviceToHost);
+  }
+  int chosen = 0;
+  for (int i = 0; i < ncand && rc == FD_OK; ++i) {
+    p.n_stab = candidates[i];
+    rc = run(ctx, 1, &p, d_ld, nullptr, nullptr, prec, nullptr, K_FWD);
+    if (rc != FD_OK) break;
+    double got[2];
+    cudaDeviceSynchronize();
+    cudaMemcpy(got, d_ld, sizeof(got), cudaMemcpyDeviceToHost);
+    double dre = fabs(got[0] - ref[0]);
+    double dim = fabs(remainder(got[1] - ref[1], 2.0 * 3.14159265358979323846));
+    double scale = std::max(1.0, hypot(ref[0], ref[1]));
+    if (std::max(dre, dim) / scale <= rel_budget && candidates[i] > chosen) chosen = candidates[i];
+  }
+  cudaFree(d_ld);
+  if (rc != FD_OK) return rc;
+  *best = chosen;
+  return FD_OK;
+}
+
+int fd_tune_save(fd_ctx* ctx, const char* path) {
+  if (!ctx || !path) return FD_ERR_INVALID;
+  FILE* f = fopen(path, "w");
+  if (!f) return fail(ctx, FD_ERR_INVALID, "cannot write %s", path);
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, ctx->device);
+  fprintf(f, "[\n");
+  size_t i = 0;
+  for (auto& kv : ctx->tuned) {
+    long long k = kv.first;
+    fprintf(f, "  {\"gpu\": \"%s\", \"kind\": %lld, \"mixed\": %lld, \"three\": %lld, "
+               "\"nx\": %lld, \"threads\": %d}%s\n",
+            prop.name, (k >> 40) & 0xff, (k >> 36) & 0xf, (k >> 32) & 0xf, k & 0xffffffffLL,
+            kv.second, ++i < ctx->tuned.size() ? "," : "");
+  }
+  fprintf(f, "]\n");
+  fclose(f);
+  return FD_OK;
+}
+
+int fd_tune_load(fd_ctx* ctx, const char* path) {
+  if (!ctx || !path) return FD_ERR_INVALID;
+  FILE* f = fopen(path, "r");
+  if (!f) return fail(ctx, FD_ERR_INVALID, "cannot read %s", path);
+  char line[512];
+  int loaded = 0;
+  while (fgets(line, sizeof(line), f)) {
+    long long kind, mixed, three, nx;
+    int threads;
+    const char* q = strstr(line, "\"kind\"");
+    if (!q) continue;
+    if (sscanf(q, "\"kind\": %lld, \"mixed\": %lld, \"three\": %lld, \"nx\": %lld, "
+                  "\"threads\": %d", &kind, &mixed, &three, &nx, &threads) == 5 &&
+        (threads == 128 || threads == 256)) {
+      ctx->tuned[tune_key((int)kind, (int)mixed, (int)three, (int)nx)] = threads;
+      ++loaded;
+    }
+  }
+  fclose(f);
+  return loaded;
+}
 
 int fd_plan_query(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec, int* info,
                   int max_groups) {

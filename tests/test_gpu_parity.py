@@ -275,3 +275,73 @@ def test_mixed_force(ctx, prec, L, nt, beta, U, n_stab):
         ref_F = oforce.force(p.E, p.phi, n_stab)
         scale = max(1.0, float(np.abs(ref_F).max())) ** 2
         assert float(np.abs(F[c] - ref_F).max()) / scale <= tol["F_scaled"]
+
+
+# ------------------------------------------------------------------ graphs and uneven batches
+def _uneven_small(seed=1004):
+    # every honeycomb size of the uneven workload (Nx = 8 ... 288), short Nt, delta = 1/16
+    probs = []
+    shapes = [(2, 64), (3, 32), (4, 64), (5, 32), (6, 32), (7, 16), (8, 16), (12, 16),
+              (2, 128), (3, 64), (4, 32), (6, 64)]
+    for c, (L, nt) in enumerate(shapes):
+        probs.append(fi.make_problem(L, nt, nt / 16.0, 3.0, min(16, nt), seed, c))
+    return probs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32"])
+def test_uneven_graph_replay(ctx, prec):
+    """An uneven batch captured into one CUDA graph; two replays with a field update between."""
+    from paper_2604_02130_gb300 import api
+
+    probs = _uneven_small()
+    tens = to_dev(probs)
+    b = api.Batch(ctx, tens, "force+green", prec)
+    g = b.graph()
+    for rep in range(2):
+        if rep == 1:  # update the fields in place and replay
+            for p, t in zip(probs, tens):
+                p.phi = p.phi[::-1].copy()
+                t[2].copy_(torch.from_numpy(p.phi))
+        g.launch()
+        torch.cuda.synchronize()
+        assert all(s == 0 for s in g.status())
+        for c, p in enumerate(probs):
+            ref_ld, ref_G = stable.logdet_green(p.E, p.phi, p.n_stab)
+            got = complex(b.logdet_buf[c, 0].item(), b.logdet_buf[c, 1].item())
+            Gc = b.G[c].cpu().numpy()
+            if prec == "fp64" or p.nx > 128:
+                assert logdet_err(got, ref_ld) <= LOGDET_RTOL_FP64
+                assert np.abs(Gc - ref_G).max() <= G_ATOL_FP64
+            else:
+                tol = MIXED_TOL[prec]
+                assert logdet_err(got, ref_ld) * max(1.0, abs(ref_ld)) / abs(ref_ld) \
+                    <= tol["logdet_rel"]
+                assert g_scaled_err(Gc, ref_G) <= tol["G_scaled"]
+            rows = [0, p.nt - 1]
+            ref = oforce.force_rows(p.E, p.phi, p.n_stab, rows)
+            Fc = b.F[c].cpu().numpy()
+            for r in rows:
+                if prec == "fp64" or p.nx > 128:
+                    assert np.abs(Fc[r] - ref[r]).max() <= F_ATOL_FP64
+                else:
+                    scale = max(1.0, float(np.abs(ref[r]).max())) ** 2
+                    assert float(np.abs(Fc[r] - ref[r]).max()) / scale <= MIXED_TOL[prec]["F_scaled"]
+    g.close()
+
+
+def test_graph_matches_direct_call(ctx):
+    from paper_2604_02130_gb300 import api
+
+    probs = fi.workload("batch18", batch=40)
+    tens = to_dev(probs)
+    direct = api.Batch(ctx, tens, "force", "3xtf32").run()
+    torch.cuda.synchronize()
+    ld0 = direct.logdet.clone()
+    F0 = [f.clone() for f in direct.F]
+    b = api.Batch(ctx, tens, "force", "3xtf32")
+    g = b.graph()
+    g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(b.logdet_buf.view(-1, 2), torch.view_as_real(ld0))
+    assert all(torch.equal(a, c) for a, c in zip(b.F, F0))
+    g.close()

@@ -1,0 +1,53 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks shard the workload's configurations
+(disjoint, covering), take the max of their times and aggregate the rate like bench.py does."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+
+    import fd_inputs as fi
+    from paper_2604_02130_gb300 import shard
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    per = 6
+    idx = list(shard.shard_range(rank, per))
+    probs = fi.workload("batch18", batch=per, first=idx[0])
+    # the first field value of every configuration identifies it
+    mine = torch.tensor([p.phi[0, 0] for p in probs], dtype=torch.float64)
+    gathered = [torch.zeros(per, dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(gathered, mine)
+    t = shard.max_over_ranks(10.0 + rank)
+    rate = shard.aggregate_rate(per, world, steps=3, max_ms=t)
+    if rank == 0:
+        out.put((torch.cat(gathered).numpy(), t, rate))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_shards_are_disjoint_and_time_is_max():
+    import multiprocessing as mp
+
+    import fd_inputs as fi
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + (os.getpid() % 1000)
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    firsts, t, rate = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    ref = np.array([p.phi[0, 0] for p in fi.workload("batch18", batch=12)])
+    assert np.array_equal(firsts, ref)          # rank 0 took 0..5, rank 1 took 6..11
+    assert t == 11.0                            # max over ranks
+    assert abs(rate - 12 * 3 / 11e-3) < 1e-9    # all configurations over the slowest rank
