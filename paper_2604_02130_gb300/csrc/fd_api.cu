@@ -361,6 +361,7 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       if (it != ctx->tuned.end()) M.nthreads = it->second;
       if (M.smem_bytes > 0) {
         g.mixed = 1;
+        M.num_sms = ctx->num_sms;
         g.ML = M;
         memset(&g.L, 0, sizeof(g.L));
         int occ = resident_ctas(ctx, true, kind == K_FORCE, M.nthreads, M.smem_bytes);
@@ -382,6 +383,7 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
     else
       budget = ctx->max_smem_optin;
     g.L = plan_layout(n, kind, budget, nth, max_nb, min_ns);
+    g.L.num_sms = ctx->num_sms;
     int occ = resident_ctas(ctx, false, kind == K_FORCE, nth, g.L.smem_bytes);
     g.occ = occ;
     g.grid = std::min<int>((int)g.idx.size(), ctx->num_sms * occ);

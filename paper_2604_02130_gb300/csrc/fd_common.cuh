@@ -27,6 +27,10 @@ __device__ __forceinline__ double abs2(cplx a) { return fma(a.re, a.re, a.im * a
 __device__ __forceinline__ cplx cmulc(cplx a, cplx b) {
   return cplx{fma(a.re, b.re, a.im * b.im), fma(a.re, b.im, -a.im * b.re)};
 }
+// a - b c with four fused multiply-adds
+__device__ __forceinline__ cplx cfms(cplx a, cplx b, cplx c) {
+  return cplx{fma(-b.re, c.re, fma(b.im, c.im, a.re)), fma(-b.re, c.im, fma(-b.im, c.re, a.im))};
+}
 __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
   // scaled division (Smith-free but overflow-safe enough for O(1)..1e150 magnitudes)
   double s = fmax(fabs(b.re), fabs(b.im));
@@ -73,6 +77,7 @@ enum Buf {
 
 struct Layout {
   int nthreads;
+  int num_sms;                 // SMs of the device (CTA wave index -> leader-warp offset)
   int smem_bytes;              // dynamic shared memory per CTA
   int small_off;               // offset (bytes, in smem) of the small-vector area
   int in_smem[B_NBUF];         // 1 = shared memory
@@ -91,6 +96,7 @@ __host__ __device__ __forceinline__ int small_bytes(int n) {
 // fd_tc.cuh: A = E (Np rows x Kp, TF32), B = the current product (2*Np rows: Re then Im, x Kp).
 struct MLayout {
   int nthreads;
+  int num_sms;
   int smem_bytes;
   int n, Np, Kp, N;      // N = 2*Np MMA columns; Kp = Np
   int tmem_cols;

@@ -190,6 +190,75 @@ __device__ __forceinline__ Small carve_small(char* base, int n) {
   return s;
 }
 
+// ---------------------------------------------------------------- fast FP64 reciprocal / rsqrt
+// The FP64 pipe of this GPU runs at 1/64 of the FP32 rate, so the serial steps of the QR and LU
+// use short sequences: an FP32 hardware estimate refined by two Newton-Raphson steps (quadratic
+// convergence: ~23 -> ~46 -> full 53 bits).  Arguments outside the FP32 normal range take the
+// plain IEEE operation.
+__device__ __forceinline__ double rcp64(double x) {
+  const float xf = (float)x;
+  const float af = fabsf(xf);
+  if (!(af > 1e-36f && af < 1e36f)) return 1.0 / x;
+  double r = (double)__frcp_rn(xf);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ double rsqrt64(double x) {
+  const float xf = (float)x;
+  if (!(xf > 1e-36f && xf < 1e36f)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf(xf);
+  const double h = 0.5 * x;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+__device__ __forceinline__ double sqrt64(double x) { return x > 0.0 ? x * rsqrt64(x) : 0.0; }
+
+// Natural log of a positive double as an FP32 ordering key: exponent from the bit pattern,
+// FP32 log of the mantissa in [1, 2).
+__device__ __forceinline__ float log_key(double a) {
+  const int hi = __double2hiint(a), lo = __double2loint(a);
+  const int ex = ((hi >> 20) & 0x7ff) - 1023;
+  const double m = __hiloint2double((hi & 0x800fffff) | 0x3ff00000, lo);
+  return logf((float)m) + 0.69314718f * (float)ex;
+}
+
+// Serial steps (a reflector, a pivot search) run on a "leader" warp that rotates with the step,
+// offset per CTA (s.misc[5]), so that the serial work of consecutive steps -- and of CTAs that
+// share an SM -- lands on different SM sub-partitions and their FP64 pipes.
+struct Small;
+__device__ __forceinline__ int leader_warp(int step, const int* misc) {
+  const int nw = nwarps();
+  return ((step + misc[5]) % nw + nw) % nw;
+}
+
+// Segment width W for `cols` independent column reductions over `rows` rows, chosen to minimise
+// the FP64 warp-instructions on the busiest SM sub-partition (the bound on this GPU):
+//   (column groups per sub-partition) x (8 per row-iteration + 2 per reduction level + 2).
+__device__ __forceinline__ int seg_width_cols(int rows, int cols) {
+  int best_w = 32, best_c = 1 << 30;
+  for (int W = 1, lg = 0; W <= 32; W <<= 1, ++lg) {
+    const int S = 32 / W;
+    const int warps = (cols + S - 1) / S;
+    const int per_sp = (warps + 3) / 4;
+    const int cost = per_sp * (8 * ((rows + W - 1) / W) + 2 * lg + 2);
+    if (cost < best_c || (cost == best_c && W > best_w)) {
+      best_c = cost;
+      best_w = W;
+    }
+  }
+  return best_w;
+}
+
+// Segment width for a reduction over `rows` rows: about four rows per lane, at most a warp.
+__device__ __forceinline__ int seg_width4(int rows) {
+  int w = 1;
+  while (w * 4 < rows && w < 32) w <<= 1;
+  return w;
+}
+
 // ---------------------------------------------------------------- Householder helpers
 // Reflector for column k of A (rows k..n-1), computed by one segment of W lanes (sl = lane in
 // segment, all 32 lanes of the warp call this; only the owning segment's results are stored).
@@ -210,9 +279,9 @@ __device__ __forceinline__ void seg_reflector(int n, int k, double2* A, int W, i
     }
     return;
   }
-  double ax = sqrt(abs2(x));
-  double nrm = sqrt(fma(ax, ax, sig));
-  if (nrm == 0.0) {  // exactly zero column: singular product
+  const double x2 = abs2(x);
+  const double n2 = x2 + sig;
+  if (!(n2 > 0.0)) {  // exactly zero column: singular product
     if (sl == 0) {
       s.tau[k] = 0.0;
       st(s.rdiag + k, cx(0, 0));
@@ -220,15 +289,68 @@ __device__ __forceinline__ void seg_reflector(int n, int k, double2* A, int W, i
     }
     return;
   }
-  cplx ph = ax > 0.0 ? cx(x.re / ax, x.im / ax) : cx(1.0, 0.0);
-  cplx alpha = cx(-ph.re * nrm, -ph.im * nrm);
-  cplx c = x - alpha;  // |c| = |x_k| + nrm >= nrm > 0
-  double c2 = abs2(c);
-  cplx cinv = cx(c.re / c2, -c.im / c2);
+  const double nrm = sqrt64(n2);
+  // alpha = -(x/|x|) nrm;  c = x - alpha = x (1 + nrm/|x|)  (c = nrm if x = 0)
+  cplx alpha, c;
+  if (x2 > 0.0) {
+    const double rx = rsqrt64(x2);  // 1/|x|
+    const double g = nrm * rx;
+    alpha = cx(-x.re * g, -x.im * g);
+    c = cx(x.re * (1.0 + g), x.im * (1.0 + g));
+  } else {
+    alpha = cx(-nrm, 0.0);
+    c = cx(nrm, 0.0);
+  }
+  const double c2 = abs2(c);
+  const double ic2 = rcp64(c2);
+  const cplx cinv = cx(c.re * ic2, -c.im * ic2);
   for (int i = k + 1 + sl; i < n; i += W) st(A + i + k * n, ld(A + i + k * n) * cinv);
   if (sl == 0) {
-    s.tau[k] = 2.0 / (1.0 + sig / c2);
+    s.tau[k] = 2.0 * rcp64(fma(sig, ic2, 1.0));
     st(s.rdiag + k, alpha);
+  }
+}
+
+// Apply H_k = I - tau v v^H (v_k = 1, v_i = A(i,k) below the diagonal) to columns j of A in
+// [j_begin, n), rows k..n-1.  Segments of W lanes own one column each; the segment owning
+// column k+1 (warp 0, first round) then builds the reflector of column k+1.
+__device__ __forceinline__ void householder_step(int n, int k, double2* A, Small& s,
+                                                 bool next_reflector) {
+  const int lane = lane_id(), w = warp_id(), NW = nwarps();
+  const int W = seg_width_cols(n - k, n - k - 1);
+  const int spw = 32 / W;
+  const int sl = lane % W;
+  const double tk = s.tau[k];
+  const int lead = leader_warp(k + 1, s.misc);  // owns column k+1 and its reflector
+  const int slot0 = (w - lead + NW) % NW;
+  for (int base = k + 1 + slot0 * spw; base < n; base += NW * spw) {
+    const int j = base + lane / W;
+    const bool act = j < n;
+    double sr = 0.0, si = 0.0;
+    if (act) {
+      for (int i = k + sl; i < n; i += W) {
+        const cplx v = (i == k) ? cx(1.0, 0.0) : ld(A + i + k * n);
+        const cplx a = ld(A + i + j * n);
+        sr = fma(v.re, a.re, sr);
+        sr = fma(v.im, a.im, sr);
+        si = fma(v.re, a.im, si);
+        si = fma(-v.im, a.re, si);
+      }
+    }
+    sr = seg_sum(sr, W);
+    si = seg_sum(si, W);
+    if (act) {
+      const cplx f = cx(tk * sr, tk * si);
+      for (int i = k + sl; i < n; i += W) {
+        const cplx v = (i == k) ? cx(1.0, 0.0) : ld(A + i + k * n);
+        st(A + i + j * n, cfms(ld(A + i + j * n), f, v));
+      }
+    }
+    if (next_reflector && base == k + 1) {
+      __syncwarp();
+      seg_reflector(n, k + 1, A, seg_width4(n - k - 1), lane % seg_width4(n - k - 1),
+                    lane < seg_width4(n - k - 1), s);
+    }
   }
 }
 
@@ -241,124 +363,107 @@ __device__ __forceinline__ void seg_reflector(int n, int k, double2* A, int W, i
 // Result: Xn = Q, logD_k = log|R_kk| + logD_{pi(k)},
 //         Tn = diag(D')^{-1} R Pi^T Tc  with coefficients R'_kj e^{logw_j - logw_k} / |R'_kk|.
 __device__ inline void cta_reortho(int n, const double2* Xc, double2* Xn, const double2* Tc,
-                            double2* Tn, double* logD, Small& s) {
-  const int W0 = seg_width(n);
-  const int spw0 = 32 / W0;
+                                   double2* Tn, double* logD, Small& s) {
   const int lane = lane_id(), w = warp_id(), NW = nwarps();
-  // 1. pivot keys
-  for (int base = w * spw0; base < n; base += NW * spw0) {
-    int j = base + lane / W0;
-    int sl = lane % W0;
-    double a = 0.0;
-    if (j < n)
-      for (int i = sl; i < n; i += W0) a += abs2(ld(Xc + i + j * n));
-    a = seg_sum(a, W0);
-    if (j < n && sl == 0) {
-      double kk = logD[j] + 0.5 * log(a);
-      if (kk != kk) {  // NaN
-        kk = -INFINITY;
-        atomicOr(&s.misc[0], 1);
+  float* keyf = (float*)s.key;
+  // 1. pivot keys (FP32 ordering keys: the pre-pivot order only has to be approximately sorted)
+  {
+    const int W0 = seg_width_cols(n, n);
+    const int spw0 = 32 / W0;
+    for (int base = w * spw0; base < n; base += NW * spw0) {
+      const int j = base + lane / W0;
+      const int sl = lane % W0;
+      double a = 0.0;
+      if (j < n)
+        for (int i = sl; i < n; i += W0) a += abs2(ld(Xc + i + j * n));
+      a = seg_sum(a, W0);
+      if (j < n && sl == 0) {
+        float kk = (float)logD[j] + 0.5f * log_key(a);
+        if (!(a == a) || !(kk == kk)) {  // NaN
+          kk = -INFINITY;
+          atomicOr(&s.misc[0], 1);
+        }
+        keyf[j] = kk;
       }
-      s.key[j] = kk;
     }
   }
   __syncthreads();
   // 2. rank sort, descending key, ties by index
   for (int j = tid(); j < n; j += nthr()) {
-    double kj = s.key[j];
+    const float kj = keyf[j];
     int r = 0;
     for (int i = 0; i < n; ++i) {
-      double ki = s.key[i];
+      const float ki = keyf[i];
       r += (ki > kj) || (ki == kj && i < j);
     }
     s.perm[r] = j;
   }
   __syncthreads();
-  // 3. gather columns
+  // 3. gather columns; column-scale factors sc_k = e^{logw_k - m} (m = mid-range) when the
+  //    range of log D fits FP64 (|logw - m| < 600), else the per-element form below
   for (int e = tid(); e < n * n; e += nthr()) {
-    int i = e % n, k = e / n;
+    const int i = e % n, k = e / n;
     Xn[e] = Xc[i + s.perm[k] * n];
   }
   for (int k = tid(); k < n; k += nthr()) s.logw[k] = logD[s.perm[k]];
+  if (w == 0) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int k = lane; k < n; k += 32) {
+      const double v = logD[k];
+      lo = fmin(lo, v);
+      hi = fmax(hi, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      s.red[8] = 0.5 * (lo + hi);
+      s.misc[4] = (hi - lo) < 1200.0 ? 1 : 0;
+    }
+  }
   __syncthreads();
+  const bool scaled = s.misc[4] != 0;
   // 4. Householder factorisation, one barrier per column
-  if (w == 0) seg_reflector(n, 0, Xn, W0, lane % W0, lane < W0, s);
+  if (w == leader_warp(0, s.misc))
+    seg_reflector(n, 0, Xn, seg_width4(n), lane % seg_width4(n), lane < seg_width4(n), s);
   __syncthreads();
   for (int k = 0; k < n - 1; ++k) {
-    const int rows = n - k;
-    const int W = seg_width(rows);
-    const int spw = 32 / W;
-    const int sl = lane % W;
-    const double tk = s.tau[k];
-    for (int base = k + 1 + w * spw; base < n; base += NW * spw) {
-      int j = base + lane / W;
-      bool act = j < n;
-      double sr = 0.0, si = 0.0;
-      if (act) {
-        for (int i = k + sl; i < n; i += W) {
-          cplx v = (i == k) ? cx(1.0, 0.0) : ld(Xn + i + k * n);
-          cplx a = ld(Xn + i + j * n);
-          cplx p = cmulc(v, a);
-          sr += p.re;
-          si += p.im;
-        }
-      }
-      sr = seg_sum(sr, W);
-      si = seg_sum(si, W);
-      if (act) {
-        cplx f = cx(tk * sr, tk * si);
-        for (int i = k + sl; i < n; i += W) {
-          cplx v = (i == k) ? cx(1.0, 0.0) : ld(Xn + i + k * n);
-          st(Xn + i + j * n, ld(Xn + i + j * n) - f * v);
-        }
-      }
-      // the segment that owns column k+1 (warp 0, segment 0, first round) makes its reflector
-      if (base == k + 1) {
-        __syncwarp();
-        seg_reflector(n, k + 1, Xn, W, sl, lane < W, s);
-      }
-    }
+    householder_step(n, k, Xn, s, true);
     __syncthreads();
   }
-  if (n == 1) {
-    // seg_reflector(k = n-1) already stored rdiag[0], tau[0]
-  }
-  // 5. new log D and the T-update coefficients (in place in the upper triangle)
+  // 5. new log D, the row factors q_k = 1 / (sc_k |R_kk|), and the T-update coefficients
+  //    C_kj = R'_kj sc_j q_k (j > k), C_kk = R_kk / |R_kk| (in place in the upper triangle)
   for (int k = tid(); k < n; k += nthr()) {
-    double r = sqrt(abs2(ld(s.rdiag + k)));
-    if (!(r > 0.0)) atomicOr(&s.misc[0], 1);
-    logD[k] = log(r) + s.logw[k];
+    const double r2 = abs2(ld(s.rdiag + k));
+    if (!(r2 > 0.0)) atomicOr(&s.misc[0], 1);
+    const double ir = rsqrt64(r2);  // 1 / |R_kk|
+    logD[k] = -log(ir) + s.logw[k];
+    const double sc = scaled ? exp(s.logw[k] - s.red[8]) : 1.0;
+    s.sa[k] = sc;
+    s.sb[k] = scaled ? ir * rcp64(sc) : ir;
   }
+  __syncthreads();
   for (int e = tid(); e < n * n; e += nthr()) {
-    int k = e % n, j = e / n;
+    const int k = e % n, j = e / n;
     if (j < k) continue;
-    cplx rkk = ld(s.rdiag + k);
-    double r = sqrt(abs2(rkk));
     cplx c;
     if (j == k) {
-      c = cx(rkk.re / r, rkk.im / r);
+      c = s.sb[k] * ld(s.rdiag + k);
+      if (scaled) c = s.sa[k] * c;
+    } else if (scaled) {
+      c = s.sb[k] * (s.sa[j] * ld(Xn + e));
     } else {
-      cplx rkj = ld(Xn + e);
-      double ex = s.logw[j] - s.logw[k];
-      if (ex < 600.0) {
-        double f = exp(ex) / r;
-        c = f * rkj;
-      } else {
-        double m = sqrt(abs2(rkj));
-        if (m == 0.0) {
-          c = cx(0, 0);
-        } else {
-          double f = exp(log(m) - log(r) + ex) / m;
-          c = f * rkj;
-        }
-      }
+      const cplx rkj = ld(Xn + e);
+      const double ex = s.logw[j] - s.logw[k];
+      const double m = sqrt64(abs2(rkj));
+      c = m == 0.0 ? cx(0, 0) : (exp(log(m) + ex) * s.sb[k] * rcp64(m)) * rkj;
     }
     st(Xn + e, c);
   }
   __syncthreads();
   // 6. Tn = C (Pi^T Tc), C upper triangular
   {
-    const double2* Tg = Tc;
     const int* perm = s.perm;
     struct CUp {
       const double2* p;
@@ -374,12 +479,12 @@ __device__ inline void cta_reortho(int n, const double2* Xc, double2* Xn, const 
       __device__ __forceinline__ cplx operator()(int k, int c) const {
         return ld(p + perm[k] + c * n);
       }
-    } Top{Tg, perm, n};
+    } Top{Tc, perm, n};
     cta_gemm<true>(n, Cop, Top, [&](int i, int j, cplx v) { st(Tn + i + j * n, v); });
   }
   // 7. form Q in place: Q = H_0 H_1 ... H_{n-2}, accumulated backwards
   for (int e = tid(); e < n * n; e += nthr()) {
-    int i = e % n, j = e / n;
+    const int i = e % n, j = e / n;
     if (i < j) Xn[e] = make_double2(0.0, 0.0);
     if (i == n - 1 && j == n - 1) Xn[e] = make_double2(1.0, 0.0);
   }
@@ -388,28 +493,30 @@ __device__ inline void cta_reortho(int n, const double2* Xc, double2* Xn, const 
       s.vbuf[((n - 2) & 1) * n + i] = Xn[i + (n - 2) * n];
   __syncthreads();
   for (int k = n - 2; k >= 0; --k) {
-    const int rows = n - k;
-    const int W = seg_width(rows);
+    const int W = seg_width_cols(n - k, n - k);
     const int spw = 32 / W;
     const int sl = lane % W;
     const double tk = s.tau[k];
     const double2* vk = s.vbuf + (k & 1) * n;
-    for (int base = k + w * spw; base < n; base += NW * spw) {
-      int j = base + lane / W;
-      bool act = j < n && j > k;
+    const int slot0 = (w - leader_warp(k, s.misc) + NW) % NW;
+    for (int base = k + slot0 * spw; base < n; base += NW * spw) {
+      const int j = base + lane / W;
+      const bool act = j < n && j > k;
       double sr = 0.0, si = 0.0;
       if (act)
         for (int i = k + 1 + sl; i < n; i += W) {
-          cplx p = cmulc(ld(vk + i), ld(Xn + i + j * n));
-          sr += p.re;
-          si += p.im;
+          const cplx v = ld(vk + i), a = ld(Xn + i + j * n);
+          sr = fma(v.re, a.re, sr);
+          sr = fma(v.im, a.im, sr);
+          si = fma(v.re, a.im, si);
+          si = fma(-v.im, a.re, si);
         }
       sr = seg_sum(sr, W);
       si = seg_sum(si, W);
       if (act) {
-        cplx f = cx(tk * sr, tk * si);
+        const cplx f = cx(tk * sr, tk * si);
         if (sl == 0) st(Xn + k + j * n, cx(-f.re, -f.im));
-        for (int i = k + 1 + sl; i < n; i += W) st(Xn + i + j * n, ld(Xn + i + j * n) - f * ld(vk + i));
+        for (int i = k + 1 + sl; i < n; i += W) st(Xn + i + j * n, cfms(ld(Xn + i + j * n), f, ld(vk + i)));
       }
       if (j == k) {  // this segment sets column k and copies v_{k-1}
         if (sl == 0) Xn[k + k * n] = make_double2(1.0 - tk, 0.0);
@@ -430,25 +537,28 @@ __device__ inline void cta_reortho(int n, const double2* Xc, double2* Xn, const 
 // Factor A in place (A = P^T L U, unit L), applying the same row operations to the n columns of
 // Bm (so that Bm <- L^{-1} P Bm), then back-substitute Bm <- U^{-1} Bm.  On return Bm holds
 // A^{-1} Bm_in and *logdet_out = log det A (principal logs of the pivots + i pi * swaps).
+// Pivot search on FP32 magnitudes (partial pivoting only needs an approximately largest pivot);
+// one complex reciprocal per pivot; back substitution with the columns of U pre-scaled by the
+// reciprocal pivots, one barrier per step, rows scaled at the end.
 __device__ inline void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, double* logdet_re,
-                             double* logdet_im) {
+                                    double* logdet_im) {
   const int lane = lane_id(), w = warp_id();
   if (tid() == 0) s.misc[1] = 0;
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    if (w == 0) {
-      double best = -1.0;
+    if (w == leader_warp(k, s.misc)) {
+      float best = -1.f;
       int bi = k;
       for (int i = k + lane; i < n; i += 32) {
-        double m = abs2(ld(A + i + k * n));
+        const float m = (float)abs2(ld(A + i + k * n));
         if (m > best) {
           best = m;
           bi = i;
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) {
           best = ob;
           bi = oi;
@@ -468,12 +578,15 @@ __device__ inline void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, do
       }
       __syncwarp();
       cplx piv = ld(A + k + k * n);
-      if (!(abs2(piv) > 0.0)) {
-        if (lane == 0) atomicOr(&s.misc[0], 1);
-        piv = cx(1e-300, 0.0);
-      }
       double p2 = abs2(piv);
-      cplx pinv = cx(piv.re / p2, -piv.im / p2);
+      if (!(p2 > 0.0)) {  // singular: flagged; continue with a unit pivot
+        if (lane == 0) atomicOr(&s.misc[0], 1);
+        piv = cx(1.0, 0.0);
+        p2 = 1.0;
+      }
+      const double ip2 = rcp64(p2);
+      const cplx pinv = cx(piv.re * ip2, -piv.im * ip2);
+      if (lane == 0) st(s.rdiag + k, pinv);
       for (int i = k + 1 + lane; i < n; i += 32) st(A + i + k * n, ld(A + i + k * n) * pinv);
     }
     __syncthreads();
@@ -481,24 +594,24 @@ __device__ inline void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, do
     const int m = n - k - 1;
     const int cols = m + n;
     for (int e = tid(); e < m * cols; e += nthr()) {
-      int i = k + 1 + e % m;
-      int c = e / m;
-      cplx l = ld(A + i + k * n);
+      const int i = k + 1 + e % m;
+      const int c = e / m;
+      const cplx l = ld(A + i + k * n);
       if (c < m) {
-        int j = k + 1 + c;
-        st(A + i + j * n, ld(A + i + j * n) - l * ld(A + k + j * n));
+        const int j = k + 1 + c;
+        st(A + i + j * n, cfms(ld(A + i + j * n), l, ld(A + k + j * n)));
       } else {
-        int j = c - m;
-        st(Bm + i + j * n, ld(Bm + i + j * n) - l * ld(Bm + k + j * n));
+        const int j = c - m;
+        st(Bm + i + j * n, cfms(ld(Bm + i + j * n), l, ld(Bm + k + j * n)));
       }
     }
     __syncthreads();
   }
-  // log det A
+  // log det A, and U's strict upper part pre-scaled by the pivot reciprocals: W(i,k) = U(i,k)/U(k,k)
   if (w == 0) {
     double lr = 0.0, li = 0.0;
     for (int k = lane; k < n; k += 32) {
-      cplx u = ld(A + k + k * n);
+      const cplx u = ld(A + k + k * n);
       lr += 0.5 * log(abs2(u));
       li += atan2(u.im, u.re);
     }
@@ -509,19 +622,24 @@ __device__ inline void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, do
       *logdet_im = li + (s.misc[1] ? 3.14159265358979323846 : 0.0);
     }
   }
-  // back substitution U X = Bm
-  for (int k = n - 1; k >= 0; --k) {
-    for (int j = tid(); j < n; j += nthr()) {
-      cplx u = ld(A + k + k * n);
-      st(Bm + k + j * n, cdiv(ld(Bm + k + j * n), u));
-    }
-    __syncthreads();
+  for (int e = tid(); e < n * n; e += nthr()) {
+    const int i = e % n, k = e / n;
+    if (i < k) st(A + e, ld(A + e) * ld(s.rdiag + k));
+  }
+  __syncthreads();
+  // back substitution, unscaled rows: B(i,:) -= W(i,k) B(k,:) for i < k, then B(k,:) /= U(k,k)
+  for (int k = n - 1; k >= 1; --k) {
     for (int e = tid(); e < k * n; e += nthr()) {
-      int i = e % k, j = e / k;
-      st(Bm + i + j * n, ld(Bm + i + j * n) - ld(A + i + k * n) * ld(Bm + k + j * n));
+      const int i = e % k, j = e / k;
+      st(Bm + i + j * n, cfms(ld(Bm + i + j * n), ld(A + i + k * n), ld(Bm + k + j * n)));
     }
     __syncthreads();
   }
+  for (int e = tid(); e < n * n; e += nthr()) {
+    const int i = e % n;
+    st(Bm + e, ld(Bm + e) * ld(s.rdiag + i));
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------- assembly (Section 7)

@@ -118,7 +118,10 @@ __global__ void __launch_bounds__(256) k_fwd_fp64(const Desc* __restrict__ descs
     const Desc d = descs[c];
     const int n = d.nx;
     Small s = carve_small(smem + L.small_off, n);
-    if (tid() == 0) s.misc[0] = 0;
+    if (tid() == 0) {
+      s.misc[0] = 0;
+      s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
+    }
     Bufs B = setup_bufs(smem, slotp, d, L, false);
     double2* X = B.X[0];
     double2* Xo = B.X[1];
@@ -187,7 +190,10 @@ __global__ void __launch_bounds__(256) k_force_fp64(const Desc* __restrict__ des
     const Desc d = descs[c];
     const int n = d.nx, ns = d.nstab, nb = d.nt / d.nstab;
     Small s = carve_small(smem + L.small_off, n);
-    if (tid() == 0) s.misc[0] = 0;
+    if (tid() == 0) {
+      s.misc[0] = 0;
+      s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
+    }
     Bufs B = setup_bufs(smem, slotp, d, L, true);
     // checkpoint b (1..nb-1): X (n*n), T (n*n), logD (n doubles, padded to n/2+1 complex)
     const size_t ck_stride = (size_t)2 * n * n + (n + 1) / 2;

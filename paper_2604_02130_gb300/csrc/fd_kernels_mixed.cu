@@ -252,7 +252,10 @@ __global__ void __launch_bounds__(256) k_fwd_mixed(const Desc* __restrict__ desc
     const Desc d = descs[c];
     Small s = carve_small(smem + L.small_off, n);
     float2* pf = (float2*)s.ph;  // FP32 phases: two halves of n
-    if (tid() == 0) s.misc[0] = 0;
+    if (tid() == 0) {
+      s.misc[0] = 0;
+      s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
+    }
     fill_a(L, m.a_hi, m.a_lo, d.E);
     cta_identity(n, T);
     for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
@@ -345,7 +348,10 @@ __global__ void __launch_bounds__(256) k_force_mixed(const Desc* __restrict__ de
     };
     Small s = carve_small(smem + L.small_off, n);
     float2* pf = (float2*)s.ph;  // FP32 phases: two halves of n
-    if (tid() == 0) s.misc[0] = 0;
+    if (tid() == 0) {
+      s.misc[0] = 0;
+      s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
+    }
     fill_a(L, m.a_hi, m.a_lo, d.E);
     fill_a(L, e2_hi, e2_lo, d.Einv);
     cta_identity(n, T);

@@ -86,7 +86,10 @@ __global__ void __launch_bounds__(FD_NOALLOC_THREADS) k_fwd_fp64_noalloc(NPack p
   Small s = carve_small(smem + so, n);
   double2* T = (double2*)slot;  // every buffer is fully written before it is read
   double2* To = T + (size_t)n * n;
-  if (tid() == 0) s.misc[0] = 0;
+  if (tid() == 0) {
+    s.misc[0] = 0;
+    s.misc[5] = 0;  // leader-warp offset of the shared CTA routines
+  }
   cta_load_real(n * n, Es, d.E);
   cta_identity(n, X);
   cta_identity(n, T);
