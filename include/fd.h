@@ -153,10 +153,11 @@ int fd_graph_launch(fd_ctx* ctx, void* graph, void* stream);
 int fd_graph_destroy(fd_ctx* ctx, void* graph);
 
 /* The launch plan a call with these arguments would use, without launching anything: one
- * record of 8 ints per launch (size class) in info[8*g .. 8*g+7]:
- *   nx, kernel (0 FP64 log det/G, 1 FP64 force, 2 mixed log det/G, 3 mixed force),
- *   threads per CTA, dynamic shared memory bytes, grid (persistent CTAs), resident CTAs per SM,
- *   scratch KiB per CTA, configurations in the class.
+ * record of 8 ints per kernel launch in info[8*g .. 8*g+7]:
+ *   nx, kernel (+4 when it runs on the tensor cores): 0 log det/G, 1 force chains (forward and
+ *   backward products, two tasks per configuration), 2 block-boundary Green's functions,
+ *   3 wraps and force rows;  threads per CTA, dynamic shared memory bytes, grid (persistent
+ *   CTAs), resident CTAs per SM, scratch KiB per CTA, tasks of the launch.
  * Returns the number of launches (>= 0, records beyond max_groups are not written) or a
  * negative FD_ERR_* code.  Synchronous, host only (queries the device's occupancy limits). */
 int fd_plan_query(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec, int* info,

@@ -24,6 +24,10 @@ struct fd_ctx {
   size_t h_desc_cap = 0;
   int* d_queue = nullptr;
   int queue_cap = 0;
+  fd::Task* d_tasks = nullptr;  // force boundary/wrap task table
+  size_t tasks_cap = 0;
+  fd::Task* h_tasks = nullptr;  // pinned staging
+  size_t h_tasks_cap = 0;
   int* d_status = nullptr;
   int status_cap = 0;
   cudaEvent_t staging_done = nullptr;
@@ -73,17 +77,33 @@ int cuda_fail(fd_ctx* ctx, cudaError_t e, const char* what) {
 
 enum Kind { K_FWD = 0, K_FORCE = 1 };
 
+// One launch of a size class.  which: 0 log det/G, 1 force chains, 2 boundary G, 3 wraps.
+struct Phase {
+  int which;
+  int mixed;  // 1: tcgen05 kernel (ML), 0: FP64 kernel (L)
+  Layout L;
+  fd::MLayout ML;
+  int nthreads, smem, grid, occ;
+  long long slot_bytes;
+  int ntasks;
+};
+
 struct Group {
   int kind;
   int nx;
-  int mixed;   // 1: tcgen05 slice path (ML), 0: FP64 path (L)
-  Layout L;
-  fd::MLayout ML;
-  int grid;
-  int occ;     // resident CTAs per SM assumed by the plan
-  std::vector<int> idx;  // user indices, cost-sorted (descending)
-  size_t desc_off;       // first descriptor of this group in the table
-  size_t scratch_off;    // byte offset of this group's slots
+  int mixed;              // any phase on the tensor cores
+  std::vector<int> idx;   // user indices, cost-sorted (descending)
+  std::vector<Phase> ph;  // launches, in order (one for log det/G, three for the force)
+  size_t desc_off;        // first descriptor of this group in the table
+  size_t scratch_off;     // byte offset of this group's scratch (slots, then FWork)
+  size_t slots_bytes;     // CTA slots, shared by the phases (they run one after the other)
+  std::vector<fd::Task> tB, tC;  // force: boundary and wrap tasks
+  size_t tB_off, tC_off;         // their offsets in the task table
+  std::vector<size_t> fws_off;   // force: per configuration, bytes from the group's FWork base
+  size_t fws_bytes;
+  int qbase;                     // first queue counter of the group
+  int grid;                      // largest grid of the phases (reported)
+  int occ;
 };
 
 // Threads per CTA.  The FP64 pipe of this GPU (about 2 DFMA/clk/SM, spread over the four SM
@@ -98,11 +118,11 @@ long long round16(long long x) { return (x + 15) & ~15LL; }
 
 // Resident CTAs per SM for a kernel: the runtime's occupancy calculator, cross-checked by a
 // direct count from the kernel's registers and shared memory (the smaller wins; 1 at least).
-int resident_ctas(fd_ctx* ctx, bool mixed, bool force, int nthreads, int smem_bytes) {
-  int api = mixed ? fd::occupancy_mixed(force, nthreads, smem_bytes)
-                  : fd::occupancy_fp64(force, nthreads, smem_bytes);
+int resident_ctas(fd_ctx* ctx, bool mixed, int which, int nthreads, int smem_bytes) {
+  int api = mixed ? fd::occupancy_mixed(which, nthreads, smem_bytes)
+                  : fd::occupancy_fp64(which, nthreads, smem_bytes);
   cudaFuncAttributes fa;
-  cudaError_t e = mixed ? fd::attrs_mixed(force, &fa) : fd::attrs_fp64(force, &fa);
+  cudaError_t e = mixed ? fd::attrs_mixed(which, &fa) : fd::attrs_fp64(which, &fa);
   int manual = 1;
   if (e == cudaSuccess) {
     const int warps = (nthreads + 31) / 32;
@@ -124,20 +144,23 @@ long long tune_key(int kind, int mixed, int three, int nx) {
   return ((long long)kind << 40) | ((long long)mixed << 36) | ((long long)three << 32) | nx;
 }
 
+// Buffer sets of the kernels ("roles"): log det/G and the force chains (R_FWD), the boundary
+// Green's functions (R_BOUND) and the wraps (R_WRAP).
+enum Role { R_FWD = 0, R_BOUND = 2, R_WRAP = 3 };
+
 // Greedy placement: the buffers touched every slice first, then the per-block ones.
-Layout plan_layout(int n, int kind, int budget, int nthreads, int max_nt, int max_nstab_min) {
+Layout plan_layout(int n, int role, int budget, int nthreads) {
   Layout L;
   memset(&L, 0, sizeof(L));
   L.nthreads = nthreads;
   const long long cm = 16LL * n * n, rm = 8LL * n * n;
   std::vector<std::pair<int, long long>> order;
-  if (kind == K_FWD) {
+  if (role == R_FWD)
     order = {{fd::B_E, rm}, {fd::B_X0, cm}, {fd::B_X1, cm}, {fd::B_T0, cm}, {fd::B_T1, cm}};
-  } else {
-    order = {{fd::B_E, rm},   {fd::B_X0, cm},  {fd::B_X1, cm},  {fd::B_EINV, rm},
-             {fd::B_GA, cm},  {fd::B_GB, cm},  {fd::B_GLO, cm}, {fd::B_GHI, cm},
-             {fd::B_T0, cm},  {fd::B_T1, cm}};
-  }
+  else if (role == R_BOUND)
+    order = {{fd::B_GA, cm}, {fd::B_GB, cm}};
+  else
+    order = {{fd::B_E, rm}, {fd::B_EINV, rm}, {fd::B_GA, cm}, {fd::B_GB, cm}};
   long long used = round16(fd::small_bytes(n)) + 16;  // small vectors + queue slot
   long long gbytes = 0;
   std::vector<std::pair<int, long long>> placed;
@@ -164,22 +187,15 @@ Layout plan_layout(int n, int kind, int budget, int nthreads, int max_nt, int ma
   L.small_off = (int)o;
   L.smem_bytes = (int)(o + round16(fd::small_bytes(n)) + 16);
   L.ws_bytes = round16(gbytes);
-  long long ck = 0;
-  if (kind == K_FORCE) {
-    // (nb - 1) checkpoints of X, T (n*n complex each) and log D (n doubles, padded)
-    long long stride = (2LL * n * n + (n + 1) / 2) * 16;
-    long long nb = max_nt / std::max(1, max_nstab_min);
-    ck = std::max(0LL, nb - 1) * stride;
-  }
-  L.slot_bytes = round16(L.ws_bytes + ck);
-  if (L.slot_bytes == 0) L.slot_bytes = 16;
+  L.slot_bytes = std::max(16LL, L.ws_bytes);
   return L;
 }
 
-// Mixed path: A = E and B = the product in shared memory (K-major TF32), then the FP64
-// result Xc (aliasing B when it fits), the QR output Xn, small vectors; T and whatever did not
-// fit in the CTA's scratch slot.  Returns smem_bytes = 0 if A and B alone do not fit.
-fd::MLayout plan_mixed(int n, int kind, bool three, int budget, int smem_per_sm, int max_nb) {
+// Mixed path: A = E (and, for the wraps, A2 = E^{-1}) and B = the product in shared memory
+// (K-major TF32); for R_FWD then the FP64 block result Xc (aliasing B when it fits), the QR
+// output Xn and the T pair, each in shared memory when it fits, else in the CTA's scratch slot.
+// Returns smem_bytes = 0 if the tensor-core operands alone do not fit (or nx > 128).
+fd::MLayout plan_mixed(int n, int role, bool three, int budget, int smem_per_sm) {
   fd::MLayout M;
   memset(&M, 0, sizeof(M));
   M.n = n;
@@ -199,14 +215,13 @@ fd::MLayout plan_mixed(int n, int kind, bool three, int budget, int smem_per_sm,
   long long o = 0;
   M.a_hi = 0;
   o = round16(a_bytes);
+  M.a_lo = -1;
   if (three) {
     M.a_lo = (int)o;
     o += round16(a_bytes);
-  } else {
-    M.a_lo = -1;
   }
   M.a2_hi = M.a2_lo = -1;
-  if (kind == K_FORCE) {  // E^{-1} for the wraps
+  if (role == R_WRAP) {
     M.a2_hi = (int)o;
     o += round16(a_bytes);
     if (three) {
@@ -214,51 +229,55 @@ fd::MLayout plan_mixed(int n, int kind, bool three, int budget, int smem_per_sm,
       o += round16(a_bytes);
     }
   }
-  const long long last_a = kind == K_FORCE ? (three ? M.a2_lo : M.a2_hi) : (three ? M.a_lo : M.a_hi);
+  const long long last_a = role == R_WRAP ? (three ? M.a2_lo : M.a2_hi) : (three ? M.a_lo : M.a_hi);
   o = (o + 127) & ~127LL;
   M.b_hi = (int)o;
   M.b_lo = three ? (int)(o + round16(b_one)) : -1;
   long long breg = round16(b_bytes);
   const long long fixed = round16(fd::small_bytes(n)) + 64;
   long long g = 0;  // scratch-slot bytes
-  // Xn first (the QR works in place on it), then Xc
-  const bool xn_fits = o + breg + cm + fixed <= budget;
-  const bool xc_alias = cm <= breg || (xn_fits ? o + std::max(breg, cm) + cm + fixed <= budget
-                                               : o + std::max(breg, cm) + fixed <= budget);
-  if (xc_alias) {
-    breg = std::max(breg, round16(cm));
-    M.xc_smem = 1;
-    M.xc_off = M.b_hi;
-  } else {
-    M.xc_smem = 0;
-    M.xc_off = g;
-    g += round16(cm);
-  }
-  o += breg;
-  if (o + cm + fixed <= budget) {
-    M.xn_smem = 1;
-    M.xn_off = o;
-    o += round16(cm);
-  } else {
-    M.xn_smem = 0;
-    M.xn_off = g;
-    g += round16(cm);
-  }
-  // T pair, then (force) the four G buffers: shared memory when they fit
-  M.t_smem = o + 2 * round16(cm) + fixed <= budget ? 1 : 0;
-  if (M.t_smem) {
-    M.t0_off = o;
-    o += round16(cm);
-    M.t1_off = o;
-    o += round16(cm);
-  }
-  M.g_smem = 0;
-  if (kind == K_FORCE && o + 4 * round16(cm) + fixed <= budget) {
-    M.g_smem = 1;
-    for (int i = 0; i < 4; ++i) {
-      M.g_off[i] = o;
-      o += round16(cm);
+  if (role == R_FWD) {
+    // Xn first (the QR works in place on it), then Xc
+    const bool xn_fits = o + breg + cm + fixed <= budget;
+    const bool xc_alias = cm <= breg || (xn_fits ? o + std::max(breg, cm) + cm + fixed <= budget
+                                                 : o + std::max(breg, cm) + fixed <= budget);
+    if (xc_alias) {
+      breg = std::max(breg, round16(cm));
+      M.xc_smem = 1;
+      M.xc_off = M.b_hi;
+    } else {
+      M.xc_smem = 0;
+      M.xc_off = g;
+      g += round16(cm);
     }
+    o += breg;
+    if (o + cm + fixed <= budget) {
+      M.xn_smem = 1;
+      M.xn_off = o;
+      o += round16(cm);
+    } else {
+      M.xn_smem = 0;
+      M.xn_off = g;
+      g += round16(cm);
+    }
+    M.t_smem = o + 2 * round16(cm) + fixed <= budget ? 1 : 0;
+    if (M.t_smem) {
+      M.t0_off = o;
+      o += round16(cm);
+      M.t1_off = o;
+      o += round16(cm);
+    } else {
+      M.t0_off = g;
+      g += round16(cm);
+      M.t1_off = g;
+      g += round16(cm);
+    }
+  } else {  // wraps: no FP64 working matrices (Xc/Xn point at B, unused)
+    o += breg;
+    M.xc_smem = M.xn_smem = 1;
+    M.xc_off = M.xn_off = M.b_hi;
+    M.t_smem = 1;
+    M.t0_off = M.t1_off = M.b_hi;
   }
   M.small_off = (int)o;
   o += round16(fd::small_bytes(n));
@@ -277,23 +296,8 @@ fd::MLayout plan_mixed(int n, int kind, bool three, int budget, int smem_per_sm,
     M.smem_bytes = 0;
     return M;
   }
-  if (!M.t_smem) {
-    M.t0_off = g;
-    g += round16(cm);
-    M.t1_off = g;
-    g += round16(cm);
-  }
-  if (kind == K_FORCE && !M.g_smem) {
-    for (int i = 0; i < 4; ++i) {
-      M.g_off[i] = g;
-      g += round16(cm);
-    }
-  }
   M.ws_bytes = round16(g);
-  long long ck = 0;
-  if (kind == K_FORCE) ck = std::max(0, max_nb - 1) * (2LL * n * n + (n + 1) / 2) * 16;
-  M.slot_bytes = round16(M.ws_bytes + ck);
-  if (M.slot_bytes == 0) M.slot_bytes = 16;
+  M.slot_bytes = std::max(16LL, M.ws_bytes);
   return M;
 }
 
@@ -322,77 +326,131 @@ int validate(fd_ctx* ctx, int batch, const fd_problem* probs, const void* logdet
   return FD_OK;
 }
 
+Phase fp64_phase(fd_ctx* ctx, int n, int role, int which, int ntasks) {
+  Phase P;
+  memset(&P.ML, 0, sizeof(P.ML));
+  P.which = which;
+  P.mixed = 0;
+  int nth = threads_for(n);
+  auto it = ctx->tuned.find(tune_key(which, 0, 0, n));
+  if (it != ctx->tuned.end()) nth = it->second;
+  // a budget that keeps several CTAs per SM when everything fits, else the full opt-in budget
+  Layout full = plan_layout(n, role, 1 << 30, nth);
+  const int budget =
+      full.smem_bytes <= ctx->smem_per_sm / 2 - 1024 ? full.smem_bytes : ctx->max_smem_optin;
+  P.L = plan_layout(n, role, budget, nth);
+  P.L.num_sms = ctx->num_sms;
+  P.nthreads = nth;
+  P.smem = P.L.smem_bytes;
+  P.occ = resident_ctas(ctx, false, which, nth, P.smem);
+  P.grid = std::max(1, std::min(ntasks, ctx->num_sms * P.occ));
+  P.slot_bytes = P.L.slot_bytes;
+  P.ntasks = ntasks;
+  return P;
+}
+
+bool mixed_phase(fd_ctx* ctx, int n, int role, int which, bool three, int ntasks, Phase& P) {
+  fd::MLayout M = plan_mixed(n, role, three, ctx->max_smem_optin, ctx->smem_per_sm);
+  if (M.smem_bytes == 0) return false;
+  auto it = ctx->tuned.find(tune_key(which, 1, three ? 1 : 0, n));
+  if (it != ctx->tuned.end()) M.nthreads = it->second;
+  M.num_sms = ctx->num_sms;
+  memset(&P.L, 0, sizeof(P.L));
+  P.which = which;
+  P.mixed = 1;
+  P.ML = M;
+  P.nthreads = M.nthreads;
+  P.smem = M.smem_bytes;
+  P.occ = std::max(1, std::min(resident_ctas(ctx, true, which, M.nthreads, M.smem_bytes),
+                               512 / M.tmem_cols));
+  P.grid = std::max(1, std::min(ntasks, ctx->num_sms * P.occ));
+  P.slot_bytes = M.slot_bytes;
+  P.ntasks = ntasks;
+  return true;
+}
+
 std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kind, int prec) {
   std::vector<Group> groups;
   std::vector<int> order(batch);
   for (int c = 0; c < batch; ++c) order[c] = c;
-  // size classes by nx
+  // size classes by nx, longest chains first inside a class
   std::sort(order.begin(), order.end(), [&](int a, int b) {
     if (probs[a].nx != probs[b].nx) return probs[a].nx > probs[b].nx;
+    const int na = probs[a].nt / probs[a].n_stab, nb = probs[b].nt / probs[b].n_stab;
     if (probs[a].nt != probs[b].nt) return probs[a].nt > probs[b].nt;
+    if (na != nb) return na > nb;
     return a < b;
   });
+  const bool mixed = prec != FD_PREC_FP64;
+  const bool three = prec == FD_PREC_MIXED_3XTF32;
+  int qnext = 0;
   size_t i = 0;
   while (i < order.size()) {
     Group g;
     g.kind = kind;
     g.nx = probs[order[i]].nx;
-    int max_nt = 0, min_ns = 1 << 30;
-    while (i < order.size() && probs[order[i]].nx == g.nx) {
-      g.idx.push_back(order[i]);
-      max_nt = std::max(max_nt, probs[order[i]].nt);
-      ++i;
-    }
-    // checkpoint count bound: max over the group of nt / n_stab
-    int max_nb = 0;
-    for (int c : g.idx) max_nb = std::max(max_nb, probs[c].nt / probs[c].n_stab);
-    min_ns = 1;
-    const int n = g.nx;
-    int nth = threads_for(n);
-    {
-      auto it = ctx->tuned.find(tune_key(kind, 0, 0, n));
-      if (it != ctx->tuned.end()) nth = it->second;
-    }
+    while (i < order.size() && probs[order[i]].nx == g.nx) g.idx.push_back(order[i++]);
+    const int n = g.nx, nd = (int)g.idx.size();
     g.mixed = 0;
-    if (prec != FD_PREC_FP64) {
-      const bool three = prec == FD_PREC_MIXED_3XTF32;
-      fd::MLayout M = plan_mixed(n, kind, three, ctx->max_smem_optin, ctx->smem_per_sm, max_nb);
-      auto it = ctx->tuned.find(tune_key(kind, 1, three ? 1 : 0, n));
-      if (it != ctx->tuned.end()) M.nthreads = it->second;
-      if (M.smem_bytes > 0) {
-        g.mixed = 1;
-        M.num_sms = ctx->num_sms;
-        g.ML = M;
-        memset(&g.L, 0, sizeof(g.L));
-        int occ = resident_ctas(ctx, true, kind == K_FORCE, M.nthreads, M.smem_bytes);
-        occ = std::max(1, std::min(occ, 512 / M.tmem_cols));
-        g.occ = occ;
-        g.grid = std::min<int>((int)g.idx.size(), ctx->num_sms * occ);
-        g.L.slot_bytes = M.slot_bytes;
-        groups.push_back(g);
-        continue;
+    g.fws_bytes = 0;
+    if (kind == K_FWD) {
+      Phase P;
+      if (!(mixed && mixed_phase(ctx, n, R_FWD, 0, three, nd, P))) P = fp64_phase(ctx, n, R_FWD, 0, nd);
+      g.ph.push_back(P);
+    } else {
+      for (int k = 0; k < nd; ++k) {
+        const int c = g.idx[k];
+        const int nb = probs[c].nt / probs[c].n_stab;
+        for (int b = 2; b <= nb; ++b) g.tB.push_back(fd::Task{k, b});
+        for (int b = 1; b <= nb; ++b) g.tC.push_back(fd::Task{k, b});
+        g.fws_off.push_back(g.fws_bytes);
+        g.fws_bytes += (fd::FWork::elems(n, nb) * 16 + 255) & ~(size_t)255;
       }
+      Phase A, C;
+      if (!(mixed && mixed_phase(ctx, n, R_FWD, 1, three, 2 * nd, A)))
+        A = fp64_phase(ctx, n, R_FWD, 1, 2 * nd);
+      Phase B = fp64_phase(ctx, n, R_BOUND, 2, std::max(1, (int)g.tB.size()));
+      if (!(mixed && mixed_phase(ctx, n, R_WRAP, 3, three, (int)g.tC.size(), C)))
+        C = fp64_phase(ctx, n, R_WRAP, 3, (int)g.tC.size());
+      g.ph.push_back(A);
+      g.ph.push_back(B);
+      g.ph.push_back(C);
     }
-    // try a budget that keeps several CTAs per SM, else the full opt-in budget
-    Layout full = plan_layout(n, kind, 1 << 30, nth, max_nb, min_ns);
-    int budget;
-    if (full.smem_bytes <= ctx->smem_per_sm / 4 - 1024)
-      budget = full.smem_bytes;
-    else if (full.smem_bytes <= ctx->smem_per_sm / 2 - 1024)
-      budget = full.smem_bytes;
-    else
-      budget = ctx->max_smem_optin;
-    g.L = plan_layout(n, kind, budget, nth, max_nb, min_ns);
-    g.L.num_sms = ctx->num_sms;
-    int occ = resident_ctas(ctx, false, kind == K_FORCE, nth, g.L.smem_bytes);
-    g.occ = occ;
-    g.grid = std::min<int>((int)g.idx.size(), ctx->num_sms * occ);
+    g.slots_bytes = 0;
+    g.grid = 0;
+    g.occ = 0;
+    for (auto& P : g.ph) {
+      g.mixed |= P.mixed;
+      g.slots_bytes = std::max(g.slots_bytes, (size_t)P.grid * (size_t)P.slot_bytes);
+      g.grid = std::max(g.grid, P.grid);
+      g.occ = std::max(g.occ, P.occ);
+    }
+    g.slots_bytes = (g.slots_bytes + 255) & ~(size_t)255;
+    g.qbase = qnext;
+    qnext += (int)g.ph.size();
     groups.push_back(g);
   }
   return groups;
 }
 
-int ensure(fd_ctx* ctx, size_t ndesc, size_t nstatus, size_t nqueue, size_t scratch_bytes) {
+int ensure(fd_ctx* ctx, size_t ndesc, size_t nstatus, size_t nqueue, size_t scratch_bytes,
+           size_t ntasks) {
+  if (ntasks > ctx->tasks_cap) {
+    if (ctx->d_tasks) cudaFree(ctx->d_tasks);
+    ctx->d_tasks = nullptr;
+    size_t cap = std::max<size_t>(ntasks, 1024);
+    FD_CUDA(ctx, cudaMalloc(&ctx->d_tasks, cap * sizeof(fd::Task)));
+    ctx->tasks_cap = cap;
+  }
+  if (ntasks > ctx->h_tasks_cap) {
+    if (ctx->staging_pending) cudaEventSynchronize(ctx->staging_done);
+    ctx->staging_pending = false;
+    if (ctx->h_tasks) cudaFreeHost(ctx->h_tasks);
+    ctx->h_tasks = nullptr;
+    size_t cap = std::max<size_t>(ntasks, 1024);
+    FD_CUDA(ctx, cudaMallocHost(&ctx->h_tasks, cap * sizeof(fd::Task)));
+    ctx->h_tasks_cap = cap;
+  }
   if (ndesc > ctx->desc_cap) {
     if (ctx->d_desc) cudaFree(ctx->d_desc);
     ctx->d_desc = nullptr;
@@ -436,18 +494,34 @@ size_t scratch_need(std::vector<Group>& groups) {
   size_t off = 0;
   for (auto& g : groups) {
     g.scratch_off = off;
-    off += (size_t)g.grid * (size_t)g.L.slot_bytes;
+    off += g.slots_bytes + g.fws_bytes;
     off = (off + 255) & ~(size_t)255;
   }
   return off;
 }
 
-void build_descs(std::vector<Group>& groups, const fd_problem* probs, double* logdet,
-                 double* const* G, double* const* F, Desc* out) {
-  size_t k = 0;
+size_t task_count(const std::vector<Group>& groups) {
+  size_t t = 0;
+  for (auto& g : groups) t += g.tB.size() + g.tC.size();
+  return t;
+}
+
+int queue_count(const std::vector<Group>& groups) {
+  int q = 0;
+  for (auto& g : groups) q += (int)g.ph.size();
+  return q;
+}
+
+// Host descriptor and task tables of a call.  `scratch` is the device scratch base (the force
+// workspace of each configuration lives inside it).
+void build_tables(std::vector<Group>& groups, const fd_problem* probs, double* logdet,
+                  double* const* G, double* const* F, char* scratch, Desc* out,
+                  fd::Task* tasks) {
+  size_t k = 0, t = 0;
   for (auto& g : groups) {
     g.desc_off = k;
-    for (int c : g.idx) {
+    for (size_t q = 0; q < g.idx.size(); ++q) {
+      const int c = g.idx[q];
       const fd_problem& p = probs[c];
       Desc d;
       d.nx = p.nx;
@@ -460,8 +534,15 @@ void build_descs(std::vector<Group>& groups, const fd_problem* probs, double* lo
       d.logdet = logdet + 2 * (size_t)c;
       d.G = G ? (double2*)G[c] : nullptr;
       d.F = F ? (double2*)F[c] : nullptr;
+      d.fws = g.kind == K_FORCE
+                  ? (double2*)(scratch + g.scratch_off + g.slots_bytes + g.fws_off[q])
+                  : nullptr;
       out[k++] = d;
     }
+    g.tB_off = t;
+    for (auto& x : g.tB) tasks[t++] = x;
+    g.tC_off = t;
+    for (auto& x : g.tC) tasks[t++] = x;
   }
 }
 
@@ -480,19 +561,22 @@ int ensure_side(fd_ctx* ctx, size_t n) {
   return FD_OK;
 }
 
-// Enqueue one call: reset the queues and the status words, then one persistent kernel per size
-// class -- on `stream` itself for a single class, else forked onto side streams and joined back.
-int enqueue(fd_ctx* ctx, std::vector<Group>& groups, int kind, Desc* d_desc, int* d_queue,
-            int* d_status, char* scratch, int batch, cudaStream_t stream, bool timing) {
-  FD_CUDA(ctx, cudaMemsetAsync(d_queue, 0, sizeof(int) * groups.size(), stream));
+// Enqueue one call: reset the queues and the status words, then each size class's launches in
+// order (one persistent kernel for log det/G; chains, boundary and wrap kernels for the force) --
+// on `stream` itself for a single class, else forked onto side streams and joined back.
+int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_tasks,
+            int* d_queue, int* d_status, char* scratch, int batch, cudaStream_t stream,
+            bool timing) {
+  const int nq = queue_count(groups);
+  FD_CUDA(ctx, cudaMemsetAsync(d_queue, 0, sizeof(int) * nq, stream));
   FD_CUDA(ctx, cudaMemsetAsync(d_status, 0xFF, sizeof(int) * batch, stream));  // pending
   if (timing) {
-    while (ctx->ev.size() < 2 * groups.size()) {
+    while ((int)ctx->ev.size() < 2 * nq) {
       cudaEvent_t e;
       FD_CUDA(ctx, cudaEventCreate(&e));
       ctx->ev.push_back(e);
     }
-    ctx->ev_used = 2 * (int)groups.size();
+    ctx->ev_used = 2 * nq;
   }
   const bool fork = groups.size() > 1;
   const size_t nside = std::min<size_t>(groups.size(), 8);
@@ -505,23 +589,47 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, int kind, Desc* d_desc, int
   for (size_t gi = 0; gi < groups.size(); ++gi) {
     Group& g = groups[gi];
     cudaStream_t s = fork ? ctx->side[gi % nside] : stream;
-    if (timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * gi], s));
-    if (g.mixed && kind == K_FORCE)
-      fd::launch_force_mixed(d_desc + g.desc_off, (int)g.idx.size(), d_queue + gi, d_status,
-                             scratch + g.scratch_off, g.ML, g.grid, s);
-    else if (g.mixed)
-      fd::launch_fwd_mixed(d_desc + g.desc_off, (int)g.idx.size(), d_queue + gi, d_status,
-                           scratch + g.scratch_off, g.ML, g.grid, s);
-    else if (kind == K_FWD)
-      fd::launch_fwd_fp64(d_desc + g.desc_off, (int)g.idx.size(), d_queue + gi, d_status,
-                          scratch + g.scratch_off, g.L, g.grid, s);
-    else
-      fd::launch_force_fp64(d_desc + g.desc_off, (int)g.idx.size(), d_queue + gi, d_status,
-                            scratch + g.scratch_off, g.L, g.grid, s);
-    ctx->last_launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
-    if (timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * gi + 1], s));
+    const Desc* dd = d_desc + g.desc_off;
+    const int nd = (int)g.idx.size();
+    char* scr = scratch + g.scratch_off;
+    for (size_t pi = 0; pi < g.ph.size(); ++pi) {
+      const Phase& P = g.ph[pi];
+      const int qi = g.qbase + (int)pi;
+      if (timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * qi], s));
+      if (P.which == 2 && g.tB.empty()) {  // single-block configurations: no boundary phase
+        if (timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * qi + 1], s));
+        continue;
+      }
+      switch (P.which) {
+        case 0:
+          if (P.mixed)
+            fd::launch_fwd_mixed(dd, nd, d_queue + qi, d_status, scr, P.ML, P.grid, s);
+          else
+            fd::launch_fwd_fp64(dd, nd, d_queue + qi, d_status, scr, P.L, P.grid, s);
+          break;
+        case 1:
+          if (P.mixed)
+            fd::launch_chain_mixed(dd, nd, d_queue + qi, d_status, scr, P.ML, P.grid, s);
+          else
+            fd::launch_chain_fp64(dd, nd, d_queue + qi, d_status, scr, P.L, P.grid, s);
+          break;
+        case 2:
+          fd::launch_boundary_fp64(dd, d_tasks + g.tB_off, (int)g.tB.size(), d_queue + qi,
+                                   d_status, scr, P.L, P.grid, s);
+          break;
+        default:
+          if (P.mixed)
+            fd::launch_wrap_mixed(dd, d_tasks + g.tC_off, (int)g.tC.size(), d_queue + qi,
+                                  d_status, scr, P.ML, P.grid, s);
+          else
+            fd::launch_wrap_fp64(dd, d_tasks + g.tC_off, (int)g.tC.size(), d_queue + qi,
+                                 d_status, scr, P.L, P.grid, s);
+      }
+      ctx->last_launches++;
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+      if (timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * qi + 1], s));
+    }
   }
   if (fork) {
     for (size_t i = 0; i < nside; ++i) {
@@ -544,19 +652,23 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double*
   // its operands in shared memory); larger classes run the FP64 kernels (fd_plan_query says so).
   std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
   size_t need = scratch_need(groups);
-  int rc = ensure(ctx, (size_t)batch, (size_t)batch, groups.size(), need);
+  const size_t ntasks = task_count(groups);
+  int rc = ensure(ctx, (size_t)batch, (size_t)batch, queue_count(groups), need, ntasks);
   if (rc != FD_OK) return rc;
   if (ctx->staging_pending) {
     FD_CUDA(ctx, cudaEventSynchronize(ctx->staging_done));
     ctx->staging_pending = false;
   }
-  build_descs(groups, probs, logdet, G, F, ctx->h_desc);
+  build_tables(groups, probs, logdet, G, F, ctx->scratch, ctx->h_desc, ctx->h_tasks);
   FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(Desc) * batch,
                                cudaMemcpyHostToDevice, stream));
+  if (ntasks)
+    FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_tasks, ctx->h_tasks, sizeof(fd::Task) * ntasks,
+                                 cudaMemcpyHostToDevice, stream));
   FD_CUDA(ctx, cudaEventRecord(ctx->staging_done, stream));
   ctx->staging_pending = true;
-  return enqueue(ctx, groups, kind, ctx->d_desc, ctx->d_queue, ctx->d_status, ctx->scratch,
-                 batch, stream, ctx->timing);
+  return enqueue(ctx, groups, ctx->d_desc, ctx->d_tasks, ctx->d_queue, ctx->d_status,
+                 ctx->scratch, batch, stream, ctx->timing);
 }
 
 // A captured call: its own descriptor table, queues, status words and scratch (so later calls
@@ -565,6 +677,7 @@ struct GraphObj {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   Desc* d_desc = nullptr;
+  fd::Task* d_tasks = nullptr;
   int* d_queue = nullptr;
   int* d_status = nullptr;
   char* scratch = nullptr;
@@ -577,6 +690,7 @@ void graph_free(GraphObj* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->d_desc) cudaFree(g->d_desc);
+  if (g->d_tasks) cudaFree(g->d_tasks);
   if (g->d_queue) cudaFree(g->d_queue);
   if (g->d_status) cudaFree(g->d_status);
   if (g->scratch) cudaFree(g->scratch);
@@ -619,6 +733,8 @@ void fd_ctx_destroy(fd_ctx* ctx) {
   if (ctx->d_desc) cudaFree(ctx->d_desc);
   if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
   if (ctx->d_queue) cudaFree(ctx->d_queue);
+  if (ctx->d_tasks) cudaFree(ctx->d_tasks);
+  if (ctx->h_tasks) cudaFreeHost(ctx->h_tasks);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
   for (auto e : ctx->ev) cudaEventDestroy(e);
@@ -639,7 +755,7 @@ int fd_reserve(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int pr
   std::vector<Group> groups =
       plan(ctx, batch, probs, (what & FD_WANT_FORCE) ? K_FORCE : K_FWD, prec);
   size_t need = scratch_need(groups);
-  rc = ensure(ctx, (size_t)batch, (size_t)batch, groups.size(), need);
+  rc = ensure(ctx, (size_t)batch, (size_t)batch, queue_count(groups), need, task_count(groups));
   if (rc != FD_OK) return rc;
   if (ctx->max_smem_optin > ctx->smem_attr) {
     FD_CUDA(ctx, fd::set_smem_fp64(ctx->max_smem_optin));
@@ -717,8 +833,9 @@ int fd_graph_create(fd_ctx* ctx, int batch, const fd_problem* probs, double* log
   GraphObj* g = new GraphObj();
   g->batch = batch;
   std::vector<Desc> h(batch);
-  build_descs(groups, probs, logdet, G, F, h.data());
   size_t need = scratch_need(groups);
+  const size_t ntasks = task_count(groups);
+  std::vector<fd::Task> ht(std::max<size_t>(ntasks, 1));
   cudaStream_t cs = nullptr;
   int saved_launches = ctx->last_launches;
   auto bail = [&](int code) {
@@ -729,16 +846,20 @@ int fd_graph_create(fd_ctx* ctx, int batch, const fd_problem* probs, double* log
   };
 #define FD_G(call)                                                do {                                                              cudaError_t e_ = (call);                                        if (e_ != cudaSuccess) return bail(cuda_fail(ctx, e_, #call));   } while (0)
   FD_G(cudaMalloc(&g->d_desc, sizeof(Desc) * batch));
-  FD_G(cudaMalloc(&g->d_queue, sizeof(int) * groups.size()));
+  FD_G(cudaMalloc(&g->d_tasks, sizeof(fd::Task) * ht.size()));
+  FD_G(cudaMalloc(&g->d_queue, sizeof(int) * std::max(1, queue_count(groups))));
   FD_G(cudaMalloc(&g->d_status, sizeof(int) * batch));
   FD_G(cudaMalloc(&g->scratch, std::max<size_t>(need, 256)));
+  build_tables(groups, probs, logdet, G, F, g->scratch, h.data(), ht.data());
   FD_G(cudaMemcpy(g->d_desc, h.data(), sizeof(Desc) * batch, cudaMemcpyHostToDevice));
+  FD_G(cudaMemcpy(g->d_tasks, ht.data(), sizeof(fd::Task) * ht.size(), cudaMemcpyHostToDevice));
   FD_G(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   rc = ensure_side(ctx, std::min<size_t>(groups.size(), 8));
   if (rc != FD_OK) return bail(rc);
   FD_G(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   ctx->last_launches = 0;
-  rc = enqueue(ctx, groups, kind, g->d_desc, g->d_queue, g->d_status, g->scratch, batch, cs, false);
+  rc = enqueue(ctx, groups, g->d_desc, g->d_tasks, g->d_queue, g->d_status, g->scratch, batch, cs,
+               false);
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(cs, &captured);
   g->graph = captured;
@@ -818,11 +939,12 @@ int fd_tune(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec,
       sf.push_back(Fp[c]);
     }
     const int three = prec == FD_PREC_MIXED_3XTF32 ? 1 : 0;
-    const long long key = tune_key(kind, g.mixed, g.mixed ? three : 0, g.nx);
+    std::vector<long long> keys;
+    for (auto& P : g.ph) keys.push_back(tune_key(P.which, P.mixed, P.mixed ? three : 0, g.nx));
     float best = 1e30f;
     int best_t = 0;
     for (int nth : {128, 256}) {
-      ctx->tuned[key] = nth;
+      for (long long key : keys) ctx->tuned[key] = nth;
       float tot = 0.f;
       for (int r = 0; r <= reps; ++r) {  // first run is a warm-up
         cudaEventRecord(e0, 0);
@@ -842,7 +964,7 @@ int fd_tune(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec,
       }
     }
     if (result != FD_OK) break;
-    ctx->tuned[key] = best_t;
+    for (long long key : keys) ctx->tuned[key] = best_t;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -946,20 +1068,23 @@ int fd_plan_query(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
   const int kind = (what & FD_WANT_FORCE) ? K_FORCE : K_FWD;
   std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
-  int k = 0;
+  int k = 0, total = 0;
   for (auto& g : groups) {
-    if (k >= max_groups) break;
-    int* o = info + 8 * k++;
-    o[0] = g.nx;
-    o[1] = (g.mixed ? 2 : 0) + (kind == K_FORCE ? 1 : 0);
-    o[2] = g.mixed ? g.ML.nthreads : g.L.nthreads;
-    o[3] = g.mixed ? g.ML.smem_bytes : g.L.smem_bytes;
-    o[4] = g.grid;
-    o[5] = g.occ;
-    o[6] = (int)((g.mixed ? g.ML.slot_bytes : g.L.slot_bytes) >> 10);
-    o[7] = (int)g.idx.size();
+    for (auto& P : g.ph) {
+      ++total;
+      if (k >= max_groups) continue;
+      int* o = info + 8 * k++;
+      o[0] = g.nx;
+      o[1] = P.which + (P.mixed ? 4 : 0);
+      o[2] = P.nthreads;
+      o[3] = P.smem;
+      o[4] = P.grid;
+      o[5] = P.occ;
+      o[6] = (int)(P.slot_bytes >> 10);
+      o[7] = P.ntasks;
+    }
   }
-  return (int)groups.size();
+  return total;
 }
 
 int fd_set_timing(fd_ctx* ctx, int on) {

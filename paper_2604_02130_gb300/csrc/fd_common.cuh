@@ -54,6 +54,36 @@ struct Desc {
   double* logdet;      // 2 doubles
   double2* G;          // nx*nx row-major or null
   double2* F;          // nt*nx row-major or null
+  double2* fws;        // force: per-configuration workspace (FWork), else null
+};
+
+// Per-configuration force workspace in global memory (the force is split into phases that run
+// on different CTAs):  left checkpoints L_b = B_{b ns}...B_1 as (X, T, log D) for b = 1..nb-1,
+// right checkpoints (B_Nt...B_{(b-1)ns+1})^H as (X, T, log D) for b = 2..nb, and the
+// block-boundary Green's functions G_{(b-1) ns} (column-major) for b = 1..nb.
+struct FWork {
+  double2* base;
+  int n, nb;
+  __host__ __device__ static size_t stride(int n) { return (size_t)2 * n * n + (n + 1) / 2; }
+  __host__ __device__ static size_t elems(int n, int nb) {
+    return (size_t)2 * (nb - 1) * stride(n) + (size_t)nb * n * n;
+  }
+  __device__ double2* LX(int b) const { return base + (size_t)(b - 1) * stride(n); }
+  __device__ double2* LT(int b) const { return LX(b) + (size_t)n * n; }
+  __device__ double* LD(int b) const { return (double*)(LX(b) + (size_t)2 * n * n); }
+  __device__ double2* RX(int b) const { return base + (size_t)(nb - 1 + b - 2) * stride(n); }
+  __device__ double2* RT(int b) const { return RX(b) + (size_t)n * n; }
+  __device__ double* RD(int b) const { return (double*)(RX(b) + (size_t)2 * n * n); }
+  // G_{(b-1) ns}; b = nb + 1 wraps to b = 1 (G_Nt = G_0)
+  __device__ double2* Gb(int b) const {
+    return base + (size_t)2 * (nb - 1) * stride(n) + (size_t)((b - 1) % nb) * n * n;
+  }
+};
+
+// A (configuration, block) work item of the boundary and wrap phases of the force.
+struct Task {
+  int desc;  // index into the launch's descriptor array
+  int b;     // block, 1-based
 };
 
 // Where each working matrix lives: shared memory (offset in bytes from the dynamic smem base)
@@ -118,7 +148,8 @@ struct MLayout {
   long long ws_bytes;    // slot bytes before the checkpoints
 };
 
-// status codes written per configuration (device side); the host pre-fills ST_PENDING
+// status codes written per configuration (device side); the host pre-fills ST_PENDING and the
+// phases of a configuration combine theirs with atomicMax (any failure wins over OK)
 enum { ST_OK = 0, ST_NUMERIC = 1, ST_TIMEOUT = 2, ST_PENDING = -1 };
 
 }  // namespace fd

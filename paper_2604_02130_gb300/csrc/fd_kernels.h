@@ -8,20 +8,30 @@ namespace fd {
 // FP64 path
 void launch_fwd_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                      const Layout& L, int grid, cudaStream_t stream);
-void launch_force_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
+// force phases: A chains (2 tasks per configuration), B boundary Green's functions, C wraps
+void launch_chain_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                        const Layout& L, int grid, cudaStream_t stream);
+void launch_boundary_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue,
+                          int* status, char* scratch, const Layout& L, int grid,
+                          cudaStream_t stream);
+void launch_wrap_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
+                      char* scratch, const Layout& L, int grid, cudaStream_t stream);
 cudaError_t set_smem_fp64(int bytes);
-int occupancy_fp64(bool force, int nthreads, int smem_bytes);  // -1 on error
-cudaError_t attrs_fp64(bool force, cudaFuncAttributes* a);
+// kernel ids: 0 log det/G, 1 force chains, 2 boundary, 3 wraps
+int occupancy_fp64(int which, int nthreads, int smem_bytes);  // -1 on error
+cudaError_t attrs_fp64(int which, cudaFuncAttributes* a);
 
 // mixed path (tcgen05 slice GEMMs)
 void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                       const MLayout& L, int grid, cudaStream_t stream);
-void launch_force_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
+void launch_chain_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                         const MLayout& L, int grid, cudaStream_t stream);
+void launch_wrap_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
+                       char* scratch, const MLayout& L, int grid, cudaStream_t stream);
 cudaError_t set_smem_mixed(int bytes);
-int occupancy_mixed(bool force, int nthreads, int smem_bytes);  // -1 on error
-cudaError_t attrs_mixed(bool force, cudaFuncAttributes* a);
+// kernel ids as for the FP64 kernels: 0 log det/G, 1 force chains, 3 wraps
+int occupancy_mixed(int which, int nthreads, int smem_bytes);  // -1 on error
+cudaError_t attrs_mixed(int which, cudaFuncAttributes* a);
 
 // FP64 throughput probe
 cudaError_t run_fp64_probe(int grid, int threads, int iters, double* out, cudaStream_t stream);

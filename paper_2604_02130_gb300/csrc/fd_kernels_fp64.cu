@@ -177,31 +177,31 @@ __device__ void wrap_backward(int n, const double* E, const double* Einv, const 
   });
 }
 
-__global__ void __launch_bounds__(256) k_force_fp64(const Desc* __restrict__ descs, int ndesc,
+// ------------------------------------------------------------------ force, phase A
+// Two independent chains per configuration (task q: configuration q/2, direction q%2).
+//   forward : X D T <- B_t ... B_1 with a QR every n_stab slices; left checkpoints after blocks
+//             1..nb-1; at the end log det and G_0 = G (also the boundary G of block 1).
+//   backward: the right products as adjoints, X_R D_R T_R <- B_{t+1}^H ... B_Nt^H, a QR every
+//             n_stab slices; right checkpoints at t = (b-1) n_stab for blocks b = nb..2.
+__global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ descs, int ndesc,
                                                      int* queue, int* status, char* scratch,
                                                      Layout L) {
   extern __shared__ __align__(16) char smem[];
   char* slotp = scratch + (size_t)blockIdx.x * L.slot_bytes;
-  double2* ckbase = (double2*)(slotp + L.ws_bytes);
   for (;;) {
     int* slot = (int*)(smem + L.smem_bytes - 16);
-    int c = grab(queue, slot);
-    if (c >= ndesc) return;
-    const Desc d = descs[c];
+    const int q = grab(queue, slot);
+    if (q >= 2 * ndesc) return;
+    const Desc d = descs[q >> 1];
+    const bool fwd = (q & 1) == 0;
     const int n = d.nx, ns = d.nstab, nb = d.nt / d.nstab;
+    const FWork W{d.fws, n, nb};
     Small s = carve_small(smem + L.small_off, n);
     if (tid() == 0) {
       s.misc[0] = 0;
       s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
     }
-    Bufs B = setup_bufs(smem, slotp, d, L, true);
-    // checkpoint b (1..nb-1): X (n*n), T (n*n), logD (n doubles, padded to n/2+1 complex)
-    const size_t ck_stride = (size_t)2 * n * n + (n + 1) / 2;
-    auto ckX = [&](int b) { return ckbase + (size_t)(b - 1) * ck_stride; };
-    auto ckT = [&](int b) { return ckbase + (size_t)(b - 1) * ck_stride + (size_t)n * n; };
-    auto ckD = [&](int b) { return (double*)(ckbase + (size_t)(b - 1) * ck_stride + (size_t)2 * n * n); };
-
-    // ---- forward pass with checkpoints
+    Bufs B = setup_bufs(smem, slotp, d, L, false);
     double2* X = B.X[0];
     double2* Xo = B.X[1];
     double2* T = B.T[0];
@@ -210,68 +210,120 @@ __global__ void __launch_bounds__(256) k_force_fp64(const Desc* __restrict__ des
     cta_identity(n, T);
     for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
     __syncthreads();
-    for (int b = 1; b <= nb; ++b) {
-      fwd_slices(n, B.E, d.phi, (b - 1) * ns, b * ns, X, Xo, s);
-      cta_reortho(n, X, Xo, T, To, s.logD, s);
-      double2* t1 = X; X = Xo; Xo = t1;
-      double2* t2 = T; T = To; To = t2;
-      if (b < nb) {
-        cta_copy(n * n, ckX(b), X);
-        cta_copy(n * n, ckT(b), T);
-        for (int k = tid(); k < n; k += nthr()) ckD(b)[k] = s.logD[k];
-        __syncthreads();
+    if (fwd) {
+      for (int b = 1; b <= nb; ++b) {
+        fwd_slices(n, B.E, d.phi, (b - 1) * ns, b * ns, X, Xo, s);
+        cta_reortho(n, X, Xo, T, To, s.logD, s);
+        double2* t1 = X; X = Xo; Xo = t1;
+        double2* t2 = T; T = To; To = t2;
+        if (b < nb) {
+          cta_copy(n * n, W.LX(b), X);
+          cta_copy(n * n, W.LT(b), T);
+          for (int k = tid(); k < n; k += nthr()) W.LD(b)[k] = s.logD[k];
+        }
       }
+      cta_assemble(n, X, T, s.logD, Xo, To, s, s.red + 2, s.red + 3);
+      const double re = s.red[2], im = wrap_pi(s.red[3]);
+      if (tid() == 0) {
+        d.logdet[0] = re;
+        d.logdet[1] = im;
+      }
+      cta_copy(n * n, W.Gb(1), To);
+      if (d.G) write_green(n, To, d.G);
+      if (tid() == 0)
+        atomicMax(status + d.user_index,
+                  (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
+    } else {
+      for (int b = nb; b >= 2; --b) {
+        bwd_slices(n, B.E, d.phi, (b - 1) * ns, b * ns, X, Xo, s);
+        cta_reortho(n, X, Xo, T, To, s.logD, s);
+        double2* t1 = X; X = Xo; Xo = t1;
+        double2* t2 = T; T = To; To = t2;
+        cta_copy(n * n, W.RX(b), X);
+        cta_copy(n * n, W.RT(b), T);
+        for (int k = tid(); k < n; k += nthr()) W.RD(b)[k] = s.logD[k];
+      }
+      if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     }
-    cta_assemble(n, X, T, s.logD, B.Ga, B.Ghi, s, s.red + 2, s.red + 3);
-    double re = s.red[2], im = wrap_pi(s.red[3]);
-    if (tid() == 0) {
-      d.logdet[0] = re;
-      d.logdet[1] = im;
-    }
-    if (d.G) write_green(n, B.Ghi, d.G);
     __syncthreads();
+  }
+}
 
-    // ---- backward (adjoint) sweep
-    double2* Glo = B.Glo;
-    double2* Ghi = B.Ghi;  // G_{b*ns}; starts as G_Nt = G_0
-    cta_identity(n, X);
-    cta_identity(n, T);
-    for (int k = tid(); k < n; k += nthr()) s.logDR[k] = 0.0;
-    __syncthreads();
-    const int h = (ns - 1) / 2;  // forward wraps per block; ns-1-h backward wraps
-    for (int b = nb; b >= 1; --b) {
-      const int t0 = (b - 1) * ns;  // boundary time of this block
-      bwd_slices(n, B.E, d.phi, t0, b * ns, X, Xo, s);
-      cta_reortho(n, X, Xo, T, To, s.logDR, s);
-      double2* t1 = X; X = Xo; Xo = t1;
-      double2* t2 = T; T = To; To = t2;
-      // G_{t0} at the boundary: left = checkpoint b-1 (identity for b = 1)
-      if (b == 1)
-        boundary_green(n, true, nullptr, nullptr, nullptr, X, T, s.logDR, B.Ga, B.Gb, Glo, s);
-      else
-        boundary_green(n, false, ckX(b - 1), ckT(b - 1), ckD(b - 1), X, T, s.logDR, B.Ga, B.Gb,
-                       Glo, s);
-      // F row t0 (slice t0+1) uses G_{t0}
-      emit_force_row(n, Glo, d.F + (size_t)t0 * n);
-      // forward wraps: G_{t0+j} = B_{t0+j} G_{t0+j-1} B_{t0+j}^{-1}, j = 1..h  (phi row t0+j-1)
-      const double2* src = Glo;
-      for (int j = 1; j <= h; ++j) {
-        wrap_forward(n, B.E, B.Einv, d.phi + (size_t)(t0 + j - 1) * n, src, B.Ga, B.Gb, s);
-        emit_force_row(n, B.Ga, d.F + (size_t)(t0 + j) * n);
-        src = B.Ga;
-      }
-      __syncthreads();
-      // backward wraps from G_{b*ns}: G_{q-1} = B_q^{-1} G_q B_q, q = b*ns .. t0+h+2 (phi row q-1)
-      src = Ghi;
-      for (int q = b * ns; q >= t0 + h + 2; --q) {
-        wrap_backward(n, B.E, B.Einv, d.phi + (size_t)(q - 1) * n, src, B.Ga, B.Gb, s);
-        emit_force_row(n, B.Ga, d.F + (size_t)(q - 1) * n);
-        src = B.Ga;
-      }
-      __syncthreads();
-      double2* tg = Ghi; Ghi = Glo; Glo = tg;
+// ------------------------------------------------------------------ force, phase B
+// Boundary Green's function of block b (b = 2..nb): G_{(b-1)ns} from the left checkpoint b-1
+// and the right checkpoint b (Section 7 steps 7-9 with t1 = t2; Section 5.3).
+__global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ descs,
+                                                        const Task* __restrict__ tasks,
+                                                        int ntasks, int* queue, int* status,
+                                                        char* scratch, Layout L) {
+  extern __shared__ __align__(16) char smem[];
+  char* slotp = scratch + (size_t)blockIdx.x * L.slot_bytes;
+  for (;;) {
+    int* slot = (int*)(smem + L.smem_bytes - 16);
+    const int q = grab(queue, slot);
+    if (q >= ntasks) return;
+    const Task tk = tasks[q];
+    const Desc d = descs[tk.desc];
+    const int n = d.nx, nb = d.nt / d.nstab, b = tk.b;
+    const FWork W{d.fws, n, nb};
+    Small s = carve_small(smem + L.small_off, n);
+    if (tid() == 0) {
+      s.misc[0] = 0;
+      s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2 + b);
     }
-    finish_status(d, s, status, re, im);
+    double2* Ma = (double2*)place(smem, slotp, L, B_GA);
+    double2* Mb = (double2*)place(smem, slotp, L, B_GB);
+    __syncthreads();
+    boundary_green(n, false, W.LX(b - 1), W.LT(b - 1), W.LD(b - 1), W.RX(b), W.RT(b), W.RD(b),
+                   Ma, Mb, W.Gb(b), s);
+    if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ force, phase C
+// Block b: F row (b-1)ns from G_{(b-1)ns}; forward wraps from it for the first (n_stab-1)/2
+// slices, backward wraps from G_{b ns} (the next block's boundary, G_0 for the last block).
+__global__ void __launch_bounds__(256) k_wrap_fp64(const Desc* __restrict__ descs,
+                                                    const Task* __restrict__ tasks, int ntasks,
+                                                    int* queue, int* status, char* scratch,
+                                                    Layout L) {
+  extern __shared__ __align__(16) char smem[];
+  char* slotp = scratch + (size_t)blockIdx.x * L.slot_bytes;
+  for (;;) {
+    int* slot = (int*)(smem + L.smem_bytes - 16);
+    const int q = grab(queue, slot);
+    if (q >= ntasks) return;
+    const Task tk = tasks[q];
+    const Desc d = descs[tk.desc];
+    const int n = d.nx, ns = d.nstab, nb = d.nt / d.nstab, b = tk.b;
+    const FWork W{d.fws, n, nb};
+    Small s = carve_small(smem + L.small_off, n);
+    if (tid() == 0) s.misc[0] = 0;
+    const double* E = L.in_smem[B_E] ? (double*)(smem + L.off[B_E]) : d.E;
+    const double* Einv = L.in_smem[B_EINV] ? (double*)(smem + L.off[B_EINV]) : d.Einv;
+    if (L.in_smem[B_E]) cta_load_real(n * n, (double*)E, d.E);
+    if (L.in_smem[B_EINV]) cta_load_real(n * n, (double*)Einv, d.Einv);
+    double2* Ga = (double2*)place(smem, slotp, L, B_GA);
+    double2* Gb = (double2*)place(smem, slotp, L, B_GB);
+    __syncthreads();
+    const int t0 = (b - 1) * ns, h = (ns - 1) / 2;
+    const double2* Glo = W.Gb(b);
+    emit_force_row(n, Glo, d.F + (size_t)t0 * n);
+    const double2* src = Glo;
+    for (int j = 1; j <= h; ++j) {
+      wrap_forward(n, E, Einv, d.phi + (size_t)(t0 + j - 1) * n, src, Ga, Gb, s);
+      emit_force_row(n, Ga, d.F + (size_t)(t0 + j) * n);
+      src = Ga;
+    }
+    __syncthreads();
+    src = W.Gb(b + 1);
+    for (int qq = b * ns; qq >= t0 + h + 2; --qq) {
+      wrap_backward(n, E, Einv, d.phi + (size_t)(qq - 1) * n, src, Ga, Gb, s);
+      emit_force_row(n, Ga, d.F + (size_t)(qq - 1) * n);
+      src = Ga;
+    }
+    __syncthreads();
   }
 }
 
@@ -279,22 +331,39 @@ void launch_fwd_fp64(const Desc* descs, int ndesc, int* queue, int* status, char
                      const Layout& L, int grid, cudaStream_t stream) {
   k_fwd_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch, L);
 }
-void launch_force_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
+void launch_chain_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                        const Layout& L, int grid, cudaStream_t stream) {
-  k_force_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch,
+  k_chain_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch,
                                                             L);
 }
-int occupancy_fp64(bool force, int nthreads, int smem_bytes) {
+void launch_boundary_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue,
+                          int* status, char* scratch, const Layout& L, int grid,
+                          cudaStream_t stream) {
+  k_boundary_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue, status,
+                                                               scratch, L);
+}
+void launch_wrap_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
+                      char* scratch, const Layout& L, int grid, cudaStream_t stream) {
+  k_wrap_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue, status,
+                                                           scratch, L);
+}
+static const void* fp64_kernel(int which) {
+  switch (which) {
+    case 1: return (const void*)k_chain_fp64;
+    case 2: return (const void*)k_boundary_fp64;
+    case 3: return (const void*)k_wrap_fp64;
+    default: return (const void*)k_fwd_fp64;
+  }
+}
+int occupancy_fp64(int which, int nthreads, int smem_bytes) {
   int nb = 0;
-  cudaError_t e;
-  if (force)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_fp64, nthreads, smem_bytes);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_fp64, nthreads, smem_bytes);
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fp64_kernel(which), nthreads, smem_bytes);
   return e == cudaSuccess ? nb : -1;
 }
 cudaError_t set_smem_fp64(int bytes) {
-  for (const void* k : {(const void*)k_fwd_fp64, (const void*)k_force_fp64}) {
+  for (const void* k : {(const void*)k_fwd_fp64, (const void*)k_chain_fp64,
+                        (const void*)k_boundary_fp64, (const void*)k_wrap_fp64}) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -303,8 +372,8 @@ cudaError_t set_smem_fp64(int bytes) {
   }
   return cudaSuccess;
 }
-cudaError_t attrs_fp64(bool force, cudaFuncAttributes* a) {
-  return cudaFuncGetAttributes(a, force ? (const void*)k_force_fp64 : (const void*)k_fwd_fp64);
+cudaError_t attrs_fp64(int which, cudaFuncAttributes* a) {
+  return cudaFuncGetAttributes(a, fp64_kernel(which));
 }
 
 }  // namespace fd

@@ -299,10 +299,116 @@ __global__ void __launch_bounds__(256) k_fwd_mixed(const Desc* __restrict__ desc
 }
 
 // ------------------------------------------------------------------ force (mixed)
-// Forward pass as k_fwd_mixed plus FP64 checkpoints; adjoint sweep with the right products
-// X_R <- diag(e^{-i phi_s}) E X_R on the tensor core (the conjugate phase applied in the
-// epilogue), FP64 QR and boundary Green's function, and the wraps inside a block on the tensor
-// core as two MMAs each:
+// Phase A: the forward and backward chains of the force as separate tasks (task q:
+// configuration q/2, direction q%2); slices on the tensor core, QR in FP64; checkpoints and
+// G_0 go to the configuration's global workspace (FWork).  The backward chain multiplies the
+// right products as adjoints, X_R <- diag(e^{-i phi_s}) E X_R, the conjugate phase applied in the
+// epilogue.
+__global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ descs, int ndesc,
+                                                      int* queue, int* status, char* scratch,
+                                                      MLayout L) {
+  extern __shared__ __align__(128) char smem[];
+  char* slot = scratch + (size_t)blockIdx.x * L.slot_bytes;
+  MixedSmem m = mixed_smem(smem, slot, L);
+  if (warp_id() == 0) tc::tmem_alloc(m.taddr, (uint32_t)L.tmem_cols);
+  if (tid() == 0) tc::mbar_init(m.mbar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *m.taddr;
+  uint32_t phase = 0;
+  const int n = L.n;
+  double2* T = (double2*)((L.t_smem ? smem : slot) + L.t0_off);
+  double2* To = (double2*)((L.t_smem ? smem : slot) + L.t1_off);
+  const Scale one{nullptr, false};
+  for (;;) {
+    const int q = grab_m(queue, m.qslot);
+    if (q >= 2 * ndesc) break;
+    const Desc d = descs[q >> 1];
+    const bool fwd = (q & 1) == 0;
+    const int ns = d.nstab, nb = d.nt / d.nstab;
+    const FWork W{d.fws, n, nb};
+    Small s = carve_small(smem + L.small_off, n);
+    float2* pf = (float2*)s.ph;  // FP32 phases: two halves of n
+    if (tid() == 0) {
+      s.misc[0] = 0;
+      s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
+    }
+    fill_a(L, m.a_hi, m.a_lo, d.E);
+    cta_identity(n, T);
+    for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
+    bool ok = true;
+    if (fwd) {
+      for (int b = 1; b <= nb && ok; ++b) {
+        const int t0 = (b - 1) * ns;
+        cta_phase32(n, pf, d.phi + (size_t)t0 * n, 1.f);
+        __syncthreads();
+        fill_b2(L, m, b == 1 ? nullptr : m.Xn, Scale{pf, false}, one);
+        for (int t = t0; t < t0 + ns; ++t) {
+          const bool last = t + 1 == t0 + ns;
+          float2* phn = pf + ((t - t0 + 1) & 1) * n;
+          if (!last) cta_phase32(n, phn, d.phi + (size_t)(t + 1) * n, 1.f);
+          if (!slice_mma(L, m, tbase, phase)) { ok = false; break; }
+          slice_epilogue(L, m, tbase, phn, !last);
+        }
+        if (!ok) break;
+        cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
+        double2* t2 = T; T = To; To = t2;
+        if (b < nb) {
+          cta_copy(n * n, W.LX(b), m.Xn);
+          cta_copy(n * n, W.LT(b), T);
+          for (int k = tid(); k < n; k += nthr()) W.LD(b)[k] = s.logD[k];
+        }
+      }
+      if (ok) {
+        double2* G0 = W.Gb(1);
+        cta_assemble(n, m.Xn, T, s.logD, m.Xc, G0, s, s.red + 2, s.red + 3);
+        const double re = s.red[2], im = wrap_pi(s.red[3]);
+        if (tid() == 0) {
+          d.logdet[0] = re;
+          d.logdet[1] = im;
+          atomicMax(status + d.user_index,
+                    (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
+        }
+        if (d.G)
+          for (int e = tid(); e < n * n; e += nthr()) d.G[e] = G0[(e / n) + (e % n) * n];
+      }
+    } else {
+      for (int b = nb; b >= 2 && ok; --b) {
+        const int t0 = (b - 1) * ns;
+        fill_b2(L, m, b == nb ? nullptr : m.Xn, one, one);
+        for (int t = b * ns - 1; t >= t0; --t) {
+          const bool last = t == t0;
+          cta_phase32(n, pf, d.phi + (size_t)t * n, -1.f);
+          if (!slice_mma(L, m, tbase, phase)) { ok = false; break; }
+          if (last)
+            epilogue<TO_FP64>(L, m, tbase, Scale{pf, false}, one, m.Xc, nullptr);
+          else
+            epilogue<TO_B_K>(L, m, tbase, Scale{pf, false}, one, nullptr, nullptr);
+        }
+        if (!ok) break;
+        cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
+        double2* t2 = T; T = To; To = t2;
+        cta_copy(n * n, W.RX(b), m.Xn);
+        cta_copy(n * n, W.RT(b), T);
+        for (int k = tid(); k < n; k += nthr()) W.RD(b)[k] = s.logD[k];
+      }
+      if (ok && tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
+    }
+    if (!ok) {
+      if (tid() == 0) atomicMax(status + d.user_index, ST_TIMEOUT);
+      break;
+    }
+    __syncthreads();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp_id() == 0) tc::tmem_dealloc(tbase, (uint32_t)L.tmem_cols);
+}
+
+// Phase C on the tensor core: block b's force rows.  Row (b-1)ns from the boundary G_{(b-1)ns};
+// the wraps inside the block as two MMAs each (both TMEM layouts alternate, so no transposes):
 //   forward  G_s     = E [D_s G_{s-1} D_s^*] E^{-1}:  MMA(A = E, B = D G D^*) gives
 //            W = E (D G D^*) with lane = row; written lane-as-N it is the B operand of
 //            MMA(A = E^{-1}), whose result E^{-1} W^T = G_s^T leaves column m of G_s in lane m.
@@ -310,9 +416,10 @@ __global__ void __launch_bounds__(256) k_fwd_mixed(const Desc* __restrict__ desc
 //            B = (E^{-1} G_q)^T) leaves column m of E^{-1} G_q E in lane m.
 // The diagonal (the force row) is read straight out of the second accumulator; the phases of
 // the next wrap are applied while writing the next B operand.
-__global__ void __launch_bounds__(256) k_force_mixed(const Desc* __restrict__ descs, int ndesc,
-                                                      int* queue, int* status, char* scratch,
-                                                      MLayout L) {
+__global__ void __launch_bounds__(256) k_wrap_mixed(const Desc* __restrict__ descs,
+                                                     const Task* __restrict__ tasks, int ntasks,
+                                                     int* queue, int* status, char* scratch,
+                                                     MLayout L) {
   extern __shared__ __align__(128) char smem[];
   char* slot = scratch + (size_t)blockIdx.x * L.slot_bytes;
   MixedSmem m = mixed_smem(smem, slot, L);
@@ -326,150 +433,73 @@ __global__ void __launch_bounds__(256) k_force_mixed(const Desc* __restrict__ de
   const uint32_t tbase = *m.taddr;
   uint32_t phase = 0;
   const int n = L.n;
-  double2* T = (double2*)((L.t_smem ? smem : slot) + L.t0_off);
-  double2* To = (double2*)((L.t_smem ? smem : slot) + L.t1_off);
-  char* gb = L.g_smem ? smem : slot;
-  double2* Glo = (double2*)(gb + L.g_off[0]);
-  double2* Ghi = (double2*)(gb + L.g_off[1]);
-  double2* Ga = (double2*)(gb + L.g_off[2]);
-  double2* Gb = (double2*)(gb + L.g_off[3]);
-  double2* ckbase = (double2*)(slot + L.ws_bytes);
   const Scale one{nullptr, false};
+  int last_desc = -1;
   for (;;) {
-    int c = grab_m(queue, m.qslot);
-    if (c >= ndesc) break;
-    const Desc d = descs[c];
-    const int ns = d.nstab, nb = d.nt / d.nstab;
-    const size_t ck_stride = (size_t)2 * n * n + (n + 1) / 2;
-    auto ckX = [&](int b) { return ckbase + (size_t)(b - 1) * ck_stride; };
-    auto ckT = [&](int b) { return ckbase + (size_t)(b - 1) * ck_stride + (size_t)n * n; };
-    auto ckD = [&](int b) {
-      return (double*)(ckbase + (size_t)(b - 1) * ck_stride + (size_t)2 * n * n);
-    };
+    const int q = grab_m(queue, m.qslot);
+    if (q >= ntasks) break;
+    const Task tk = tasks[q];
+    const Desc d = descs[tk.desc];
+    const int ns = d.nstab, nb = d.nt / d.nstab, b = tk.b;
+    const FWork W{d.fws, n, nb};
     Small s = carve_small(smem + L.small_off, n);
-    float2* pf = (float2*)s.ph;  // FP32 phases: two halves of n
-    if (tid() == 0) {
-      s.misc[0] = 0;
-      s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
+    float2* pf = (float2*)s.ph;
+    if (tk.desc != last_desc) {  // tasks of one configuration are contiguous: reload E only then
+      fill_a(L, m.a_hi, m.a_lo, d.E);
+      fill_a(L, e2_hi, e2_lo, d.Einv);
+      last_desc = tk.desc;
     }
-    fill_a(L, m.a_hi, m.a_lo, d.E);
-    fill_a(L, e2_hi, e2_lo, d.Einv);
-    cta_identity(n, T);
-    for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
     bool ok = true;
-    // ---- forward pass with checkpoints
-    for (int b = 1; b <= nb && ok; ++b) {
-      const int t0 = (b - 1) * ns;
-      cta_phase32(n, pf, d.phi + (size_t)t0 * n, 1.f);
-      __syncthreads();
-      fill_b2(L, m, b == 1 ? nullptr : m.Xn, Scale{pf, false}, one);
-      for (int t = t0; t < t0 + ns; ++t) {
-        const bool last = t + 1 == t0 + ns;
-        float2* phn = pf + ((t - t0 + 1) & 1) * n;
-        if (!last) cta_phase32(n, phn, d.phi + (size_t)(t + 1) * n, 1.f);
-        if (!slice_mma(L, m, tbase, phase)) { ok = false; break; }
-        slice_epilogue(L, m, tbase, phn, !last);
-      }
-      if (!ok) break;
-      cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
-      double2* t2 = T; T = To; To = t2;
-      if (b < nb) {
-        cta_copy(n * n, ckX(b), m.Xn);
-        cta_copy(n * n, ckT(b), T);
-        for (int k = tid(); k < n; k += nthr()) ckD(b)[k] = s.logD[k];
+    const int t0 = (b - 1) * ns, h = (ns - 1) / 2;
+    const double2* Glo = W.Gb(b);
+    emit_force_row(n, Glo, d.F + (size_t)t0 * n);
+    // forward wraps from G_{t0}: G_{t0+j}, j = 1..h; slice t0+j uses phi row t0+j-1
+    for (int j = 1; j <= h && ok; ++j) {
+      float2* ph = pf + ((j & 1) ? n : 0);
+      cta_phase32(n, ph, d.phi + (size_t)(t0 + j - 1) * n, 1.f);
+      if (j == 1) {
         __syncthreads();
+        fill_b2(L, m, Glo, Scale{ph, false}, Scale{ph, true});
       }
-    }
-    if (!ok) {
-      if (tid() == 0) status[d.user_index] = ST_TIMEOUT;
-      break;
-    }
-    cta_assemble(n, m.Xn, T, s.logD, m.Xc, Ghi, s, s.red + 2, s.red + 3);
-    const double re = s.red[2], im = wrap_pi(s.red[3]);
-    if (tid() == 0) {
-      d.logdet[0] = re;
-      d.logdet[1] = im;
-    }
-    if (d.G)
-      for (int e = tid(); e < n * n; e += nthr()) d.G[e] = Ghi[(e / n) + (e % n) * n];
-    // ---- adjoint sweep
-    cta_identity(n, T);
-    for (int k = tid(); k < n; k += nthr()) s.logDR[k] = 0.0;
-    __syncthreads();
-    const int h = (ns - 1) / 2;
-    for (int b = nb; b >= 1 && ok; --b) {
-      const int t0 = (b - 1) * ns;
-      // right product: X_R <- diag(e^{-i phi_t}) E X_R, t = b*ns-1 .. t0 (rows of phi)
-      fill_b2(L, m, b == nb ? nullptr : m.Xn, one, one);
-      for (int t = b * ns - 1; t >= t0; --t) {
-        const bool last = t == t0;
-        cta_phase32(n, pf, d.phi + (size_t)t * n, -1.f);
-        if (!slice_mma(L, m, tbase, phase)) { ok = false; break; }
-        if (last)
-          epilogue<TO_FP64>(L, m, tbase, Scale{pf, false}, one, m.Xc, nullptr);
-        else
-          epilogue<TO_B_K>(L, m, tbase, Scale{pf, false}, one, nullptr, nullptr);
-      }
-      if (!ok) break;
-      cta_reortho(n, m.Xc, m.Xn, T, To, s.logDR, s);
-      double2* t2 = T; T = To; To = t2;
-      if (b == 1)
-        boundary_green(n, true, nullptr, nullptr, nullptr, m.Xn, T, s.logDR, Ga, Gb, Glo, s);
+      if (!mma_ab(L, m, m.a_hi, m.a_lo, tbase, phase)) { ok = false; break; }
+      epilogue<TO_B_N>(L, m, tbase, one, one, nullptr, nullptr);
+      float2* phn = pf + ((j & 1) ? 0 : n);
+      const bool more = j < h;
+      if (more) cta_phase32(n, phn, d.phi + (size_t)(t0 + j) * n, 1.f);
+      if (!mma_ab(L, m, e2_hi, e2_lo, tbase, phase)) { ok = false; break; }
+      if (more)
+        epilogue<TO_B_N>(L, m, tbase, Scale{phn, true}, Scale{phn, false}, nullptr,
+                         d.F + (size_t)(t0 + j) * n);
       else
-        boundary_green(n, false, ckX(b - 1), ckT(b - 1), ckD(b - 1), m.Xn, T, s.logDR, Ga, Gb,
-                       Glo, s);
-      emit_force_row(n, Glo, d.F + (size_t)t0 * n);
-      // forward wraps from G_{t0}: G_{t0+j}, j = 1..h; slice t0+j uses phi row t0+j-1
-      for (int j = 1; j <= h && ok; ++j) {
-        float2* ph = pf + ((j & 1) ? n : 0);
-        cta_phase32(n, ph, d.phi + (size_t)(t0 + j - 1) * n, 1.f);
-        if (j == 1) {
-          __syncthreads();
-          fill_b2(L, m, Glo, Scale{ph, false}, Scale{ph, true});
-        }
-        if (!mma_ab(L, m, m.a_hi, m.a_lo, tbase, phase)) { ok = false; break; }
-        epilogue<TO_B_N>(L, m, tbase, one, one, nullptr, nullptr);
-        // the next wrap's phase (slice t0+j+1, phi row t0+j) is applied while writing B
-        float2* phn = pf + ((j & 1) ? 0 : n);
-        const bool more = j < h;
-        if (more) cta_phase32(n, phn, d.phi + (size_t)(t0 + j) * n, 1.f);
-        if (!mma_ab(L, m, e2_hi, e2_lo, tbase, phase)) { ok = false; break; }
-        if (more)
-          epilogue<TO_B_N>(L, m, tbase, Scale{phn, true}, Scale{phn, false}, nullptr,
-                           d.F + (size_t)(t0 + j) * n);
-        else
-          epilogue<NONE>(L, m, tbase, one, one, nullptr, d.F + (size_t)(t0 + j) * n);
+        epilogue<NONE>(L, m, tbase, one, one, nullptr, d.F + (size_t)(t0 + j) * n);
+    }
+    // backward wraps from G_{b*ns}: G_{q-1}, q = b*ns .. t0+h+2; slice q uses phi row q-1
+    bool first = true;
+    for (int qq = b * ns; qq >= t0 + h + 2 && ok; --qq) {
+      float2* ph = pf + ((qq & 1) ? n : 0);
+      cta_phase32(n, ph, d.phi + (size_t)(qq - 1) * n, 1.f);
+      if (first) {
+        __syncthreads();
+        fill_b2(L, m, W.Gb(b + 1), one, one);
+        first = false;
       }
-      // backward wraps from G_{b*ns}: G_{q-1}, q = b*ns .. t0+h+2; slice q uses phi row q-1
-      bool first = true;
-      for (int q = b * ns; q >= t0 + h + 2 && ok; --q) {
-        float2* ph = pf + ((q & 1) ? n : 0);
-        cta_phase32(n, ph, d.phi + (size_t)(q - 1) * n, 1.f);
-        if (first) {
-          __syncthreads();
-          fill_b2(L, m, Ghi, one, one);
-          first = false;
-        }
-        if (!mma_ab(L, m, e2_hi, e2_lo, tbase, phase)) { ok = false; break; }
-        epilogue<TO_B_N>(L, m, tbase, one, one, nullptr, nullptr);
-        if (!mma_ab(L, m, m.a_hi, m.a_lo, tbase, phase)) { ok = false; break; }
-        // lane m holds column m of E^{-1} G_q E; G_{q-1} = D^* (.) D has the same diagonal.
-        // Next B: B(n = m, k = i) = G_{q-1}[i, m] = conj(ph_i) X[i, m] ph_m
-        const bool more = q - 1 >= t0 + h + 2;
-        if (more)
-          epilogue<TO_B_N>(L, m, tbase, Scale{ph, false}, Scale{ph, true}, nullptr,
-                           d.F + (size_t)(q - 1) * n);
-        else
-          epilogue<NONE>(L, m, tbase, one, one, nullptr, d.F + (size_t)(q - 1) * n);
-      }
-      double2* tg = Ghi; Ghi = Glo; Glo = tg;
+      if (!mma_ab(L, m, e2_hi, e2_lo, tbase, phase)) { ok = false; break; }
+      epilogue<TO_B_N>(L, m, tbase, one, one, nullptr, nullptr);
+      if (!mma_ab(L, m, m.a_hi, m.a_lo, tbase, phase)) { ok = false; break; }
+      // lane m holds column m of E^{-1} G_q E; G_{q-1} = D^* (.) D has the same diagonal.
+      // Next B: B(n = m, k = i) = G_{q-1}[i, m] = conj(ph_i) X[i, m] ph_m
+      const bool more = qq - 1 >= t0 + h + 2;
+      if (more)
+        epilogue<TO_B_N>(L, m, tbase, Scale{ph, false}, Scale{ph, true}, nullptr,
+                         d.F + (size_t)(qq - 1) * n);
+      else
+        epilogue<NONE>(L, m, tbase, one, one, nullptr, d.F + (size_t)(qq - 1) * n);
     }
     if (!ok) {
-      if (tid() == 0) status[d.user_index] = ST_TIMEOUT;
+      if (tid() == 0) atomicMax(status + d.user_index, ST_TIMEOUT);
       break;
     }
-    if (tid() == 0)
-      status[d.user_index] = (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK;
+    __syncthreads();
   }
   tc::fence_before();
   __syncthreads();
@@ -477,10 +507,15 @@ __global__ void __launch_bounds__(256) k_force_mixed(const Desc* __restrict__ de
   if (warp_id() == 0) tc::tmem_dealloc(tbase, (uint32_t)L.tmem_cols);
 }
 
-void launch_force_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
+void launch_chain_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                         const MLayout& L, int grid, cudaStream_t stream) {
-  k_force_mixed<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status,
-                                                             scratch, L);
+  k_chain_mixed<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch,
+                                                             L);
+}
+void launch_wrap_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
+                       char* scratch, const MLayout& L, int grid, cudaStream_t stream) {
+  k_wrap_mixed<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue, status,
+                                                            scratch, L);
 }
 
 void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
@@ -489,7 +524,8 @@ void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, cha
                                                            L);
 }
 cudaError_t set_smem_mixed(int bytes) {
-  for (const void* k : {(const void*)k_fwd_mixed, (const void*)k_force_mixed}) {
+  for (const void* k :
+       {(const void*)k_fwd_mixed, (const void*)k_chain_mixed, (const void*)k_wrap_mixed}) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -498,16 +534,20 @@ cudaError_t set_smem_mixed(int bytes) {
   }
   return cudaSuccess;
 }
-cudaError_t attrs_mixed(bool force, cudaFuncAttributes* a) {
-  return cudaFuncGetAttributes(a, force ? (const void*)k_force_mixed : (const void*)k_fwd_mixed);
+static const void* mixed_kernel(int which) {
+  switch (which) {
+    case 1: return (const void*)k_chain_mixed;
+    case 3: return (const void*)k_wrap_mixed;
+    default: return (const void*)k_fwd_mixed;
+  }
 }
-int occupancy_mixed(bool force, int nthreads, int smem_bytes) {
+cudaError_t attrs_mixed(int which, cudaFuncAttributes* a) {
+  return cudaFuncGetAttributes(a, mixed_kernel(which));
+}
+int occupancy_mixed(int which, int nthreads, int smem_bytes) {
   int nb = 0;
-  cudaError_t e;
-  if (force)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_mixed, nthreads, smem_bytes);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fwd_mixed, nthreads, smem_bytes);
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mixed_kernel(which), nthreads, smem_bytes);
   return e == cudaSuccess ? nb : -1;
 }
 
