@@ -216,14 +216,6 @@ def _measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def _tensor_flops(nx, nt, n_stab):
-    """Flops of the steps the mixed path runs on tensor cores: slice products and right products
-    (4 Nx^3 each per slice) and the in-block wraps (8 Nx^3 each)."""
-    n3 = float(nx) ** 3
-    nb = nt // n_stab
-    return 4 * n3 * nt * 2 + 8 * n3 * (nt - nb)
-
-
 def _time_batch(batch, ctx, steps, flush, stream, barrier, sample_clocks, gpu):
     import torch
 
@@ -242,7 +234,7 @@ def _time_batch(batch, ctx, steps, flush, stream, barrier, sample_clocks, gpu):
             batch.run()
             ev[k][1].record(stream)
             launches += ctx.last_launch_count()
-            kernel_ms.append(sum(ctx.last_kernel_ms()))
+            kernel_ms.append(ctx.last_kernel_ms())
         barrier()
     finally:
         if clk:
@@ -323,8 +315,6 @@ def run_ours(args):
 
     n_total = w_batch * ws
     fl = force_flops(nx, nt, ns)
-    fl_tensor = _tensor_flops(nx, nt, ns)
-    fl_fp64_mixed = fl["total"] - fl_tensor
 
     # ---- headline path: device-resident timing, L2 flushed between steps
     batch = make(args.prec)
@@ -366,33 +356,48 @@ def run_ours(args):
         ms64 = allmax(r64["total_ms"]) / max(3, args.steps // 2)
         fp64 = {"value": n_total / (ms64 * 1e-3), "unit": "configs/s", "ms_per_step": ms64,
                 "tflops": fl["total"] * n_total / (ms64 * 1e-3) / 1e12,
-                "kernel_ms": statistics.mean(r64["kernel_ms"])}
+                "kernel_ms": [statistics.mean(k[i] for k in r64["kernel_ms"]) for i in range(3)]}
 
     if rank != 0:
         torch.distributed.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel (the force kernel is the step's only launch)
+    # ---- roofline: the step is three launches (chains, boundary Green's functions, wraps);
+    #      the chain kernel dominates.  Per-launch durations from CUDA events on the launch stream.
+    from paper_2604_02130_gb300.flops import force_phase_flops
+
     peaks, peak_src = _measured_peaks()
     peak_fp64 = ctx.measure_fp64_peak() / 1e3
-    k_ms = statistics.mean(head["kernel_ms"])
+    tf32_peak = peaks["bf16_tflops"] / 2.0
     mixed = args.prec != "fp64"
-    kname = "k_force_mixed" if mixed else "k_force_fp64"
-    fp64_work = (fl_fp64_mixed if mixed else fl["total"]) * w_batch
-    achieved = fp64_work / (k_ms * 1e-3) / 1e12
+    pf = force_phase_flops(nx, nt, ns, mixed)
+    per_launch = [statistics.mean(k[i] for k in head["kernel_ms"]) for i in range(3)]
+    names = ["k_chain_mixed" if mixed else "k_chain_fp64", "k_boundary_fp64",
+             "k_wrap_mixed" if mixed else "k_wrap_fp64"]
+    phases = []
+    for i, key in enumerate("ABC"):
+        ms = per_launch[i]
+        f64 = pf[key]["fp64"] * w_batch / (ms * 1e-3) / 1e12
+        tns = pf[key]["tensor"] * w_batch / (ms * 1e-3) / 1e12
+        phases.append({"kernel": names[i], "ms": ms, "fp64_tflops": f64,
+                       "fp64_frac": f64 / peak_fp64, "tensor_tflops": tns,
+                       "tensor_frac": tns / tf32_peak})
+    k_ms = per_launch[0]
+    achieved = phases[0]["fp64_tflops"]
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-            "frac": achieved / peak_fp64, "traffic": _traffic(kname, name, args.prec),
-            "kernel": kname, "kernel_ms": k_ms,
-            "what": "FP64 algorithmic work of the kernel (QR, boundary G, assembly%s) per launch "
-                    "over its CUDA-event duration" % ("" if mixed else ", slices, wraps"),
-            "peak_source": "FP64 DFMA probe over all SMs in this run (fd_measure_fp64_peak)"}
+            "frac": achieved / peak_fp64, "traffic": _traffic(names[0], name, args.prec),
+            "kernel": names[0], "kernel_ms": k_ms,
+            "what": "FP64 algorithmic work of the chain kernel (QRs, assembly%s) per launch over "
+                    "its CUDA-event duration" % ("" if mixed else ", slice products"),
+            "peak_source": "FP64 DFMA probe over all SMs in this run (fd_measure_fp64_peak)",
+            "fp64_issue_cycles": dict(zip(("one_lane", "full_warp", "one_of_8_warps"),
+                                          ctx.measure_fp64_issue())),
+            "phases": phases}
     if mixed:
-        tf32_peak = peaks["bf16_tflops"] / 2.0
-        t_ach = fl_tensor * w_batch / (k_ms * 1e-3) / 1e12
-        roof["tensor"] = {"achieved": t_ach, "peak": tf32_peak, "unit": "TFLOP/s",
-                          "frac": t_ach / tf32_peak,
-                          "what": "tensor-core work (slice and right products, wraps; one "
-                                  "product counted once, not x3 for split TF32)",
+        roof["tensor"] = {"achieved": phases[0]["tensor_tflops"], "peak": tf32_peak,
+                          "unit": "TFLOP/s", "frac": phases[0]["tensor_tflops"] / tf32_peak,
+                          "what": "tensor-core work of the chain kernel (slice and right "
+                                  "products; a product counted once, not x3 for split TF32)",
                           "peak_source": "%s bf16 dense x 1/2 (TF32:BF16 nominal ratio)"
                                          % peak_src}
 

@@ -174,6 +174,12 @@ int fd_last_kernel_ms(fd_ctx* ctx, double* ms, int max);
  * used to state roofline fractions.  Synchronous. */
 int fd_measure_fp64_peak(fd_ctx* ctx, double* gflops);
 
+/* Issue cost of FP64 instructions on this device (clock cycles per dependent DFMA), which decides
+ * how the latency-bound QR and LU steps are laid out: cycles[0] one warp with 1 active lane,
+ * cycles[1] one warp with 32 active lanes, cycles[2] seen by one of 8 warps of a CTA that all
+ * issue independent DFMAs (the SM's shared FP64 pipe).  Synchronous. */
+int fd_measure_fp64_issue(fd_ctx* ctx, double* cycles);
+
 /* ---------------------------------------------------------------------------------------
  * fd_logdet_noalloc: log det (and optionally G) without any memory allocation.
  * The paper has no counterpart; this entry point exists for callers that cannot allocate

@@ -56,6 +56,7 @@ SIGNATURES = [
     ("fd_status", _I, [_VP, _VP, ctypes.POINTER(_I), _I]),
     ("fd_last_launch_count", _I, [_VP]),
     ("fd_measure_fp64_peak", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    ("fd_measure_fp64_issue", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
     ("fd_set_timing", _I, [_VP, _I]),
     ("fd_last_kernel_ms", _I, [_VP, ctypes.POINTER(ctypes.c_double), _I]),
     ("fd_logdet_noalloc", _I, [_I, _PP, _VP, _VP, _VP, _VP]),

@@ -97,6 +97,12 @@ class Context:
             self.check(n)
         return n
 
+    def measure_fp64_issue(self) -> List[float]:
+        """Cycles per FP64 instruction: [1 lane, 32 lanes, 1 of 8 busy warps]."""
+        arr = (ctypes.c_double * 3)()
+        self.check(self.lib.fd_measure_fp64_issue(self.h, arr))
+        return [arr[0], arr[1], arr[2]]
+
     def measure_fp64_peak(self) -> float:
         g = ctypes.c_double()
         self.check(self.lib.fd_measure_fp64_peak(self.h, ctypes.byref(g)))

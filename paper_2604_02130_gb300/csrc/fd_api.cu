@@ -326,6 +326,12 @@ int validate(fd_ctx* ctx, int batch, const fd_problem* probs, const void* logdet
   return FD_OK;
 }
 
+// Waves a launch of `ntasks` tasks needs at `occ` resident CTAs per SM.
+int waves(fd_ctx* ctx, int ntasks, int occ) {
+  const int slots = std::max(1, ctx->num_sms * occ);
+  return (ntasks + slots - 1) / slots;
+}
+
 Phase fp64_phase(fd_ctx* ctx, int n, int role, int which, int ntasks) {
   Phase P;
   memset(&P.ML, 0, sizeof(P.ML));
@@ -333,11 +339,33 @@ Phase fp64_phase(fd_ctx* ctx, int n, int role, int which, int ntasks) {
   P.mixed = 0;
   int nth = threads_for(n);
   auto it = ctx->tuned.find(tune_key(which, 0, 0, n));
-  if (it != ctx->tuned.end()) nth = it->second;
-  // a budget that keeps several CTAs per SM when everything fits, else the full opt-in budget
+  if (it != ctx->tuned.end()) {
+    nth = it->second;
+  } else if (nth == 256) {
+    // with more tasks than resident 8-warp CTAs, 4-warp CTAs may take them all in one wave
+    Layout l8 = plan_layout(n, role, ctx->max_smem_optin, 256);
+    Layout l4 = plan_layout(n, role, ctx->max_smem_optin, 128);
+    const int w8 = waves(ctx, ntasks, resident_ctas(ctx, false, which, 256, l8.smem_bytes));
+    const int w4 = waves(ctx, ntasks, resident_ctas(ctx, false, which, 128, l4.smem_bytes));
+    if (w4 < w8) nth = 128;
+  }
+  // a budget that keeps several CTAs per SM when everything fits, else the full opt-in budget;
+  // with more tasks than SMs, a smaller budget (buffers in L1/L2-cached scratch) when that
+  // needs fewer waves
   Layout full = plan_layout(n, role, 1 << 30, nth);
-  const int budget =
+  int budget =
       full.smem_bytes <= ctx->smem_per_sm / 2 - 1024 ? full.smem_bytes : ctx->max_smem_optin;
+  if (ntasks > ctx->num_sms && budget == ctx->max_smem_optin) {
+    int best_w = waves(ctx, ntasks, resident_ctas(ctx, false, which, nth, plan_layout(n, role, budget, nth).smem_bytes));
+    for (int div : {2, 3, 4}) {
+      const int b2 = ctx->smem_per_sm / div - 2048;
+      const int w2 = waves(ctx, ntasks, resident_ctas(ctx, false, which, nth, plan_layout(n, role, b2, nth).smem_bytes));
+      if (w2 < best_w) {
+        best_w = w2;
+        budget = b2;
+      }
+    }
+  }
   P.L = plan_layout(n, role, budget, nth);
   P.L.num_sms = ctx->num_sms;
   P.nthreads = nth;
@@ -353,7 +381,14 @@ bool mixed_phase(fd_ctx* ctx, int n, int role, int which, bool three, int ntasks
   fd::MLayout M = plan_mixed(n, role, three, ctx->max_smem_optin, ctx->smem_per_sm);
   if (M.smem_bytes == 0) return false;
   auto it = ctx->tuned.find(tune_key(which, 1, three ? 1 : 0, n));
-  if (it != ctx->tuned.end()) M.nthreads = it->second;
+  if (it != ctx->tuned.end()) {
+    M.nthreads = it->second;
+  } else if (M.nthreads == 256) {
+    const int cap = 512 / M.tmem_cols;
+    const int w8 = waves(ctx, ntasks, std::min(cap, resident_ctas(ctx, true, which, 256, M.smem_bytes)));
+    const int w4 = waves(ctx, ntasks, std::min(cap, resident_ctas(ctx, true, which, 128, M.smem_bytes)));
+    if (w4 < w8) M.nthreads = 128;
+  }
   M.num_sms = ctx->num_sms;
   memset(&P.L, 0, sizeof(P.L));
   P.which = which;
@@ -1105,6 +1140,13 @@ int fd_last_kernel_ms(fd_ctx* ctx, double* ms, int max) {
     ms[i] = t;
   }
   return n;
+}
+
+int fd_measure_fp64_issue(fd_ctx* ctx, double* cycles) {
+  if (!ctx || !cycles) return FD_ERR_INVALID;
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  FD_CUDA(ctx, fd::run_fp64_issue(cycles));
+  return FD_OK;
 }
 
 int fd_measure_fp64_peak(fd_ctx* ctx, double* gflops) {

@@ -35,5 +35,6 @@ cudaError_t attrs_mixed(int which, cudaFuncAttributes* a);
 
 // FP64 throughput probe
 cudaError_t run_fp64_probe(int grid, int threads, int iters, double* out, cudaStream_t stream);
+cudaError_t run_fp64_issue(double* out3);
 
 }  // namespace fd

@@ -44,4 +44,55 @@ cudaError_t run_fp64_probe(int grid, int threads, int iters, double* out, cudaSt
   return cudaGetLastError();
 }
 
+// Issue cost of FP64 instructions, from inside one CTA: cycles per DFMA of one warp running one
+// dependent chain with `lanes` active lanes (1 or 32), and with `warps` warps each running eight
+// independent chains (the SM's shared FP64 throughput).  out[0] = cycles per instruction.
+__global__ void k_fp64_issue(int lanes, int chains8, int iters, long long* out, double* sink) {
+  const int lane = threadIdx.x & 31;
+  double a0 = 1.0 + lane * 1e-9, a1 = a0 + 1e-10, a2 = a0 + 2e-10, a3 = a0 + 3e-10;
+  double a4 = a0 + 4e-10, a5 = a0 + 5e-10, a6 = a0 + 6e-10, a7 = a0 + 7e-10;
+  const double m = 0.999999999, c = 1e-12;
+  __syncthreads();
+  const long long t0 = clock64();
+  if (lane < lanes) {
+    if (!chains8) {
+      for (int i = 0; i < iters; ++i) a0 = fma(a0, m, c);
+    } else {
+      for (int i = 0; i < iters; ++i) {
+        a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+        a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+      }
+    }
+  }
+  __syncwarp();
+  const long long t1 = clock64();
+  if (threadIdx.x == 0) out[0] = t1 - t0;
+  const double s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == 42.0) sink[lane] = s;
+}
+
+cudaError_t run_fp64_issue(double* out3) {
+  long long* d_out = nullptr;
+  double* sink = nullptr;
+  cudaError_t e = cudaMalloc(&d_out, sizeof(long long));
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&sink, 32 * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaFree(d_out);
+    return e;
+  }
+  const int iters = 4096;
+  struct Case { int threads, lanes, chains8; } cases[3] = {{32, 1, 0}, {32, 32, 0}, {256, 32, 1}};
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    k_fp64_issue<<<1, cases[i].threads>>>(cases[i].lanes, cases[i].chains8, 64, d_out, sink);
+    k_fp64_issue<<<1, cases[i].threads>>>(cases[i].lanes, cases[i].chains8, iters, d_out, sink);
+    long long cyc = 0;
+    e = cudaMemcpy(&cyc, d_out, sizeof(cyc), cudaMemcpyDeviceToHost);
+    out3[i] = (double)cyc / ((double)iters * (cases[i].chains8 ? 8 : 1));
+  }
+  cudaFree(d_out);
+  cudaFree(sink);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
 }  // namespace fd

@@ -6,9 +6,10 @@ Per configuration with n = Nx, blocks nb = Nt / n_stab:
   slice products  (Section 7 products, Section 9 blocking):  4 n^3 per slice  (E real)
   QR re-orthogonalisation per block: factor 16/3 n^3 + form Q 16/3 n^3 + T update 4 n^3
   assembly (Section 7 steps 4-6, scale separated): LU 8/3 n^3 + solve 8 n^3
-  force (Section 4 response, Section 5.3 pre/suffix): right products 4 n^3 per slice,
-    wraps 8 n^3 per slice, one QR (44/3 n^3) and one boundary Green's function
-    (2 GEMMs 16 n^3 + LU 8/3 + solve 8 + product 8 = 104/3 n^3) per block.
+  force (Section 4 response, Section 5.3 pre/suffix): right products 4 n^3 per slice for all
+    but the first block, wraps 8 n^3 per slice (all slices but the nb block boundaries), one QR
+    (44/3 n^3) and one boundary Green's function (2 GEMMs 16 n^3 + LU 8/3 + solve 8 +
+    product 8 = 104/3 n^3) per interior block boundary (nb - 1 of each).
 """
 from __future__ import annotations
 
@@ -27,11 +28,32 @@ def force_flops(nx: int, nt: int, n_stab: int) -> dict:
     f = fwd_flops(nx, nt, n_stab)
     n3 = float(nx) ** 3
     nb = nt // n_stab
-    right = 4.0 * n3 * nt
+    right = 4.0 * n3 * (nt - n_stab)
     wraps = 8.0 * n3 * (nt - nb)
-    qr = (44.0 / 3.0) * n3 * nb
-    boundary = (104.0 / 3.0) * n3 * nb
+    qr = (44.0 / 3.0) * n3 * (nb - 1)
+    boundary = (104.0 / 3.0) * n3 * (nb - 1)
     bwd = right + wraps + qr + boundary
     return {"forward": f["total"], "backward": bwd, "total": f["total"] + bwd,
             "slices_and_wraps": f["slices"] + right + wraps,
             "per_block_fp64": f["qr"] + f["assembly"] + qr + boundary}
+
+
+def force_phase_flops(nx: int, nt: int, n_stab: int, mixed: bool) -> dict:
+    """Algorithmic work of the three launches of the force, split by arithmetic pipe.
+
+    A (chains): forward slices 4n^3 Nt and QRs (44/3 n^3 each, nb of them), backward right
+       products 4n^3 (Nt - n_stab) and QRs (nb - 1), the assembly (32/3 n^3);
+    B (boundary Green's functions): (104/3) n^3 for each of the nb - 1 interior boundaries;
+    C (wraps): 8 n^3 for each of the Nt - nb wrapped slices.
+    With mixed=True the slice/right products and wraps are tensor-core work, else FP64."""
+    n3 = float(nx) ** 3
+    nb = nt // n_stab
+    a_prod = 4 * n3 * nt + 4 * n3 * (nt - n_stab)
+    a_qr = (44.0 / 3.0) * n3 * (2 * nb - 1) + (32.0 / 3.0) * n3
+    b = (104.0 / 3.0) * n3 * (nb - 1)
+    c = 8 * n3 * (nt - nb)
+    if mixed:
+        return {"A": {"fp64": a_qr, "tensor": a_prod}, "B": {"fp64": b, "tensor": 0.0},
+                "C": {"fp64": 0.0, "tensor": c}}
+    return {"A": {"fp64": a_qr + a_prod, "tensor": 0.0}, "B": {"fp64": b, "tensor": 0.0},
+            "C": {"fp64": c, "tensor": 0.0}}
