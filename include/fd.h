@@ -70,7 +70,8 @@ typedef struct fd_ctx fd_ctx;
  *   nt        time slices, nt >= 1
  *   n_stab    slices between QR re-orthogonalisations, 1 <= n_stab <= nt, nt % n_stab == 0
  *   expA      E = exp(delta*kappa*A), nx*nx float64 (symmetric)
- *   expA_inv  E^{-1}, nx*nx float64 (symmetric); needed by fd_force, may be NULL otherwise
+ *   expA_inv  E^{-1}, nx*nx float64 (symmetric); needed by fd_force and fd_green_tau, may be
+ *             NULL otherwise
  *   phi       nt*nx float64 row-major; row t-1 is the field of slice t */
 typedef struct {
   int32_t nx;
@@ -89,7 +90,7 @@ const char* fd_last_error(const fd_ctx* ctx);
 
 /* Pre-size the workspace for up to `batch` configurations like `probs` with the given outputs
  * (`what` = bitmask of FD_WANT_*), so that later calls of that shape allocate nothing. */
-enum { FD_WANT_LOGDET = 1, FD_WANT_GREEN = 2, FD_WANT_FORCE = 4 };
+enum { FD_WANT_LOGDET = 1, FD_WANT_GREEN = 2, FD_WANT_FORCE = 4, FD_WANT_GTAU = 8 };
 int fd_reserve(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec);
 
 /* log det(1 + B_Nt...B_1) for `batch` configurations.
@@ -113,12 +114,28 @@ int fd_green(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, do
 int fd_force(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
              double* const* F, int prec, void* stream);
 
+/* log det, (optionally) G and F, and the unequal-time Green's function
+ * G(tau, 0) = (M^{-1})_{tau,0} = B_tau...B_1 (1 + B_Nt...B_1)^{-1}, tau = 0..nt-1 (Section 4.2,
+ * Eq. sausage_all_in_denominator with t0 = 0).  At the block boundaries tau = (b-1) n_stab it is
+ * formed stably from the left and right (X, D, T) checkpoints (Section 7 steps 7-9:
+ * G(tau, 0) = X_R D_Rb^{-1} M^{-1} D_Ls T_L, M the boundary matrix of G_tau); inside a block it
+ * is propagated one slice at a time, forward G(t+1, 0) = B_{t+1} G(t, 0) from the lower boundary
+ * for (n_stab-1)/2 slices and backward G(t-1, 0) = B_t^{-1} G(t, 0) from the upper one
+ * (G(nt, 0) = 1 - G for the last block), so no propagation runs over more than n_stab/2 slices.
+ *   Gtau  host array of `batch` device pointers; Gtau[c] receives nt*nx*nx complex128, block
+ *         tau row-major at offset tau*nx*nx (Gtau[c] block 0 = G)
+ *   G, F  host arrays of device pointers, or NULL (not wanted); as for fd_force
+ * With a mixed precision the chains run on the tensor cores and the G(tau, 0) wraps in FP64.
+ * Not available through fd_graph_create. */
+int fd_green_tau(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet,
+                 double* const* G, double* const* Gtau, double* const* F, int prec, void* stream);
+
 /* Wait for `stream` and copy the per-configuration device status of the LAST call on this
  * context into per_config_status[0..batch-1] (host): FD_OK, FD_ERR_NUMERIC or FD_ERR_TIMEOUT.
  * Returns the worst code seen (FD_OK if all succeeded). */
 int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch);
 
-/* Number of kernel launches the last fd_logdet/fd_green/fd_force call issued. */
+/* Number of kernel launches the last fd_logdet/fd_green/fd_force/fd_green_tau call issued. */
 int fd_last_launch_count(const fd_ctx* ctx);
 
 /* Autotuner.  fd_tune times every size class of this batch with 128 and 256 threads per CTA

@@ -36,3 +36,11 @@ def green_blocks(E: np.ndarray, phi: np.ndarray) -> np.ndarray:
     nt, nx = phi.shape
     Minv = np.linalg.inv(full_matrix(E, phi))
     return np.stack([Minv[t * nx:(t + 1) * nx, t * nx:(t + 1) * nx] for t in range(nt)])
+
+
+def inverse_column(E: np.ndarray, phi: np.ndarray, t0: int = 0) -> np.ndarray:
+    """Blocks (M^{-1})[tau, t0] for tau = 0..Nt-1, shape (Nt, Nx, Nx): the unequal-time Green's
+    function G(tau, t0) (Section 4.2)."""
+    nt, nx = phi.shape
+    Minv = np.linalg.inv(full_matrix(E, phi))
+    return np.stack([Minv[t * nx:(t + 1) * nx, t0 * nx:(t0 + 1) * nx] for t in range(nt)])

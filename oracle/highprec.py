@@ -34,3 +34,33 @@ def logdet_green(E: np.ndarray, phi: np.ndarray, dps: int = 250):
     im = float(mp.im(logdet))
     im = float(np.angle(np.exp(1j * im)))
     return complex(float(mp.re(logdet)), im), G
+
+
+def green_tau(E: np.ndarray, phi: np.ndarray, taus, dps: int = 250) -> dict:
+    """{tau: (L_tau^{-1} + R_tau)^{-1}} from the plain products in mpmath (Section 4.2)."""
+    import mpmath as mp
+
+    mp.mp.dps = dps
+    nt, nx = phi.shape
+    Em = mp.matrix([[mp.mpf(float(E[i, j])) for j in range(nx)] for i in range(nx)])
+
+    def slice_m(t):
+        ph = [mp.expj(mp.mpf(float(phi[t, k]))) for k in range(nx)]
+        B = mp.matrix(nx, nx)
+        for i in range(nx):
+            for k in range(nx):
+                B[i, k] = Em[i, k] * ph[k]
+        return B
+
+    slices = [slice_m(t) for t in range(nt)]
+    out = {}
+    for tau in taus:
+        L = mp.eye(nx)
+        for t in range(tau):
+            L = slices[t] * L
+        R = mp.eye(nx)
+        for t in range(tau, nt):
+            R = slices[t] * R
+        Gt = mp.inverse(mp.inverse(L) + R)
+        out[int(tau)] = np.array([[complex(Gt[i, j]) for j in range(nx)] for i in range(nx)])
+    return out

@@ -9,6 +9,7 @@ computation runs in libfd.so's CUDA kernels; torch provides device memory and st
 from __future__ import annotations
 
 import ctypes
+import math
 from dataclasses import dataclass
 from typing import List, Optional, Sequence, Tuple
 
@@ -114,20 +115,30 @@ class Result:
     logdet: torch.Tensor  # (batch,) complex128
     G: Optional[List[torch.Tensor]]  # nx x nx complex128 each
     F: Optional[List[torch.Tensor]]  # nt x nx complex128 each
+    Gtau: Optional[List[torch.Tensor]] = None  # nt x nx x nx complex128 each: G(tau, 0)
 
 
 class Batch:
     """A fixed batch of configurations with preallocated outputs; run() enqueues one call.
 
     problems: sequence of (E, Einv, phi, n_stab) with E, Einv (nx, nx) float64 and phi (nt, nx)
-    float64 CUDA tensors (Einv may be None unless want == "force")."""
+    float64 CUDA tensors (Einv may be None unless the force or G(tau, 0) is wanted).
+
+    want: "logdet", or "+"-joined outputs among "green" (G), "force" (F) and "gtau" (the
+    unequal-time G(tau, 0), tau = 0..nt-1); log det always comes along."""
+
+    WANT_BITS = {"logdet": 1, "green": 2, "force": 4, "gtau": 8}
 
     def __init__(self, ctx: Context, problems: Sequence[Tuple], want: str = "logdet",
                  prec: str = "fp64"):
-        if want not in ("logdet", "green", "force", "force+green"):
+        parts = set(want.split("+"))
+        if not parts or not parts <= set(self.WANT_BITS):
             raise ValueError(want)
         self.ctx = ctx
         self.want = want
+        self.what = 1
+        for p in parts:
+            self.what |= self.WANT_BITS[p]
         self.prec = L.PRECISIONS[prec]
         self.n = len(problems)
         self._keep = []
@@ -147,63 +158,72 @@ class Batch:
         self.logdet_buf = torch.empty((self.n, 2), dtype=torch.float64, device=dev)
         self.G = None
         self.F = None
+        self.Gtau = None
         self._Gp = None
         self._Fp = None
+        self._Gtp = None
         # outputs live in one flat buffer each (one host copy fetches them all)
         self.G_flat = None
         self.F_flat = None
-        if want in ("green", "force+green"):
+        self.Gtau_flat = None
+        if self.what & 2:
             self.G_flat, self.G = self._flat(dev, [(p.nx, p.nx) for p in arr[:self.n]])
             self._Gp = (ctypes.c_void_p * self.n)(*[g.data_ptr() for g in self.G])
-        if want.startswith("force"):
+        if self.what & 4:
             self.F_flat, self.F = self._flat(dev, [(p.nt, p.nx) for p in arr[:self.n]])
             self._Fp = (ctypes.c_void_p * self.n)(*[f.data_ptr() for f in self.F])
+        if self.what & 8:
+            self.Gtau_flat, self.Gtau = self._flat(
+                dev, [(p.nt, p.nx, p.nx) for p in arr[:self.n]])
+            self._Gtp = (ctypes.c_void_p * self.n)(*[g.data_ptr() for g in self.Gtau])
 
     @staticmethod
     def _flat(dev, shapes):
-        total = sum(a * b for a, b in shapes)
-        flat = torch.empty(max(1, total), dtype=torch.complex128, device=dev)
+        sizes = [math.prod(s) for s in shapes]
+        flat = torch.empty(max(1, sum(sizes)), dtype=torch.complex128, device=dev)
         views, o = [], 0
-        for a, b in shapes:
-            views.append(flat[o:o + a * b].view(a, b))
-            o += a * b
+        for s, k in zip(shapes, sizes):
+            views.append(flat[o:o + k].view(*s))
+            o += k
         return flat, views
 
     def plan(self) -> List[dict]:
         """The launch plan of this batch (one dict per size class), see fd_plan_query."""
-        what = {"logdet": 1, "green": 3, "force": 5, "force+green": 7}[self.want]
         info = (ctypes.c_int * (8 * 64))()
-        n = self.ctx.lib.fd_plan_query(self.ctx.h, self.n, self.problems, what, self.prec, info, 64)
+        n = self.ctx.lib.fd_plan_query(self.ctx.h, self.n, self.problems, self.what, self.prec,
+                                       info, 64)
         if n < 0:
             self.ctx.check(n)
         keys = ("nx", "kernel", "threads", "smem", "grid", "ctas_per_sm", "scratch_kib", "configs")
         return [dict(zip(keys, info[8 * g:8 * g + 8])) for g in range(min(n, 64))]
 
     def reserve(self):
-        what = {"logdet": 1, "green": 3, "force": 5, "force+green": 7}[self.want]
-        self.ctx.check(self.ctx.lib.fd_reserve(self.ctx.h, self.n, self.problems, what, self.prec))
+        self.ctx.check(self.ctx.lib.fd_reserve(self.ctx.h, self.n, self.problems, self.what,
+                                               self.prec))
 
     def run(self, stream=None) -> Result:
         lib, h = self.ctx.lib, self.ctx.h
         s = _stream_ptr(stream)
         ld = ctypes.c_void_p(self.logdet_buf.data_ptr())
-        if self.want == "logdet":
-            rc = lib.fd_logdet(h, self.n, self.problems, ld, self.prec, s)
-        elif self.want == "green":
+        if self.what & 8:
+            rc = lib.fd_green_tau(h, self.n, self.problems, ld, self._Gp, self._Gtp, self._Fp,
+                                  self.prec, s)
+        elif self.what & 4:
+            rc = lib.fd_force(h, self.n, self.problems, ld, self._Gp, self._Fp, self.prec, s)
+        elif self.what & 2:
             rc = lib.fd_green(h, self.n, self.problems, ld, self._Gp, self.prec, s)
         else:
-            rc = lib.fd_force(h, self.n, self.problems, ld, self._Gp, self._Fp, self.prec, s)
+            rc = lib.fd_logdet(h, self.n, self.problems, ld, self.prec, s)
         self.ctx.check(rc)
-        return Result(torch.view_as_complex(self.logdet_buf), self.G, self.F)
+        return Result(torch.view_as_complex(self.logdet_buf), self.G, self.F, self.Gtau)
 
     def status(self, stream=None) -> List[int]:
         return self.ctx.status(self.n, stream)
 
     def tune(self, reps: int = 2):
         """Time 128 vs 256 threads per CTA for every size class of this batch (fd_tune)."""
-        what = {"logdet": 1, "green": 3, "force": 5, "force+green": 7}[self.want]
-        self.ctx.check(self.ctx.lib.fd_tune(self.ctx.h, self.n, self.problems, what, self.prec,
-                                            reps))
+        self.ctx.check(self.ctx.lib.fd_tune(self.ctx.h, self.n, self.problems, self.what,
+                                            self.prec, reps))
 
     def graph(self) -> "BatchGraph":
         """Capture this batch's call into a CUDA graph (fd_graph_create)."""
@@ -215,11 +235,13 @@ class BatchGraph:
     Inputs are read and outputs written through the Batch's tensors (update phi in place)."""
 
     def __init__(self, batch: Batch):
+        if batch.what & 8:
+            raise ValueError("G(tau, 0) is not available through CUDA graphs")
         self.batch = batch
         ctx = batch.ctx
         h = ctypes.c_void_p()
         ld = ctypes.c_void_p(batch.logdet_buf.data_ptr())
-        F = batch._Fp if batch.want.startswith("force") else None
+        F = batch._Fp if batch.what & 4 else None
         ctx.check(ctx.lib.fd_graph_create(ctx.h, batch.n, batch.problems, ld, batch._Gp, F,
                                           batch.prec, ctypes.byref(h)))
         self.h = h
@@ -270,6 +292,16 @@ def force(problems, prec: str = "fp64", with_green: bool = False,
     r = Batch(ctx or default_context(), problems, "force+green" if with_green else "force",
               prec).run()
     return r.logdet.clone(), r.G, r.F
+
+
+def green_tau(problems, prec: str = "fp64", with_green: bool = False,
+              with_force: bool = False, ctx: Optional[Context] = None):
+    """log det and the unequal-time Green's function G(tau, 0), tau = 0..nt-1 (Section 4.2);
+    returns (logdet, G or None, F or None, [Gtau (nt, nx, nx) per configuration])."""
+    want = "+".join(["gtau"] + (["green"] if with_green else []) +
+                    (["force"] if with_force else []))
+    r = Batch(ctx or default_context(), problems, want, prec).run()
+    return r.logdet.clone(), r.G, r.F, r.Gtau
 
 
 class FermionLogDet(torch.autograd.Function):

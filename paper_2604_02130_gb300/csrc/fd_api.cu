@@ -75,7 +75,12 @@ int cuda_fail(fd_ctx* ctx, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
-enum Kind { K_FWD = 0, K_FORCE = 1 };
+// What a call computes: log det/G (one persistent kernel), or the phased path (chains, boundary
+// Green's functions, wraps) for the force F and/or the unequal-time G(tau, 0) (bit mask).
+enum Kind { K_FWD = 0, K_FORCE = 1, K_GTAU = 2, K_FORCE_GTAU = 3 };
+int kind_of(int what) {
+  return ((what & FD_WANT_FORCE) ? K_FORCE : 0) | ((what & FD_WANT_GTAU) ? K_GTAU : 0);
+}
 
 // One launch of a size class.  which: 0 log det/G, 1 force chains, 2 boundary G, 3 wraps.
 struct Phase {
@@ -145,8 +150,9 @@ long long tune_key(int kind, int mixed, int three, int nx) {
 }
 
 // Buffer sets of the kernels ("roles"): log det/G and the force chains (R_FWD), the boundary
-// Green's functions (R_BOUND) and the wraps (R_WRAP).
-enum Role { R_FWD = 0, R_BOUND = 2, R_WRAP = 3 };
+// Green's functions (R_BOUND; R_BOUND2 with the second right-hand side of G(t, 0) beside G_t)
+// and the wraps (R_WRAP).
+enum Role { R_FWD = 0, R_BOUND = 2, R_WRAP = 3, R_BOUND2 = 4 };
 
 // Greedy placement: the buffers touched every slice first, then the per-block ones.
 Layout plan_layout(int n, int role, int budget, int nthreads) {
@@ -159,6 +165,8 @@ Layout plan_layout(int n, int role, int budget, int nthreads) {
     order = {{fd::B_E, rm}, {fd::B_X0, cm}, {fd::B_X1, cm}, {fd::B_T0, cm}, {fd::B_T1, cm}};
   else if (role == R_BOUND)
     order = {{fd::B_GA, cm}, {fd::B_GB, cm}};
+  else if (role == R_BOUND2)
+    order = {{fd::B_GA, cm}, {fd::B_GB, 2 * cm}};
   else
     order = {{fd::B_E, rm}, {fd::B_EINV, rm}, {fd::B_GA, cm}, {fd::B_GB, cm}};
   long long used = round16(fd::small_bytes(n)) + 16;  // small vectors + queue slot
@@ -321,7 +329,7 @@ int validate(fd_ctx* ctx, int batch, const fd_problem* probs, const void* logdet
     if (p.reserved != 0) return fail(ctx, FD_ERR_INVALID, "config %d: reserved != 0", c);
     if (!p.expA || !p.phi) return fail(ctx, FD_ERR_INVALID, "config %d: null expA or phi", c);
     if (need_einv && !p.expA_inv)
-      return fail(ctx, FD_ERR_INVALID, "config %d: fd_force needs expA_inv", c);
+      return fail(ctx, FD_ERR_INVALID, "config %d: fd_force and fd_green_tau need expA_inv", c);
   }
   return FD_OK;
 }
@@ -439,13 +447,16 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
         for (int b = 2; b <= nb; ++b) g.tB.push_back(fd::Task{k, b});
         for (int b = 1; b <= nb; ++b) g.tC.push_back(fd::Task{k, b});
         g.fws_off.push_back(g.fws_bytes);
-        g.fws_bytes += (fd::FWork::elems(n, nb) * 16 + 255) & ~(size_t)255;
+        g.fws_bytes += (fd::FWork::elems(n, nb, (kind & K_GTAU) != 0) * 16 + 255) & ~(size_t)255;
       }
       Phase A, C;
       if (!(mixed && mixed_phase(ctx, n, R_FWD, 1, three, 2 * nd, A)))
         A = fp64_phase(ctx, n, R_FWD, 1, 2 * nd);
-      Phase B = fp64_phase(ctx, n, R_BOUND, 2, std::max(1, (int)g.tB.size()));
-      if (!(mixed && mixed_phase(ctx, n, R_WRAP, 3, three, (int)g.tC.size(), C)))
+      Phase B = fp64_phase(ctx, n, kind == K_FORCE_GTAU ? R_BOUND2 : R_BOUND, 2,
+                           std::max(1, (int)g.tB.size()));
+      // the tensor-core wrap kernel covers the force rows; G(tau, 0) wraps run in FP64
+      const bool mixed_wrap = mixed && !(kind & K_GTAU);
+      if (!(mixed_wrap && mixed_phase(ctx, n, R_WRAP, 3, three, (int)g.tC.size(), C)))
         C = fp64_phase(ctx, n, R_WRAP, 3, (int)g.tC.size());
       g.ph.push_back(A);
       g.ph.push_back(B);
@@ -550,8 +561,8 @@ int queue_count(const std::vector<Group>& groups) {
 // Host descriptor and task tables of a call.  `scratch` is the device scratch base (the force
 // workspace of each configuration lives inside it).
 void build_tables(std::vector<Group>& groups, const fd_problem* probs, double* logdet,
-                  double* const* G, double* const* F, char* scratch, Desc* out,
-                  fd::Task* tasks) {
+                  double* const* G, double* const* F, double* const* Gt, char* scratch,
+                  Desc* out, fd::Task* tasks) {
   size_t k = 0, t = 0;
   for (auto& g : groups) {
     g.desc_off = k;
@@ -569,7 +580,8 @@ void build_tables(std::vector<Group>& groups, const fd_problem* probs, double* l
       d.logdet = logdet + 2 * (size_t)c;
       d.G = G ? (double2*)G[c] : nullptr;
       d.F = F ? (double2*)F[c] : nullptr;
-      d.fws = g.kind == K_FORCE
+      d.Gt = Gt ? (double2*)Gt[c] : nullptr;
+      d.fws = g.kind != K_FWD
                   ? (double2*)(scratch + g.scratch_off + g.slots_bytes + g.fws_off[q])
                   : nullptr;
       out[k++] = d;
@@ -676,7 +688,7 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
 }
 
 int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
-        double* const* F, int prec, void* stream_, int kind) {
+        double* const* F, double* const* Gt, int prec, void* stream_, int kind) {
   cudaStream_t stream = (cudaStream_t)stream_;
   ctx->last_launches = 0;
   ctx->last_batch = batch;
@@ -694,7 +706,7 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double*
     FD_CUDA(ctx, cudaEventSynchronize(ctx->staging_done));
     ctx->staging_pending = false;
   }
-  build_tables(groups, probs, logdet, G, F, ctx->scratch, ctx->h_desc, ctx->h_tasks);
+  build_tables(groups, probs, logdet, G, F, Gt, ctx->scratch, ctx->h_desc, ctx->h_tasks);
   FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(Desc) * batch,
                                cudaMemcpyHostToDevice, stream));
   if (ntasks)
@@ -783,12 +795,11 @@ const char* fd_last_error(const fd_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 
 int fd_reserve(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec) {
   double dummy;
-  int rc = validate(ctx, batch, probs, &dummy, prec, (what & FD_WANT_FORCE) != 0);
+  int rc = validate(ctx, batch, probs, &dummy, prec, kind_of(what) != K_FWD);
   if (rc != FD_OK) return rc;
   if (batch == 0) return FD_OK;
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
-  std::vector<Group> groups =
-      plan(ctx, batch, probs, (what & FD_WANT_FORCE) ? K_FORCE : K_FWD, prec);
+  std::vector<Group> groups = plan(ctx, batch, probs, kind_of(what), prec);
   size_t need = scratch_need(groups);
   rc = ensure(ctx, (size_t)batch, (size_t)batch, queue_count(groups), need, task_count(groups));
   if (rc != FD_OK) return rc;
@@ -803,7 +814,7 @@ int fd_logdet(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, i
               void* stream) {
   int rc = validate(ctx, batch, probs, logdet, prec, false);
   if (rc != FD_OK) return rc;
-  return run(ctx, batch, probs, logdet, nullptr, nullptr, prec, stream, K_FWD);
+  return run(ctx, batch, probs, logdet, nullptr, nullptr, nullptr, prec, stream, K_FWD);
 }
 
 int fd_green(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
@@ -813,7 +824,7 @@ int fd_green(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, do
   if (batch > 0 && !G) return fail(ctx, FD_ERR_INVALID, "null G array");
   for (int c = 0; c < batch; ++c)
     if (!G[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null G", c);
-  return run(ctx, batch, probs, logdet, G, nullptr, prec, stream, K_FWD);
+  return run(ctx, batch, probs, logdet, G, nullptr, nullptr, prec, stream, K_FWD);
 }
 
 int fd_force(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
@@ -825,7 +836,20 @@ int fd_force(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, do
     if (!F[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null F", c);
     if (G && !G[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null G", c);
   }
-  return run(ctx, batch, probs, logdet, G, F, prec, stream, K_FORCE);
+  return run(ctx, batch, probs, logdet, G, F, nullptr, prec, stream, K_FORCE);
+}
+
+int fd_green_tau(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet,
+                 double* const* G, double* const* Gtau, double* const* F, int prec, void* stream) {
+  int rc = validate(ctx, batch, probs, logdet, prec, true);
+  if (rc != FD_OK) return rc;
+  if (batch > 0 && !Gtau) return fail(ctx, FD_ERR_INVALID, "null Gtau array");
+  for (int c = 0; c < batch; ++c) {
+    if (!Gtau[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null Gtau", c);
+    if (G && !G[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null G", c);
+    if (F && !F[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null F", c);
+  }
+  return run(ctx, batch, probs, logdet, G, F, Gtau, prec, stream, F ? K_FORCE_GTAU : K_GTAU);
 }
 
 int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch) {
@@ -885,7 +909,7 @@ int fd_graph_create(fd_ctx* ctx, int batch, const fd_problem* probs, double* log
   FD_G(cudaMalloc(&g->d_queue, sizeof(int) * std::max(1, queue_count(groups))));
   FD_G(cudaMalloc(&g->d_status, sizeof(int) * batch));
   FD_G(cudaMalloc(&g->scratch, std::max<size_t>(need, 256)));
-  build_tables(groups, probs, logdet, G, F, g->scratch, h.data(), ht.data());
+  build_tables(groups, probs, logdet, G, F, nullptr, g->scratch, h.data(), ht.data());
   FD_G(cudaMemcpy(g->d_desc, h.data(), sizeof(Desc) * batch, cudaMemcpyHostToDevice));
   FD_G(cudaMemcpy(g->d_tasks, ht.data(), sizeof(fd::Task) * ht.size(), cudaMemcpyHostToDevice));
   FD_G(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -984,7 +1008,7 @@ int fd_tune(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec,
       for (int r = 0; r <= reps; ++r) {  // first run is a warm-up
         cudaEventRecord(e0, 0);
         int rr = run(ctx, (int)sub.size(), sub.data(), d_ld, sg.data(), force ? sf.data() : nullptr,
-                     prec, nullptr, kind);
+                     nullptr, prec, nullptr, kind);
         cudaEventRecord(e1, 0);
         if (rr != FD_OK) { result = rr; break; }
         cudaEventSynchronize(e1);
@@ -1027,7 +1051,7 @@ int fd_tune_nstab(fd_ctx* ctx, const fd_problem* prob, const int* candidates, in
   // reference: FP64 with the smallest candidate interval
   fd_problem p = *prob;
   p.n_stab = nmin;
-  int rc = run(ctx, 1, &p, d_ld, nullptr, nullptr, FD_PREC_FP64, nullptr, K_FWD);
+  int rc = run(ctx, 1, &p, d_ld, nullptr, nullptr, nullptr, FD_PREC_FP64, nullptr, K_FWD);
   double ref[2] = {0, 0};
   if (rc == FD_OK) {
     cudaDeviceSynchronize();
@@ -1036,7 +1060,7 @@ int fd_tune_nstab(fd_ctx* ctx, const fd_problem* prob, const int* candidates, in
   int chosen = 0;
   for (int i = 0; i < ncand && rc == FD_OK; ++i) {
     p.n_stab = candidates[i];
-    rc = run(ctx, 1, &p, d_ld, nullptr, nullptr, prec, nullptr, K_FWD);
+    rc = run(ctx, 1, &p, d_ld, nullptr, nullptr, nullptr, prec, nullptr, K_FWD);
     if (rc != FD_OK) break;
     double got[2];
     cudaDeviceSynchronize();
@@ -1097,11 +1121,11 @@ int fd_tune_load(fd_ctx* ctx, const char* path) {
 int fd_plan_query(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec, int* info,
                   int max_groups) {
   double dummy;
-  int rc = validate(ctx, batch, probs, &dummy, prec, (what & FD_WANT_FORCE) != 0);
+  int rc = validate(ctx, batch, probs, &dummy, prec, kind_of(what) != K_FWD);
   if (rc != FD_OK) return rc;
   if (max_groups > 0 && !info) return fail(ctx, FD_ERR_INVALID, "null info");
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
-  const int kind = (what & FD_WANT_FORCE) ? K_FORCE : K_FWD;
+  const int kind = kind_of(what);
   std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
   int k = 0, total = 0;
   for (auto& g : groups) {

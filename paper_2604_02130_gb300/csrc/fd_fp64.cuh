@@ -541,7 +541,8 @@ __device__ inline void cta_reortho(int n, const double2* Xc, double2* Xn, const 
 // one complex reciprocal per pivot; back substitution with the columns of U pre-scaled by the
 // reciprocal pivots, one barrier per step, rows scaled at the end.
 __device__ inline void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, double* logdet_re,
-                                    double* logdet_im) {
+                                    double* logdet_im, int ncols = -1) {
+  if (ncols < 0) ncols = n;  // right-hand sides: Bm is n x ncols, leading dimension n
   const int lane = lane_id(), w = warp_id();
   if (tid() == 0) s.misc[1] = 0;
   __syncthreads();
@@ -570,7 +571,9 @@ __device__ inline void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, do
           double2 t = A[k + j * n];
           A[k + j * n] = A[p + j * n];
           A[p + j * n] = t;
-          t = Bm[k + j * n];
+        }
+        for (int j = lane; j < ncols; j += 32) {
+          double2 t = Bm[k + j * n];
           Bm[k + j * n] = Bm[p + j * n];
           Bm[p + j * n] = t;
         }
@@ -592,7 +595,7 @@ __device__ inline void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, do
     __syncthreads();
     // trailing update of A (columns k+1..n-1) and of all columns of Bm, rows k+1..n-1
     const int m = n - k - 1;
-    const int cols = m + n;
+    const int cols = m + ncols;
     for (int e = tid(); e < m * cols; e += nthr()) {
       const int i = k + 1 + e % m;
       const int c = e / m;
@@ -629,13 +632,13 @@ __device__ inline void cta_lu_solve(int n, double2* A, double2* Bm, Small& s, do
   __syncthreads();
   // back substitution, unscaled rows: B(i,:) -= W(i,k) B(k,:) for i < k, then B(k,:) /= U(k,k)
   for (int k = n - 1; k >= 1; --k) {
-    for (int e = tid(); e < k * n; e += nthr()) {
+    for (int e = tid(); e < k * ncols; e += nthr()) {
       const int i = e % k, j = e / k;
       st(Bm + i + j * n, cfms(ld(Bm + i + j * n), ld(A + i + k * n), ld(Bm + k + j * n)));
     }
     __syncthreads();
   }
-  for (int e = tid(); e < n * n; e += nthr()) {
+  for (int e = tid(); e < n * ncols; e += nthr()) {
     const int i = e % n;
     st(Bm + e, ld(Bm + e) * ld(s.rdiag + i));
   }
@@ -685,10 +688,14 @@ __device__ inline void cta_assemble(int n, const double2* X, const double2* T, c
 //   1 + L R = X_L D_Lb [ D_Lb^{-1} X_L^H X_R D_Rb^{-1} + D_Ls T_L T_R^H D_Rs ] D_Rb X_R^H,
 //   G_t = X_R D_Rb^{-1} M^{-1} D_Lb^{-1} X_L^H.
 // identity_left: L = 1 (t = 0).  Scratch: Mb, Wb.  Result in Gout.
+// With Gt_out (and a Wb of 2n columns) it also gives the unequal-time Green's function
+// G(t, 0) = (L^{-1} + R)^{-1} (Section 4.2) from the same factored M:
+//   L^{-1} + R = T_L^{-1} D_Ls^{-1} M D_Rb X_R^H  =>  G(t, 0) = X_R D_Rb^{-1} M^{-1} D_Ls T_L.
+// Gout or Gt_out may be null (not wanted).
 __device__ inline void boundary_green(int n, bool identity_left, const double2* XL, const double2* TL,
                                const double* logDL, const double2* XR, const double2* TR,
                                const double* logDR, double2* Mb, double2* Wb, double2* Gout,
-                               Small& s) {
+                               Small& s, double2* Gt_out = nullptr) {
   for (int k = tid(); k < n; k += nthr()) {
     double lL = identity_left ? 0.0 : logDL[k];
     double lR = logDR[k];
@@ -705,7 +712,8 @@ __device__ inline void boundary_green(int n, bool identity_left, const double2* 
       int i = e % n, j = e / n;
       cplx m = b[j] * ld(XR + e) + dd[j] * conj(ld(TR + j + i * n));
       st(Mb + e, m);
-      Wb[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      if (Gout) Wb[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      if (Gt_out) Wb[(Gout ? n * n : 0) + e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
     }
     __syncthreads();
   } else {
@@ -716,19 +724,29 @@ __device__ inline void boundary_green(int n, bool identity_left, const double2* 
     });
     for (int e = tid(); e < n * n; e += nthr()) {
       int i = e % n, j = e / n;
-      st(Wb + e, a[i] * conj(ld(XL + j + i * n)));
+      if (Gout) st(Wb + e, a[i] * conj(ld(XL + j + i * n)));
+      if (Gt_out) st(Wb + (Gout ? n * n : 0) + e, c[i] * ld(TL + e));
     }
     __syncthreads();
   }
-  cta_lu_solve(n, Mb, Wb, s, s.red + 4, s.red + 5);
+  const int nr = (Gout ? n : 0) + (Gt_out ? n : 0);
+  cta_lu_solve(n, Mb, Wb, s, s.red + 4, s.red + 5, nr);
   // Gout = X_R diag(b) W
   struct BW {
     const double2* p;
     const double* b;
     int n;
     __device__ __forceinline__ cplx operator()(int k, int j) const { return b[k] * ld(p + k + j * n); }
-  } Bop{Wb, b, n};
-  cta_gemm<false>(n, CMat{XR, 1, n}, Bop, [&](int i, int j, cplx v) { st(Gout + i + j * n, v); });
+  };
+  if (Gout) {
+    BW Bop{Wb, b, n};
+    cta_gemm<false>(n, CMat{XR, 1, n}, Bop, [&](int i, int j, cplx v) { st(Gout + i + j * n, v); });
+  }
+  if (Gt_out) {
+    BW Bop{Wb + (Gout ? n * n : 0), b, n};
+    cta_gemm<false>(n, CMat{XR, 1, n}, Bop,
+                    [&](int i, int j, cplx v) { st(Gt_out + i + j * n, v); });
+  }
 }
 
 __device__ __forceinline__ void emit_force_row(int n, const double2* G, double2* Frow) {

@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
       }
       cta_copy(n * n, W.Gb(1), To);
       if (d.G) write_green(n, To, d.G);
+      if (d.Gt) write_green(n, To, d.Gt);  // G(0, 0) = G
       if (tid() == 0)
         atomicMax(status + d.user_index,
                   (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
@@ -275,7 +276,8 @@ __global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ 
     double2* Mb = (double2*)place(smem, slotp, L, B_GB);
     __syncthreads();
     boundary_green(n, false, W.LX(b - 1), W.LT(b - 1), W.LD(b - 1), W.RX(b), W.RT(b), W.RD(b),
-                   Ma, Mb, W.Gb(b), s);
+                   Ma, Mb, d.F ? W.Gb(b) : nullptr, s, d.Gt ? W.GT(b) : nullptr);
+    if (d.Gt) write_green(n, W.GT(b), d.Gt + (size_t)(b - 1) * d.nstab * n * n);
     if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     __syncthreads();
   }
@@ -308,22 +310,65 @@ __global__ void __launch_bounds__(256) k_wrap_fp64(const Desc* __restrict__ desc
     double2* Gb = (double2*)place(smem, slotp, L, B_GB);
     __syncthreads();
     const int t0 = (b - 1) * ns, h = (ns - 1) / 2;
-    const double2* Glo = W.Gb(b);
-    emit_force_row(n, Glo, d.F + (size_t)t0 * n);
-    const double2* src = Glo;
-    for (int j = 1; j <= h; ++j) {
-      wrap_forward(n, E, Einv, d.phi + (size_t)(t0 + j - 1) * n, src, Ga, Gb, s);
-      emit_force_row(n, Ga, d.F + (size_t)(t0 + j) * n);
-      src = Ga;
+    if (d.F) {
+      const double2* Glo = W.Gb(b);
+      emit_force_row(n, Glo, d.F + (size_t)t0 * n);
+      const double2* src = Glo;
+      for (int j = 1; j <= h; ++j) {
+        wrap_forward(n, E, Einv, d.phi + (size_t)(t0 + j - 1) * n, src, Ga, Gb, s);
+        emit_force_row(n, Ga, d.F + (size_t)(t0 + j) * n);
+        src = Ga;
+      }
+      __syncthreads();
+      src = W.Gb(b + 1);
+      for (int qq = b * ns; qq >= t0 + h + 2; --qq) {
+        wrap_backward(n, E, Einv, d.phi + (size_t)(qq - 1) * n, src, Ga, Gb, s);
+        emit_force_row(n, Ga, d.F + (size_t)(qq - 1) * n);
+        src = Ga;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    src = W.Gb(b + 1);
-    for (int qq = b * ns; qq >= t0 + h + 2; --qq) {
-      wrap_backward(n, E, Einv, d.phi + (size_t)(qq - 1) * n, src, Ga, Gb, s);
-      emit_force_row(n, Ga, d.F + (size_t)(qq - 1) * n);
-      src = Ga;
+    if (d.Gt) {
+      // G(tau, 0) inside the block: forward G(t+1, 0) = E diag(ph_{t+1}) G(t, 0) from the lower
+      // boundary, backward G(q-1, 0) = diag(ph_q^*) E^{-1} G(q, 0) from the upper one
+      // (G(Nt, 0) = B_Nt...B_1 G = 1 - G for the last block).
+      const size_t nn = (size_t)n * n;
+      const double2* src = W.GT(b);
+      for (int j = 1; j <= h; ++j) {
+        cta_phase(n, s.ph, d.phi + (size_t)(t0 + j - 1) * n, 1.0);
+        __syncthreads();
+        for (int e = tid(); e < n * n; e += nthr()) st(Gb + e, ld(s.ph + e % n) * ld(src + e));
+        __syncthreads();
+        cta_gemm<false>(n, RealMat{E, 1, n}, CMat{Gb, 1, n},
+                        [&](int i, int jj, cplx v) { st(Ga + i + jj * n, v); });
+        write_green(n, Ga, d.Gt + (size_t)(t0 + j) * nn);
+        src = Ga;
+      }
+      __syncthreads();
+      double2* cur = Ga;
+      if (b == nb) {  // 1 - G
+        const double2* G0 = W.Gb(1);
+        for (int e = tid(); e < n * n; e += nthr())
+          st(Gb + e, cx((e % n == e / n) ? 1.0 : 0.0, 0.0) - ld(G0 + e));
+        __syncthreads();
+        src = Gb;
+        cur = Ga;
+      } else {
+        src = W.GT(b + 1);
+      }
+      for (int qq = b * ns; qq >= t0 + h + 2; --qq) {
+        cta_phase(n, s.ph, d.phi + (size_t)(qq - 1) * n, -1.0);
+        __syncthreads();
+        const double2* ph = s.ph;
+        cta_gemm<false>(n, RealMat{Einv, 1, n}, CMat{src, 1, n},
+                        [&](int i, int jj, cplx v) { st(cur + i + jj * n, ld(ph + i) * v); });
+        write_green(n, cur, d.Gt + (size_t)(qq - 1) * nn);
+        __syncthreads();
+        src = cur;
+        cur = (cur == Ga) ? Gb : Ga;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 

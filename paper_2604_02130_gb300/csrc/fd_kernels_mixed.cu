@@ -372,6 +372,8 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
         }
         if (d.G)
           for (int e = tid(); e < n * n; e += nthr()) d.G[e] = G0[(e / n) + (e % n) * n];
+        if (d.Gt)  // G(0, 0) = G
+          for (int e = tid(); e < n * n; e += nthr()) d.Gt[e] = G0[(e / n) + (e % n) * n];
       }
     } else {
       for (int b = nb; b >= 2 && ok; --b) {

@@ -34,6 +34,17 @@ def main():
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "highprec_beta64.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
+    # unequal-time Green's function G(tau, 0) = (L_tau^{-1} + R_tau)^{-1} at beta = 32
+    case = dict(L=2, nt=256, beta=32.0, U=3.0, n_stab=8, seed=1003, c=1, taus=[1, 37, 128, 255])
+    p = fi.make_problem(case["L"], case["nt"], case["beta"], case["U"], case["n_stab"],
+                        case["seed"], case["c"])
+    gt = highprec.green_tau(p.E, p.phi, case["taus"], dps=250)
+    out2 = {"source": "oracle.highprec.green_tau (mpmath, dps=250), Section 4.2", "case": case,
+            "G_re": {str(t): gt[t].real.tolist() for t in case["taus"]},
+            "G_im": {str(t): gt[t].imag.tolist() for t in case["taus"]}}
+    path2 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "highprec_gtau.json")
+    with open(path2, "w") as f:
+        json.dump(out2, f, indent=1)
 
 
 if __name__ == "__main__":
