@@ -24,12 +24,14 @@ Modules:
     highprec       -- the plain product in mpmath at 250 digits (low-temperature pin).
     unequal        -- the unequal-time Green's function G(tau, 0) (Section 4.2, Section 7
                       steps 7-9).
+    observables    -- fermion number and single-time response traces tr(O G_r) (Section 4.1).
 
 Parity pins (tests/test_oracle_*.py) tie every module to something other than itself.
 """
-from . import plain, fermion_matrix, stable, naive, free, force, unequal  # noqa: F401
+from . import plain, fermion_matrix, stable, naive, free, force, unequal, observables  # noqa: F401
 
-__all__ = ["plain", "fermion_matrix", "stable", "naive", "free", "force", "unequal", "wrap_phase"]
+__all__ = ["plain", "fermion_matrix", "stable", "naive", "free", "force", "unequal", "observables",
+           "wrap_phase"]
 
 
 def wrap_phase(z):
