@@ -70,7 +70,7 @@ typedef struct fd_ctx fd_ctx;
  *   nt        time slices, nt >= 1
  *   n_stab    slices between QR re-orthogonalisations, 1 <= n_stab <= nt, nt % n_stab == 0
  *   expA      E = exp(delta*kappa*A), nx*nx float64 (symmetric)
- *   expA_inv  E^{-1}, nx*nx float64 (symmetric); needed by fd_force and fd_green_tau, may be
+ *   expA_inv  E^{-1}, nx*nx float64 (symmetric); needed for F, G(tau, 0) and R, may be
  *             NULL otherwise
  *   phi       nt*nx float64 row-major; row t-1 is the field of slice t */
 typedef struct {
@@ -90,7 +90,13 @@ const char* fd_last_error(const fd_ctx* ctx);
 
 /* Pre-size the workspace for up to `batch` configurations like `probs` with the given outputs
  * (`what` = bitmask of FD_WANT_*), so that later calls of that shape allocate nothing. */
-enum { FD_WANT_LOGDET = 1, FD_WANT_GREEN = 2, FD_WANT_FORCE = 4, FD_WANT_GTAU = 8 };
+enum {
+  FD_WANT_LOGDET = 1,
+  FD_WANT_GREEN = 2,
+  FD_WANT_FORCE = 4,
+  FD_WANT_GTAU = 8,
+  FD_WANT_RESPONSE = 16
+};
 int fd_reserve(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec);
 
 /* log det(1 + B_Nt...B_1) for `batch` configurations.
@@ -135,7 +141,25 @@ int fd_green_tau(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet
  * Returns the worst code seen (FD_OK if all succeeded). */
 int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch);
 
-/* Number of kernel launches the last fd_logdet/fd_green/fd_force/fd_green_tau call issued. */
+/* Single-time observables (Section 4.1), with log det and optionally G and F in the same call:
+ *   nferm  device, 2*batch float64 or NULL: the fermion number n = 1 - tr G / nx (re, im),
+ *          Eq. fermion_number (the response to the chemical potential)
+ *   O, R   both NULL, or host arrays of `batch` device pointers: O[c] an nx*nx float64 operator
+ *          (row-major, read only), R[c] receives nt complex128, the response traces
+ *          R[c][r] = tr(O G_r), G_r = (1 + B_r...B_1 B_Nt...B_{r+1})^{-1}, r = 0..nt-1 (G_0 = G;
+ *          the thermal trace of the operator with the Green's function at every time slice).
+ *          With O = A (the hopping matrix), -delta sum_r R[r] = d logdet / d kappa exactly.
+ *   G, F   as for fd_force, each optional.
+ * nferm alone (or with G) runs the single log det/G kernel; F or R run the phased force path
+ * (chains, boundary Green's functions, wraps), so expA_inv is then required.  In the mixed
+ * precisions the traces of the wrapped G_r accumulate in FP32 in the tensor-core epilogue.
+ * Not available through fd_graph_create. */
+int fd_observables(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet,
+                   double* const* G, double* const* F, double* nferm, const double* const* O,
+                   double* const* R, int prec, void* stream);
+
+/* Number of kernel launches the last fd_logdet/fd_green/fd_force/fd_green_tau/fd_observables
+ * call issued. */
 int fd_last_launch_count(const fd_ctx* ctx);
 
 /* Autotuner.  fd_tune times every size class of this batch with 128 and 256 threads per CTA

@@ -54,6 +54,7 @@ SIGNATURES = [
     ("fd_green", _I, [_VP, _I, _PP, _VP, _VP, _I, _VP]),
     ("fd_force", _I, [_VP, _I, _PP, _VP, _VP, _VP, _I, _VP]),
     ("fd_green_tau", _I, [_VP, _I, _PP, _VP, _VP, _VP, _VP, _I, _VP]),
+    ("fd_observables", _I, [_VP, _I, _PP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP]),
     ("fd_status", _I, [_VP, _VP, ctypes.POINTER(_I), _I]),
     ("fd_last_launch_count", _I, [_VP]),
     ("fd_measure_fp64_peak", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),

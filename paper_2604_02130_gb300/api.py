@@ -116,24 +116,33 @@ class Result:
     G: Optional[List[torch.Tensor]]  # nx x nx complex128 each
     F: Optional[List[torch.Tensor]]  # nt x nx complex128 each
     Gtau: Optional[List[torch.Tensor]] = None  # nt x nx x nx complex128 each: G(tau, 0)
+    nferm: Optional[torch.Tensor] = None  # (batch,) complex128: 1 - tr G / nx
+    R: Optional[List[torch.Tensor]] = None  # (nt,) complex128 each: tr(O G_r)
 
 
 class Batch:
     """A fixed batch of configurations with preallocated outputs; run() enqueues one call.
 
     problems: sequence of (E, Einv, phi, n_stab) with E, Einv (nx, nx) float64 and phi (nt, nx)
-    float64 CUDA tensors (Einv may be None unless the force or G(tau, 0) is wanted).
+    float64 CUDA tensors (Einv may be None unless F, G(tau, 0) or R is wanted).
 
-    want: "logdet", or "+"-joined outputs among "green" (G), "force" (F) and "gtau" (the
-    unequal-time G(tau, 0), tau = 0..nt-1); log det always comes along."""
+    want: "logdet", or "+"-joined outputs among "green" (G), "force" (F), "gtau" (the
+    unequal-time G(tau, 0), tau = 0..nt-1), "nferm" (fermion number 1 - tr G / nx) and
+    "response" (R[r] = tr(O G_r) for the per-configuration operators `operators`, (nx, nx)
+    float64 CUDA tensors); log det always comes along.  "gtau" does not combine with "nferm" or
+    "response"."""
 
-    WANT_BITS = {"logdet": 1, "green": 2, "force": 4, "gtau": 8}
+    WANT_BITS = {"logdet": 1, "green": 2, "force": 4, "gtau": 8, "response": 16, "nferm": 32}
 
     def __init__(self, ctx: Context, problems: Sequence[Tuple], want: str = "logdet",
-                 prec: str = "fp64"):
+                 prec: str = "fp64", operators: Optional[Sequence[torch.Tensor]] = None):
         parts = set(want.split("+"))
         if not parts or not parts <= set(self.WANT_BITS):
             raise ValueError(want)
+        if "gtau" in parts and parts & {"nferm", "response"}:
+            raise ValueError("gtau does not combine with nferm/response")
+        if ("response" in parts) != (operators is not None):
+            raise ValueError("want 'response' needs operators (and only then)")
         self.ctx = ctx
         self.want = want
         self.what = 1
@@ -166,6 +175,24 @@ class Batch:
         self.G_flat = None
         self.F_flat = None
         self.Gtau_flat = None
+        self.nferm_buf = None
+        self.R = None
+        self.R_flat = None
+        self._Op = None
+        self._Rp = None
+        if self.what & 32:
+            self.nferm_buf = torch.empty((self.n, 2), dtype=torch.float64, device=dev)
+        if self.what & 16:
+            if len(operators) != self.n:
+                raise ValueError("one operator per configuration")
+            for c, O in enumerate(operators):
+                if not (O.is_cuda and O.dtype == torch.float64 and O.is_contiguous()
+                        and tuple(O.shape) == (arr[c].nx, arr[c].nx)):
+                    raise ValueError("operators must be contiguous (nx, nx) float64 CUDA tensors")
+            self._keep += list(operators)
+            self._Op = (ctypes.c_void_p * self.n)(*[O.data_ptr() for O in operators])
+            self.R_flat, self.R = self._flat(dev, [(p.nt,) for p in arr[:self.n]])
+            self._Rp = (ctypes.c_void_p * self.n)(*[r.data_ptr() for r in self.R])
         if self.what & 2:
             self.G_flat, self.G = self._flat(dev, [(p.nx, p.nx) for p in arr[:self.n]])
             self._Gp = (ctypes.c_void_p * self.n)(*[g.data_ptr() for g in self.G])
@@ -190,16 +217,16 @@ class Batch:
     def plan(self) -> List[dict]:
         """The launch plan of this batch (one dict per size class), see fd_plan_query."""
         info = (ctypes.c_int * (8 * 64))()
-        n = self.ctx.lib.fd_plan_query(self.ctx.h, self.n, self.problems, self.what, self.prec,
-                                       info, 64)
+        n = self.ctx.lib.fd_plan_query(self.ctx.h, self.n, self.problems, self.what & 31,
+                                       self.prec, info, 64)
         if n < 0:
             self.ctx.check(n)
         keys = ("nx", "kernel", "threads", "smem", "grid", "ctas_per_sm", "scratch_kib", "configs")
         return [dict(zip(keys, info[8 * g:8 * g + 8])) for g in range(min(n, 64))]
 
     def reserve(self):
-        self.ctx.check(self.ctx.lib.fd_reserve(self.ctx.h, self.n, self.problems, self.what,
-                                               self.prec))
+        self.ctx.check(self.ctx.lib.fd_reserve(self.ctx.h, self.n, self.problems,
+                                               self.what & 31, self.prec))
 
     def run(self, stream=None) -> Result:
         lib, h = self.ctx.lib, self.ctx.h
@@ -208,6 +235,10 @@ class Batch:
         if self.what & 8:
             rc = lib.fd_green_tau(h, self.n, self.problems, ld, self._Gp, self._Gtp, self._Fp,
                                   self.prec, s)
+        elif self.what & (16 | 32):
+            nf = ctypes.c_void_p(self.nferm_buf.data_ptr()) if self.nferm_buf is not None else None
+            rc = lib.fd_observables(h, self.n, self.problems, ld, self._Gp, self._Fp, nf,
+                                    self._Op, self._Rp, self.prec, s)
         elif self.what & 4:
             rc = lib.fd_force(h, self.n, self.problems, ld, self._Gp, self._Fp, self.prec, s)
         elif self.what & 2:
@@ -215,14 +246,16 @@ class Batch:
         else:
             rc = lib.fd_logdet(h, self.n, self.problems, ld, self.prec, s)
         self.ctx.check(rc)
-        return Result(torch.view_as_complex(self.logdet_buf), self.G, self.F, self.Gtau)
+        nf = torch.view_as_complex(self.nferm_buf) if self.nferm_buf is not None else None
+        return Result(torch.view_as_complex(self.logdet_buf), self.G, self.F, self.Gtau, nf,
+                      self.R)
 
     def status(self, stream=None) -> List[int]:
         return self.ctx.status(self.n, stream)
 
     def tune(self, reps: int = 2):
         """Time 128 vs 256 threads per CTA for every size class of this batch (fd_tune)."""
-        self.ctx.check(self.ctx.lib.fd_tune(self.ctx.h, self.n, self.problems, self.what,
+        self.ctx.check(self.ctx.lib.fd_tune(self.ctx.h, self.n, self.problems, self.what & 31,
                                             self.prec, reps))
 
     def graph(self) -> "BatchGraph":
@@ -235,8 +268,8 @@ class BatchGraph:
     Inputs are read and outputs written through the Batch's tensors (update phi in place)."""
 
     def __init__(self, batch: Batch):
-        if batch.what & 8:
-            raise ValueError("G(tau, 0) is not available through CUDA graphs")
+        if batch.what & (8 | 16 | 32):
+            raise ValueError("G(tau, 0) and observables are not available through CUDA graphs")
         self.batch = batch
         ctx = batch.ctx
         h = ctypes.c_void_p()
@@ -302,6 +335,17 @@ def green_tau(problems, prec: str = "fp64", with_green: bool = False,
                     (["force"] if with_force else []))
     r = Batch(ctx or default_context(), problems, want, prec).run()
     return r.logdet.clone(), r.G, r.F, r.Gtau
+
+
+def observables(problems, operators=None, prec: str = "fp64", with_force: bool = False,
+                ctx: Optional[Context] = None):
+    """log det, the fermion number 1 - tr G / nx (Section 4.1) and, with `operators` (one
+    (nx, nx) float64 CUDA tensor per configuration), the response traces tr(O G_r) at every
+    time slice; returns (logdet, nferm, [R (nt,)] or None, [F] or None)."""
+    want = "+".join(["nferm"] + (["response"] if operators is not None else []) +
+                    (["force"] if with_force else []))
+    r = Batch(ctx or default_context(), problems, want, prec, operators).run()
+    return r.logdet.clone(), r.nferm.clone(), r.R, r.F
 
 
 class FermionLogDet(torch.autograd.Function):

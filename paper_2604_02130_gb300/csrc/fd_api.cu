@@ -76,11 +76,24 @@ int cuda_fail(fd_ctx* ctx, cudaError_t e, const char* what) {
   } while (0)
 
 // What a call computes: log det/G (one persistent kernel), or the phased path (chains, boundary
-// Green's functions, wraps) for the force F and/or the unequal-time G(tau, 0) (bit mask).
-enum Kind { K_FWD = 0, K_FORCE = 1, K_GTAU = 2, K_FORCE_GTAU = 3 };
+// Green's functions, wraps) for the force F, the unequal-time G(tau, 0) and/or the response
+// traces tr(O G_r) (bit mask).
+enum Kind { K_FWD = 0, K_FORCE = 1, K_GTAU = 2, K_FORCE_GTAU = 3, K_RESP = 4 };
 int kind_of(int what) {
-  return ((what & FD_WANT_FORCE) ? K_FORCE : 0) | ((what & FD_WANT_GTAU) ? K_GTAU : 0);
+  return ((what & FD_WANT_FORCE) ? K_FORCE : 0) | ((what & FD_WANT_GTAU) ? K_GTAU : 0) |
+         ((what & FD_WANT_RESPONSE) ? K_RESP : 0);
 }
+
+// The output pointers of one call (host arrays of device pointers, or null when not wanted).
+struct Outs {
+  double* logdet = nullptr;
+  double* const* G = nullptr;
+  double* const* F = nullptr;
+  double* const* Gt = nullptr;
+  double* nf = nullptr;
+  const double* const* O = nullptr;
+  double* const* R = nullptr;
+};
 
 // One launch of a size class.  which: 0 log det/G, 1 force chains, 2 boundary G, 3 wraps.
 struct Phase {
@@ -329,7 +342,7 @@ int validate(fd_ctx* ctx, int batch, const fd_problem* probs, const void* logdet
     if (p.reserved != 0) return fail(ctx, FD_ERR_INVALID, "config %d: reserved != 0", c);
     if (!p.expA || !p.phi) return fail(ctx, FD_ERR_INVALID, "config %d: null expA or phi", c);
     if (need_einv && !p.expA_inv)
-      return fail(ctx, FD_ERR_INVALID, "config %d: fd_force and fd_green_tau need expA_inv", c);
+      return fail(ctx, FD_ERR_INVALID, "config %d: the force path (F, G(tau, 0), R) needs expA_inv", c);
   }
   return FD_OK;
 }
@@ -447,12 +460,14 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
         for (int b = 2; b <= nb; ++b) g.tB.push_back(fd::Task{k, b});
         for (int b = 1; b <= nb; ++b) g.tC.push_back(fd::Task{k, b});
         g.fws_off.push_back(g.fws_bytes);
-        g.fws_bytes += (fd::FWork::elems(n, nb, (kind & K_GTAU) != 0) * 16 + 255) & ~(size_t)255;
+        g.fws_bytes += (fd::FWork::elems(n, nb, (kind & K_GTAU) != 0, (kind & K_RESP) != 0) * 16 +
+                        255) & ~(size_t)255;
       }
       Phase A, C;
       if (!(mixed && mixed_phase(ctx, n, R_FWD, 1, three, 2 * nd, A)))
         A = fp64_phase(ctx, n, R_FWD, 1, 2 * nd);
-      Phase B = fp64_phase(ctx, n, kind == K_FORCE_GTAU ? R_BOUND2 : R_BOUND, 2,
+      const bool two_rhs = (kind & K_GTAU) && (kind & (K_FORCE | K_RESP));
+      Phase B = fp64_phase(ctx, n, two_rhs ? R_BOUND2 : R_BOUND, 2,
                            std::max(1, (int)g.tB.size()));
       // the tensor-core wrap kernel covers the force rows; G(tau, 0) wraps run in FP64
       const bool mixed_wrap = mixed && !(kind & K_GTAU);
@@ -560,9 +575,8 @@ int queue_count(const std::vector<Group>& groups) {
 
 // Host descriptor and task tables of a call.  `scratch` is the device scratch base (the force
 // workspace of each configuration lives inside it).
-void build_tables(std::vector<Group>& groups, const fd_problem* probs, double* logdet,
-                  double* const* G, double* const* F, double* const* Gt, char* scratch,
-                  Desc* out, fd::Task* tasks) {
+void build_tables(std::vector<Group>& groups, const fd_problem* probs, const Outs& o,
+                  char* scratch, Desc* out, fd::Task* tasks) {
   size_t k = 0, t = 0;
   for (auto& g : groups) {
     g.desc_off = k;
@@ -577,10 +591,13 @@ void build_tables(std::vector<Group>& groups, const fd_problem* probs, double* l
       d.E = p.expA;
       d.Einv = p.expA_inv;
       d.phi = p.phi;
-      d.logdet = logdet + 2 * (size_t)c;
-      d.G = G ? (double2*)G[c] : nullptr;
-      d.F = F ? (double2*)F[c] : nullptr;
-      d.Gt = Gt ? (double2*)Gt[c] : nullptr;
+      d.logdet = o.logdet + 2 * (size_t)c;
+      d.G = o.G ? (double2*)o.G[c] : nullptr;
+      d.F = o.F ? (double2*)o.F[c] : nullptr;
+      d.Gt = o.Gt ? (double2*)o.Gt[c] : nullptr;
+      d.nf = o.nf ? o.nf + 2 * (size_t)c : nullptr;
+      d.O = o.O ? o.O[c] : nullptr;
+      d.R = o.R ? (double2*)o.R[c] : nullptr;
       d.fws = g.kind != K_FWD
                   ? (double2*)(scratch + g.scratch_off + g.slots_bytes + g.fws_off[q])
                   : nullptr;
@@ -687,8 +704,8 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
   return FD_OK;
 }
 
-int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
-        double* const* F, double* const* Gt, int prec, void* stream_, int kind) {
+int run(fd_ctx* ctx, int batch, const fd_problem* probs, const Outs& o, int prec, void* stream_,
+        int kind) {
   cudaStream_t stream = (cudaStream_t)stream_;
   ctx->last_launches = 0;
   ctx->last_batch = batch;
@@ -706,7 +723,7 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double*
     FD_CUDA(ctx, cudaEventSynchronize(ctx->staging_done));
     ctx->staging_pending = false;
   }
-  build_tables(groups, probs, logdet, G, F, Gt, ctx->scratch, ctx->h_desc, ctx->h_tasks);
+  build_tables(groups, probs, o, ctx->scratch, ctx->h_desc, ctx->h_tasks);
   FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(Desc) * batch,
                                cudaMemcpyHostToDevice, stream));
   if (ntasks)
@@ -814,7 +831,9 @@ int fd_logdet(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, i
               void* stream) {
   int rc = validate(ctx, batch, probs, logdet, prec, false);
   if (rc != FD_OK) return rc;
-  return run(ctx, batch, probs, logdet, nullptr, nullptr, nullptr, prec, stream, K_FWD);
+  Outs o;
+  o.logdet = logdet;
+  return run(ctx, batch, probs, o, prec, stream, K_FWD);
 }
 
 int fd_green(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
@@ -824,7 +843,10 @@ int fd_green(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, do
   if (batch > 0 && !G) return fail(ctx, FD_ERR_INVALID, "null G array");
   for (int c = 0; c < batch; ++c)
     if (!G[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null G", c);
-  return run(ctx, batch, probs, logdet, G, nullptr, nullptr, prec, stream, K_FWD);
+  Outs o;
+  o.logdet = logdet;
+  o.G = G;
+  return run(ctx, batch, probs, o, prec, stream, K_FWD);
 }
 
 int fd_force(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, double* const* G,
@@ -836,7 +858,11 @@ int fd_force(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, do
     if (!F[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null F", c);
     if (G && !G[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null G", c);
   }
-  return run(ctx, batch, probs, logdet, G, F, nullptr, prec, stream, K_FORCE);
+  Outs o;
+  o.logdet = logdet;
+  o.G = G;
+  o.F = F;
+  return run(ctx, batch, probs, o, prec, stream, K_FORCE);
 }
 
 int fd_green_tau(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet,
@@ -849,7 +875,36 @@ int fd_green_tau(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet
     if (G && !G[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null G", c);
     if (F && !F[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null F", c);
   }
-  return run(ctx, batch, probs, logdet, G, F, Gtau, prec, stream, F ? K_FORCE_GTAU : K_GTAU);
+  Outs o;
+  o.logdet = logdet;
+  o.G = G;
+  o.F = F;
+  o.Gt = Gtau;
+  return run(ctx, batch, probs, o, prec, stream, F ? K_FORCE_GTAU : K_GTAU);
+}
+
+int fd_observables(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet,
+                   double* const* G, double* const* F, double* nferm, const double* const* O,
+                   double* const* R, int prec, void* stream) {
+  if (!ctx) return FD_ERR_INVALID;
+  if ((O == nullptr) != (R == nullptr))
+    return fail(ctx, FD_ERR_INVALID, "O and R must both be given or both be NULL");
+  const int kind = (F ? K_FORCE : 0) | (R ? K_RESP : 0);
+  int rc = validate(ctx, batch, probs, logdet, prec, kind != K_FWD);
+  if (rc != FD_OK) return rc;
+  for (int c = 0; c < batch; ++c) {
+    if (G && !G[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null G", c);
+    if (F && !F[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null F", c);
+    if (R && (!R[c] || !O[c])) return fail(ctx, FD_ERR_INVALID, "config %d: null O or R", c);
+  }
+  Outs o;
+  o.logdet = logdet;
+  o.G = G;
+  o.F = F;
+  o.nf = nferm;
+  o.O = O;
+  o.R = R;
+  return run(ctx, batch, probs, o, prec, stream, kind);
 }
 
 int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch) {
@@ -909,7 +964,11 @@ int fd_graph_create(fd_ctx* ctx, int batch, const fd_problem* probs, double* log
   FD_G(cudaMalloc(&g->d_queue, sizeof(int) * std::max(1, queue_count(groups))));
   FD_G(cudaMalloc(&g->d_status, sizeof(int) * batch));
   FD_G(cudaMalloc(&g->scratch, std::max<size_t>(need, 256)));
-  build_tables(groups, probs, logdet, G, F, nullptr, g->scratch, h.data(), ht.data());
+  Outs o;
+  o.logdet = logdet;
+  o.G = G;
+  o.F = F;
+  build_tables(groups, probs, o, g->scratch, h.data(), ht.data());
   FD_G(cudaMemcpy(g->d_desc, h.data(), sizeof(Desc) * batch, cudaMemcpyHostToDevice));
   FD_G(cudaMemcpy(g->d_tasks, ht.data(), sizeof(fd::Task) * ht.size(), cudaMemcpyHostToDevice));
   FD_G(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1007,8 +1066,11 @@ int fd_tune(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec,
       float tot = 0.f;
       for (int r = 0; r <= reps; ++r) {  // first run is a warm-up
         cudaEventRecord(e0, 0);
-        int rr = run(ctx, (int)sub.size(), sub.data(), d_ld, sg.data(), force ? sf.data() : nullptr,
-                     nullptr, prec, nullptr, kind);
+        Outs o;
+        o.logdet = d_ld;
+        o.G = sg.data();
+        o.F = force ? sf.data() : nullptr;
+        int rr = run(ctx, (int)sub.size(), sub.data(), o, prec, nullptr, kind);
         cudaEventRecord(e1, 0);
         if (rr != FD_OK) { result = rr; break; }
         cudaEventSynchronize(e1);
@@ -1051,7 +1113,9 @@ int fd_tune_nstab(fd_ctx* ctx, const fd_problem* prob, const int* candidates, in
   // reference: FP64 with the smallest candidate interval
   fd_problem p = *prob;
   p.n_stab = nmin;
-  int rc = run(ctx, 1, &p, d_ld, nullptr, nullptr, nullptr, FD_PREC_FP64, nullptr, K_FWD);
+  Outs o;
+  o.logdet = d_ld;
+  int rc = run(ctx, 1, &p, o, FD_PREC_FP64, nullptr, K_FWD);
   double ref[2] = {0, 0};
   if (rc == FD_OK) {
     cudaDeviceSynchronize();
@@ -1060,7 +1124,7 @@ int fd_tune_nstab(fd_ctx* ctx, const fd_problem* prob, const int* candidates, in
   int chosen = 0;
   for (int i = 0; i < ncand && rc == FD_OK; ++i) {
     p.n_stab = candidates[i];
-    rc = run(ctx, 1, &p, d_ld, nullptr, nullptr, nullptr, prec, nullptr, K_FWD);
+    rc = run(ctx, 1, &p, o, prec, nullptr, K_FWD);
     if (rc != FD_OK) break;
     double got[2];
     cudaDeviceSynchronize();

@@ -56,20 +56,25 @@ struct Desc {
   double2* F;          // nt*nx row-major or null
   double2* Gt;         // unequal-time G(tau, 0): nt*nx*nx row-major [tau][i][j], or null
   double2* fws;        // force / G(tau, 0): per-configuration workspace (FWork), else null
+  double* nf;          // fermion number 1 - tr G / nx (re, im), or null
+  const double* O;     // response operator, nx*nx row-major, or null
+  double2* R;          // response traces tr(O G_r), r = 0..nt-1, or null
 };
 
 // Per-configuration force workspace in global memory (the force is split into phases that run
 // on different CTAs):  left checkpoints L_b = B_{b ns}...B_1 as (X, T, log D) for b = 1..nb-1,
 // right checkpoints (B_Nt...B_{(b-1)ns+1})^H as (X, T, log D) for b = 2..nb, and the
 // block-boundary Green's functions G_{(b-1) ns} (column-major) for b = 1..nb, and, when the
-// unequal-time Green's function is wanted, its boundary values G((b-1) ns, 0) for b = 2..nb.
+// unequal-time Green's function is wanted, its boundary values G((b-1) ns, 0) for b = 2..nb,
+// then (response traces) the operator O in FP32 for the tensor-core wraps.
 struct FWork {
   double2* base;
   int n, nb;
   __host__ __device__ static size_t stride(int n) { return (size_t)2 * n * n + (n + 1) / 2; }
   // gt: room for the boundary values G((b-1) ns, 0) of the unequal-time Green's function
-  __host__ __device__ static size_t elems(int n, int nb, bool gt) {
-    return (size_t)2 * (nb - 1) * stride(n) + (size_t)(gt ? 2 : 1) * nb * n * n;
+  __host__ __device__ static size_t elems(int n, int nb, bool gt, bool op = false) {
+    return (size_t)2 * (nb - 1) * stride(n) + (size_t)(gt ? 2 : 1) * nb * n * n +
+           (op ? ((size_t)n * n + 3) / 4 : 0);
   }
   __device__ double2* LX(int b) const { return base + (size_t)(b - 1) * stride(n); }
   __device__ double2* LT(int b) const { return LX(b) + (size_t)n * n; }
@@ -85,6 +90,10 @@ struct FWork {
   __device__ double2* GT(int b) const {
     return b == 1 ? Gb(1)
                   : base + (size_t)2 * (nb - 1) * stride(n) + (size_t)(nb + b - 1) * n * n;
+  }
+  // O (row-major) in FP32, after the G(tau, 0) values when those are kept (gt)
+  __device__ float* OF(bool gt) const {
+    return (float*)(base + (size_t)2 * (nb - 1) * stride(n) + (size_t)(gt ? 2 : 1) * nb * n * n);
   }
 };
 

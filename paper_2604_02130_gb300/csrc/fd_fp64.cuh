@@ -749,6 +749,52 @@ __device__ inline void boundary_green(int n, bool identity_left, const double2* 
   }
 }
 
+// tr(O G) for O row-major and G column-major: both store (x, y) of O and (y, x) of G at x n + y,
+// so the trace is the element-wise product summed.  red: 2 doubles per warp of scratch.
+__device__ inline void cta_trace(int n, const double* O, const double2* G, double2* out,
+                                 double* red) {
+  double re = 0.0, im = 0.0;
+  for (int e = tid(); e < n * n; e += nthr()) {
+    const double o = O[e];
+    const double2 g = G[e];
+    re = fma(o, g.x, re);
+    im = fma(o, g.y, im);
+  }
+  re = seg_sum(re, 32);
+  im = seg_sum(im, 32);
+  if (lane_id() == 0) {
+    red[2 * warp_id()] = re;
+    red[2 * warp_id() + 1] = im;
+  }
+  __syncthreads();
+  if (tid() == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < nwarps(); ++w) {
+      a += red[2 * w];
+      b += red[2 * w + 1];
+    }
+    *out = make_double2(a, b);
+  }
+  __syncthreads();
+}
+
+// Fermion number n = 1 - tr G / nx (Section 4.1, Eq. fermion_number); G column-major.
+__device__ inline void cta_fermion_number(int n, const double2* G, double* out) {
+  if (warp_id() == 0) {
+    double re = 0.0, im = 0.0;
+    for (int x = lane_id(); x < n; x += 32) {
+      re += G[x + x * n].x;
+      im += G[x + x * n].y;
+    }
+    re = seg_sum(re, 32);
+    im = seg_sum(im, 32);
+    if (lane_id() == 0) {
+      out[0] = 1.0 - re / n;
+      out[1] = -im / n;
+    }
+  }
+}
+
 __device__ __forceinline__ void emit_force_row(int n, const double2* G, double2* Frow) {
   // F[t,x] = i (1 - G_xx) = (Im G_xx, 1 - Re G_xx)
   for (int x = tid(); x < n; x += nthr()) {

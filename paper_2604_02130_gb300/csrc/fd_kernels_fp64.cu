@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(256) k_fwd_fp64(const Desc* __restrict__ descs
       d.logdet[1] = im;
     }
     if (d.G) write_green(n, To, d.G);
+    if (d.nf) cta_fermion_number(n, To, d.nf);
     finish_status(d, s, status, re, im);
   }
 }
@@ -231,6 +232,11 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
       cta_copy(n * n, W.Gb(1), To);
       if (d.G) write_green(n, To, d.G);
       if (d.Gt) write_green(n, To, d.Gt);  // G(0, 0) = G
+      if (d.nf) cta_fermion_number(n, To, d.nf);
+      if (d.O) {  // FP32 copy of the response operator for the tensor-core wraps
+        float* of = W.OF(d.Gt != nullptr);
+        for (int e = tid(); e < n * n; e += nthr()) of[e] = (float)d.O[e];
+      }
       if (tid() == 0)
         atomicMax(status + d.user_index,
                   (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
@@ -276,7 +282,7 @@ __global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ 
     double2* Mb = (double2*)place(smem, slotp, L, B_GB);
     __syncthreads();
     boundary_green(n, false, W.LX(b - 1), W.LT(b - 1), W.LD(b - 1), W.RX(b), W.RT(b), W.RD(b),
-                   Ma, Mb, d.F ? W.Gb(b) : nullptr, s, d.Gt ? W.GT(b) : nullptr);
+                   Ma, Mb, (d.F || d.R) ? W.Gb(b) : nullptr, s, d.Gt ? W.GT(b) : nullptr);
     if (d.Gt) write_green(n, W.GT(b), d.Gt + (size_t)(b - 1) * d.nstab * n * n);
     if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     __syncthreads();
@@ -310,20 +316,25 @@ __global__ void __launch_bounds__(256) k_wrap_fp64(const Desc* __restrict__ desc
     double2* Gb = (double2*)place(smem, slotp, L, B_GB);
     __syncthreads();
     const int t0 = (b - 1) * ns, h = (ns - 1) / 2;
-    if (d.F) {
+    if (d.F || d.R) {
+      // G_r for every r of the block: force rows and/or response traces
+      auto emit = [&](const double2* G, int r) {
+        if (d.F) emit_force_row(n, G, d.F + (size_t)r * n);
+        if (d.R) cta_trace(n, d.O, G, d.R + r, s.red + 32);
+      };
       const double2* Glo = W.Gb(b);
-      emit_force_row(n, Glo, d.F + (size_t)t0 * n);
+      emit(Glo, t0);
       const double2* src = Glo;
       for (int j = 1; j <= h; ++j) {
         wrap_forward(n, E, Einv, d.phi + (size_t)(t0 + j - 1) * n, src, Ga, Gb, s);
-        emit_force_row(n, Ga, d.F + (size_t)(t0 + j) * n);
+        emit(Ga, t0 + j);
         src = Ga;
       }
       __syncthreads();
       src = W.Gb(b + 1);
       for (int qq = b * ns; qq >= t0 + h + 2; --qq) {
         wrap_backward(n, E, Einv, d.phi + (size_t)(qq - 1) * n, src, Ga, Gb, s);
-        emit_force_row(n, Ga, d.F + (size_t)(qq - 1) * n);
+        emit(Ga, qq - 1);
         src = Ga;
       }
       __syncthreads();

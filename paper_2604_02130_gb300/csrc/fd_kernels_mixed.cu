@@ -140,14 +140,26 @@ __device__ __forceinline__ void put_b(const MLayout& L, const MixedSmem& m, int 
   if (L.three) m.b_lo[o] = tc::to_tf32(v - hi);
 }
 
+// Response trace of a wrapped Green's function held in TMEM as G[c, l] = trs(l) v(l, c) tcs(c):
+// *out = sum_{l,c} O[l n + c] G[c, l] = tr(O G), O row-major FP32; slot: one float2 per warp.
+struct Trace {
+  const float* O;  // null: no trace
+  Scale rs, cs;
+  float2* slot;
+  double2* out;
+};
+
 // Epilogue of one MMA.  TMEM lane l (< n) holds v(l, c) = D[l, c] + i D[l, Np + c], c < n.
 //   TO_B_K : B(n = c, k = l) = rs(l) v cs(c)   (the lane indexes K: slices, right products)
 //   TO_B_N : B(n = l, k = c) = rs(l) v cs(c)   (the lane indexes N: wraps)
 //   TO_FP64: out[l + c n]    = rs(l) v cs(c)   (column-major FP64)
 // diag (optional): diag[l] = (Im v(l,l), 1 - Re v(l,l)), a force row F = i (1 - G_ll).
+// tr (optional): the response trace above.
 template <int MODE>
 __device__ void epilogue(const MLayout& L, const MixedSmem& m, uint32_t tbase, Scale rs,
-                         Scale cs, double2* out, double2* diag) {
+                         Scale cs, double2* out, double2* diag,
+                         const Trace& tr = Trace{nullptr, {nullptr, false}, {nullptr, false},
+                                                 nullptr, nullptr}) {
   const int n = L.n, Np = L.Np;
   const int w = warp_id(), nw = nwarps();
   const int quad = w & 3;
@@ -155,10 +167,12 @@ __device__ void epilogue(const MLayout& L, const MixedSmem& m, uint32_t tbase, S
   const int nhalf = nw > 4 ? 2 : 1;
   const int l = row_of_lane(L, quad * 32 + lane_id());  // matrix row held by this thread
   const int first_row = row_of_lane(L, quad * 32);
+  float2 acc = make_float2(0.f, 0.f);
   if (first_row < n) {
     const uint32_t lane_base = tbase + ((uint32_t)(quad * 32) << 16);
     const int nchunk = (Np + 15) / 16;
     const float2 r = l < n ? rs.at(l) : make_float2(1.f, 0.f);
+    const float2 tr_r = (tr.O && l < n) ? tr.rs.at(l) : make_float2(1.f, 0.f);
     for (int c = half; c < nchunk; c += nhalf) {
       float re[16], im[16];
       tc::tmem_ld16(lane_base + (uint32_t)(c * 16), re);
@@ -170,6 +184,12 @@ __device__ void epilogue(const MLayout& L, const MixedSmem& m, uint32_t tbase, S
           if (j < n) {
             const float2 v = make_float2(re[u], im[u]);
             if (diag && j == l) diag[l] = make_double2((double)v.y, 1.0 - (double)v.x);
+            if (tr.O) {
+              const float o = tr.O[l * n + j];
+              const float2 g = cmul32(cmul32(tr_r, v), tr.cs.at(j));
+              acc.x = fmaf(o, g.x, acc.x);
+              acc.y = fmaf(o, g.y, acc.y);
+            }
             if (MODE == NONE) continue;
             const float2 y = cmul32(cmul32(r, v), cs.at(j));
             if (MODE == TO_B_K) {
@@ -186,8 +206,26 @@ __device__ void epilogue(const MLayout& L, const MixedSmem& m, uint32_t tbase, S
       }
     }
   }
+  if (tr.O) {
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane_id() == 0) tr.slot[w] = acc;
+  }
   tc::fence_before();
   __syncthreads();
+  if (tr.O) {
+    if (tid() == 0) {
+      float2 t = make_float2(0.f, 0.f);
+      for (int k = 0; k < nw; ++k) {
+        t.x += tr.slot[k].x;
+        t.y += tr.slot[k].y;
+      }
+      *tr.out = make_double2((double)t.x, (double)t.y);
+    }
+    __syncthreads();
+  }
 }
 
 // B operand from an FP64 column-major matrix G (identity if G == nullptr):
@@ -291,6 +329,7 @@ __global__ void __launch_bounds__(256) k_fwd_mixed(const Desc* __restrict__ desc
     }
     if (d.G)
       for (int e = tid(); e < n * n; e += nthr()) d.G[e] = To[(e / n) + (e % n) * n];
+    if (d.nf) cta_fermion_number(n, To, d.nf);
   }
   tc::fence_before();
   __syncthreads();
@@ -374,6 +413,11 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
           for (int e = tid(); e < n * n; e += nthr()) d.G[e] = G0[(e / n) + (e % n) * n];
         if (d.Gt)  // G(0, 0) = G
           for (int e = tid(); e < n * n; e += nthr()) d.Gt[e] = G0[(e / n) + (e % n) * n];
+        if (d.nf) cta_fermion_number(n, G0, d.nf);
+        if (d.O) {  // FP32 copy of the response operator for the wrap epilogues
+          float* of = W.OF(d.Gt != nullptr);
+          for (int e = tid(); e < n * n; e += nthr()) of[e] = (float)d.O[e];
+        }
       }
     } else {
       for (int b = nb; b >= 2 && ok; --b) {
@@ -454,7 +498,12 @@ __global__ void __launch_bounds__(256) k_wrap_mixed(const Desc* __restrict__ des
     bool ok = true;
     const int t0 = (b - 1) * ns, h = (ns - 1) / 2;
     const double2* Glo = W.Gb(b);
-    emit_force_row(n, Glo, d.F + (size_t)t0 * n);
+    // force rows and/or response traces tr(O G_r) of every G_r of the block
+    auto frow = [&](int r) { return d.F ? d.F + (size_t)r * n : nullptr; };
+    const float* Of = d.R ? W.OF(d.Gt != nullptr) : nullptr;
+    float2* tslot = (float2*)(s.red + 48);
+    if (d.F) emit_force_row(n, Glo, frow(t0));
+    if (d.R) cta_trace(n, d.O, Glo, d.R + t0, s.red + 32);
     // forward wraps from G_{t0}: G_{t0+j}, j = 1..h; slice t0+j uses phi row t0+j-1
     for (int j = 1; j <= h && ok; ++j) {
       float2* ph = pf + ((j & 1) ? n : 0);
@@ -469,11 +518,13 @@ __global__ void __launch_bounds__(256) k_wrap_mixed(const Desc* __restrict__ des
       const bool more = j < h;
       if (more) cta_phase32(n, phn, d.phi + (size_t)(t0 + j) * n, 1.f);
       if (!mma_ab(L, m, e2_hi, e2_lo, tbase, phase)) { ok = false; break; }
+      // lane l holds column l of G_{t0+j} itself
+      const Trace trf{Of, one, one, tslot, d.R ? d.R + t0 + j : nullptr};
       if (more)
         epilogue<TO_B_N>(L, m, tbase, Scale{phn, true}, Scale{phn, false}, nullptr,
-                         d.F + (size_t)(t0 + j) * n);
+                         frow(t0 + j), trf);
       else
-        epilogue<NONE>(L, m, tbase, one, one, nullptr, d.F + (size_t)(t0 + j) * n);
+        epilogue<NONE>(L, m, tbase, one, one, nullptr, frow(t0 + j), trf);
     }
     // backward wraps from G_{b*ns}: G_{q-1}, q = b*ns .. t0+h+2; slice q uses phi row q-1
     bool first = true;
@@ -491,11 +542,13 @@ __global__ void __launch_bounds__(256) k_wrap_mixed(const Desc* __restrict__ des
       // lane m holds column m of E^{-1} G_q E; G_{q-1} = D^* (.) D has the same diagonal.
       // Next B: B(n = m, k = i) = G_{q-1}[i, m] = conj(ph_i) X[i, m] ph_m
       const bool more = qq - 1 >= t0 + h + 2;
+      const Trace trb{Of, Scale{ph, false}, Scale{ph, true}, tslot,
+                      d.R ? d.R + (qq - 1) : nullptr};
       if (more)
         epilogue<TO_B_N>(L, m, tbase, Scale{ph, false}, Scale{ph, true}, nullptr,
-                         d.F + (size_t)(qq - 1) * n);
+                         frow(qq - 1), trb);
       else
-        epilogue<NONE>(L, m, tbase, one, one, nullptr, d.F + (size_t)(qq - 1) * n);
+        epilogue<NONE>(L, m, tbase, one, one, nullptr, frow(qq - 1), trb);
     }
     if (!ok) {
       if (tid() == 0) atomicMax(status + d.user_index, ST_TIMEOUT);
