@@ -6,6 +6,12 @@ beta = 8, Nt = 64, U = 3, n_stab = 8.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec 3xtf32|tf32|fp64]
                     [--workload batch18|cold72|force72|tiny8] [--impl ours|reference]
+                    [--path force|gtau|observables]
+
+--path picks what one step computes (default `force`, the headline):
+  force        log det + G + force
+  gtau         log det + the unequal-time G(tau, 0) for every tau (Section 4.2)
+  observables  log det + fermion number + response traces tr(A G_t) at every slice (Section 4.1)
 
 The headline is the mixed-precision path (slice products on tensor cores, FP64 QR/assembly);
 the plain FP64 path is measured on the same inputs and reported beside it (`fp64_path`).
@@ -36,28 +42,45 @@ FLUSH_BYTES = 4 * L2_BYTES
 
 WORKLOAD_TEXT = {
     "batch18": "honeycomb L=3 (Nx=18), kappa=1, beta=8, Nt=64, U=3, phi~N(0,delta*U), n_stab=8, "
-               "256 configs; log det + G + force",
-    "cold72": "honeycomb L=6 (Nx=72), beta=64, Nt=512, U=3.5, n_stab=16, 64 configs; "
-              "log det + G + force",
-    "force72": "honeycomb L=6 (Nx=72), beta=32, Nt=256, U=3, n_stab=8, 32 configs; "
-               "log det + G + force",
-    "tiny8": "honeycomb L=2 (Nx=8), beta=2, Nt=16, U=2, n_stab=4, 1 config; log det + G + force",
+               "256 configs",
+    "cold72": "honeycomb L=6 (Nx=72), beta=64, Nt=512, U=3.5, n_stab=16, 64 configs",
+    "force72": "honeycomb L=6 (Nx=72), beta=32, Nt=256, U=3, n_stab=8, 32 configs",
+    "tiny8": "honeycomb L=2 (Nx=8), beta=2, Nt=16, U=2, n_stab=4, 1 config",
+}
+
+# what one step computes: Batch outputs, metric, and the text appended to the workload
+PATHS = {
+    "force": {"want": "force+green", "metric": "configs/s (log det + G + force)",
+              "what": "log det + G + force"},
+    "gtau": {"want": "gtau", "metric": "configs/s (log det + G(tau,0) for all tau)",
+             "what": "log det + unequal-time G(tau,0), tau=0..Nt-1"},
+    "observables": {"want": "nferm+response",
+                    "metric": "configs/s (log det + n + tr(A G_t) for all t)",
+                    "what": "log det + fermion number + response traces tr(A G_t), t=0..Nt-1"},
 }
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
 def _oracle_worker(args):
-    """One configuration through the CPU oracle: stabilised log det and G, and the force."""
-    name, c = args
+    """One configuration through the CPU oracle: stabilised log det and, by path, G and the
+    force, G(tau, 0) for every tau, or the fermion number and the response traces tr(A G_t)."""
+    name, c, path = args
     import fd_inputs as fi
     from oracle import force as oforce
-    from oracle import stable
+    from oracle import observables, stable, unequal
 
     p = fi.workload(name, batch=1, first=c)[0]
     t0 = time.perf_counter()
     ld, G = stable.logdet_green(p.E, p.phi, p.n_stab)
-    F = oforce.force(p.E, p.phi, p.n_stab)
-    return c, ld, G, F, time.perf_counter() - t0
+    if path == "force":
+        out = {"G": G, "F": oforce.force(p.E, p.phi, p.n_stab)}
+    elif path == "gtau":
+        gt = unequal.green_tau_stable(p.E, p.phi, p.n_stab)
+        out = {"Gtau": [gt[t] for t in range(p.nt)]}
+    else:
+        out = {"nferm": 1.0 - complex(G.trace()) / p.nx, "gmax": float(abs(G).max()),
+               "R": observables.response_traces(p.E, p.phi, p.n_stab, p.A)}
+    return c, ld, out, time.perf_counter() - t0
 
 
 def _pool(cores):
@@ -74,9 +97,9 @@ def _pool(cores):
     return pool
 
 
-def oracle_sample(pool, name, configs):
+def oracle_sample(pool, name, configs, path="force"):
     t0 = time.perf_counter()
-    res = pool.map(_oracle_worker, [(name, c) for c in configs])
+    res = pool.map(_oracle_worker, [(name, c, path) for c in configs])
     return res, time.perf_counter() - t0
 
 
@@ -153,7 +176,7 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel, workload, prec):
+def _traffic(kernel, workload, prec, step_path="force"):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
     current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -161,7 +184,10 @@ def _traffic(kernel, workload, prec):
         return None
     try:
         db = json.load(open(path))
-        e = db.get("%s|%s|%s" % (kernel, workload, prec))
+        key = "%s|%s|%s" % (kernel, workload, prec)
+        if step_path != "force":
+            key += "|" + step_path
+        e = db.get(key)
         if e and e.get("source_hash") == _kernel_source_hash():
             return e["dram_bytes_per_launch"]
     except Exception:
@@ -189,20 +215,21 @@ def run_reference(args):
     pool = _pool(cores)
     sample = list(range(min(batch, 8 * cores)))
     for _ in range(args.warmup):
-        oracle_sample(pool, name, sample[:cores])
+        oracle_sample(pool, name, sample[:cores], args.path)
     times = []
     for _ in range(args.steps):
-        _, dt = oracle_sample(pool, name, sample)
+        _, dt = oracle_sample(pool, name, sample, args.path)
         times.append(dt)
     pool.close()
     total = sum(times)
     value = len(sample) * args.steps / total
     line = {
-        "impl": "reference", "metric": "configs/s (log det + G + force)", "value": value,
+        "impl": "reference", "metric": PATHS[args.path]["metric"], "value": value,
         "unit": "configs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[name], "l2": "n/a (CPU)"},
+        "config": {"workload": WORKLOAD_TEXT[name] + "; " + PATHS[args.path]["what"],
+                   "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": "configs/s", "cores": cores, "kind": "oracle",
                          "sample": "%d of the %d configurations per step, one per process"
                                    % (len(sample), batch)},
@@ -250,21 +277,41 @@ def _time_batch(batch, ctx, steps, flush, stream, barrier, sample_clocks, gpu):
             "launches": launches, "clocks": clk.summary() if clk else None}
 
 
-def _errors(batch, res):
+def _scaled_err(a, ref):
+    import numpy as np
+
+    return float(np.abs(a - ref).max()) / max(1.0, float(np.abs(ref).max())) ** 2
+
+
+def _errors(batch, res, path="force"):
     import numpy as np
 
     ld = batch.logdet_buf.cpu().numpy()
-    e_ld = e_g = e_f = 0.0
-    for c, ldr, Gr, Fr, _ in res:
+    e_ld = 0.0
+    e = {}
+    for c, ldr, out, _ in res:
         g = complex(ld[c, 0], ld[c, 1])
         dim = abs(np.angle(np.exp(1j * (g.imag - ldr.imag))))
         e_ld = max(e_ld, max(abs(g.real - ldr.real), dim) / abs(ldr))
-        sg = max(1.0, float(np.abs(Gr).max())) ** 2
-        e_g = max(e_g, float(np.abs(batch.G[c].cpu().numpy() - Gr).max()) / sg)
-        sf = max(1.0, float(np.abs(Fr).max())) ** 2
-        e_f = max(e_f, float(np.abs(batch.F[c].cpu().numpy() - Fr).max()) / sf)
-    return {"logdet_rel": e_ld, "G_abs_over_maxG2": e_g, "F_abs_over_maxF2": e_f,
-            "configs_checked": len(res)}
+        if path == "force":
+            e["G_abs_over_maxG2"] = max(e.get("G_abs_over_maxG2", 0.0),
+                                        _scaled_err(batch.G[c].cpu().numpy(), out["G"]))
+            e["F_abs_over_maxF2"] = max(e.get("F_abs_over_maxF2", 0.0),
+                                        _scaled_err(batch.F[c].cpu().numpy(), out["F"]))
+        elif path == "gtau":
+            gt = batch.Gtau[c].cpu().numpy()
+            e["Gtau_abs_over_max2"] = max(
+                [e.get("Gtau_abs_over_max2", 0.0)] +
+                [_scaled_err(gt[t], out["Gtau"][t]) for t in range(gt.shape[0])])
+        else:
+            nf = complex(*batch.nferm_buf[c].cpu().numpy())
+            e["nferm_abs_over_maxG2"] = max(e.get("nferm_abs_over_maxG2", 0.0),
+                                            abs(nf - out["nferm"]) / max(1.0, out["gmax"]) ** 2)
+            e["R_abs_over_max"] = max(e.get("R_abs_over_max", 0.0),
+                                      float(np.abs(batch.R[c].cpu().numpy() - out["R"]).max())
+                                      / max(1.0, float(np.abs(out["R"]).max())))
+    e.update({"logdet_rel": e_ld, "configs_checked": len(res)})
+    return e
 
 
 def run_ours(args):
@@ -286,7 +333,9 @@ def run_ours(args):
 
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    from paper_2604_02130_gb300 import api, force_flops, shard
+    from paper_2604_02130_gb300 import api, shard
+    from paper_2604_02130_gb300.flops import (force_phase_flops, gtau_phase_flops,
+                                              response_phase_flops)
 
     dev = torch.device("cuda", local)
     mine = shard.shard_range(rank, w_batch)  # disjoint configuration indices per rank
@@ -297,6 +346,8 @@ def run_ours(args):
     phi_dev = phi_host.to(dev)
     E = torch.from_numpy(probs[0].E).to(dev)
     Einv = torch.from_numpy(probs[0].Einv).to(dev)
+    A = torch.from_numpy(probs[0].A).to(dev)  # operator of the response traces
+    spec = PATHS[args.path]
     ctx = api.Context(local)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -307,8 +358,9 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def make(prec):
+        ops = [A] * len(probs) if args.path == "observables" else None
         b = api.Batch(ctx, [(E, Einv, phi_dev[c], p.n_stab) for c, p in enumerate(probs)],
-                      "force+green", prec)
+                      spec["want"], prec, ops)
         b.reserve()
         for _ in range(max(3, args.warmup)):
             b.run()
@@ -320,7 +372,12 @@ def run_ours(args):
         return shard.max_over_ranks(x, dev)
 
     n_total = w_batch * ws
-    fl = force_flops(nx, nt, ns)
+    phase_flops = {"force": force_phase_flops, "gtau": gtau_phase_flops,
+                   "observables": response_phase_flops}[args.path]
+
+    def step_flops(mixed):
+        pf = phase_flops(nx, nt, ns, mixed)
+        return sum(v["fp64"] + v["tensor"] for v in pf.values())
 
     # ---- headline path: device-resident timing, L2 flushed between steps
     batch = make(args.prec)
@@ -330,11 +387,12 @@ def run_ours(args):
     value = shard.aggregate_rate(w_batch, ws, args.steps, total_ms)
 
     # ---- end to end through the public API: pinned host inputs in, results out
-    ld_host = torch.empty((w_batch, 2), dtype=torch.float64).pin_memory()
-    G_host = torch.empty(batch.G_flat.shape, dtype=torch.complex128).pin_memory()
-    F_host = torch.empty(batch.F_flat.shape, dtype=torch.complex128).pin_memory()
+    outs = {"force": [batch.logdet_buf, batch.G_flat, batch.F_flat],
+            "gtau": [batch.logdet_buf, batch.Gtau_flat],
+            "observables": [batch.logdet_buf, batch.nferm_buf, batch.R_flat]}[args.path]
+    hosts = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
     h2d = phi_host.numel() * 8
-    d2h = ld_host.numel() * 8 + G_host.numel() * 16 + F_host.numel() * 16
+    d2h = sum(t.numel() * t.element_size() for t in hosts)
     ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     barrier()
@@ -343,9 +401,8 @@ def run_ours(args):
         ev2[k][0].record(stream)
         phi_dev.copy_(phi_host, non_blocking=True)
         batch.run()
-        ld_host.copy_(batch.logdet_buf, non_blocking=True)
-        G_host.copy_(batch.G_flat, non_blocking=True)
-        F_host.copy_(batch.F_flat, non_blocking=True)
+        for h, t in zip(hosts, outs):
+            h.copy_(t, non_blocking=True)
         ev2[k][1].record(stream)
     barrier()
     e2e_ms = allmax(sum(a.elapsed_time(b) for a, b in ev2))
@@ -361,7 +418,7 @@ def run_ours(args):
         r64 = _time_batch(b64, ctx, max(3, args.steps // 2), flush, stream, barrier, False, local)
         ms64 = allmax(r64["total_ms"]) / max(3, args.steps // 2)
         fp64 = {"value": n_total / (ms64 * 1e-3), "unit": "configs/s", "ms_per_step": ms64,
-                "tflops": fl["total"] * n_total / (ms64 * 1e-3) / 1e12,
+                "tflops": step_flops(False) * n_total / (ms64 * 1e-3) / 1e12,
                 "kernel_ms": [statistics.mean(k[i] for k in r64["kernel_ms"]) for i in range(3)]}
 
     if rank != 0:
@@ -369,17 +426,17 @@ def run_ours(args):
         return 0
 
     # ---- roofline: the step is three launches (chains, boundary Green's functions, wraps);
-    #      the chain kernel dominates.  Per-launch durations from CUDA events on the launch stream.
-    from paper_2604_02130_gb300.flops import force_phase_flops
-
+    #      the longest one is reported.  Per-launch durations from CUDA events on the launch
+    #      stream.
     peaks, peak_src = _measured_peaks()
     peak_fp64 = ctx.measure_fp64_peak() / 1e3
     tf32_peak = peaks["bf16_tflops"] / 2.0
     mixed = args.prec != "fp64"
-    pf = force_phase_flops(nx, nt, ns, mixed)
+    pf = phase_flops(nx, nt, ns, mixed)
     per_launch = [statistics.mean(k[i] for k in head["kernel_ms"]) for i in range(3)]
-    names = ["k_chain_mixed" if mixed else "k_chain_fp64", "k_boundary_fp64",
-             "k_wrap_mixed" if mixed else "k_wrap_fp64"]
+    kinds = [p["kernel"] for p in plan]
+    names = [("k_chain_", "k_boundary_", "k_wrap_")[i] + ("mixed" if kinds[i] >= 4 else "fp64")
+             for i in range(3)]
     phases = []
     for i, key in enumerate("ABC"):
         ms = per_launch[i]
@@ -388,22 +445,35 @@ def run_ours(args):
         phases.append({"kernel": names[i], "ms": ms, "fp64_tflops": f64,
                        "fp64_frac": f64 / peak_fp64, "tensor_tflops": tns,
                        "tensor_frac": tns / tf32_peak})
-    k_ms = per_launch[0]
-    achieved = phases[0]["fp64_tflops"]
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-            "frac": achieved / peak_fp64, "traffic": _traffic(names[0], name, args.prec),
-            "kernel": names[0], "kernel_ms": k_ms,
-            "what": "FP64 algorithmic work of the chain kernel (QRs, assembly%s) per launch over "
-                    "its CUDA-event duration" % ("" if mixed else ", slice products"),
-            "peak_source": "FP64 DFMA probe over all SMs in this run (fd_measure_fp64_peak)",
-            "fp64_issue_cycles": dict(zip(("one_lane", "full_warp", "one_of_8_warps"),
-                                          ctx.measure_fp64_issue())),
-            "phases": phases}
-    if mixed:
-        roof["tensor"] = {"achieved": phases[0]["tensor_tflops"], "peak": tf32_peak,
-                          "unit": "TFLOP/s", "frac": phases[0]["tensor_tflops"] / tf32_peak,
-                          "what": "tensor-core work of the chain kernel (slice and right "
-                                  "products; a product counted once, not x3 for split TF32)",
+    dom = max(range(3), key=lambda i: per_launch[i])
+    k_ms = per_launch[dom]
+    what = {0: "the chain kernel (QRs, assembly%s)" % ("" if mixed else ", slice products"),
+            1: "the boundary kernel (boundary Green's functions: GEMMs, LU, solves)",
+            2: "the wrap kernel (%s)" % ("wrap products" if args.path != "gtau"
+                                         else "slice propagation of G(tau,0)")}[dom]
+    if phases[dom]["fp64_tflops"] > 0 or phases[dom]["tensor_tflops"] == 0:
+        achieved = phases[dom]["fp64_tflops"]
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+                "frac": achieved / peak_fp64,
+                "what": "FP64 algorithmic work of %s per launch over its CUDA-event duration"
+                        % what,
+                "peak_source": "FP64 DFMA probe over all SMs in this run (fd_measure_fp64_peak)"}
+    else:
+        achieved = phases[dom]["tensor_tflops"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": achieved / tf32_peak,
+                "what": "tensor-core work of %s per launch over its CUDA-event duration" % what,
+                "peak_source": "%s bf16 dense x 1/2 (TF32:BF16 nominal ratio)" % peak_src}
+    roof.update({"traffic": _traffic(names[dom], name, args.prec, args.path),
+                 "kernel": names[dom], "kernel_ms": k_ms,
+                 "fp64_issue_cycles": dict(zip(("one_lane", "full_warp", "one_of_8_warps"),
+                                               ctx.measure_fp64_issue())),
+                 "phases": phases})
+    if mixed and phases[dom]["tensor_tflops"] > 0 and roof["bound"] == "alu":
+        roof["tensor"] = {"achieved": phases[dom]["tensor_tflops"], "peak": tf32_peak,
+                          "unit": "TFLOP/s", "frac": phases[dom]["tensor_tflops"] / tf32_peak,
+                          "what": "tensor-core work of the same kernel (a product counted once, "
+                                  "not x3 for split TF32)",
                           "peak_source": "%s bf16 dense x 1/2 (TF32:BF16 nominal ratio)"
                                          % peak_src}
 
@@ -412,17 +482,17 @@ def run_ours(args):
     err = None
     if pool is not None:
         sample = list(range(min(w_batch, 8 * cores)))
-        res, dt = oracle_sample(pool, name, sample)
+        res, dt = oracle_sample(pool, name, sample, args.path)
         pool.close()
         cpu = {"value": len(sample) / dt, "unit": "configs/s", "cores": cores, "kind": "oracle",
-               "sample": "%d of the %d configurations (log det + G + force), one per process"
-                         % (len(sample), w_batch)}
-        err = {args.prec: _errors(batch, res)}
+               "sample": "%d of the %d configurations (%s), one per process"
+                         % (len(sample), w_batch, spec["what"])}
+        err = {args.prec: _errors(batch, res, args.path)}
         if b64 is not None:
-            err["fp64"] = _errors(b64, res)
+            err["fp64"] = _errors(b64, res, args.path)
 
     line = {
-        "metric": "configs/s (log det + G + force)",
+        "metric": spec["metric"],
         "value": value,
         "unit": "configs/s",
         "n_gpus": ws,
@@ -434,9 +504,10 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32+f64", "3xtf32": "3xtf32+f64"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[name], "prec": args.prec, "plan": plan,
+        "config": {"workload": WORKLOAD_TEXT[name] + "; " + spec["what"], "prec": args.prec,
+                   "plan": plan,
                    "l2": "flushed between timed steps (%d MB write)" % (FLUSH_BYTES >> 20)},
-        "tflops": fl["total"] * n_total * args.steps / (total_ms * 1e-3) / 1e12,
+        "tflops": step_flops(mixed) * n_total * args.steps / (total_ms * 1e-3) / 1e12,
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roof,
@@ -457,6 +528,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--prec", choices=("fp64", "tf32", "3xtf32"), default="3xtf32")
     ap.add_argument("--workload", choices=tuple(WORKLOAD_TEXT), default="batch18")
+    ap.add_argument("--path", choices=tuple(PATHS), default="force",
+                    help="what one step computes (default: log det + G + force)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true",
                     help="skip the FP64-path measurement reported beside the mixed path")

@@ -10,6 +10,10 @@ Per configuration with n = Nx, blocks nb = Nt / n_stab:
     but the first block, wraps 8 n^3 per slice (all slices but the nb block boundaries), one QR
     (44/3 n^3) and one boundary Green's function (2 GEMMs 16 n^3 + LU 8/3 + solve 8 +
     product 8 = 104/3 n^3) per interior block boundary (nb - 1 of each).
+  unequal-time G(tau, 0) (Section 4.2, Section 7 steps 7-9): the chains of the force, a boundary
+    solve per interior boundary (104/3 n^3; 16 n^3 more when G_t is formed beside it: a second
+    right-hand side and product), and one real x complex product 4 n^3 per propagated slice.
+  response traces tr(O G_r): 4 n^2 per slice (real O, complex G) on top of the force's G_r.
 """
 from __future__ import annotations
 
@@ -57,3 +61,22 @@ def force_phase_flops(nx: int, nt: int, n_stab: int, mixed: bool) -> dict:
                 "C": {"fp64": 0.0, "tensor": c}}
     return {"A": {"fp64": a_qr + a_prod, "tensor": 0.0}, "B": {"fp64": b, "tensor": 0.0},
             "C": {"fp64": c, "tensor": 0.0}}
+
+
+def gtau_phase_flops(nx: int, nt: int, n_stab: int, mixed: bool) -> dict:
+    """The three launches of log det + G(tau, 0) (no force): chains as for the force, boundary
+    solves for G((b-1) n_stab, 0), and the propagation inside the blocks (FP64 in every mode)."""
+    base = force_phase_flops(nx, nt, n_stab, mixed)
+    n3 = float(nx) ** 3
+    nb = nt // n_stab
+    return {"A": base["A"], "B": {"fp64": (104.0 / 3.0) * n3 * (nb - 1), "tensor": 0.0},
+            "C": {"fp64": 4 * n3 * (nt - nb), "tensor": 0.0}}
+
+
+def response_phase_flops(nx: int, nt: int, n_stab: int, mixed: bool) -> dict:
+    """log det + response traces: the force's launches plus 4 n^2 per slice for the traces
+    (FP64 in the FP64 path; FP32 CUDA-core work in the mixed epilogue, not counted there)."""
+    base = force_phase_flops(nx, nt, n_stab, mixed)
+    if not mixed:
+        base["C"] = {"fp64": base["C"]["fp64"] + 4.0 * nx * nx * nt, "tensor": 0.0}
+    return base
