@@ -116,7 +116,8 @@ struct Group {
   size_t scratch_off;     // byte offset of this group's scratch (slots, then FWork)
   size_t slots_bytes;     // CTA slots, shared by the phases (they run one after the other)
   std::vector<fd::Task> tB, tC;  // force: boundary and wrap tasks
-  size_t tB_off, tC_off;         // their offsets in the task table
+  std::vector<fd::Task> tA;      // force: chain tasks (b = 0 forward, 1 backward), LPT order
+  size_t tA_off, tB_off, tC_off;  // their offsets in the task table
   std::vector<size_t> fws_off;   // force: per configuration, bytes from the group's FWork base
   size_t fws_bytes;
   int qbase;                     // first queue counter of the group
@@ -457,12 +458,26 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       for (int k = 0; k < nd; ++k) {
         const int c = g.idx[k];
         const int nb = probs[c].nt / probs[c].n_stab;
+        g.tA.push_back(fd::Task{k, 0});
+        g.tA.push_back(fd::Task{k, 1});
         for (int b = 2; b <= nb; ++b) g.tB.push_back(fd::Task{k, b});
         for (int b = 1; b <= nb; ++b) g.tC.push_back(fd::Task{k, b});
         g.fws_off.push_back(g.fws_bytes);
         g.fws_bytes += (fd::FWork::elems(n, nb, (kind & K_GTAU) != 0, (kind & K_RESP) != 0) * 16 +
                         255) & ~(size_t)255;
       }
+      // chains longest first (LPT): a forward chain carries one more QR and the assembly, so for
+      // equal configurations all forward chains go out before the backward ones and the SMs that
+      // receive an extra chain get a short one
+      auto chain_cost = [&](const fd::Task& t) {
+        const fd_problem& p = probs[g.idx[t.desc]];
+        const long long nb = p.nt / p.n_stab;
+        return t.b == 0 ? (long long)p.nt + 16 * (nb + 1)
+                        : (long long)(p.nt - p.n_stab) + 16 * (nb - 1);
+      };
+      std::stable_sort(g.tA.begin(), g.tA.end(), [&](const fd::Task& a, const fd::Task& b) {
+        return chain_cost(a) > chain_cost(b);
+      });
       Phase A, C;
       if (!(mixed && mixed_phase(ctx, n, R_FWD, 1, three, 2 * nd, A)))
         A = fp64_phase(ctx, n, R_FWD, 1, 2 * nd);
@@ -563,7 +578,7 @@ size_t scratch_need(std::vector<Group>& groups) {
 
 size_t task_count(const std::vector<Group>& groups) {
   size_t t = 0;
-  for (auto& g : groups) t += g.tB.size() + g.tC.size();
+  for (auto& g : groups) t += g.tA.size() + g.tB.size() + g.tC.size();
   return t;
 }
 
@@ -603,6 +618,8 @@ void build_tables(std::vector<Group>& groups, const fd_problem* probs, const Out
                   : nullptr;
       out[k++] = d;
     }
+    g.tA_off = t;
+    for (auto& x : g.tA) tasks[t++] = x;
     g.tB_off = t;
     for (auto& x : g.tB) tasks[t++] = x;
     g.tC_off = t;
@@ -673,9 +690,11 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
           break;
         case 1:
           if (P.mixed)
-            fd::launch_chain_mixed(dd, nd, d_queue + qi, d_status, scr, P.ML, P.grid, s);
+            fd::launch_chain_mixed(dd, d_tasks + g.tA_off, (int)g.tA.size(), d_queue + qi,
+                                   d_status, scr, P.ML, P.grid, s);
           else
-            fd::launch_chain_fp64(dd, nd, d_queue + qi, d_status, scr, P.L, P.grid, s);
+            fd::launch_chain_fp64(dd, d_tasks + g.tA_off, (int)g.tA.size(), d_queue + qi,
+                                  d_status, scr, P.L, P.grid, s);
           break;
         case 2:
           fd::launch_boundary_fp64(dd, d_tasks + g.tB_off, (int)g.tB.size(), d_queue + qi,

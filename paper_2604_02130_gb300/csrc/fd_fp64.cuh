@@ -71,7 +71,10 @@ __device__ __forceinline__ void gemm_tiles(int n, const AOp& A, const BOp& B, co
   const int tm = (n + TM - 1) / TM, tn = (n + TN - 1) / TN;
   const int ntiles = tm * tn;
   for (int tile = tid(); tile < ntiles; tile += nthr()) {
-    const int i0 = (tile % tm) * TM, j0 = (tile / tm) * TN;
+    // TRI: row-major tile order, so that the lanes of a warp span one or two tile rows and the
+    // triangular k-loop (from i0) saves work for the whole warp; else column-major
+    const int i0 = TRI ? (tile / tn) * TM : (tile % tm) * TM;
+    const int j0 = TRI ? (tile % tn) * TN : (tile / tm) * TN;
     int ii[TM], jj[TN];
 #pragma unroll
     for (int a = 0; a < TM; ++a) ii[a] = min(i0 + a, n - 1);
@@ -163,7 +166,8 @@ struct Small {
   double* sd;      // n
   int* perm;       // n
   int* piv;        // n
-  int* misc;       // 32 ints: [0] status bits, [1] swap parity, [2] pivot index
+  int* misc;       // 32 ints: [0] status bits, [1] swap parity, [2] pivot index, [4] scaled QR,
+                   // [5] leader-warp offset, [6] throughput mode (several CTAs per SM)
   double* red;     // 64 doubles: cross-warp reductions
 };
 
@@ -234,15 +238,20 @@ __device__ __forceinline__ int leader_warp(int step, const int* misc) {
   return ((step + misc[5]) % nw + nw) % nw;
 }
 
-// Segment width W for `cols` independent column reductions over `rows` rows, chosen to minimise
-// the FP64 warp-instructions on the busiest SM sub-partition (the bound on this GPU):
-//   (column groups per sub-partition) x (8 per row-iteration + 2 per reduction level + 2).
-__device__ __forceinline__ int seg_width_cols(int rows, int cols) {
+// Segment width W for `cols` independent column reductions over `rows` rows.  The SM's FP64 unit
+// takes one warp-instruction per ~19 cycles whatever the number of active lanes, with 64 cycles
+// of latency.  With one CTA on the SM (latency mode, tput = false) W minimises the FP64
+// instructions of the busiest warp slot, (column groups per sub-partition) x (8 per
+// row-iteration + 2 per reduction level + 2); with several CTAs sharing the unit (throughput
+// mode) it minimises the total, (column groups) x (the same per-group count).  `slots`: warps
+// that share the columns (at most one per sub-partition counts).
+__device__ __forceinline__ int seg_width_cols(int rows, int cols, bool tput, int slots = 4) {
+  slots = max(1, min(4, slots));
   int best_w = 32, best_c = 1 << 30;
   for (int W = 1, lg = 0; W <= 32; W <<= 1, ++lg) {
     const int S = 32 / W;
     const int warps = (cols + S - 1) / S;
-    const int per_sp = (warps + 3) / 4;
+    const int per_sp = tput ? warps : (warps + slots - 1) / slots;
     const int cost = per_sp * (8 * ((rows + W - 1) / W) + 2 * lg + 2);
     if (cost < best_c || (cost == best_c && W > best_w)) {
       best_c = cost;
@@ -260,18 +269,74 @@ __device__ __forceinline__ int seg_width4(int rows) {
 }
 
 // ---------------------------------------------------------------- Householder helpers
-// Reflector for column k of A (rows k..n-1), computed by one segment of W lanes (sl = lane in
-// segment, all 32 lanes of the warp call this; only the owning segment's results are stored).
-// H = I - tau v v^H with v_k = 1, tau real = 2/(v^H v), H x = alpha e_k,
-// alpha = -(x_k/|x_k|) ||x||.  v (rows > k) overwrites A; rdiag[k] = alpha.
-__device__ __forceinline__ void seg_reflector(int n, int k, double2* A, int W, int sl, bool owner,
-                                              Small& s) {
-  double sig = 0.0;
-  if (owner)
-    for (int i = k + 1 + sl; i < n; i += W) sig += abs2(ld(A + i + k * n));
-  sig = seg_sum(sig, W);
-  if (!owner) return;
-  cplx x = ld(A + k + k * n);
+// Reflector of a column with leading entry x and sig = sum of |a_i|^2 below it:
+// H = I - tau v v^H with v_k = 1, v_i = a_i / c (i > k), H a = alpha e_k,
+//   alpha = -(x/|x|) nrm,  c = x - alpha = x (|x| + nrm) / |x|,  nrm = sqrt(|x|^2 + sig),
+//   tau = 2 / (v^H v) = 1 + |x| / nrm,   1 / c = conj(x) / (|x| (|x| + nrm)).
+// The dependent chain is kept short for the FP64 pipe (64-cycle latency per dependent
+// operation on this GPU): 1/|x|, 1/nrm and 1/(|x| + nrm) are seeded in FP32 from one FP64->FP32
+// conversion each and refined in FP64 by one third-order step of Householder's iteration
+// (Householder, "The Numerical Treatment of a Single Nonlinear Equation", 1970):
+//   1/sqrt(a): e = 1 - a y^2,  y <- y (1 + e/2 + 3e^2/8);   1/s: e = 1 - s y,  y <- y (1 + e + e^2),
+// which takes the ~2^-22 FP32 seeds past FP64 precision.  Arguments outside the FP32 range take
+// the plain IEEE operations.
+struct Refl {
+  cplx alpha, cinv;
+  double tau;
+  bool zero;  // the column is exactly zero (singular product)
+};
+__device__ __forceinline__ double rsqrt_step3(double a, double y) {
+  const double t = a * y;
+  const double e = fma(-t, y, 1.0);
+  return fma(y, e * fma(e, 0.375, 0.5), y);
+}
+__device__ __forceinline__ Refl reflector_math(cplx x, double sig) {
+  const double x2 = abs2(x);
+  const double n2 = x2 + sig;
+  const float x2f = (float)x2, n2f = (float)n2;
+  Refl r;
+  r.zero = false;
+  if (x2f > 1e-36f && n2f < 1e36f) {
+    const float rxf = rsqrtf(x2f), rnf = rsqrtf(n2f);
+    const float icf = __frcp_rn(fmaf(x2f, rxf, n2f * rnf));
+    const double rx = rsqrt_step3(x2, (double)rxf), rn = rsqrt_step3(n2, (double)rnf);
+    const double ax = x2 * rx, nrm = n2 * rn;
+    double ic = (double)icf;
+    const double e = fma(-(ax + nrm), ic, 1.0);
+    ic = fma(ic, fma(e, e, e), ic);
+    const double cf = rx * ic, g = nrm * rx;
+    r.cinv = cx(x.re * cf, -x.im * cf);
+    r.alpha = cx(-x.re * g, -x.im * g);
+    r.tau = fma(ax, rn, 1.0);
+    return r;
+  }
+  if (!(n2 > 0.0)) {
+    r.zero = true;
+    r.alpha = cx(0, 0);
+    r.cinv = cx(0, 0);
+    r.tau = 0.0;
+    return r;
+  }
+  const double nrm = sqrt(n2);
+  if (x2 > 0.0) {
+    const double ax = sqrt(x2);
+    const double cf = 1.0 / (ax * (ax + nrm)), g = nrm / ax;
+    r.cinv = cx(x.re * cf, -x.im * cf);
+    r.alpha = cx(-x.re * g, -x.im * g);
+    r.tau = 1.0 + ax / nrm;
+  } else {
+    r.cinv = cx(1.0 / nrm, 0.0);
+    r.alpha = cx(-nrm, 0.0);
+    r.tau = 1.0;
+  }
+  return r;
+}
+
+// Finish the reflector of column k inside one segment of W lanes (sl = lane in segment) given
+// its sig and leading entry x (known to every lane of the segment): scale the rows below the
+// diagonal by 1/c, store tau and R_kk = alpha.
+__device__ __forceinline__ void seg_reflector_finish(int n, int k, double2* A, int W, int sl,
+                                                     cplx x, double sig, Small& s) {
   if (k == n - 1) {
     if (sl == 0) {
       s.tau[k] = 0.0;
@@ -279,9 +344,8 @@ __device__ __forceinline__ void seg_reflector(int n, int k, double2* A, int W, i
     }
     return;
   }
-  const double x2 = abs2(x);
-  const double n2 = x2 + sig;
-  if (!(n2 > 0.0)) {  // exactly zero column: singular product
+  const Refl r = reflector_math(x, sig);
+  if (r.zero) {
     if (sl == 0) {
       s.tau[k] = 0.0;
       st(s.rdiag + k, cx(0, 0));
@@ -289,69 +353,130 @@ __device__ __forceinline__ void seg_reflector(int n, int k, double2* A, int W, i
     }
     return;
   }
-  const double nrm = sqrt64(n2);
-  // alpha = -(x/|x|) nrm;  c = x - alpha = x (1 + nrm/|x|)  (c = nrm if x = 0)
-  cplx alpha, c;
-  if (x2 > 0.0) {
-    const double rx = rsqrt64(x2);  // 1/|x|
-    const double g = nrm * rx;
-    alpha = cx(-x.re * g, -x.im * g);
-    c = cx(x.re * (1.0 + g), x.im * (1.0 + g));
-  } else {
-    alpha = cx(-nrm, 0.0);
-    c = cx(nrm, 0.0);
-  }
-  const double c2 = abs2(c);
-  const double ic2 = rcp64(c2);
-  const cplx cinv = cx(c.re * ic2, -c.im * ic2);
-  for (int i = k + 1 + sl; i < n; i += W) st(A + i + k * n, ld(A + i + k * n) * cinv);
+  for (int i = k + 1 + sl; i < n; i += W) st(A + i + k * n, ld(A + i + k * n) * r.cinv);
   if (sl == 0) {
-    s.tau[k] = 2.0 * rcp64(fma(sig, ic2, 1.0));
-    st(s.rdiag + k, alpha);
+    s.tau[k] = r.tau;
+    st(s.rdiag + k, r.alpha);
   }
 }
 
-// Apply H_k = I - tau v v^H (v_k = 1, v_i = A(i,k) below the diagonal) to columns j of A in
-// [j_begin, n), rows k..n-1.  Segments of W lanes own one column each; the segment owning
-// column k+1 (warp 0, first round) then builds the reflector of column k+1.
-__device__ __forceinline__ void householder_step(int n, int k, double2* A, Small& s,
-                                                 bool next_reflector) {
-  const int lane = lane_id(), w = warp_id(), NW = nwarps();
-  const int W = seg_width_cols(n - k, n - k - 1);
-  const int spw = 32 / W;
+// Reflector for column k of A (rows k..n-1), computed by one segment of W lanes (all 32 lanes of
+// the warp call this; only the owning segment's results are stored).  v (rows > k) overwrites A;
+// rdiag[k] = alpha.
+__device__ __forceinline__ void seg_reflector(int n, int k, double2* A, int W, int sl, bool owner,
+                                              Small& s) {
+  double sa = 0.0, sb = 0.0;
+  if (owner)
+    for (int i = k + 1 + sl; i < n; i += W) {
+      const cplx a = ld(A + i + k * n);
+      sa = fma(a.re, a.re, sa);
+      sb = fma(a.im, a.im, sb);
+    }
+  const double sig = seg_sum(sa + sb, W);
+  if (!owner) return;
+  seg_reflector_finish(n, k, A, W, sl, ld(A + k + k * n), sig, s);
+}
+
+// One warp's share of a Householder step: apply H_k = I - tau v v^H (v_k = 1, v_i = A(i,k) below
+// the diagonal, rows k..n-1) to the columns j = base + lane/W, base = b0, b0 + bstep, ... < n,
+// segments of W lanes per column.  If build_next, the segment that owns column k+1 (base b0 =
+// k+1, first segment) accumulates that column's norm below row k+1 while it updates it and then
+// builds the reflector of column k+1 without another pass.
+__device__ __forceinline__ void hh_columns(int n, int k, double2* A, Small& s, int W, int b0,
+                                           int bstep, bool build_next, bool tput) {
+  const int lane = lane_id();
   const int sl = lane % W;
   const double tk = s.tau[k];
-  const int lead = leader_warp(k + 1, s.misc);  // owns column k+1 and its reflector
-  const int slot0 = (w - lead + NW) % NW;
-  for (int base = k + 1 + slot0 * spw; base < n; base += NW * spw) {
+  for (int base = b0; base < n; base += bstep) {
     const int j = base + lane / W;
     const bool act = j < n;
-    double sr = 0.0, si = 0.0;
+    // two accumulators per component in latency mode (half the dependent chain), one in
+    // throughput mode (two FP64 instructions fewer per column group)
+    double sr0 = 0.0, sr1 = 0.0, si0 = 0.0, si1 = 0.0;
     if (act) {
-      for (int i = k + sl; i < n; i += W) {
-        const cplx v = (i == k) ? cx(1.0, 0.0) : ld(A + i + k * n);
-        const cplx a = ld(A + i + j * n);
-        sr = fma(v.re, a.re, sr);
-        sr = fma(v.im, a.im, sr);
-        si = fma(v.re, a.im, si);
-        si = fma(-v.im, a.re, si);
+      if (tput) {
+        for (int i = k + sl; i < n; i += W) {
+          const cplx v = (i == k) ? cx(1.0, 0.0) : ld(A + i + k * n);
+          const cplx a = ld(A + i + j * n);
+          sr0 = fma(v.re, a.re, sr0);
+          sr0 = fma(v.im, a.im, sr0);
+          si0 = fma(v.re, a.im, si0);
+          si0 = fma(-v.im, a.re, si0);
+        }
+      } else {
+        for (int i = k + sl; i < n; i += W) {
+          const cplx v = (i == k) ? cx(1.0, 0.0) : ld(A + i + k * n);
+          const cplx a = ld(A + i + j * n);
+          sr0 = fma(v.re, a.re, sr0);
+          sr1 = fma(v.im, a.im, sr1);
+          si0 = fma(v.re, a.im, si0);
+          si1 = fma(-v.im, a.re, si1);
+        }
       }
     }
-    sr = seg_sum(sr, W);
-    si = seg_sum(si, W);
+    const double sr = seg_sum(tput ? sr0 : sr0 + sr1, W);
+    const double si = seg_sum(tput ? si0 : si0 + si1, W);
+    const bool first = build_next && base == b0;  // warp-uniform
+    const bool mine = first && j == k + 1;        // this segment builds the next reflector
+    double sg0 = 0.0, sg1 = 0.0;
+    cplx xn = cx(0.0, 0.0);
     if (act) {
       const cplx f = cx(tk * sr, tk * si);
       for (int i = k + sl; i < n; i += W) {
         const cplx v = (i == k) ? cx(1.0, 0.0) : ld(A + i + k * n);
-        st(A + i + j * n, cfms(ld(A + i + j * n), f, v));
+        const cplx a = cfms(ld(A + i + j * n), f, v);
+        st(A + i + j * n, a);
+        if (mine) {
+          if (i > k + 1) {
+            sg0 = fma(a.re, a.re, sg0);
+            sg1 = fma(a.im, a.im, sg1);
+          } else if (i == k + 1) {
+            xn = a;
+          }
+        }
       }
     }
-    if (next_reflector && base == k + 1) {
+    if (first) {
+      const double sig = seg_sum(sg0 + sg1, W);
+      // x = new A(k+1, k+1), held by the lane of the segment that owns row k+1
+      const int src = (lane & ~(W - 1)) + (1 % W);
+      xn.re = __shfl_sync(0xffffffffu, xn.re, src);
+      xn.im = __shfl_sync(0xffffffffu, xn.im, src);
       __syncwarp();
-      seg_reflector(n, k + 1, A, seg_width4(n - k - 1), lane % seg_width4(n - k - 1),
-                    lane < seg_width4(n - k - 1), s);
+      if (lane < W) seg_reflector_finish(n, k + 1, A, W, sl, xn, sig, s);
     }
   }
+}
+
+// Householder step k on the CTA.  The serial reflector of column k+1 is the critical path of
+// the factorisation, so the warp that builds it (the step's leader) only updates the first few
+// columns, with wide segments (short dependent chains); the other warps share the remaining
+// columns with the segment width of seg_width_cols.
+__device__ __forceinline__ void householder_step(int n, int k, double2* A, Small& s,
+                                                 bool next_reflector) {
+  const int w = warp_id(), NW = nwarps();
+  const bool tput = s.misc[6] != 0;
+  const int rows = n - k, cols = n - k - 1;
+  const int lead = leader_warp(k + 1, s.misc);
+  if (NW == 1) {
+    const int W = seg_width_cols(rows, cols, tput);
+    hh_columns(n, k, A, s, W, k + 1, 32 / W, next_reflector, tput);
+    return;
+  }
+  int W1 = 32;  // smallest power of two with at most two rows per lane
+  while (W1 > 1 && 2 * (W1 / 2) >= rows) W1 >>= 1;
+  const int S1 = 32 / W1;
+  if (w == lead) {
+    hh_columns(n, k, A, s, W1, k + 1, n, next_reflector, tput);  // one round: k+1 .. k+S1
+    return;
+  }
+  const int rest = cols - S1;
+  if (rest <= 0) return;
+  const int others = NW - 1;
+  const int slot = (w - lead - 1 + NW) % NW;  // 0 .. others-1
+  const int W = seg_width_cols(rows, rest, tput, others);
+  const int spw = 32 / W;
+  hh_columns(n, k, A, s, W, k + 1 + S1 + slot * spw, others * spw, false, tput);
 }
 
 // ---------------------------------------------------------------- QR re-orthogonalisation
@@ -368,7 +493,7 @@ __device__ inline void cta_reortho(int n, const double2* Xc, double2* Xn, const 
   float* keyf = (float*)s.key;
   // 1. pivot keys (FP32 ordering keys: the pre-pivot order only has to be approximately sorted)
   {
-    const int W0 = seg_width_cols(n, n);
+    const int W0 = seg_width_cols(n, n, s.misc[6] != 0, NW);
     const int spw0 = 32 / W0;
     for (int base = w * spw0; base < n; base += NW * spw0) {
       const int j = base + lane / W0;
@@ -493,7 +618,7 @@ __device__ inline void cta_reortho(int n, const double2* Xc, double2* Xn, const 
       s.vbuf[((n - 2) & 1) * n + i] = Xn[i + (n - 2) * n];
   __syncthreads();
   for (int k = n - 2; k >= 0; --k) {
-    const int W = seg_width_cols(n - k, n - k);
+    const int W = seg_width_cols(n - k, n - k, s.misc[6] != 0, NW);
     const int spw = 32 / W;
     const int sl = lane % W;
     const double tk = s.tau[k];

@@ -8,9 +8,10 @@ namespace fd {
 // FP64 path
 void launch_fwd_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                      const Layout& L, int grid, cudaStream_t stream);
-// force phases: A chains (2 tasks per configuration), B boundary Green's functions, C wraps
-void launch_chain_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
-                       const Layout& L, int grid, cudaStream_t stream);
+// force phases: A chains (2 tasks per configuration: Task.b = 0 forward, 1 backward),
+// B boundary Green's functions, C wraps
+void launch_chain_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
+                       char* scratch, const Layout& L, int grid, cudaStream_t stream);
 void launch_boundary_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue,
                           int* status, char* scratch, const Layout& L, int grid,
                           cudaStream_t stream);
@@ -24,8 +25,9 @@ cudaError_t attrs_fp64(int which, cudaFuncAttributes* a);
 // mixed path (tcgen05 slice GEMMs)
 void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                       const MLayout& L, int grid, cudaStream_t stream);
-void launch_chain_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
-                        const MLayout& L, int grid, cudaStream_t stream);
+void launch_chain_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue,
+                        int* status, char* scratch, const MLayout& L, int grid,
+                        cudaStream_t stream);
 void launch_wrap_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                        char* scratch, const MLayout& L, int grid, cudaStream_t stream);
 cudaError_t set_smem_mixed(int bytes);

@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(256) k_fwd_fp64(const Desc* __restrict__ descs
     if (tid() == 0) {
       s.misc[0] = 0;
       s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
+      s.misc[6] = gridDim.x > (unsigned)L.num_sms;  // several CTAs per SM: throughput mode
     }
     Bufs B = setup_bufs(smem, slotp, d, L, false);
     double2* X = B.X[0];
@@ -184,7 +185,8 @@ __device__ void wrap_backward(int n, const double* E, const double* Einv, const 
 //             1..nb-1; at the end log det and G_0 = G (also the boundary G of block 1).
 //   backward: the right products as adjoints, X_R D_R T_R <- B_{t+1}^H ... B_Nt^H, a QR every
 //             n_stab slices; right checkpoints at t = (b-1) n_stab for blocks b = nb..2.
-__global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ descs, int ndesc,
+__global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ descs,
+                                                     const Task* __restrict__ tasks, int ntasks,
                                                      int* queue, int* status, char* scratch,
                                                      Layout L) {
   extern __shared__ __align__(16) char smem[];
@@ -192,15 +194,17 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
   for (;;) {
     int* slot = (int*)(smem + L.smem_bytes - 16);
     const int q = grab(queue, slot);
-    if (q >= 2 * ndesc) return;
-    const Desc d = descs[q >> 1];
-    const bool fwd = (q & 1) == 0;
+    if (q >= ntasks) return;
+    const Task tk = tasks[q];
+    const Desc d = descs[tk.desc];
+    const bool fwd = tk.b == 0;
     const int n = d.nx, ns = d.nstab, nb = d.nt / d.nstab;
     const FWork W{d.fws, n, nb};
     Small s = carve_small(smem + L.small_off, n);
     if (tid() == 0) {
       s.misc[0] = 0;
       s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
+      s.misc[6] = gridDim.x > (unsigned)L.num_sms;  // several CTAs per SM: throughput mode
     }
     Bufs B = setup_bufs(smem, slotp, d, L, false);
     double2* X = B.X[0];
@@ -277,6 +281,7 @@ __global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ 
     if (tid() == 0) {
       s.misc[0] = 0;
       s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2 + b);
+      s.misc[6] = gridDim.x > (unsigned)L.num_sms;  // several CTAs per SM: throughput mode
     }
     double2* Ma = (double2*)place(smem, slotp, L, B_GA);
     double2* Mb = (double2*)place(smem, slotp, L, B_GB);
@@ -387,10 +392,10 @@ void launch_fwd_fp64(const Desc* descs, int ndesc, int* queue, int* status, char
                      const Layout& L, int grid, cudaStream_t stream) {
   k_fwd_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch, L);
 }
-void launch_chain_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
-                       const Layout& L, int grid, cudaStream_t stream) {
-  k_chain_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch,
-                                                            L);
+void launch_chain_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
+                       char* scratch, const Layout& L, int grid, cudaStream_t stream) {
+  k_chain_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue, status,
+                                                            scratch, L);
 }
 void launch_boundary_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue,
                           int* status, char* scratch, const Layout& L, int grid,

@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(256) k_fwd_mixed(const Desc* __restrict__ desc
     if (tid() == 0) {
       s.misc[0] = 0;
       s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
+      s.misc[6] = gridDim.x > (unsigned)L.num_sms;  // several CTAs per SM: throughput mode
     }
     fill_a(L, m.a_hi, m.a_lo, d.E);
     cta_identity(n, T);
@@ -343,7 +344,8 @@ __global__ void __launch_bounds__(256) k_fwd_mixed(const Desc* __restrict__ desc
 // G_0 go to the configuration's global workspace (FWork).  The backward chain multiplies the
 // right products as adjoints, X_R <- diag(e^{-i phi_s}) E X_R, the conjugate phase applied in the
 // epilogue.
-__global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ descs, int ndesc,
+__global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ descs,
+                                                      const Task* __restrict__ tasks, int ntasks,
                                                       int* queue, int* status, char* scratch,
                                                       MLayout L) {
   extern __shared__ __align__(128) char smem[];
@@ -362,9 +364,10 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
   const Scale one{nullptr, false};
   for (;;) {
     const int q = grab_m(queue, m.qslot);
-    if (q >= 2 * ndesc) break;
-    const Desc d = descs[q >> 1];
-    const bool fwd = (q & 1) == 0;
+    if (q >= ntasks) break;
+    const Task tk = tasks[q];
+    const Desc d = descs[tk.desc];
+    const bool fwd = tk.b == 0;
     const int ns = d.nstab, nb = d.nt / d.nstab;
     const FWork W{d.fws, n, nb};
     Small s = carve_small(smem + L.small_off, n);
@@ -372,6 +375,7 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
     if (tid() == 0) {
       s.misc[0] = 0;
       s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
+      s.misc[6] = gridDim.x > (unsigned)L.num_sms;  // several CTAs per SM: throughput mode
     }
     fill_a(L, m.a_hi, m.a_lo, d.E);
     cta_identity(n, T);
@@ -562,10 +566,11 @@ __global__ void __launch_bounds__(256) k_wrap_mixed(const Desc* __restrict__ des
   if (warp_id() == 0) tc::tmem_dealloc(tbase, (uint32_t)L.tmem_cols);
 }
 
-void launch_chain_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
-                        const MLayout& L, int grid, cudaStream_t stream) {
-  k_chain_mixed<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch,
-                                                             L);
+void launch_chain_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue,
+                        int* status, char* scratch, const MLayout& L, int grid,
+                        cudaStream_t stream) {
+  k_chain_mixed<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue, status,
+                                                             scratch, L);
 }
 void launch_wrap_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                        char* scratch, const MLayout& L, int grid, cudaStream_t stream) {

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(FD_NOALLOC_THREADS) k_fwd_fp64_noalloc(NPack p
   if (tid() == 0) {
     s.misc[0] = 0;
     s.misc[5] = 0;  // leader-warp offset of the shared CTA routines
+    s.misc[6] = 0;  // latency-mode segment widths
   }
   cta_load_real(n * n, Es, d.E);
   cta_identity(n, X);

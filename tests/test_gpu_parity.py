@@ -82,14 +82,21 @@ def test_tiny_workload(ctx):
     assert np.abs(F[0] - oforce.force(p.E, p.phi, p.n_stab)).max() <= F_ATOL_FP64
 
 
+def _inv_tol(M):
+    # FP64 element tolerance of G (and of F = i (1 - diag G_t)): G = (1 + P)^{-1} moves by
+    # -G dP G under a relative perturbation dP of the product, so element errors scale with
+    # max|G|^2 (single beta = 64 configurations reach max|G| ~ 300)
+    return max(1e-10, 1e-12 * max(1.0, float(np.abs(M).max())) ** 2)
+
+
 def _invariants(probs, ld, G=None, F=None):
     for c, p in enumerate(probs):
         r = (ld[c].imag - 0.5 * p.phi.sum()) / np.pi
         assert abs(r - round(r)) < 1e-8
         if G is not None:
-            assert np.abs(np.diag(G[c]).real - 0.5).max() < 1e-8
+            assert np.abs(np.diag(G[c]).real - 0.5).max() < _inv_tol(G[c])
         if F is not None:
-            assert np.abs(F[c].imag - 0.5).max() < 1e-8
+            assert np.abs(F[c].imag - 0.5).max() < _inv_tol(F[c])
 
 
 def test_batch18_full(ctx):
