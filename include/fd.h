@@ -162,9 +162,10 @@ int fd_observables(fd_ctx* ctx, int batch, const fd_problem* probs, double* logd
  * call issued. */
 int fd_last_launch_count(const fd_ctx* ctx);
 
-/* Autotuner.  fd_tune times every size class of this batch with 128 and 256 threads per CTA
- * (`reps` timed runs each after a warm-up, FP64 or mixed as `prec` says) and keeps the faster
- * choice in the context's plan cache, which later plans (calls, graphs, fd_plan_query) use.
+/* Autotuner.  fd_tune times every launch (phase) of every size class of this batch with 128 and
+ * 256 threads per CTA, one launch at a time on its own CUDA-event time (`reps` timed runs each
+ * after a warm-up, FP64 or mixed as `prec` says), and keeps the faster choice per launch in the
+ * context's plan cache, which later plans (calls, graphs, fd_plan_query) use.
  * Synchronous; allocates and frees its own trial outputs.
  * fd_tune_nstab picks, for one configuration, the largest QR interval among `candidates`
  * (each must divide nt) whose log det at precision `prec` stays within `rel_budget`

@@ -234,24 +234,38 @@ fd::MLayout plan_mixed(int n, int role, bool three, int budget, int smem_per_sm)
   const long long b_one = (long long)M.N * M.Kp * 4;
   const long long b_bytes = b_one * (three ? 2 : 1);
   const long long cm = 16LL * n * n;
+  // A operands (E hi/lo, and E^{-1} hi/lo for the wraps).  With the lane permutation the
+  // matrix rows sit in the first ceil(n/32) eight-row groups of each 32-lane quarter of the
+  // 128-row operand; the MMA reads all 128 rows but only those lanes of the accumulator are
+  // used, so up to 4 / ceil(n/32) operands share one 128-row footprint, each shifted by
+  // ceil(n/32) row groups (fill_a writes only the used rows).
+  const int nops = (three ? 2 : 1) * (role == R_WRAP ? 2 : 1);
+  int op_off[4] = {0, 0, 0, 0};
   long long o = 0;
-  M.a_hi = 0;
-  o = round16(a_bytes);
-  M.a_lo = -1;
-  if (three) {
-    M.a_lo = (int)o;
-    o += round16(a_bytes);
-  }
-  M.a2_hi = M.a2_lo = -1;
-  if (role == R_WRAP) {
-    M.a2_hi = (int)o;
-    o += round16(a_bytes);
-    if (three) {
-      M.a2_lo = (int)o;
+  if (M.perm) {
+    const long long rg = (long long)(M.Kp / 4) * 128;  // one eight-row group (the SBO)
+    const long long foot = (128LL * M.Kp * 4 + 127) & ~127LL;
+    const int g = (n + 31) / 32, per = 4 / g;
+    for (int k = 0; k < nops; ++k) {
+      op_off[k] = (int)((k / per) * ((foot + 3 * rg + 127) & ~127LL) + (k % per) * g * rg);
+      o = std::max(o, (long long)op_off[k] + foot);
+    }
+  } else {
+    for (int k = 0; k < nops; ++k) {
+      op_off[k] = (int)o;
       o += round16(a_bytes);
     }
   }
-  const long long last_a = role == R_WRAP ? (three ? M.a2_lo : M.a2_hi) : (three ? M.a_lo : M.a_hi);
+  int next = 0;
+  M.a_hi = op_off[next++];
+  M.a_lo = three ? op_off[next++] : -1;
+  M.a2_hi = M.a2_lo = -1;
+  if (role == R_WRAP) {
+    M.a2_hi = op_off[next++];
+    if (three) M.a2_lo = op_off[next++];
+  }
+  long long last_a = 0;
+  for (int k = 0; k < nops; ++k) last_a = std::max(last_a, (long long)op_off[k]);
   o = (o + 127) & ~127LL;
   M.b_hi = (int)o;
   M.b_lo = three ? (int)(o + round16(b_one)) : -1;
@@ -1063,9 +1077,6 @@ int fd_tune(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec,
     of += (size_t)probs[c].nt * probs[c].nx;
   }
   std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
   int result = FD_OK;
   for (auto& g : groups) {
     std::vector<fd_problem> sub;
@@ -1076,38 +1087,45 @@ int fd_tune(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec,
       sf.push_back(Fp[c]);
     }
     const int three = prec == FD_PREC_MIXED_3XTF32 ? 1 : 0;
-    std::vector<long long> keys;
-    for (auto& P : g.ph) keys.push_back(tune_key(P.which, P.mixed, P.mixed ? three : 0, g.nx));
-    float best = 1e30f;
-    int best_t = 0;
-    for (int nth : {128, 256}) {
-      for (long long key : keys) ctx->tuned[key] = nth;
-      float tot = 0.f;
-      for (int r = 0; r <= reps; ++r) {  // first run is a warm-up
-        cudaEventRecord(e0, 0);
-        Outs o;
-        o.logdet = d_ld;
-        o.G = sg.data();
-        o.F = force ? sf.data() : nullptr;
-        int rr = run(ctx, (int)sub.size(), sub.data(), o, prec, nullptr, kind);
-        cudaEventRecord(e1, 0);
-        if (rr != FD_OK) { result = rr; break; }
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (r > 0) tot += ms;
+    // one launch at a time (coordinate search): each phase's threads per CTA is chosen on that
+    // phase's own CUDA-event time, the other phases keeping their current choice
+    for (size_t pi = 0; pi < g.ph.size() && result == FD_OK; ++pi) {
+      const Phase& P = g.ph[pi];
+      const long long key = tune_key(P.which, P.mixed, P.mixed ? three : 0, g.nx);
+      float best = 1e30f;
+      int best_t = 0;
+      for (int nth : {128, 256}) {
+        ctx->tuned[key] = nth;
+        float tot = 0.f;
+        for (int r = 0; r <= reps; ++r) {  // first run is a warm-up
+          Outs o;
+          o.logdet = d_ld;
+          o.G = sg.data();
+          o.F = force ? sf.data() : nullptr;
+          const bool saved = ctx->timing;
+          ctx->timing = true;
+          int rr = run(ctx, (int)sub.size(), sub.data(), o, prec, nullptr, kind);
+          ctx->timing = saved;
+          if (rr != FD_OK) {
+            result = rr;
+            break;
+          }
+          cudaDeviceSynchronize();
+          float ms = 0.f;
+          if ((int)ctx->ev.size() > 2 * (int)pi + 1)
+            cudaEventElapsedTime(&ms, ctx->ev[2 * pi], ctx->ev[2 * pi + 1]);
+          if (r > 0) tot += ms;
+        }
+        if (result != FD_OK) break;
+        if (tot < best) {
+          best = tot;
+          best_t = nth;
+        }
       }
-      if (result != FD_OK) break;
-      if (tot < best) {
-        best = tot;
-        best_t = nth;
-      }
+      if (result == FD_OK) ctx->tuned[key] = best_t;
     }
     if (result != FD_OK) break;
-    for (long long key : keys) ctx->tuned[key] = best_t;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   cudaDeviceSynchronize();
   cudaFree(d_ld);
   cudaFree(d_g);

@@ -55,12 +55,15 @@ __device__ __forceinline__ int row_of_lane(const MLayout& L, int l) {
   return L.perm ? 4 * (l & 31) + (l >> 5) : l;
 }
 
+// A operand from E: the n matrix rows (at their permuted lanes), K padded with zeros.  Rows
+// that hold no matrix row are not written: with the lane permutation they belong to other
+// operands that share the 128-row footprint (their accumulator lanes are never read).
 __device__ void fill_a(const MLayout& L, float* a_hi, float* a_lo, const double* E) {
   const int n = L.n, Kp = L.Kp;
-  const int rows = L.perm ? 128 : L.Np;
+  const int rows = L.perm ? n : L.Np;
   for (int e = tid(); e < rows * Kp; e += nthr()) {
-    int r = e / Kp, k = e % Kp;
-    int i = row_of_lane(L, r);
+    const int i = e / Kp, k = e % Kp;
+    const int r = lane_of_row(L, i);
     double v = (i < n && k < n) ? E[i * n + k] : 0.0;
     float f = (float)v;
     float hi = tc::to_tf32(f);
