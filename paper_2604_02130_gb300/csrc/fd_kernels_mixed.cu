@@ -133,7 +133,7 @@ __device__ __forceinline__ void cta_phase32(int n, float2* ph, const double* phi
   }
 }
 
-enum EpiMode { TO_B_K = 0, TO_B_N = 1, TO_FP64 = 2, NONE = 3 };
+enum EpiMode { TO_B_K = 0, TO_B_N = 1, TO_F32 = 2, NONE = 3 };
 
 __device__ __forceinline__ void put_b(const MLayout& L, const MixedSmem& m, int row, int k,
                                       float v) {
@@ -155,12 +155,15 @@ struct Trace {
 // Epilogue of one MMA.  TMEM lane l (< n) holds v(l, c) = D[l, c] + i D[l, Np + c], c < n.
 //   TO_B_K : B(n = c, k = l) = rs(l) v cs(c)   (the lane indexes K: slices, right products)
 //   TO_B_N : B(n = l, k = c) = rs(l) v cs(c)   (the lane indexes N: wraps)
-//   TO_FP64: out[l + c n]    = rs(l) v cs(c)   (column-major FP64)
-// diag (optional): diag[l] = (Im v(l,l), 1 - Re v(l,l)), a force row F = i (1 - G_ll).
+//   TO_F32 : out[l + c n]    = rs(l) v cs(c)   (column-major FP32 staging, out read as float2;
+//            stage_to_fp64 converts it with full warps afterwards)
+// diag (optional): diag[l] = v(l,l) in FP32 (shared memory), the diagonal of a wrapped G for a
+// force row F = i (1 - G_ll); emit_force_row32 converts it after the epilogue's barrier (the
+// FP64 conversions then run on full warps instead of one lane per instruction).
 // tr (optional): the response trace above.
 template <int MODE>
 __device__ void epilogue(const MLayout& L, const MixedSmem& m, uint32_t tbase, Scale rs,
-                         Scale cs, double2* out, double2* diag,
+                         Scale cs, double2* out, float2* diag,
                          const Trace& tr = Trace{nullptr, {nullptr, false}, {nullptr, false},
                                                  nullptr, nullptr}) {
   const int n = L.n, Np = L.Np;
@@ -186,7 +189,7 @@ __device__ void epilogue(const MLayout& L, const MixedSmem& m, uint32_t tbase, S
           const int j = c * 16 + u;
           if (j < n) {
             const float2 v = make_float2(re[u], im[u]);
-            if (diag && j == l) diag[l] = make_double2((double)v.y, 1.0 - (double)v.x);
+            if (diag && j == l) diag[l] = v;
             if (tr.O) {
               const float o = tr.O[l * n + j];
               const float2 g = cmul32(cmul32(tr_r, v), tr.cs.at(j));
@@ -202,7 +205,7 @@ __device__ void epilogue(const MLayout& L, const MixedSmem& m, uint32_t tbase, S
               put_b(L, m, l, j, y.x);
               put_b(L, m, Np + l, j, y.y);
             } else {
-              out[l + j * n] = make_double2((double)y.x, (double)y.y);
+              ((float2*)out)[l + j * n] = y;
             }
           }
         }
@@ -232,35 +235,55 @@ __device__ void epilogue(const MLayout& L, const MixedSmem& m, uint32_t tbase, S
 }
 
 // B operand from an FP64 column-major matrix G (identity if G == nullptr):
-// B(n = j, k = i) = rs(i) G[i, j] cs(j).
+// B(n = j, k = i) = rs(i) G[i, j] cs(j).  The padding (j >= n or k >= n) is zeroed in a separate
+// pass so that the FP64 -> FP32 conversions run once per element of G on full warps.
 __device__ void fill_b2(const MLayout& L, const MixedSmem& m, const double2* G, Scale rs,
                         Scale cs) {
   const int n = L.n, Np = L.Np, Kp = L.Kp;
   for (int e = tid(); e < 2 * Np * Kp; e += nthr()) {
-    int k = e % Kp, row = e / Kp;
-    int j = row < Np ? row : row - Np;
-    float v = 0.f;
-    if (j < n && k < n) {
-      float2 x;
-      if (G) {
-        double2 g = G[k + j * n];
-        x = make_float2((float)g.x, (float)g.y);
-      } else {
-        x = make_float2(k == j ? 1.f : 0.f, 0.f);
-      }
-      float2 y = cmul32(cmul32(rs.at(k), x), cs.at(j));
-      v = row < Np ? y.x : y.y;
+    const int k = e % Kp, row = e / Kp;
+    const int j = row < Np ? row : row - Np;
+    if (j >= n || k >= n) put_b(L, m, row, k, 0.f);
+  }
+  for (int e = tid(); e < n * n; e += nthr()) {
+    const int k = e % n, j = e / n;  // element (k, j) of G
+    float2 x;
+    if (G) {
+      const double2 g = G[k + j * n];
+      x = make_float2((float)g.x, (float)g.y);
+    } else {
+      x = make_float2(k == j ? 1.f : 0.f, 0.f);
     }
-    put_b(L, m, row, k, v);
+    const float2 y = cmul32(cmul32(rs.at(k), x), cs.at(j));
+    put_b(L, m, j, k, y.x);
+    put_b(L, m, Np + j, k, y.y);
   }
 }
 
+// Force row F[x] = i (1 - G_xx) = (Im G_xx, 1 - Re G_xx) from an FP32 diagonal.
+__device__ __forceinline__ void emit_force_row32(int n, const float2* dg, double2* Frow) {
+  for (int x = tid(); x < n; x += nthr())
+    Frow[x] = make_double2((double)dg[x].y, 1.0 - (double)dg[x].x);
+}
+
+// FP32 staging (column-major n x n) -> FP64 block result, one element per thread-iteration.
+__device__ __forceinline__ void stage_to_fp64(int n, const float2* stage, double2* X) {
+  for (int e = tid(); e < n * n; e += nthr())
+    X[e] = make_double2((double)stage[e].x, (double)stage[e].y);
+  __syncthreads();
+}
+
+// After a slice MMA: the next B operand (with the next slice's phase), or, for the last slice
+// of a block, the FP64 block result Xc by way of the FP32 staging buffer `stage`.
 __device__ __forceinline__ void slice_epilogue(const MLayout& L, const MixedSmem& m,
-                                               uint32_t tbase, const float2* ph, bool to_b) {
-  if (to_b)
+                                               uint32_t tbase, const float2* ph, bool to_b,
+                                               double2* stage) {
+  if (to_b) {
     epilogue<TO_B_K>(L, m, tbase, Scale{ph, false}, Scale{nullptr, false}, nullptr, nullptr);
-  else
-    epilogue<TO_FP64>(L, m, tbase, Scale{nullptr, false}, Scale{nullptr, false}, m.Xc, nullptr);
+  } else {
+    epilogue<TO_F32>(L, m, tbase, Scale{nullptr, false}, Scale{nullptr, false}, stage, nullptr);
+    stage_to_fp64(L.n, (const float2*)stage, m.Xc);
+  }
 }
 
 __device__ __forceinline__ int grab_m(int* queue, int* slot) {
@@ -314,7 +337,7 @@ __global__ void __launch_bounds__(256) k_fwd_mixed(const Desc* __restrict__ desc
           ok = false;
           break;
         }
-        slice_epilogue(L, m, tbase, phn, !last);
+        slice_epilogue(L, m, tbase, phn, !last, To);  // To is free until the QR
       }
       if (!ok) break;
       cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
@@ -395,7 +418,7 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
           float2* phn = pf + ((t - t0 + 1) & 1) * n;
           if (!last) cta_phase32(n, phn, d.phi + (size_t)(t + 1) * n, 1.f);
           if (!slice_mma(L, m, tbase, phase)) { ok = false; break; }
-          slice_epilogue(L, m, tbase, phn, !last);
+          slice_epilogue(L, m, tbase, phn, !last, To);  // To is free until the QR
         }
         if (!ok) break;
         cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
@@ -434,9 +457,10 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
           const bool last = t == t0;
           cta_phase32(n, pf, d.phi + (size_t)t * n, -1.f);
           if (!slice_mma(L, m, tbase, phase)) { ok = false; break; }
-          if (last)
-            epilogue<TO_FP64>(L, m, tbase, Scale{pf, false}, one, m.Xc, nullptr);
-          else
+          if (last) {
+            epilogue<TO_F32>(L, m, tbase, Scale{pf, false}, one, To, nullptr);
+            stage_to_fp64(n, (const float2*)To, m.Xc);
+          } else
             epilogue<TO_B_K>(L, m, tbase, Scale{pf, false}, one, nullptr, nullptr);
         }
         if (!ok) break;
@@ -507,6 +531,7 @@ __global__ void __launch_bounds__(256) k_wrap_mixed(const Desc* __restrict__ des
     const double2* Glo = W.Gb(b);
     // force rows and/or response traces tr(O G_r) of every G_r of the block
     auto frow = [&](int r) { return d.F ? d.F + (size_t)r * n : nullptr; };
+    float2* dstage = d.F ? (float2*)s.rdiag : nullptr;  // FP32 diagonal of the wrapped G
     const float* Of = d.R ? W.OF(d.Gt != nullptr) : nullptr;
     float2* tslot = (float2*)(s.red + 48);
     if (d.F) emit_force_row(n, Glo, frow(t0));
@@ -528,10 +553,10 @@ __global__ void __launch_bounds__(256) k_wrap_mixed(const Desc* __restrict__ des
       // lane l holds column l of G_{t0+j} itself
       const Trace trf{Of, one, one, tslot, d.R ? d.R + t0 + j : nullptr};
       if (more)
-        epilogue<TO_B_N>(L, m, tbase, Scale{phn, true}, Scale{phn, false}, nullptr,
-                         frow(t0 + j), trf);
+        epilogue<TO_B_N>(L, m, tbase, Scale{phn, true}, Scale{phn, false}, nullptr, dstage, trf);
       else
-        epilogue<NONE>(L, m, tbase, one, one, nullptr, frow(t0 + j), trf);
+        epilogue<NONE>(L, m, tbase, one, one, nullptr, dstage, trf);
+      if (d.F) emit_force_row32(n, dstage, frow(t0 + j));
     }
     // backward wraps from G_{b*ns}: G_{q-1}, q = b*ns .. t0+h+2; slice q uses phi row q-1
     bool first = true;
@@ -552,10 +577,10 @@ __global__ void __launch_bounds__(256) k_wrap_mixed(const Desc* __restrict__ des
       const Trace trb{Of, Scale{ph, false}, Scale{ph, true}, tslot,
                       d.R ? d.R + (qq - 1) : nullptr};
       if (more)
-        epilogue<TO_B_N>(L, m, tbase, Scale{ph, false}, Scale{ph, true}, nullptr,
-                         frow(qq - 1), trb);
+        epilogue<TO_B_N>(L, m, tbase, Scale{ph, false}, Scale{ph, true}, nullptr, dstage, trb);
       else
-        epilogue<NONE>(L, m, tbase, one, one, nullptr, frow(qq - 1), trb);
+        epilogue<NONE>(L, m, tbase, one, one, nullptr, dstage, trb);
+      if (d.F) emit_force_row32(n, dstage, frow(qq - 1));
     }
     if (!ok) {
       if (tid() == 0) atomicMax(status + d.user_index, ST_TIMEOUT);
