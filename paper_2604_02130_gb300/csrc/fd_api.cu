@@ -103,6 +103,7 @@ struct Phase {
   fd::MLayout ML;
   int nthreads, smem, grid, occ;
   long long slot_bytes;
+  size_t slot_off;  // byte offset of this launch's CTA slots in the group's scratch
   int ntasks;
 };
 
@@ -114,7 +115,7 @@ struct Group {
   std::vector<Phase> ph;  // launches, in order (one for log det/G, three for the force)
   size_t desc_off;        // first descriptor of this group in the table
   size_t scratch_off;     // byte offset of this group's scratch (slots, then FWork)
-  size_t slots_bytes;     // CTA slots, shared by the phases (they run one after the other)
+  size_t slots_bytes;     // CTA slots: one region per launch (the phases overlap)
   std::vector<fd::Task> tB, tC;  // force: boundary and wrap tasks
   std::vector<fd::Task> tA;      // force: chain tasks (b = 0 forward, 1 backward), LPT order
   size_t tA_off, tB_off, tC_off;  // their offsets in the task table
@@ -511,11 +512,12 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
     g.occ = 0;
     for (auto& P : g.ph) {
       g.mixed |= P.mixed;
-      g.slots_bytes = std::max(g.slots_bytes, (size_t)P.grid * (size_t)P.slot_bytes);
+      // the launches of the phased path run concurrently: each gets its own slots
+      P.slot_off = g.slots_bytes;
+      g.slots_bytes += ((size_t)P.grid * (size_t)P.slot_bytes + 255) & ~(size_t)255;
       g.grid = std::max(g.grid, P.grid);
       g.occ = std::max(g.occ, P.occ);
     }
-    g.slots_bytes = (g.slots_bytes + 255) & ~(size_t)255;
     g.qbase = qnext;
     qnext += (int)g.ph.size();
     groups.push_back(g);
@@ -605,7 +607,7 @@ int queue_count(const std::vector<Group>& groups) {
 // Host descriptor and task tables of a call.  `scratch` is the device scratch base (the force
 // workspace of each configuration lives inside it).
 void build_tables(std::vector<Group>& groups, const fd_problem* probs, const Outs& o,
-                  char* scratch, Desc* out, fd::Task* tasks) {
+                  char* scratch, int* sync, Desc* out, fd::Task* tasks) {
   size_t k = 0, t = 0;
   for (auto& g : groups) {
     g.desc_off = k;
@@ -627,6 +629,7 @@ void build_tables(std::vector<Group>& groups, const fd_problem* probs, const Out
       d.nf = o.nf ? o.nf + 2 * (size_t)c : nullptr;
       d.O = o.O ? o.O[c] : nullptr;
       d.R = o.R ? (double2*)o.R[c] : nullptr;
+      d.sync = g.kind != K_FWD ? sync + fd::SF_NUM * (size_t)c : nullptr;
       d.fws = g.kind != K_FWD
                   ? (double2*)(scratch + g.scratch_off + g.slots_bytes + g.fws_off[q])
                   : nullptr;
@@ -665,6 +668,8 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
   const int nq = queue_count(groups);
   FD_CUDA(ctx, cudaMemsetAsync(d_queue, 0, sizeof(int) * nq, stream));
   FD_CUDA(ctx, cudaMemsetAsync(d_status, 0xFF, sizeof(int) * batch, stream));  // pending
+  // progress flags of the phased path (after the status words)
+  FD_CUDA(ctx, cudaMemsetAsync(d_status + batch, 0, sizeof(int) * fd::SF_NUM * batch, stream));
   if (timing) {
     while ((int)ctx->ev.size() < 2 * nq) {
       cudaEvent_t e;
@@ -686,9 +691,9 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
     cudaStream_t s = fork ? ctx->side[gi % nside] : stream;
     const Desc* dd = d_desc + g.desc_off;
     const int nd = (int)g.idx.size();
-    char* scr = scratch + g.scratch_off;
     for (size_t pi = 0; pi < g.ph.size(); ++pi) {
       const Phase& P = g.ph[pi];
+      char* scr = scratch + g.scratch_off + P.slot_off;
       const int qi = g.qbase + (int)pi;
       if (timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * qi], s));
       if (P.which == 2 && g.tB.empty()) {  // single-block configurations: no boundary phase
@@ -712,15 +717,15 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
           break;
         case 2:
           fd::launch_boundary_fp64(dd, d_tasks + g.tB_off, (int)g.tB.size(), d_queue + qi,
-                                   d_status, scr, P.L, P.grid, s);
+                                   d_status, scr, P.L, P.grid, s, !timing);
           break;
         default:
           if (P.mixed)
             fd::launch_wrap_mixed(dd, d_tasks + g.tC_off, (int)g.tC.size(), d_queue + qi,
-                                  d_status, scr, P.ML, P.grid, s);
+                                  d_status, scr, P.ML, P.grid, s, !timing);
           else
             fd::launch_wrap_fp64(dd, d_tasks + g.tC_off, (int)g.tC.size(), d_queue + qi,
-                                 d_status, scr, P.L, P.grid, s);
+                                 d_status, scr, P.L, P.grid, s, !timing);
       }
       ctx->last_launches++;
       cudaError_t e = cudaGetLastError();
@@ -750,13 +755,14 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, const Outs& o, int prec
   std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
   size_t need = scratch_need(groups);
   const size_t ntasks = task_count(groups);
-  int rc = ensure(ctx, (size_t)batch, (size_t)batch, queue_count(groups), need, ntasks);
+  int rc = ensure(ctx, (size_t)batch, (size_t)batch * (1 + fd::SF_NUM), queue_count(groups), need,
+                  ntasks);
   if (rc != FD_OK) return rc;
   if (ctx->staging_pending) {
     FD_CUDA(ctx, cudaEventSynchronize(ctx->staging_done));
     ctx->staging_pending = false;
   }
-  build_tables(groups, probs, o, ctx->scratch, ctx->h_desc, ctx->h_tasks);
+  build_tables(groups, probs, o, ctx->scratch, ctx->d_status + batch, ctx->h_desc, ctx->h_tasks);
   FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(Desc) * batch,
                                cudaMemcpyHostToDevice, stream));
   if (ntasks)
@@ -851,7 +857,8 @@ int fd_reserve(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int pr
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
   std::vector<Group> groups = plan(ctx, batch, probs, kind_of(what), prec);
   size_t need = scratch_need(groups);
-  rc = ensure(ctx, (size_t)batch, (size_t)batch, queue_count(groups), need, task_count(groups));
+  rc = ensure(ctx, (size_t)batch, (size_t)batch * (1 + fd::SF_NUM), queue_count(groups), need,
+              task_count(groups));
   if (rc != FD_OK) return rc;
   if (ctx->max_smem_optin > ctx->smem_attr) {
     FD_CUDA(ctx, fd::set_smem_fp64(ctx->max_smem_optin));
@@ -995,13 +1002,13 @@ int fd_graph_create(fd_ctx* ctx, int batch, const fd_problem* probs, double* log
   FD_G(cudaMalloc(&g->d_desc, sizeof(Desc) * batch));
   FD_G(cudaMalloc(&g->d_tasks, sizeof(fd::Task) * ht.size()));
   FD_G(cudaMalloc(&g->d_queue, sizeof(int) * std::max(1, queue_count(groups))));
-  FD_G(cudaMalloc(&g->d_status, sizeof(int) * batch));
+  FD_G(cudaMalloc(&g->d_status, sizeof(int) * batch * (1 + fd::SF_NUM)));
   FD_G(cudaMalloc(&g->scratch, std::max<size_t>(need, 256)));
   Outs o;
   o.logdet = logdet;
   o.G = G;
   o.F = F;
-  build_tables(groups, probs, o, g->scratch, h.data(), ht.data());
+  build_tables(groups, probs, o, g->scratch, g->d_status + batch, h.data(), ht.data());
   FD_G(cudaMemcpy(g->d_desc, h.data(), sizeof(Desc) * batch, cudaMemcpyHostToDevice));
   FD_G(cudaMemcpy(g->d_tasks, ht.data(), sizeof(fd::Task) * ht.size(), cudaMemcpyHostToDevice));
   FD_G(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));

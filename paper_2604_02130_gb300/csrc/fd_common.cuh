@@ -59,7 +59,91 @@ struct Desc {
   double* nf;          // fermion number 1 - tr G / nx (re, im), or null
   const double* O;     // response operator, nx*nx row-major, or null
   double2* R;          // response traces tr(O G_r), r = 0..nt-1, or null
+  int* sync;           // phased path: this configuration's progress flags (SyncFlag), else null
 };
+
+// ---------------------------------------------------------------- overlapped phases
+// The three launches of the phased path (chains, boundary Green's functions, wraps) overlap:
+// the later ones are launched as programmatic dependents (they may start while the earlier grid
+// still runs) and each task waits only for the data it reads, through per-configuration progress
+// flags written with release and read with acquire semantics at GPU scope.
+enum SyncFlag {
+  SF_FWD = 0,  // forward chain: left checkpoints 1..v written; nb once G_0 (= G) is written
+  SF_BWD = 1,  // backward chain: v right checkpoints written (blocks nb, nb-1, ...)
+  SF_BND = 2,  // boundary Green's functions written (count)
+  SF_NUM = 4   // ints per configuration (padding)
+};
+// A wait gives up after this many cycles without any change of the configuration's flags
+// (~4 s at 2 GHz; one checkpoint interval of the largest supported size takes well under that).
+#define FD_SYNC_WAIT_CYCLES (8LL * 1000 * 1000 * 1000)
+
+// Launch `kern` on `stream`, as a programmatic dependent of the previous kernel in the stream
+// when `pdl` (it may then start before that kernel has finished; its tasks wait on the flags).
+template <class... KArgs, class... Args>
+inline cudaError_t launch_maybe_pdl(void (*kern)(KArgs...), int grid, int threads, int smem,
+                                    cudaStream_t stream, bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Let the dependent grid launch (issued by every CTA at its start).
+__device__ __forceinline__ void allow_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// One thread, after a __syncthreads that follows the CTA's data writes.
+__device__ __forceinline__ void flag_store(int* f, int v) {
+  __threadfence();
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+}
+__device__ __forceinline__ void flag_add(int* f, int v) {
+  __threadfence();
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+}
+__device__ __forceinline__ int flag_load(const int* f) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+  return v;
+}
+// CTA-wide wait until flags[SF_FWD] >= fwd, flags[SF_BWD] >= bwd and flags[SF_BND] >= bnd.
+// Thread 0 polls; it gives up (false) after FD_SYNC_WAIT_CYCLES without progress of the flags.
+// `bcast` is a shared int.
+__device__ __forceinline__ bool cta_wait_flags(const int* flags, int fwd, int bwd, int bnd,
+                                               volatile int* bcast) {
+  if (threadIdx.x == 0) {
+    long long t0 = clock64();
+    int ok = 1, last = -1;
+    for (;;) {
+      const int f0 = flag_load(flags + SF_FWD), f1 = flag_load(flags + SF_BWD),
+                f2 = flag_load(flags + SF_BND);
+      if (f0 >= fwd && f1 >= bwd && f2 >= bnd) break;
+      const int sum = f0 + f1 + f2;
+      const long long now = clock64();
+      if (sum != last) {
+        last = sum;
+        t0 = now;
+      } else if (now - t0 > FD_SYNC_WAIT_CYCLES) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(256);
+    }
+    __threadfence();
+    *bcast = ok;
+  }
+  __syncthreads();
+  const bool ok = *bcast != 0;
+  __syncthreads();
+  return ok;
+}
 
 // Per-configuration force workspace in global memory (the force is split into phases that run
 // on different CTAs):  left checkpoints L_b = B_{b ns}...B_1 as (X, T, log D) for b = 1..nb-1,

@@ -12,11 +12,12 @@ void launch_fwd_fp64(const Desc* descs, int ndesc, int* queue, int* status, char
 // B boundary Green's functions, C wraps
 void launch_chain_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                        char* scratch, const Layout& L, int grid, cudaStream_t stream);
+// pdl: launch as a programmatic dependent of the previous kernel (tasks wait on the flags)
 void launch_boundary_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue,
                           int* status, char* scratch, const Layout& L, int grid,
-                          cudaStream_t stream);
+                          cudaStream_t stream, bool pdl);
 void launch_wrap_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
-                      char* scratch, const Layout& L, int grid, cudaStream_t stream);
+                      char* scratch, const Layout& L, int grid, cudaStream_t stream, bool pdl);
 cudaError_t set_smem_fp64(int bytes);
 // kernel ids: 0 log det/G, 1 force chains, 2 boundary, 3 wraps
 int occupancy_fp64(int which, int nthreads, int smem_bytes);  // -1 on error
@@ -29,7 +30,7 @@ void launch_chain_mixed(const Desc* descs, const Task* tasks, int ntasks, int* q
                         int* status, char* scratch, const MLayout& L, int grid,
                         cudaStream_t stream);
 void launch_wrap_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
-                       char* scratch, const MLayout& L, int grid, cudaStream_t stream);
+                       char* scratch, const MLayout& L, int grid, cudaStream_t stream, bool pdl);
 cudaError_t set_smem_mixed(int bytes);
 // kernel ids as for the FP64 kernels: 0 log det/G, 1 force chains, 3 wraps
 int occupancy_mixed(int which, int nthreads, int smem_bytes);  // -1 on error

@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
                                                      Layout L) {
   extern __shared__ __align__(16) char smem[];
   char* slotp = scratch + (size_t)blockIdx.x * L.slot_bytes;
+  allow_dependents();
   for (;;) {
     int* slot = (int*)(smem + L.smem_bytes - 16);
     const int q = grab(queue, slot);
@@ -225,6 +226,8 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
           cta_copy(n * n, W.LX(b), X);
           cta_copy(n * n, W.LT(b), T);
           for (int k = tid(); k < n; k += nthr()) W.LD(b)[k] = s.logD[k];
+          __syncthreads();
+          if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, b);
         }
       }
       cta_assemble(n, X, T, s.logD, Xo, To, s, s.red + 2, s.red + 3);
@@ -241,6 +244,8 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
         float* of = W.OF(d.Gt != nullptr);
         for (int e = tid(); e < n * n; e += nthr()) of[e] = (float)d.O[e];
       }
+      __syncthreads();
+      if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, nb);  // G_0 written
       if (tid() == 0)
         atomicMax(status + d.user_index,
                   (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
@@ -253,6 +258,8 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
         cta_copy(n * n, W.RX(b), X);
         cta_copy(n * n, W.RT(b), T);
         for (int k = tid(); k < n; k += nthr()) W.RD(b)[k] = s.logD[k];
+        __syncthreads();
+        if (tid() == 0 && d.sync) flag_store(d.sync + SF_BWD, nb - b + 1);
       }
       if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     }
@@ -269,6 +276,7 @@ __global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ 
                                                         char* scratch, Layout L) {
   extern __shared__ __align__(16) char smem[];
   char* slotp = scratch + (size_t)blockIdx.x * L.slot_bytes;
+  allow_dependents();
   for (;;) {
     int* slot = (int*)(smem + L.smem_bytes - 16);
     const int q = grab(queue, slot);
@@ -277,6 +285,9 @@ __global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ 
     const Desc d = descs[tk.desc];
     const int n = d.nx, nb = d.nt / d.nstab, b = tk.b;
     const FWork W{d.fws, n, nb};
+    // left checkpoint b-1 and right checkpoint b
+    if (d.sync && !cta_wait_flags(d.sync, b - 1, nb - b + 1, 0, slot + 1) && tid() == 0)
+      atomicMax(status + d.user_index, ST_TIMEOUT);
     Small s = carve_small(smem + L.small_off, n);
     if (tid() == 0) {
       s.misc[0] = 0;
@@ -291,6 +302,7 @@ __global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ 
     if (d.Gt) write_green(n, W.GT(b), d.Gt + (size_t)(b - 1) * d.nstab * n * n);
     if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     __syncthreads();
+    if (tid() == 0 && d.sync) flag_add(d.sync + SF_BND, 1);
   }
 }
 
@@ -311,6 +323,9 @@ __global__ void __launch_bounds__(256) k_wrap_fp64(const Desc* __restrict__ desc
     const Desc d = descs[tk.desc];
     const int n = d.nx, ns = d.nstab, nb = d.nt / d.nstab, b = tk.b;
     const FWork W{d.fws, n, nb};
+    // G_0 and every boundary Green's function of the configuration
+    if (d.sync && !cta_wait_flags(d.sync, nb, 0, nb - 1, slot + 1) && tid() == 0)
+      atomicMax(status + d.user_index, ST_TIMEOUT);
     Small s = carve_small(smem + L.small_off, n);
     if (tid() == 0) s.misc[0] = 0;
     const double* E = L.in_smem[B_E] ? (double*)(smem + L.off[B_E]) : d.E;
@@ -399,14 +414,14 @@ void launch_chain_fp64(const Desc* descs, const Task* tasks, int ntasks, int* qu
 }
 void launch_boundary_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue,
                           int* status, char* scratch, const Layout& L, int grid,
-                          cudaStream_t stream) {
-  k_boundary_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue, status,
-                                                               scratch, L);
+                          cudaStream_t stream, bool pdl) {
+  launch_maybe_pdl(k_boundary_fp64, grid, L.nthreads, L.smem_bytes, stream, pdl, descs, tasks,
+                   ntasks, queue, status, scratch, L);
 }
 void launch_wrap_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
-                      char* scratch, const Layout& L, int grid, cudaStream_t stream) {
-  k_wrap_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue, status,
-                                                           scratch, L);
+                      char* scratch, const Layout& L, int grid, cudaStream_t stream, bool pdl) {
+  launch_maybe_pdl(k_wrap_fp64, grid, L.nthreads, L.smem_bytes, stream, pdl, descs, tasks, ntasks,
+                   queue, status, scratch, L);
 }
 static const void* fp64_kernel(int which) {
   switch (which) {

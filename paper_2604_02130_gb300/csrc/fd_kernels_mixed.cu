@@ -388,6 +388,7 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
   double2* T = (double2*)((L.t_smem ? smem : slot) + L.t0_off);
   double2* To = (double2*)((L.t_smem ? smem : slot) + L.t1_off);
   const Scale one{nullptr, false};
+  allow_dependents();
   for (;;) {
     const int q = grab_m(queue, m.qslot);
     if (q >= ntasks) break;
@@ -427,6 +428,8 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
           cta_copy(n * n, W.LX(b), m.Xn);
           cta_copy(n * n, W.LT(b), T);
           for (int k = tid(); k < n; k += nthr()) W.LD(b)[k] = s.logD[k];
+          __syncthreads();
+          if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, b);
         }
       }
       if (ok) {
@@ -448,6 +451,8 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
           float* of = W.OF(d.Gt != nullptr);
           for (int e = tid(); e < n * n; e += nthr()) of[e] = (float)d.O[e];
         }
+        __syncthreads();
+        if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, nb);  // G_0 written
       }
     } else {
       for (int b = nb; b >= 2 && ok; --b) {
@@ -469,11 +474,17 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
         cta_copy(n * n, W.RX(b), m.Xn);
         cta_copy(n * n, W.RT(b), T);
         for (int k = tid(); k < n; k += nthr()) W.RD(b)[k] = s.logD[k];
+        __syncthreads();
+        if (tid() == 0 && d.sync) flag_store(d.sync + SF_BWD, nb - b + 1);
       }
       if (ok && tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     }
     if (!ok) {
-      if (tid() == 0) atomicMax(status + d.user_index, ST_TIMEOUT);
+      if (tid() == 0) {
+        atomicMax(status + d.user_index, ST_TIMEOUT);
+        // release the dependent tasks (their inputs are invalid; the status says so)
+        if (d.sync) flag_store(d.sync + (fwd ? SF_FWD : SF_BWD), nb);
+      }
       break;
     }
     __syncthreads();
@@ -519,6 +530,9 @@ __global__ void __launch_bounds__(256) k_wrap_mixed(const Desc* __restrict__ des
     const Desc d = descs[tk.desc];
     const int ns = d.nstab, nb = d.nt / d.nstab, b = tk.b;
     const FWork W{d.fws, n, nb};
+    // G_0 and every boundary Green's function of the configuration
+    if (d.sync && !cta_wait_flags(d.sync, nb, 0, nb - 1, m.qslot + 1) && tid() == 0)
+      atomicMax(status + d.user_index, ST_TIMEOUT);
     Small s = carve_small(smem + L.small_off, n);
     float2* pf = (float2*)s.ph;
     if (tk.desc != last_desc) {  // tasks of one configuration are contiguous: reload E only then
@@ -601,9 +615,9 @@ void launch_chain_mixed(const Desc* descs, const Task* tasks, int ntasks, int* q
                                                              scratch, L);
 }
 void launch_wrap_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
-                       char* scratch, const MLayout& L, int grid, cudaStream_t stream) {
-  k_wrap_mixed<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue, status,
-                                                            scratch, L);
+                       char* scratch, const MLayout& L, int grid, cudaStream_t stream, bool pdl) {
+  launch_maybe_pdl(k_wrap_mixed, grid, L.nthreads, L.smem_bytes, stream, pdl, descs, tasks, ntasks,
+                   queue, status, scratch, L);
 }
 
 void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
