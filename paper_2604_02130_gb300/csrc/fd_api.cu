@@ -121,6 +121,7 @@ struct Group {
   size_t tA_off, tB_off, tC_off;  // their offsets in the task table
   std::vector<size_t> fws_off;   // force: per configuration, bytes from the group's FWork base
   size_t fws_bytes;
+  std::vector<int> nseg;         // time-parallel log det/G: segments per configuration (or empty)
   int qbase;                     // first queue counter of the group
   int grid;                      // largest grid of the phases (reported)
   int occ;
@@ -166,8 +167,8 @@ long long tune_key(int kind, int mixed, int three, int nx) {
 
 // Buffer sets of the kernels ("roles"): log det/G and the force chains (R_FWD), the boundary
 // Green's functions (R_BOUND; R_BOUND2 with the second right-hand side of G(t, 0) beside G_t)
-// and the wraps (R_WRAP).
-enum Role { R_FWD = 0, R_BOUND = 2, R_WRAP = 3, R_BOUND2 = 4 };
+// and the wraps (R_WRAP); the merge of a time-parallel split (R_MERGE).
+enum Role { R_FWD = 0, R_BOUND = 2, R_WRAP = 3, R_BOUND2 = 4, R_MERGE = 5 };
 
 // Greedy placement: the buffers touched every slice first, then the per-block ones.
 Layout plan_layout(int n, int role, int budget, int nthreads) {
@@ -182,6 +183,8 @@ Layout plan_layout(int n, int role, int budget, int nthreads) {
     order = {{fd::B_GA, cm}, {fd::B_GB, cm}};
   else if (role == R_BOUND2)
     order = {{fd::B_GA, cm}, {fd::B_GB, 2 * cm}};
+  else if (role == R_MERGE)
+    order = {{fd::B_X0, cm}, {fd::B_X1, cm}, {fd::B_T0, cm}, {fd::B_T1, cm}, {fd::B_GA, cm}};
   else
     order = {{fd::B_E, rm}, {fd::B_EINV, rm}, {fd::B_GA, cm}, {fd::B_GB, cm}};
   long long used = round16(fd::small_bytes(n)) + 16;  // small vectors + queue slot
@@ -465,7 +468,30 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
     const int n = g.nx, nd = (int)g.idx.size();
     g.mixed = 0;
     g.fws_bytes = 0;
-    if (kind == K_FWD) {
+    // Time-parallel log det/G when the class has fewer configurations than SMs (each chain
+    // would be one CTA's serial work while most of the GPU idles): every chain is cut into
+    // S segments (a power of two dividing its block count, at most half of it, S * configs <=
+    // 2 * SMs), computed from the identity in parallel and merged by a stabilised product.
+    int target = 1;
+    if (kind == K_FWD && nd < ctx->num_sms)
+      while (target < 16 && 2 * target * nd <= 2 * ctx->num_sms) target *= 2;
+    if (kind == K_FWD && target >= 2) {
+      for (int k = 0; k < nd; ++k) {
+        const int c = g.idx[k];
+        const int nb = probs[c].nt / probs[c].n_stab;
+        int S = 1;
+        while (2 * S <= target && 2 * S <= nb / 2 && nb % (2 * S) == 0) S *= 2;
+        g.nseg.push_back(S);
+        for (int sg = 0; sg < S; ++sg) g.tA.push_back(fd::Task{k, 2 + sg});
+        g.fws_off.push_back(g.fws_bytes);
+        g.fws_bytes += (fd::FWork::elems(n, nb + 1, false) * 16 + 255) & ~(size_t)255;
+      }
+      Phase A;
+      if (!(mixed && mixed_phase(ctx, n, R_FWD, 1, three, (int)g.tA.size(), A)))
+        A = fp64_phase(ctx, n, R_FWD, 1, (int)g.tA.size());
+      g.ph.push_back(A);
+      g.ph.push_back(fp64_phase(ctx, n, R_MERGE, 8, nd));
+    } else if (kind == K_FWD) {
       Phase P;
       if (!(mixed && mixed_phase(ctx, n, R_FWD, 0, three, nd, P))) P = fp64_phase(ctx, n, R_FWD, 0, nd);
       g.ph.push_back(P);
@@ -630,9 +656,10 @@ void build_tables(std::vector<Group>& groups, const fd_problem* probs, const Out
       d.O = o.O ? o.O[c] : nullptr;
       d.R = o.R ? (double2*)o.R[c] : nullptr;
       d.sync = g.kind != K_FWD ? sync + fd::SF_NUM * (size_t)c : nullptr;
-      d.fws = g.kind != K_FWD
+      d.fws = (g.kind != K_FWD || !g.nseg.empty())
                   ? (double2*)(scratch + g.scratch_off + g.slots_bytes + g.fws_off[q])
                   : nullptr;
+      d.nseg = g.nseg.empty() ? 0 : g.nseg[q];
       out[k++] = d;
     }
     g.tA_off = t;
@@ -714,6 +741,9 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
           else
             fd::launch_chain_fp64(dd, d_tasks + g.tA_off, (int)g.tA.size(), d_queue + qi,
                                   d_status, scr, P.L, P.grid, s);
+          break;
+        case 8:
+          fd::launch_merge_fp64(dd, nd, d_queue + qi, d_status, scr, P.L, P.grid, s);
           break;
         case 2:
           fd::launch_boundary_fp64(dd, d_tasks + g.tB_off, (int)g.tB.size(), d_queue + qi,

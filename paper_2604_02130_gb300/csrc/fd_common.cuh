@@ -60,6 +60,7 @@ struct Desc {
   const double* O;     // response operator, nx*nx row-major, or null
   double2* R;          // response traces tr(O G_r), r = 0..nt-1, or null
   int* sync;           // phased path: this configuration's progress flags (SyncFlag), else null
+  int nseg;            // time-parallel log det/G: number of segments of the chain (0: not split)
 };
 
 // ---------------------------------------------------------------- overlapped phases

@@ -18,6 +18,9 @@ void launch_boundary_fp64(const Desc* descs, const Task* tasks, int ntasks, int*
                           cudaStream_t stream, bool pdl);
 void launch_wrap_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                       char* scratch, const Layout& L, int grid, cudaStream_t stream, bool pdl);
+// time-parallel log det/G: merge of the segment products and assembly (kernel id 8)
+void launch_merge_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
+                       const Layout& L, int grid, cudaStream_t stream);
 cudaError_t set_smem_fp64(int bytes);
 // kernel ids: 0 log det/G, 1 force chains, 2 boundary, 3 wraps
 int occupancy_fp64(int which, int nthreads, int smem_bytes);  // -1 on error

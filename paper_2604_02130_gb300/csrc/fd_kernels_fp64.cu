@@ -198,7 +198,9 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
     if (q >= ntasks) return;
     const Task tk = tasks[q];
     const Desc d = descs[tk.desc];
-    const bool fwd = tk.b == 0;
+    // Task.b: 0 forward chain, 1 backward chain, 2 + s segment s of a time-parallel split
+    const bool fwd = tk.b != 1;
+    const int sg = tk.b - 2;
     const int n = d.nx, ns = d.nstab, nb = d.nt / d.nstab;
     const FWork W{d.fws, n, nb};
     Small s = carve_small(smem + L.small_off, n);
@@ -216,7 +218,21 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
     cta_identity(n, T);
     for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
     __syncthreads();
-    if (fwd) {
+    if (fwd && sg >= 0) {
+      // one segment of the chain from the identity: blocks sg*kb+1 .. (sg+1)*kb, result in
+      // the checkpoint storage of block sg+1 (merged by k_merge_fp64)
+      const int kb = nb / d.nseg, b_first = sg * kb + 1;
+      for (int b = b_first; b < b_first + kb; ++b) {
+        fwd_slices(n, B.E, d.phi, (b - 1) * ns, b * ns, X, Xo, s);
+        cta_reortho(n, X, Xo, T, To, s.logD, s);
+        double2* t1 = X; X = Xo; Xo = t1;
+        double2* t2 = T; T = To; To = t2;
+      }
+      cta_copy(n * n, W.LX(sg + 1), X);
+      cta_copy(n * n, W.LT(sg + 1), T);
+      for (int k = tid(); k < n; k += nthr()) W.LD(sg + 1)[k] = s.logD[k];
+      if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
+    } else if (fwd) {
       for (int b = 1; b <= nb; ++b) {
         fwd_slices(n, B.E, d.phi, (b - 1) * ns, b * ns, X, Xo, s);
         cta_reortho(n, X, Xo, T, To, s.logD, s);
@@ -403,6 +419,85 @@ __global__ void __launch_bounds__(256) k_wrap_fp64(const Desc* __restrict__ desc
   }
 }
 
+// ------------------------------------------------------------------ time-parallel log det/G
+// Merge of the nseg segment products of one configuration (Section 7's stabilised product of two
+// UDV factors, applied segment by segment) and the assembly.  With the accumulated product
+// Xa Da Ta and the next segment Xs Ds Ts (acting later):
+//   Xs Ds Ts Xa Da Ta = Xs [Ds Ts Xa] Da Ta,  Xc = e^{-m} Ds (Ts Xa),  m = max log Ds,
+// re-factored by the pre-pivoted QR (Xc Da Ta = Q D' T'), so X <- Xs Q, D <- e^m D', T <- T'.
+// The row scaling by Ds is formed (e^{logDs - m} <= 1): a segment's log D must span less than
+// 700 (else FD_ERR_NUMERIC) -- beta per segment up to ~100 at kappa = 1 on this lattice.
+// After a merge X = Xs Q is a product of two Householder products: det X = +1 (the assembly
+// assumes (-1)^{n-1}, right for S = 1).
+__global__ void __launch_bounds__(256) k_merge_fp64(const Desc* __restrict__ descs, int ndesc,
+                                                     int* queue, int* status, char* scratch,
+                                                     Layout L) {
+  extern __shared__ __align__(16) char smem[];
+  char* slotp = scratch + (size_t)blockIdx.x * L.slot_bytes;
+  for (;;) {
+    int* slot = (int*)(smem + L.smem_bytes - 16);
+    const int c = grab(queue, slot);
+    if (c >= ndesc) return;
+    const Desc d = descs[c];
+    const int n = d.nx, nb = d.nt / d.nstab, S = d.nseg;
+    const FWork W{d.fws, n, nb};
+    Small s = carve_small(smem + L.small_off, n);
+    if (tid() == 0) {
+      s.misc[0] = 0;
+      s.misc[5] = (int)((blockIdx.x / max(1, L.num_sms)) * 2);
+      s.misc[6] = gridDim.x > (unsigned)L.num_sms;
+    }
+    double2* Xa = (double2*)place(smem, slotp, L, B_X0);
+    double2* Xc = (double2*)place(smem, slotp, L, B_X1);
+    double2* Ta = (double2*)place(smem, slotp, L, B_T0);
+    double2* Tn = (double2*)place(smem, slotp, L, B_T1);
+    double2* Xn = (double2*)place(smem, slotp, L, B_GA);
+    cta_copy(n * n, Xa, W.LX(1));
+    cta_copy(n * n, Ta, W.LT(1));
+    for (int k = tid(); k < n; k += nthr()) s.logD[k] = W.LD(1)[k];
+    __syncthreads();
+    for (int sg = 1; sg < S; ++sg) {
+      const double* lds = W.LD(sg + 1);
+      if (warp_id() == 0) {
+        double mx = -INFINITY;
+        for (int k = lane_id(); k < n; k += 32) mx = fmax(mx, lds[k]);
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane_id() == 0) s.red[9] = mx;
+      }
+      __syncthreads();
+      const double m = s.red[9];
+      for (int k = tid(); k < n; k += nthr()) {
+        const double e = lds[k] - m;
+        if (e < -700.0) atomicOr(&s.misc[0], 1);  // the row scaling would underflow
+        s.sa[k] = exp(e);
+      }
+      __syncthreads();
+      const double* sa = s.sa;
+      cta_gemm<false>(n, CMat{W.LT(sg + 1), 1, n}, CMat{Xa, 1, n},
+                      [&](int i, int j, cplx v) { st(Xc + i + j * n, sa[i] * v); });
+      cta_reortho(n, Xc, Xn, Ta, Tn, s.logD, s);
+      for (int k = tid(); k < n; k += nthr()) s.logD[k] += m;
+      cta_gemm<false>(n, CMat{W.LX(sg + 1), 1, n}, CMat{Xn, 1, n},
+                      [&](int i, int j, cplx v) { st(Xa + i + j * n, v); });
+      double2* t = Ta; Ta = Tn; Tn = t;
+      __syncthreads();
+    }
+    cta_assemble(n, Xa, Ta, s.logD, Xc, Xn, s, s.red + 2, s.red + 3);
+    const double pi = 3.14159265358979323846;
+    const double re = s.red[2], im = wrap_pi(s.red[3] - (S > 1 && ((n - 1) & 1) ? pi : 0.0));
+    if (tid() == 0) {
+      d.logdet[0] = re;
+      d.logdet[1] = im;
+    }
+    if (d.G) write_green(n, Xn, d.G);
+    if (d.nf) cta_fermion_number(n, Xn, d.nf);
+    if (tid() == 0)
+      atomicMax(status + d.user_index,
+                (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
+    __syncthreads();
+  }
+}
+
 void launch_fwd_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                      const Layout& L, int grid, cudaStream_t stream) {
   k_fwd_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch, L);
@@ -423,11 +518,17 @@ void launch_wrap_fp64(const Desc* descs, const Task* tasks, int ntasks, int* que
   launch_maybe_pdl(k_wrap_fp64, grid, L.nthreads, L.smem_bytes, stream, pdl, descs, tasks, ntasks,
                    queue, status, scratch, L);
 }
+void launch_merge_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
+                       const Layout& L, int grid, cudaStream_t stream) {
+  k_merge_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch,
+                                                            L);
+}
 static const void* fp64_kernel(int which) {
   switch (which) {
     case 1: return (const void*)k_chain_fp64;
     case 2: return (const void*)k_boundary_fp64;
     case 3: return (const void*)k_wrap_fp64;
+    case 8: return (const void*)k_merge_fp64;
     default: return (const void*)k_fwd_fp64;
   }
 }
@@ -439,7 +540,8 @@ int occupancy_fp64(int which, int nthreads, int smem_bytes) {
 }
 cudaError_t set_smem_fp64(int bytes) {
   for (const void* k : {(const void*)k_fwd_fp64, (const void*)k_chain_fp64,
-                        (const void*)k_boundary_fp64, (const void*)k_wrap_fp64}) {
+                        (const void*)k_boundary_fp64, (const void*)k_wrap_fp64,
+                        (const void*)k_merge_fp64}) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,

@@ -394,7 +394,9 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
     if (q >= ntasks) break;
     const Task tk = tasks[q];
     const Desc d = descs[tk.desc];
-    const bool fwd = tk.b == 0;
+    // Task.b: 0 forward chain, 1 backward chain, 2 + s segment s of a time-parallel split
+    const bool fwd = tk.b != 1;
+    const int sg = tk.b - 2;
     const int ns = d.nstab, nb = d.nt / d.nstab;
     const FWork W{d.fws, n, nb};
     Small s = carve_small(smem + L.small_off, n);
@@ -409,11 +411,13 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
     for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
     bool ok = true;
     if (fwd) {
-      for (int b = 1; b <= nb && ok; ++b) {
+      // a segment of a time-parallel split runs blocks sg*kb+1 .. (sg+1)*kb from the identity
+      const int kb = sg >= 0 ? nb / d.nseg : nb, b_first = sg >= 0 ? sg * kb + 1 : 1;
+      for (int b = b_first; b < b_first + kb && ok; ++b) {
         const int t0 = (b - 1) * ns;
         cta_phase32(n, pf, d.phi + (size_t)t0 * n, 1.f);
         __syncthreads();
-        fill_b2(L, m, b == 1 ? nullptr : m.Xn, Scale{pf, false}, one);
+        fill_b2(L, m, b == b_first ? nullptr : m.Xn, Scale{pf, false}, one);
         for (int t = t0; t < t0 + ns; ++t) {
           const bool last = t + 1 == t0 + ns;
           float2* phn = pf + ((t - t0 + 1) & 1) * n;
@@ -424,7 +428,7 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
         if (!ok) break;
         cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
         double2* t2 = T; T = To; To = t2;
-        if (b < nb) {
+        if (sg < 0 && b < nb) {
           cta_copy(n * n, W.LX(b), m.Xn);
           cta_copy(n * n, W.LT(b), T);
           for (int k = tid(); k < n; k += nthr()) W.LD(b)[k] = s.logD[k];
@@ -432,7 +436,12 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
           if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, b);
         }
       }
-      if (ok) {
+      if (ok && sg >= 0) {  // segment result in the checkpoint storage of block sg+1
+        cta_copy(n * n, W.LX(sg + 1), m.Xn);
+        cta_copy(n * n, W.LT(sg + 1), T);
+        for (int k = tid(); k < n; k += nthr()) W.LD(sg + 1)[k] = s.logD[k];
+        if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
+      } else if (ok) {
         double2* G0 = W.Gb(1);
         cta_assemble(n, m.Xn, T, s.logD, m.Xc, G0, s, s.red + 2, s.red + 3);
         const double re = s.red[2], im = wrap_pi(s.red[3]);

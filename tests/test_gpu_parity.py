@@ -258,8 +258,11 @@ def test_mixed_oversize_class_runs_fp64(ctx):
 
     probs = [fi.make_problem(12, 16, 1.0, 3.0, 16, 1, 0), fi.make_problem(3, 16, 1.0, 3.0, 8, 1, 1)]
     b = api.Batch(ctx, to_dev(probs), "green", "3xtf32")
-    kinds = {g["nx"]: g["kernel"] for g in b.plan()}
-    assert kinds == {288: 0, 18: 4}
+    first = {}
+    for g in b.plan():  # the first launch of a class does the slice products
+        first.setdefault(g["nx"], g["kernel"])
+    # kernel codes: 0 log det/G, 1 chains (time-parallel segments), +4 on the tensor cores
+    assert first[288] in (0, 1) and first[18] in (4, 5)
     ld, G, _ = _run(ctx, probs, "green", "3xtf32")
     p = probs[0]
     ref_ld, ref_G = stable.logdet_green(p.E, p.phi, p.n_stab)
