@@ -470,11 +470,18 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
     g.fws_bytes = 0;
     // Time-parallel log det/G when the class has fewer configurations than SMs (each chain
     // would be one CTA's serial work while most of the GPU idles): every chain is cut into
-    // S segments (a power of two dividing its block count, at most half of it, S * configs <=
-    // 2 * SMs), computed from the identity in parallel and merged by a stabilised product.
+    // S segments (a power of two dividing its block count, at most half of it, S * configs at
+    // most one wave of the chain kernel), computed from the identity in parallel and merged by a
+    // stabilised product.
     int target = 1;
-    if (kind == K_FWD && nd < ctx->num_sms)
-      while (target < 16 && 2 * target * nd <= 2 * ctx->num_sms) target *= 2;
+    if (kind == K_FWD && nd < ctx->num_sms) {
+      // as many segments as one wave of the chain kernel holds
+      Phase P0;
+      if (!(mixed && mixed_phase(ctx, n, R_FWD, 1, three, nd, P0)))
+        P0 = fp64_phase(ctx, n, R_FWD, 1, nd);
+      const int slots = ctx->num_sms * std::max(1, P0.occ);
+      while (target < 16 && 2 * target * nd <= slots) target *= 2;
+    }
     if (kind == K_FWD && target >= 2) {
       for (int k = 0; k < nd; ++k) {
         const int c = g.idx[k];
