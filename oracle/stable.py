@@ -55,6 +55,28 @@ def udt_product(E: np.ndarray, phi: np.ndarray, n_stab: int):
     return X, D, T
 
 
+def udv_times_udv(later, earlier):
+    """Stabilised product of two UDV factors (Section 7): (Xs Ds Ts)(Xa Da Ta) =
+    Xs [Ds (Ts Xa)] Da Ta, the bracket times Da re-factored by a pivoted QR, X = Xs Q."""
+    Xs, Ds, Ts = later
+    Xa, Da, Ta = earlier
+    C = Ds[:, None] * (Ts @ Xa)
+    Q, d, T_new = reorthogonalise(C, Da, Ta)
+    return Xs @ Q, d, T_new
+
+
+def segmented_product(E: np.ndarray, phi: np.ndarray, n_stab: int, nseg: int):
+    """B_Nt ... B_1 from nseg consecutive segments, each a udt_product from the identity, merged
+    in time order with udv_times_udv (the same product as udt_product, in another order)."""
+    nt = phi.shape[0]
+    k = nt // nseg
+    segs = [udt_product(E, phi[s * k:(s + 1) * k], n_stab) for s in range(nseg)]
+    acc = segs[0]
+    for s in range(1, nseg):
+        acc = udv_times_udv(segs[s], acc)
+    return acc
+
+
 def assemble(X: np.ndarray, D: np.ndarray, T: np.ndarray):
     """(log det(1 + X D T), (1 + X D T)^{-1}) with the D_b / D_s scale separation."""
     Db = np.maximum(D, 1.0)

@@ -169,3 +169,15 @@ def test_force_matches_finite_differences(L, nt, beta, U, n_stab):
     F = np.array([rows[r][x] for r, x in entries])
     Ffd = force.finite_difference(p.E, p.phi, n_stab, entries, h=1e-6)
     assert np.abs(F - Ffd).max() < 2e-6 * max(1.0, np.abs(F).max())
+
+
+@pytest.mark.parametrize("name,nseg", [("cold72", 4), ("cold72", 8), ("force72", 2)])
+def test_segmented_product_matches_chain(name, nseg):
+    """The time-parallel order (segments from the identity, merged by the stabilised product of
+    two UDV factors) gives the log det and G of the sequential chain at beta = 64 and 32."""
+    p = fi.workload(name, batch=1)[0]
+    ref_ld, ref_G = stable.logdet_green(p.E, p.phi, p.n_stab)
+    ld, G = stable.assemble(*stable.segmented_product(p.E, p.phi, p.n_stab, nseg))
+    assert abs(ld.real - ref_ld.real) <= 1e-12 * abs(ref_ld)
+    assert abs(np.angle(np.exp(1j * (ld.imag - ref_ld.imag)))) <= 1e-12 * abs(ref_ld)
+    assert np.abs(G - ref_G).max() <= 1e-10 * max(1.0, float(np.abs(ref_G).max())) ** 2
