@@ -100,7 +100,12 @@ enum {
 int fd_reserve(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec);
 
 /* log det(1 + B_Nt...B_1) for `batch` configurations.
- *   logdet  device, 2*batch float64: (re, im) per configuration; im wrapped to (-pi, pi]. */
+ *   logdet  device, 2*batch float64: (re, im) per configuration; im wrapped to (-pi, pi].
+ * A size class with fewer configurations than SMs runs time-parallel: each chain is cut into
+ * segments computed concurrently and merged by the stabilised product of two UDV factors
+ * (Section 7); a segment's log D must then span less than 700 (else FD_ERR_NUMERIC in fd_status),
+ * which holds for beta per segment up to ~100 at kappa = 1 on the honeycomb lattice.  The same
+ * holds for fd_green and fd_observables without F and R. */
 int fd_logdet(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, int prec,
               void* stream);
 
@@ -196,10 +201,11 @@ int fd_graph_destroy(fd_ctx* ctx, void* graph);
 
 /* The launch plan a call with these arguments would use, without launching anything: one
  * record of 8 ints per kernel launch in info[8*g .. 8*g+7]:
- *   nx, kernel (+4 when it runs on the tensor cores): 0 log det/G, 1 force chains (forward and
- *   backward products, two tasks per configuration), 2 block-boundary Green's functions,
- *   3 wraps and force rows;  threads per CTA, dynamic shared memory bytes, grid (persistent
- *   CTAs), resident CTAs per SM, scratch KiB per CTA, tasks of the launch.
+ *   nx, kernel (+4 when it runs on the tensor cores): 0 log det/G, 1 chains (force: forward and
+ *   backward products, two tasks per configuration; time-parallel log det/G: segment products),
+ *   2 block-boundary Green's functions, 3 wraps and force rows, 8 merge of the segment products
+ *   and assembly (FP64);  threads per CTA, dynamic shared memory bytes, grid (persistent CTAs),
+ *   resident CTAs per SM, scratch KiB per CTA, tasks of the launch.
  * Returns the number of launches (>= 0, records beyond max_groups are not written) or a
  * negative FD_ERR_* code.  Synchronous, host only (queries the device's occupancy limits). */
 int fd_plan_query(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec, int* info,
