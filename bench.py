@@ -213,7 +213,10 @@ def run_reference(args):
     batch = len(fi.workload(name, batch=None)) if name != "tiny8" else 1
     cores = os.cpu_count() or 1
     pool = _pool(cores)
-    sample = list(range(min(batch, 8 * cores)))
+    # per-step sample: about 8 configurations per core in all over 20 steps' worth of oracle
+    # time, at least one per core, so that any --steps K finishes within a few minutes
+    per_step = max(cores, min(8 * cores, (8 * cores * 20) // max(1, args.steps)))
+    sample = list(range(min(batch, per_step)))
     for _ in range(args.warmup):
         oracle_sample(pool, name, sample[:cores], args.path)
     times = []
@@ -534,7 +537,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--prec", choices=("fp64", "tf32", "3xtf32"), default="3xtf32")
