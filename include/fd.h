@@ -118,7 +118,12 @@ int fd_green(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, do
  * fields Im F = 1/2 exactly on a bipartite lattice).  Forward pass with checkpoints of
  * (X, D, T) every n_stab slices, then an adjoint backward sweep that recomputes the right
  * products, forms the equal-time Green's function stably at each block boundary and wraps it
- * through the block.
+ * through the block (Section 4, Eq. response_result; Section 7 steps 7-9 with t1 = t2).  The
+ * forward and backward chains run as independent tasks; the boundary and wrap launches start
+ * while the chains run (programmatic dependent launch) and each of their tasks waits only for
+ * its own checkpoints; a task that sees no progress of its inputs for ~4 s gives up with
+ * FD_ERR_TIMEOUT in fd_status.  Workspace per configuration:
+ * (2 (nb-1) (2 nx^2 + ceil(nx/2)) + nb nx^2) * 16 bytes, nb = nt / n_stab.
  *   G  host array of device pointers or NULL (G not wanted)
  *   F  host array of `batch` device pointers; F[c] receives nt*nx complex128, row-major
  *      (row t-1 is slice t, like phi). */
