@@ -25,13 +25,15 @@ Modules:
     unequal        -- the unequal-time Green's function G(tau, 0) (Section 4.2, Section 7
                       steps 7-9).
     observables    -- fermion number and single-time response traces tr(O G_r) (Section 4.1).
+    bss            -- local (BSS) updates of the field at one time slice (Section 3).
 
 Parity pins (tests/test_oracle_*.py) tie every module to something other than itself.
 """
-from . import plain, fermion_matrix, stable, naive, free, force, unequal, observables  # noqa: F401
+from . import (plain, fermion_matrix, stable, naive, free, force, unequal, observables,  # noqa: F401
+               bss)
 
 __all__ = ["plain", "fermion_matrix", "stable", "naive", "free", "force", "unequal", "observables",
-           "wrap_phase"]
+           "bss", "wrap_phase"]
 
 
 def wrap_phase(z):
