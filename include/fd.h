@@ -146,6 +146,36 @@ int fd_force(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet, do
 int fd_green_tau(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet,
                  double* const* G, double* const* Gtau, double* const* F, int prec, void* stream);
 
+/* Local (BSS) updates of the auxiliary field at one time slice t (Section 3, the BSS algorithm).
+ * One entry per configuration; all pointers are device pointers owned by the caller:
+ *   nx        sites (1 <= nx <= FD_NX_MAX); reserved must be 0
+ *   G         nx*nx complex128 row-major, in/out: on entry G_{t-1} = (1 + B_{t-1}...B_1
+ *             B_Nt...B_t)^{-1} of the current field (slice t acting first; for t = 1 this is the
+ *             G of fd_green), on return the same Green's function of the updated field
+ *   phi_row   nx float64, in/out: the field of slice t (row t-1 of phi)
+ *   dphi      nx float64: the proposals phi_x -> phi_x + dphi_x, visited for x = 0..nx-1 in order
+ *   u, w      nx float64: uniform random numbers and the ratio of every other weight factor; the
+ *             proposal at x is accepted iff u_x < |r_x| w_x with r_x = det(1+P')/det(1+P)
+ *   accepted  nx int32 out: 1 where accepted
+ * The ratio comes from the matrix determinant lemma, r_x = 1 + (e^{i dphi_x} - 1)(1 - G_xx), and
+ * an accepted proposal updates G by Sherman-Morrison (O(nx^2); a rejected one costs O(1)).
+ * dlogdet: device, 2*batch float64: sum of log r_x over the accepted sites (re, im wrapped to
+ * (-pi, pi]), i.e. the change of log det.  FP64.  Asynchronous on `stream`; not available
+ * through fd_graph_create.  Wrapping G to the next slice and re-stabilising it every n_stab
+ * slices (fd_green / fd_force) are the caller's part of a sweep. */
+typedef struct {
+  int32_t nx;
+  int32_t reserved; /* must be 0 */
+  double* G;
+  double* phi_row;
+  const double* dphi;
+  const double* u;
+  const double* w;
+  int32_t* accepted;
+} fd_bss_slice;
+int fd_bss_update(fd_ctx* ctx, int batch, const fd_bss_slice* slices, double* dlogdet,
+                  void* stream);
+
 /* Wait for `stream` and copy the per-configuration device status of the LAST call on this
  * context into per_config_status[0..batch-1] (host): FD_OK, FD_ERR_NUMERIC or FD_ERR_TIMEOUT.
  * Returns the worst code seen (FD_OK if all succeeded). */

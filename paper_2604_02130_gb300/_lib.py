@@ -41,6 +41,19 @@ class fd_problem(ctypes.Structure):
     ]
 
 
+class fd_bss_slice(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("G", ctypes.c_void_p),
+        ("phi_row", ctypes.c_void_p),
+        ("dphi", ctypes.c_void_p),
+        ("u", ctypes.c_void_p),
+        ("w", ctypes.c_void_p),
+        ("accepted", ctypes.c_void_p),
+    ]
+
+
 # (name, restype, argtypes) of every exported function of include/fd.h
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
@@ -55,6 +68,7 @@ SIGNATURES = [
     ("fd_force", _I, [_VP, _I, _PP, _VP, _VP, _VP, _I, _VP]),
     ("fd_green_tau", _I, [_VP, _I, _PP, _VP, _VP, _VP, _VP, _I, _VP]),
     ("fd_observables", _I, [_VP, _I, _PP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP]),
+    ("fd_bss_update", _I, [_VP, _I, ctypes.POINTER(fd_bss_slice), _VP, _VP]),
     ("fd_status", _I, [_VP, _VP, ctypes.POINTER(_I), _I]),
     ("fd_last_launch_count", _I, [_VP]),
     ("fd_measure_fp64_peak", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),

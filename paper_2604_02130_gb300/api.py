@@ -348,6 +348,41 @@ def observables(problems, operators=None, prec: str = "fp64", with_force: bool =
     return r.logdet.clone(), r.nferm.clone(), r.R, r.F
 
 
+def bss_update(G: Sequence[torch.Tensor], phi_rows: Sequence[torch.Tensor],
+               dphi: Sequence[torch.Tensor], u: Sequence[torch.Tensor],
+               w: Sequence[torch.Tensor], ctx: Optional[Context] = None, stream=None):
+    """Local (BSS) updates at one time slice for a batch (Section 3; fd_bss_update).
+
+    Per configuration: G (nx, nx) complex128 = G_{t-1} of the current field (updated in place),
+    phi_rows (nx,) float64 = the field of slice t (updated in place), dphi/u/w (nx,) float64.
+    Returns (dlogdet (batch,) complex128: change of log det, [accepted (nx,) int32])."""
+    ctx = ctx or default_context()
+    n = len(G)
+    dev = torch.device("cuda", ctx.device)
+    arr = (L.fd_bss_slice * max(1, n))()
+    acc = []
+    for c in range(n):
+        nx = G[c].shape[0]
+        if not (G[c].is_cuda and G[c].dtype == torch.complex128 and G[c].is_contiguous()
+                and tuple(G[c].shape) == (nx, nx)):
+            raise ValueError("G must be contiguous (nx, nx) complex128 CUDA tensors")
+        for t in (phi_rows[c], dphi[c], u[c], w[c]):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                    and t.numel() == nx):
+                raise ValueError("phi_rows, dphi, u, w must be contiguous (nx,) float64 CUDA "
+                                 "tensors")
+        a = torch.empty(nx, dtype=torch.int32, device=dev)
+        acc.append(a)
+        arr[c].nx, arr[c].reserved = nx, 0
+        arr[c].G, arr[c].phi_row = G[c].data_ptr(), phi_rows[c].data_ptr()
+        arr[c].dphi, arr[c].u, arr[c].w = dphi[c].data_ptr(), u[c].data_ptr(), w[c].data_ptr()
+        arr[c].accepted = a.data_ptr()
+    out = torch.empty((max(1, n), 2), dtype=torch.float64, device=dev)
+    ctx.check(ctx.lib.fd_bss_update(ctx.h, n, arr, ctypes.c_void_p(out.data_ptr()),
+                                    _stream_ptr(stream)))
+    return torch.view_as_complex(out)[:n], acc
+
+
 class FermionLogDet(torch.autograd.Function):
     """log det(1 + B_Nt...B_1) of one configuration as a differentiable function of phi.
 

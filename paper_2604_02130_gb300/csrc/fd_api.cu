@@ -46,6 +46,9 @@ struct fd_ctx {
   bool timing = false;
   std::vector<cudaEvent_t> ev;  // pairs (start, stop)
   int ev_used = 0;
+  // local (BSS) slice updates: device copy of the slice table
+  fd::BssSlice* d_bss = nullptr;
+  size_t bss_cap = 0;
 };
 
 namespace {
@@ -876,6 +879,7 @@ void fd_ctx_destroy(fd_ctx* ctx) {
   if (ctx->d_tasks) cudaFree(ctx->d_tasks);
   if (ctx->h_tasks) cudaFreeHost(ctx->h_tasks);
   if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_bss) cudaFree(ctx->d_bss);
   if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
   for (auto e : ctx->ev) cudaEventDestroy(e);
   for (auto s : ctx->side) cudaStreamDestroy(s);
@@ -982,6 +986,47 @@ int fd_observables(fd_ctx* ctx, int batch, const fd_problem* probs, double* logd
   o.O = O;
   o.R = R;
   return run(ctx, batch, probs, o, prec, stream, kind);
+}
+
+int fd_bss_update(fd_ctx* ctx, int batch, const fd_bss_slice* slices, double* dlogdet,
+                  void* stream_) {
+  if (!ctx) return FD_ERR_INVALID;
+  if (batch < 0) return fail(ctx, FD_ERR_INVALID, "batch < 0");
+  if (batch == 0) return FD_OK;
+  if (!slices || !dlogdet) return fail(ctx, FD_ERR_INVALID, "null slices or dlogdet");
+  std::vector<fd::BssSlice> h(batch);
+  int maxn = 1;
+  for (int c = 0; c < batch; ++c) {
+    const fd_bss_slice& s = slices[c];
+    if (s.nx < 1 || s.nx > FD_NX_MAX)
+      return fail(ctx, FD_ERR_INVALID, "slice %d: nx=%d outside [1,%d]", c, s.nx, FD_NX_MAX);
+    if (s.reserved != 0) return fail(ctx, FD_ERR_INVALID, "slice %d: reserved != 0", c);
+    if (!s.G || !s.phi_row || !s.dphi || !s.u || !s.w || !s.accepted)
+      return fail(ctx, FD_ERR_INVALID, "slice %d: null pointer", c);
+    h[c] = fd::BssSlice{s.nx, 0, (double2*)s.G, s.phi_row, s.dphi, s.u, s.w, s.accepted};
+    maxn = std::max(maxn, s.nx);
+  }
+  cudaStream_t stream = (cudaStream_t)stream_;
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  if ((size_t)batch > ctx->bss_cap) {
+    if (ctx->d_bss) {
+      FD_CUDA(ctx, cudaStreamSynchronize(stream));
+      cudaFree(ctx->d_bss);
+    }
+    ctx->d_bss = nullptr;
+    const size_t cap = std::max<size_t>(batch, 256);
+    FD_CUDA(ctx, cudaMalloc(&ctx->d_bss, cap * sizeof(fd::BssSlice)));
+    ctx->bss_cap = cap;
+  }
+  // pageable source: the copy is staged before the call returns
+  FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_bss, h.data(), sizeof(fd::BssSlice) * batch,
+                               cudaMemcpyHostToDevice, stream));
+  const int grid = std::min(batch, ctx->num_sms * 8);
+  fd::launch_bss_fp64(ctx->d_bss, batch, maxn, dlogdet, grid, stream);
+  ctx->last_launches = 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+  return FD_OK;
 }
 
 int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch) {

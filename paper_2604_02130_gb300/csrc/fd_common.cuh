@@ -63,6 +63,17 @@ struct Desc {
   int nseg;            // time-parallel log det/G: number of segments of the chain (0: not split)
 };
 
+// One configuration of a local (BSS) slice update (the public fd_bss_slice, device view).
+struct BssSlice {
+  int nx, reserved;
+  double2* G;          // nx*nx row-major, in/out
+  double* phi;         // nx, in/out: the field of the slice
+  const double* dphi;  // nx proposals
+  const double* u;     // nx uniform random numbers
+  const double* w;     // nx other-weight ratios
+  int* acc;            // nx out: accepted
+};
+
 // ---------------------------------------------------------------- overlapped phases
 // The three launches of the phased path (chains, boundary Green's functions, wraps) overlap:
 // the later ones are launched as programmatic dependents (they may start while the earlier grid

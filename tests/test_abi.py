@@ -50,6 +50,14 @@ def test_problem_struct_layout():
     assert _lib.fd_problem.expA.offset == 16
 
 
+def test_bss_struct_layout():
+    from paper_2604_02130_gb300 import _lib
+
+    assert ctypes.sizeof(_lib.fd_bss_slice) == 56
+    assert _lib.fd_bss_slice.G.offset == 8
+    assert _lib.fd_bss_slice.accepted.offset == 48
+
+
 def test_ctx_create_without_gpu_fails_cleanly(lib):
     import torch
 

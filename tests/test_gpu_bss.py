@@ -1,0 +1,105 @@
+"""GPU parity of the local (BSS) slice update (fd_bss_update) against oracle.bss.
+
+The oracle takes every ratio from two stabilised determinants of the full product and the final
+Green's function from scratch; the GPU uses the matrix determinant lemma and Sherman-Morrison
+updates.  Compared: accept/reject decisions (exact; the cases keep every u_x away from the
+threshold |r_x| w_x by more than 1e-6), the field row, the change of log det and G.
+"""
+import numpy as np
+import pytest
+
+import fd_inputs as fi
+from oracle import bss
+from oracle import force as oforce
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _case(L, nt, beta, n_stab, t, seed, c):
+    p = fi.make_problem(L, nt, beta, 3.0, n_stab, seed, c)
+    rng = np.random.default_rng([seed, c])
+    dphi = rng.normal(0.0, 0.7, size=p.nx)
+    u = rng.uniform(size=p.nx)
+    w = np.exp(rng.normal(0.0, 0.3, size=p.nx))
+    ref = bss.slice_update(p.E, p.phi, p.n_stab, t, dphi, u, w)
+    margin = np.abs(u - np.abs(ref[4]) * w).min()
+    return p, t, dphi, u, w, ref, margin
+
+
+CASES = [(2, 16, 2.0, 4, 1), (2, 16, 2.0, 4, 7), (3, 24, 3.0, 8, 1), (3, 24, 3.0, 8, 13),
+         (4, 16, 2.0, 4, 9), (6, 16, 2.0, 8, 3)]
+
+
+def test_bss_matches_oracle():
+    from paper_2604_02130_gb300 import api
+
+    dev = torch.device("cuda", 0)
+    cases = []
+    for k, (L, nt, beta, ns, t) in enumerate(CASES):
+        for c in range(3):
+            case = _case(L, nt, beta, ns, t, 500 + k, c)
+            if case[-1] > 1e-6:
+                cases.append(case)
+    assert len(cases) >= 12
+    G, rows, dp, uu, ww = [], [], [], [], []
+    for p, t, dphi, u, w, ref, _ in cases:
+        G0 = oforce.green_at(p.E, p.phi, p.n_stab, t - 1)  # G_{t-1} of the current field
+        G.append(torch.from_numpy(np.ascontiguousarray(G0)).to(dev))
+        rows.append(torch.from_numpy(p.phi[t - 1].copy()).to(dev))
+        dp.append(torch.from_numpy(dphi).to(dev))
+        uu.append(torch.from_numpy(u).to(dev))
+        ww.append(torch.from_numpy(w).to(dev))
+    dld, acc = api.bss_update(G, rows, dp, uu, ww)
+    torch.cuda.synchronize()
+    dld = dld.cpu().numpy()
+    n_acc = 0
+    for k, (p, t, dphi, u, w, ref, _) in enumerate(cases):
+        row, accepted, total, Gref, _ = ref
+        a = acc[k].cpu().numpy().astype(bool)
+        assert np.array_equal(a, accepted), k
+        n_acc += int(a.sum())
+        assert np.array_equal(rows[k].cpu().numpy(), row)
+        scale = max(1.0, float(np.abs(Gref).max())) ** 2
+        assert np.abs(G[k].cpu().numpy() - Gref).max() <= 1e-9 * scale, k
+        d = complex(dld[k])
+        assert abs(d.real - total.real) <= 1e-9 * max(1.0, abs(total))
+        assert abs(np.angle(np.exp(1j * (d.imag - total.imag)))) <= 1e-9 * max(1.0, abs(total))
+    assert 0 < n_acc < sum(p.nx for p, *_ in cases)
+
+
+def test_bss_after_fd_green_at_slice_one():
+    """t = 1: the G that fd_green returns is G_0, the input of an update at slice 1."""
+    from paper_2604_02130_gb300 import api
+
+    from gpu_helpers import to_dev
+
+    probs = fi.workload("batch18", batch=8)
+    _, G = api.green(to_dev(probs))
+    dev = torch.device("cuda", 0)
+    rows, dp, uu, ww, refs = [], [], [], [], []
+    for c, p in enumerate(probs):
+        rng = np.random.default_rng([77, c])
+        dphi = rng.normal(0.0, 0.7, size=p.nx)
+        u = rng.uniform(size=p.nx)
+        w = np.full(p.nx, 1e300)  # every proposal accepted
+        refs.append(bss.slice_update(p.E, p.phi, p.n_stab, 1, dphi, u, w))
+        rows.append(torch.from_numpy(p.phi[0].copy()).to(dev))
+        dp.append(torch.from_numpy(dphi).to(dev))
+        uu.append(torch.from_numpy(u).to(dev))
+        ww.append(torch.from_numpy(w).to(dev))
+    G = [g.clone() for g in G]
+    dld, acc = api.bss_update(G, rows, dp, uu, ww)
+    torch.cuda.synchronize()
+    for c, ref in enumerate(refs):
+        assert acc[c].cpu().numpy().all()
+        scale = max(1.0, float(np.abs(ref[3]).max())) ** 2
+        assert np.abs(G[c].cpu().numpy() - ref[3]).max() <= 1e-9 * scale
+
+
+def test_bss_validation():
+    from paper_2604_02130_gb300 import api
+
+    ctx = api.default_context()
+    rc = ctx.lib.fd_bss_update(ctx.h, 1, None, None, None)
+    assert rc == -1
