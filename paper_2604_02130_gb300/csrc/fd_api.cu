@@ -1022,10 +1022,9 @@ int fd_bss_update(fd_ctx* ctx, int batch, const fd_bss_slice* slices, double* dl
   FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_bss, h.data(), sizeof(fd::BssSlice) * batch,
                                cudaMemcpyHostToDevice, stream));
   const int grid = std::min(batch, ctx->num_sms * 8);
-  fd::launch_bss_fp64(ctx->d_bss, batch, maxn, dlogdet, grid, stream);
-  ctx->last_launches = 1;
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = fd::launch_bss(ctx->d_bss, batch, maxn, dlogdet, grid, stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+  ctx->last_launches = 1;
   return FD_OK;
 }
 

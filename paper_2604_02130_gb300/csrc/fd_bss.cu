@@ -5,76 +5,239 @@
 // and the matrix determinant lemma gives the ratio of determinants
 //   r = det(1 + P') / det(1 + P) = 1 + delta (1 - G_xx),
 // while Sherman-Morrison updates the Green's function of an accepted proposal:
-//   G'_ij = G_ij - (delta / r) (delta_ix - G_ix) G_xj.
+//   G'_ij = G_ij - a_i b_j,  a_i = (delta / r) (delta_ix - G_ix),  b_j = G_xj.
 // Accepted iff u_x < |r| w_x.  A rejected proposal costs O(1), an accepted one O(nx^2) -- the
-// complexity the paper states for BSS updates.  One CTA per configuration, FP64.
+// complexity the paper states for BSS updates.  One CTA per configuration.
+//
+// Precision.  Ratios, decisions, delta / r and the change of log det are FP64.  The nx^2 rank-1
+// updates are the bulk of the work, and on this GPU an SM retires FP64 instructions some seventy
+// times slower than FP32 ones, so for nx <= kBssDfMax the slice keeps G in shared memory as
+// double-float pairs (fd_df.cuh, ~46 significant bits) and updates it with FP32 instructions,
+// converting from and back to FP64 once per call.  Larger nx (or a G with entries beyond
+// 2^100, outside the FP32 exponent range the pairs need) runs the same steps in FP64 on G in
+// place in global memory.
 #include "fd_common.cuh"
+#include "fd_df.cuh"
 #include "fd_kernels.h"
 
 namespace fd {
 
-__global__ void __launch_bounds__(256) k_bss_fp64(const BssSlice* __restrict__ slices, int batch,
-                                                   double* dlogdet) {
-  extern __shared__ __align__(16) double2 sh[];
-  __shared__ double2 fact;
-  __shared__ int accept;
+namespace {
+
+constexpr int kBssDfMax = 110;  // 16 nx^2 + 84 nx bytes of shared memory <= 202 KB
+
+// Per-CTA shared memory (dynamic), sized for the largest nx of the launch.
+struct BssSmem {
+  df::c4* Gs;     // nx*nx df G (only when the df path is available)
+  double2* a;     // staged a_i (df c4 or FP64 double2, 16 bytes each)
+  double2* b;     // staged b_j
+  double2* dl;    // delta_x
+  double2* rs;    // r_x of accepted proposals
+  double* v;      // u_x / w_x, then log|r_x|
+  double* vv;     // (u_x / w_x)^2 or -1 when out of the range where squaring is safe, then arg r_x
+  int* acc;       // decisions
+};
+
+__device__ __forceinline__ BssSmem bss_smem(char* base, int maxn, bool df_path) {
+  BssSmem s;
+  size_t off = 0;
+  s.Gs = (df::c4*)base;
+  if (df_path) off += (size_t)maxn * maxn * sizeof(df::c4);
+  s.a = (double2*)(base + off);
+  off += (size_t)maxn * 16;
+  s.b = (double2*)(base + off);
+  off += (size_t)maxn * 16;
+  s.dl = (double2*)(base + off);
+  off += (size_t)maxn * 16;
+  s.rs = (double2*)(base + off);
+  off += (size_t)maxn * 16;
+  s.v = (double*)(base + off);
+  off += (size_t)maxn * 8;
+  s.vv = (double*)(base + off);
+  off += (size_t)maxn * 8;
+  s.acc = (int*)(base + off);
+  return s;
+}
+
+// The Metropolis decision and delta / r for site x from G_xx (thread 0 only).
+__device__ __forceinline__ bool bss_decide(const BssSmem& s, int x, double gre, double gim,
+                                           cplx& f) {
+  const double2 d = s.dl[x];
+  const double ore = 1.0 - gre, oim = -gim;
+  const double rre = fma(d.x, ore, fma(-d.y, oim, 1.0));
+  const double rim = fma(d.x, oim, d.y * ore);
+  const double t = fma(rre, rre, rim * rim);  // |r|^2
+  const double vv = s.vv[x];
+  const bool normal = t > 1e-280 && t < 1e280;
+  // u < |r| w  <=>  (u / w)^2 < |r|^2, squared where nothing under- or overflows
+  const bool acc = (vv >= 0.0 && normal) ? vv < t : s.v[x] < sqrt(t);
+  if (acc) {
+    if (normal) {
+      const double inv = 1.0 / t;  // delta conj(r) / |r|^2
+      f = cx(fma(d.x, rre, d.y * rim) * inv, fma(d.y, rre, -d.x * rim) * inv);
+    } else {
+      f = cdiv(cx(d.x, d.y), cx(rre, rim));
+    }
+    s.rs[x] = make_double2(rre, rim);
+  }
+  s.acc[x] = acc;
+  return acc;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(512) k_bss(const BssSlice* __restrict__ slices, int batch,
+                                              int maxn, int df_path, double* dlogdet) {
+  extern __shared__ __align__(16) char smem_raw[];
+  __shared__ df::c4 fdf;
+  __shared__ double2 f64;
+  __shared__ int accept[2];  // double-buffered: site x uses accept[x & 1]
+  const BssSmem s = bss_smem(smem_raw, maxn, df_path != 0);
+  const int tid = threadIdx.x, bd = blockDim.x;
   for (int c = blockIdx.x; c < batch; c += gridDim.x) {
     const BssSlice q = slices[c];
     const int n = q.nx;
-    double2* col = sh;      // delta_ix - G_ix
-    double2* row = sh + n;  // G_xj
-    double lre = 0.0, lim = 0.0;
+    for (int x = tid; x < n; x += bd) {
+      double sn, cs;
+      sincos(q.dphi[x], &sn, &cs);
+      s.dl[x] = make_double2(cs - 1.0, sn);
+      const double v = q.u[x] / q.w[x];
+      const double vv = v * v;
+      s.v[x] = v;
+      s.vv[x] = (vv >= 1e-280 && vv <= 1e280) ? vv : -1.0;
+      s.acc[x] = 0;
+    }
+    // df path: G -> shared memory as df pairs, unless an entry is beyond 2^100 (or not finite)
+    int big = 0;
+    if (df_path) {
+      for (int e = tid; e < n * n; e += bd) {
+        const double2 g = q.G[e];
+        const uint64_t mx = df::dbits(g.x) & 0x7ff0000000000000ull;
+        const uint64_t my = df::dbits(g.y) & 0x7ff0000000000000ull;
+        big |= (mx >= (uint64_t)(1023 + 100) << 52) | (my >= (uint64_t)(1023 + 100) << 52);
+        s.Gs[e] = df::csplit(g.x, g.y);
+      }
+    }
+    const bool use_df = df_path && !__syncthreads_or(big);
+    // thread layout of the rank-1 update in the df path: column j, rows i0, i0 + rpp, ...
+    const int rpp = n <= bd ? bd / n : 1;
+    const int j = tid % n, i0 = tid / n;
     for (int x = 0; x < n; ++x) {
-      if (threadIdx.x == 0) {
-        const double2 g = q.G[(size_t)x * n + x];
-        double sn, cs;
-        sincos(q.dphi[x], &sn, &cs);
-        const cplx delta = cx(cs - 1.0, sn);
-        const cplx r = cx(1.0, 0.0) + delta * cx(1.0 - g.x, -g.y);
-        const double ar = hypot(r.re, r.im);
-        const int acc = q.u[x] < ar * q.w[x];
-        if (acc) {
-          const cplx f = cdiv(delta, r);
-          fact = make_double2(f.re, f.im);
-          lre += log(ar);
-          lim += atan2(r.im, r.re);
-          q.phi[x] += q.dphi[x];
+      if (tid == 0) {
+        double gre, gim;
+        if (use_df) {
+          const df::c4 g = s.Gs[x * n + x];
+          gre = df::join(g.x, g.y);
+          gim = df::join(g.z, g.w);
+        } else {
+          const double2 g = q.G[(size_t)x * n + x];
+          gre = g.x;
+          gim = g.y;
         }
-        q.acc[x] = acc;
-        accept = acc;
+        cplx f;
+        const bool a = bss_decide(s, x, gre, gim, f);
+        if (a) {
+          if (use_df) fdf = df::csplit(f.re, f.im);
+          else f64 = make_double2(f.re, f.im);
+        }
+        accept[x & 1] = a;
       }
       __syncthreads();
-      if (accept) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          const double2 gi = q.G[(size_t)i * n + x];
-          col[i] = make_double2((i == x ? 1.0 : 0.0) - gi.x, -gi.y);
-          row[i] = q.G[(size_t)x * n + i];
+      if (!accept[x & 1]) continue;  // uniform: every thread reads the same flag
+      if (use_df) {
+        df::c4* A = (df::c4*)s.a;
+        df::c4* B = (df::c4*)s.b;
+        const df::c4 f = fdf;
+        const df::c4 zero = {0.f, 0.f, 0.f, 0.f};
+        for (int i = tid; i < n; i += bd) {
+          df::c4 g = s.Gs[i * n + x];  // G_ix - delta_ix, then a_i = -(delta / r)(G_ix - delta_ix)
+          if (i == x) g = df::add_re(g, -1.f);
+          A[i] = df::cms(zero, f, g);
+          B[i] = s.Gs[x * n + i];
         }
         __syncthreads();
-        const cplx f = cx(fact.x, fact.y);
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-          const int i = e / n, j = e % n;
-          const cplx a = f * cx(col[i].x, col[i].y);
-          const cplx upd = a * cx(row[j].x, row[j].y);
-          q.G[e] = make_double2(q.G[e].x - upd.re, q.G[e].y - upd.im);
+        if (i0 < rpp) {
+          const df::c4 bj = B[j];
+          for (int i = i0; i < n; i += rpp) s.Gs[i * n + j] = df::cms(s.Gs[i * n + j], A[i], bj);
+        }
+      } else {
+        const cplx f = cx(f64.x, f64.y);
+        for (int i = tid; i < n; i += bd) {
+          const double2 g = q.G[(size_t)i * n + x];
+          const cplx col = cx((i == x ? 1.0 : 0.0) - g.x, -g.y);
+          const cplx a = f * col;
+          s.a[i] = make_double2(a.re, a.im);
+          s.b[i] = q.G[(size_t)x * n + i];
+        }
+        __syncthreads();
+        for (int e = tid; e < n * n; e += bd) {
+          const int i = e / n, jj = e - i * n;
+          const double2 a = s.a[i], b = s.b[jj];
+          const double2 g = q.G[e];
+          q.G[e] = make_double2(fma(-a.x, b.x, fma(a.y, b.y, g.x)),
+                                fma(-a.x, b.y, fma(-a.y, b.x, g.y)));
         }
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) {
-      const double pi = 3.14159265358979323846;
-      double y = remainder(lim, 2.0 * pi);  // (-pi, pi]
-      if (y <= -pi) y += 2.0 * pi;
-      dlogdet[2 * c] = lre;
-      dlogdet[2 * c + 1] = y;
+    // outputs: field row, decisions, G back to FP64, log r_x of the accepted sites
+    for (int x = tid; x < n; x += bd) {
+      const int a = s.acc[x];
+      q.acc[x] = a;
+      double lr = 0.0, la = 0.0;
+      if (a) {
+        q.phi[x] += q.dphi[x];
+        const double2 r = s.rs[x];
+        lr = log(hypot(r.x, r.y));
+        la = atan2(r.y, r.x);
+      }
+      s.v[x] = lr;
+      s.vv[x] = la;
+    }
+    if (use_df) {
+      for (int e = tid; e < n * n; e += bd) {
+        const df::c4 g = s.Gs[e];
+        q.G[e] = make_double2(df::join(g.x, g.y), df::join(g.z, g.w));
+      }
+    }
+    __syncthreads();
+    if (tid < 32) {
+      double lr = 0.0, la = 0.0;
+      for (int x = tid; x < n; x += 32) {
+        lr += s.v[x];
+        la += s.vv[x];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        lr += __shfl_down_sync(0xffffffffu, lr, o);
+        la += __shfl_down_sync(0xffffffffu, la, o);
+      }
+      if (tid == 0) {
+        const double pi = 3.14159265358979323846;
+        double y = remainder(la, 2.0 * pi);  // (-pi, pi]
+        if (y <= -pi) y += 2.0 * pi;
+        dlogdet[2 * c] = lr;
+        dlogdet[2 * c + 1] = y;
+      }
     }
     __syncthreads();
   }
 }
 
-void launch_bss_fp64(const BssSlice* slices, int batch, int maxn, double* dlogdet, int grid,
-                     cudaStream_t stream) {
-  k_bss_fp64<<<grid, 256, (size_t)2 * maxn * sizeof(double2), stream>>>(slices, batch, dlogdet);
+size_t bss_smem_bytes(int maxn, bool df_path) {
+  return (df_path ? (size_t)maxn * maxn * sizeof(df::c4) : 0) + (size_t)maxn * 84;
+}
+
+int bss_threads(int maxn) { return maxn <= 24 ? 128 : maxn <= 48 ? 256 : 512; }
+
+cudaError_t launch_bss(const BssSlice* slices, int batch, int maxn, double* dlogdet, int grid,
+                       cudaStream_t stream) {
+  const bool df_path = maxn <= kBssDfMax;
+  const size_t smem = bss_smem_bytes(maxn, df_path);
+  cudaError_t e = cudaFuncSetAttribute(k_bss, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_bss<<<grid, bss_threads(maxn), smem, stream>>>(slices, batch, maxn, df_path ? 1 : 0, dlogdet);
+  return cudaGetLastError();
 }
 
 }  // namespace fd

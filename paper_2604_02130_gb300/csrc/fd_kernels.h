@@ -39,9 +39,10 @@ cudaError_t set_smem_mixed(int bytes);
 int occupancy_mixed(int which, int nthreads, int smem_bytes);  // -1 on error
 cudaError_t attrs_mixed(int which, cudaFuncAttributes* a);
 
-// local (BSS) slice updates (one CTA per configuration, dynamic smem 2 * maxn complex)
-void launch_bss_fp64(const BssSlice* slices, int batch, int maxn, double* dlogdet, int grid,
-                     cudaStream_t stream);
+// local (BSS) slice updates (one CTA per configuration; G in shared memory as double-float
+// pairs when maxn is small enough, else FP64 in place)
+cudaError_t launch_bss(const BssSlice* slices, int batch, int maxn, double* dlogdet, int grid,
+                       cudaStream_t stream);
 
 // FP64 throughput probe
 cudaError_t run_fp64_probe(int grid, int threads, int iters, double* out, cudaStream_t stream);

@@ -2,7 +2,7 @@
 
 The oracle takes every ratio from two stabilised determinants of the full product and the final
 Green's function from scratch; the GPU uses the matrix determinant lemma and Sherman-Morrison
-updates.  Compared: accept/reject decisions (exact; the cases keep every u_x away from the
+updates, on G held in shared memory as double-float pairs (nx <= 110) or in FP64 in place.  Compared: accept/reject decisions (exact; the cases keep every u_x away from the
 threshold |r_x| w_x by more than 1e-6), the field row, the change of log det and G.
 """
 import numpy as np
@@ -66,6 +66,37 @@ def test_bss_matches_oracle():
         assert abs(d.real - total.real) <= 1e-9 * max(1.0, abs(total))
         assert abs(np.angle(np.exp(1j * (d.imag - total.imag)))) <= 1e-9 * max(1.0, abs(total))
     assert 0 < n_acc < sum(p.nx for p, *_ in cases)
+
+
+def test_bss_fp64_in_place_path():
+    """nx = 128 is above the size whose G fits in shared memory as double-float pairs, so the
+    whole launch (including an 18-site configuration) updates G in FP64 in global memory."""
+    from paper_2604_02130_gb300 import api
+
+    dev = torch.device("cuda", 0)
+    cases = [_case(8, 4, 1.0, 2, 3, 601, 0), _case(3, 8, 1.0, 4, 5, 602, 0)]
+    assert all(case[-1] > 1e-6 for case in cases)
+    G, rows, dp, uu, ww = [], [], [], [], []
+    for p, t, dphi, u, w, ref, _ in cases:
+        G.append(torch.from_numpy(np.ascontiguousarray(
+            oforce.green_at(p.E, p.phi, p.n_stab, t - 1))).to(dev))
+        rows.append(torch.from_numpy(p.phi[t - 1].copy()).to(dev))
+        dp.append(torch.from_numpy(dphi).to(dev))
+        uu.append(torch.from_numpy(u).to(dev))
+        ww.append(torch.from_numpy(w).to(dev))
+    dld, acc = api.bss_update(G, rows, dp, uu, ww)
+    torch.cuda.synchronize()
+    dld = dld.cpu().numpy()
+    for k, (p, t, dphi, u, w, ref, _) in enumerate(cases):
+        row, accepted, total, Gref, _ = ref
+        assert np.array_equal(acc[k].cpu().numpy().astype(bool), accepted)
+        assert 0 < accepted.sum() < p.nx
+        assert np.array_equal(rows[k].cpu().numpy(), row)
+        scale = max(1.0, float(np.abs(Gref).max())) ** 2
+        assert np.abs(G[k].cpu().numpy() - Gref).max() <= 1e-9 * scale
+        d = complex(dld[k])
+        assert abs(d.real - total.real) <= 1e-9 * max(1.0, abs(total))
+        assert abs(np.angle(np.exp(1j * (d.imag - total.imag)))) <= 1e-9 * max(1.0, abs(total))
 
 
 def test_bss_after_fd_green_at_slice_one():
