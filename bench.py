@@ -6,12 +6,14 @@ beta = 8, Nt = 64, U = 3, n_stab = 8.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec 3xtf32|tf32|fp64]
                     [--workload batch18|cold72|force72|tiny8] [--impl ours|reference]
-                    [--path force|gtau|observables]
+                    [--path force|gtau|observables|bss]
 
 --path picks what one step computes (default `force`, the headline):
   force        log det + G + force
   gtau         log det + the unequal-time G(tau, 0) for every tau (Section 4.2)
   observables  log det + fermion number + response traces tr(A G_t) at every slice (Section 4.1)
+  bss          local (BSS) updates of time slice 1, every site proposed once (Section 3); the
+               unit is site proposals/s, G_0 comes from an untimed FP64 log det/G call
 
 The headline is the mixed-precision path (slice products on tensor cores, FP64 QR/assembly);
 the plain FP64 path is measured on the same inputs and reported beside it (`fp64_path`).
@@ -57,6 +59,9 @@ PATHS = {
     "observables": {"want": "nferm+response",
                     "metric": "configs/s (log det + n + tr(A G_t) for all t)",
                     "what": "log det + fermion number + response traces tr(A G_t), t=0..Nt-1"},
+    "bss": {"want": None, "metric": "site proposals/s (local updates at one time slice)",
+            "what": "local (BSS) updates of slice 1, every site proposed once per step "
+                    "(dphi ~ N(0, delta*U), u ~ U(0,1), w = 1), G_0 from FP64 log det/G"},
 }
 
 
@@ -66,10 +71,16 @@ def _oracle_worker(args):
     force, G(tau, 0) for every tau, or the fermion number and the response traces tr(A G_t)."""
     name, c, path = args
     import fd_inputs as fi
+    from oracle import bss
     from oracle import force as oforce
     from oracle import observables, stable, unequal
 
     p = fi.workload(name, batch=1, first=c)[0]
+    if path == "bss":  # step 0's proposals from the G_0 of the workload's field
+        dphi, u, w = (a[0] for a in fi.bss_proposals(name, 0, first=c, count=1))
+        t0 = time.perf_counter()
+        row, acc, total, G, _ = bss.slice_update(p.E, p.phi, p.n_stab, 1, dphi, u, w)
+        return c, total, {"row": row, "acc": acc, "G": G}, time.perf_counter() - t0
     t0 = time.perf_counter()
     ld, G = stable.logdet_green(p.E, p.phi, p.n_stab)
     if path == "force":
@@ -225,18 +236,20 @@ def run_reference(args):
         times.append(dt)
     pool.close()
     total = sum(times)
-    value = len(sample) * args.steps / total
+    per = fi.workload(name, batch=1)[0].nx if args.path == "bss" else 1
+    unit = "proposals/s" if args.path == "bss" else "configs/s"
+    value = len(sample) * per * args.steps / total
     line = {
         "impl": "reference", "metric": PATHS[args.path]["metric"], "value": value,
-        "unit": "configs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "unit": unit, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[name] + "; " + PATHS[args.path]["what"],
                    "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": "configs/s", "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
                          "sample": "%d of the %d configurations per step, one per process"
                                    % (len(sample), batch)},
-        "e2e": {"value": value, "unit": "configs/s", "h2d_bytes_per_step": 0,
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -534,6 +547,203 @@ def run_ours(args):
     return 0
 
 
+def run_bss(args):
+    """--path bss: one step = one fd_bss_update call over slice 1 of every configuration of the
+    shard, every site proposed once.  G_0 comes from an untimed FP64 log det/G call; the steps
+    continue the Markov chain of slice 1 with fresh proposals (resident on the device, one set
+    per step), so every step does the same kind of work.  A separate first call from G_0 with
+    step 0's proposals is compared with the oracle."""
+    ws, rank, local = _dist()
+    import numpy as np
+
+    import fd_inputs as fi
+
+    name = args.workload
+    if name == "tiny8":
+        raise SystemExit("--path bss needs a batched workload")
+    w_batch = fi.WORKLOADS[name]["batch"]
+    cores = os.cpu_count() or 1
+    pool = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        pool = _pool(cores)  # spawned before the first CUDA call
+    import torch
+
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2604_02130_gb300 import api, shard
+
+    dev = torch.device("cuda", local)
+    mine = shard.shard_range(rank, w_batch)
+    probs = fi.workload(name, batch=w_batch, first=mine.start)
+    nx = probs[0].nx
+    n_total = w_batch * ws
+    ctx = api.Context(local)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # G_0 (FP64) and the field rows of slice 1, resident on the device
+    phi_dev = torch.from_numpy(np.stack([p.phi for p in probs])).to(dev)
+    E = torch.from_numpy(probs[0].E).to(dev)
+    Einv = torch.from_numpy(probs[0].Einv).to(dev)
+    g0 = api.Batch(ctx, [(E, Einv, phi_dev[c], p.n_stab) for c, p in enumerate(probs)],
+                   "green", "fp64")
+    g0.run()
+    barrier()
+    G0 = torch.stack([g.clone() for g in g0.G])
+    row0 = phi_dev[:, 0, :].clone()
+    warm = max(3, args.warmup)
+    ntime = min(args.steps, 5)
+    ncalls = 1 + warm + args.steps + ntime  # check, warm-up, timed, per-launch timing pass
+    prop_host = np.stack([np.stack(fi.bss_proposals(name, s, first=mine.start, count=w_batch))
+                          for s in range(ncalls)])  # (ncalls, 3, batch, nx)
+    prop = torch.from_numpy(prop_host).to(dev)
+    acc = torch.zeros((ncalls, w_batch, nx), dtype=torch.int32, device=dev)
+    Gchk, rowchk = G0.clone(), row0.clone()
+    Gs, rows = G0.clone(), row0.clone()
+
+    def prepared(s, G, row):
+        return api.BssSlices(list(G), list(row), list(prop[s, 0]), list(prop[s, 1]),
+                             list(prop[s, 2]), list(acc[s]), ctx)
+
+    calls = [prepared(0, Gchk, rowchk)] + [prepared(s, Gs, rows) for s in range(1, ncalls)]
+    dld_chk = calls[0].run().clone()
+    for s in range(1, 1 + warm):
+        calls[s].run()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.__enter__()
+    try:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            calls[1 + warm + k].run()
+            ev[k][1].record(stream)
+        barrier()
+    finally:
+        clk.__exit__()
+    total_ms = shard.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev)
+    value = n_total * nx * args.steps / (total_ms * 1e-3)
+    launches = args.steps  # one k_bss launch per call
+    # per-launch kernel time (events around the launch alone) for the roofline
+    kernel_ms = []
+    ctx.set_timing(True)
+    for s in range(1 + warm + args.steps, ncalls):
+        flush.zero_()
+        calls[s].run()
+        kernel_ms.append(ctx.last_kernel_ms()[0])
+    ctx.set_timing(False)
+    acc_timing = int(acc[1 + warm + args.steps:].sum().item())
+    acc_timed = int(acc[1 + warm:1 + warm + args.steps].sum().item())
+
+    # end to end through the public API: the step's proposals from pinned host memory into
+    # fixed device buffers, the call, decisions and the change of log det read back
+    pin = torch.from_numpy(prop_host[1 + warm:1 + warm + args.steps]).pin_memory()
+    buf = torch.empty((3, w_batch, nx), dtype=torch.float64, device=dev)
+    acc_e = torch.empty((w_batch, nx), dtype=torch.int32, device=dev)
+    e2e_call = api.BssSlices(list(Gs), list(rows), list(buf[0]), list(buf[1]), list(buf[2]),
+                             list(acc_e), ctx)
+    acc_h = torch.empty((w_batch, nx), dtype=torch.int32).pin_memory()
+    dld_h = torch.empty((w_batch, 2), dtype=torch.float64).pin_memory()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        buf.copy_(pin[k], non_blocking=True)
+        e2e_call.run()
+        acc_h.copy_(acc_e, non_blocking=True)
+        dld_h.copy_(e2e_call.out[:w_batch], non_blocking=True)
+        ev2[k][1].record(stream)
+    barrier()
+    e2e_ms = shard.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2), dev)
+    e2e = {"value": n_total * nx * args.steps / (e2e_ms * 1e-3), "unit": "proposals/s",
+           "h2d_bytes_per_step": 3 * w_batch * nx * 8,
+           "d2h_bytes_per_step": w_batch * nx * 4 + w_batch * 16}
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
+
+    # roofline: the rank-1 updates (8 Nx^2 real flops per accepted site) against the FP32 issue
+    # bound of the double-float complex multiply-subtract (54 FP32 instructions per 8 flops on
+    # 128 lanes per SM); configurations run one per SM, so only min(batch, SMs) SMs take part
+    clocks = clk.summary()
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    sms = min(w_batch, torch.cuda.get_device_properties(dev).multi_processor_count)
+    k_ms = statistics.mean(kernel_ms)
+    achieved = 8.0 * nx * nx * acc_timing / len(kernel_ms) / (k_ms * 1e-3) / 1e12
+    peak = sms * 128 * mhz * 1e6 * 8.0 / 54.0 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": _traffic("k_bss", name, "df", "bss"),
+            "kernel": "k_bss", "kernel_ms": k_ms,
+            "what": "rank-1 updates of G (8 Nx^2 real flops per accepted site) per launch over "
+                    "the launch's CUDA-event duration",
+            "peak_source": "FP32 issue bound of the double-float update: %d SMs x 128 lanes x "
+                           "%.0f MHz (sampled) x 8 flops / 54 instructions" % (sms, mhz),
+            "accepted_fraction": acc_timed / float(w_batch * nx * args.steps)}
+
+    cpu = None
+    err = None
+    if pool is not None:
+        sample = list(range(min(w_batch, cores)))
+        res, dt = oracle_sample(pool, name, sample, "bss")
+        pool.close()
+        cpu = {"value": len(sample) * nx / dt, "unit": "proposals/s", "cores": cores,
+               "kind": "oracle",
+               "sample": "slice 1 of %d of the %d configurations, one per process (a stabilised "
+                         "determinant per proposal)" % (len(sample), w_batch)}
+        acc0 = acc[0].cpu().numpy().astype(bool)
+        d0 = dld_chk.cpu().numpy()
+        Gc = Gchk.cpu().numpy()
+        rc = rowchk.cpu().numpy()
+        e = {"decisions_differing": 0, "row_max_abs": 0.0, "G_abs_over_maxG2": 0.0,
+             "dlogdet_abs": 0.0}
+        for c, total, out, _ in res:
+            e["decisions_differing"] += int((acc0[c] != out["acc"]).sum())
+            e["row_max_abs"] = max(e["row_max_abs"], float(np.abs(rc[c] - out["row"]).max()))
+            e["G_abs_over_maxG2"] = max(e["G_abs_over_maxG2"], _scaled_err(Gc[c], out["G"]))
+            dd = complex(d0[c]) - total
+            e["dlogdet_abs"] = max(e["dlogdet_abs"],
+                                   abs(dd.real), abs(np.angle(np.exp(1j * dd.imag))))
+        e["configs_checked"] = len(res)
+        err = {"df": e}
+
+    line = {
+        "metric": PATHS["bss"]["metric"],
+        "value": value,
+        "unit": "proposals/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": warm,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 decisions, df (2 x f32) G",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[name] + "; " + PATHS["bss"]["what"],
+                   "l2": "flushed between timed steps (%d MB write)" % (FLUSH_BYTES >> 20)},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "error_vs_oracle": err,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,6 +760,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.path == "bss":
+        return run_bss(args)
     return run_ours(args)
 
 

@@ -10,7 +10,9 @@ workload is a Hubbard-type model on a periodic L x L honeycomb lattice with time
 ``B_t = E diag(exp(i phi_t))``; ``phi_{t,x}`` are iid normal with variance ``delta*U``.
 
 Seeds: workload ``k`` uses ``seed = 1000 + k``; configuration ``c`` of a batch draws its field
-from ``numpy.random.default_rng([seed, c])``.
+from ``numpy.random.default_rng([seed, c])``.  Proposals for local updates (``bss_proposals``):
+step ``s`` of workload ``k`` draws one array for every configuration of the workload from
+``numpy.random.default_rng([seed, 7, s])``.
 """
 from __future__ import annotations
 
@@ -28,6 +30,7 @@ __all__ = [
     "make_problem",
     "workload",
     "WORKLOADS",
+    "bss_proposals",
 ]
 
 
@@ -182,3 +185,21 @@ def workload(name: str, batch: int | None = None, n_stab: int | None = None,
     seed = 1000 + w["index"]
     return [make_problem(w["L"], w["nt"], w["beta"], w["U"], ns, seed, c, zero_field=zero_field)
             for c in range(first, first + b)]
+
+
+def bss_proposals(name: str, step: int, first: int = 0, count: int | None = None):
+    """Proposals for one local-update call on every site of one time slice, for configurations
+    ``first .. first+count-1`` of a named workload: ``dphi ~ N(0, delta*U)`` (the field's own
+    variance), ``u ~ U(0, 1)`` and ``w = 1`` (no weight factor besides the determinant ratio),
+    each of shape (count, Nx).  The arrays are drawn for the whole workload, so a configuration
+    gets the same proposals whichever shard asks for it."""
+    w = WORKLOADS[name]
+    nx = 2 * w["L"] * w["L"]
+    total = w["batch"]
+    count = total - first if count is None else count
+    rng = np.random.default_rng([1000 + w["index"], 7, int(step)])
+    dphi = rng.normal(0.0, np.sqrt(w["beta"] / w["nt"] * w["U"]), size=(total, nx))
+    u = rng.uniform(size=(total, nx))
+    sl = slice(first, first + count)
+    return (np.ascontiguousarray(dphi[sl]), np.ascontiguousarray(u[sl]),
+            np.ones((count, nx)))

@@ -348,39 +348,65 @@ def observables(problems, operators=None, prec: str = "fp64", with_force: bool =
     return r.logdet.clone(), r.nferm.clone(), r.R, r.F
 
 
+class BssSlices:
+    """A prepared local-update call (fd_bss_update, Section 3) over fixed device buffers.
+
+    The table of pointers is built once, so repeated calls -- a sweep over slices, or repeated
+    hits on one slice with new proposals written into the same buffers -- cost one C call each.
+    Per configuration: G (nx, nx) complex128 = G_{t-1} of the current field (updated in place),
+    phi_rows (nx,) float64 = the field of slice t (updated in place), dphi/u/w (nx,) float64,
+    accepted (nx,) int32 (written; allocated when not given).  run() returns the change of log
+    det as a (batch,) complex128 view of a buffer that the next run overwrites."""
+
+    def __init__(self, G: Sequence[torch.Tensor], phi_rows: Sequence[torch.Tensor],
+                 dphi: Sequence[torch.Tensor], u: Sequence[torch.Tensor],
+                 w: Sequence[torch.Tensor], accepted: Optional[Sequence[torch.Tensor]] = None,
+                 ctx: Optional[Context] = None):
+        self.ctx = ctx or default_context()
+        self.n = n = len(G)
+        dev = torch.device("cuda", self.ctx.device)
+        self.arr = (L.fd_bss_slice * max(1, n))()
+        self.accepted = []
+        for c in range(n):
+            nx = G[c].shape[0]
+            if not (G[c].is_cuda and G[c].dtype == torch.complex128 and G[c].is_contiguous()
+                    and tuple(G[c].shape) == (nx, nx)):
+                raise ValueError("G must be contiguous (nx, nx) complex128 CUDA tensors")
+            for t in (phi_rows[c], dphi[c], u[c], w[c]):
+                if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                        and t.numel() == nx):
+                    raise ValueError("phi_rows, dphi, u, w must be contiguous (nx,) float64 CUDA "
+                                     "tensors")
+            a = torch.empty(nx, dtype=torch.int32, device=dev) if accepted is None \
+                else accepted[c]
+            if not (a.is_cuda and a.dtype == torch.int32 and a.is_contiguous()
+                    and a.numel() == nx):
+                raise ValueError("accepted must be contiguous (nx,) int32 CUDA tensors")
+            self.accepted.append(a)
+            self.arr[c].nx, self.arr[c].reserved = nx, 0
+            self.arr[c].G, self.arr[c].phi_row = G[c].data_ptr(), phi_rows[c].data_ptr()
+            self.arr[c].dphi, self.arr[c].u = dphi[c].data_ptr(), u[c].data_ptr()
+            self.arr[c].w, self.arr[c].accepted = w[c].data_ptr(), a.data_ptr()
+        # the tensors stay referenced for as long as the table points at them
+        self._keep = (list(G), list(phi_rows), list(dphi), list(u), list(w))
+        self.out = torch.empty((max(1, n), 2), dtype=torch.float64, device=dev)
+
+    def run(self, stream=None) -> torch.Tensor:
+        self.ctx.check(self.ctx.lib.fd_bss_update(self.ctx.h, self.n, self.arr,
+                                                  ctypes.c_void_p(self.out.data_ptr()),
+                                                  _stream_ptr(stream)))
+        return torch.view_as_complex(self.out)[:self.n]
+
+
 def bss_update(G: Sequence[torch.Tensor], phi_rows: Sequence[torch.Tensor],
                dphi: Sequence[torch.Tensor], u: Sequence[torch.Tensor],
                w: Sequence[torch.Tensor], ctx: Optional[Context] = None, stream=None):
-    """Local (BSS) updates at one time slice for a batch (Section 3; fd_bss_update).
+    """Local (BSS) updates at one time slice for a batch (Section 3; fd_bss_update), one call.
 
-    Per configuration: G (nx, nx) complex128 = G_{t-1} of the current field (updated in place),
-    phi_rows (nx,) float64 = the field of slice t (updated in place), dphi/u/w (nx,) float64.
-    Returns (dlogdet (batch,) complex128: change of log det, [accepted (nx,) int32])."""
-    ctx = ctx or default_context()
-    n = len(G)
-    dev = torch.device("cuda", ctx.device)
-    arr = (L.fd_bss_slice * max(1, n))()
-    acc = []
-    for c in range(n):
-        nx = G[c].shape[0]
-        if not (G[c].is_cuda and G[c].dtype == torch.complex128 and G[c].is_contiguous()
-                and tuple(G[c].shape) == (nx, nx)):
-            raise ValueError("G must be contiguous (nx, nx) complex128 CUDA tensors")
-        for t in (phi_rows[c], dphi[c], u[c], w[c]):
-            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
-                    and t.numel() == nx):
-                raise ValueError("phi_rows, dphi, u, w must be contiguous (nx,) float64 CUDA "
-                                 "tensors")
-        a = torch.empty(nx, dtype=torch.int32, device=dev)
-        acc.append(a)
-        arr[c].nx, arr[c].reserved = nx, 0
-        arr[c].G, arr[c].phi_row = G[c].data_ptr(), phi_rows[c].data_ptr()
-        arr[c].dphi, arr[c].u, arr[c].w = dphi[c].data_ptr(), u[c].data_ptr(), w[c].data_ptr()
-        arr[c].accepted = a.data_ptr()
-    out = torch.empty((max(1, n), 2), dtype=torch.float64, device=dev)
-    ctx.check(ctx.lib.fd_bss_update(ctx.h, n, arr, ctypes.c_void_p(out.data_ptr()),
-                                    _stream_ptr(stream)))
-    return torch.view_as_complex(out)[:n], acc
+    Arguments as for BssSlices.  Returns (dlogdet (batch,) complex128: change of log det,
+    [accepted (nx,) int32])."""
+    s = BssSlices(G, phi_rows, dphi, u, w, ctx=ctx)
+    return s.run(stream).clone(), s.accepted
 
 
 class FermionLogDet(torch.autograd.Function):

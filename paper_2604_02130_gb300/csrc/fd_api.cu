@@ -1022,8 +1022,18 @@ int fd_bss_update(fd_ctx* ctx, int batch, const fd_bss_slice* slices, double* dl
   FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_bss, h.data(), sizeof(fd::BssSlice) * batch,
                                cudaMemcpyHostToDevice, stream));
   const int grid = std::min(batch, ctx->num_sms * 8);
+  if (ctx->timing) {
+    while (ctx->ev.size() < 2) {
+      cudaEvent_t ev;
+      FD_CUDA(ctx, cudaEventCreate(&ev));
+      ctx->ev.push_back(ev);
+    }
+    ctx->ev_used = 2;
+    FD_CUDA(ctx, cudaEventRecord(ctx->ev[0], stream));
+  }
   cudaError_t e = fd::launch_bss(ctx->d_bss, batch, maxn, dlogdet, grid, stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+  if (ctx->timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[1], stream));
   ctx->last_launches = 1;
   return FD_OK;
 }

@@ -24,11 +24,12 @@ namespace fd {
 
 namespace {
 
-constexpr int kBssDfMax = 110;  // 16 nx^2 + 84 nx bytes of shared memory <= 202 KB
+constexpr int kBssDfMax = 110;  // 16 nx^2 + 100 nx bytes of shared memory <= 205 KB
 
 // Per-CTA shared memory (dynamic), sized for the largest nx of the launch.
 struct BssSmem {
   df::c4* Gs;     // nx*nx df G (only when the df path is available)
+  df::c4* Dg;     // the diagonal of Gs, kept by the deciding warp
   double2* a;     // staged a_i (df c4 or FP64 double2, 16 bytes each)
   double2* b;     // staged b_j
   double2* dl;    // delta_x
@@ -43,6 +44,8 @@ __device__ __forceinline__ BssSmem bss_smem(char* base, int maxn, bool df_path) 
   size_t off = 0;
   s.Gs = (df::c4*)base;
   if (df_path) off += (size_t)maxn * maxn * sizeof(df::c4);
+  s.Dg = (df::c4*)(base + off);
+  off += (size_t)maxn * 16;
   s.a = (double2*)(base + off);
   off += (size_t)maxn * 16;
   s.b = (double2*)(base + off);
@@ -59,7 +62,7 @@ __device__ __forceinline__ BssSmem bss_smem(char* base, int maxn, bool df_path) 
   return s;
 }
 
-// The Metropolis decision and delta / r for site x from G_xx (thread 0 only).
+// The Metropolis decision and delta / r for site x from G_xx (one thread).
 __device__ __forceinline__ bool bss_decide(const BssSmem& s, int x, double gre, double gim,
                                            cplx& f) {
   const double2 d = s.dl[x];
@@ -84,14 +87,33 @@ __device__ __forceinline__ bool bss_decide(const BssSmem& s, int x, double gre, 
   return acc;
 }
 
+// df path: decide sites y, y+1, ... until one is accepted (its delta / r goes to *f); returns
+// that site or n.  Rejected sites change nothing, so they need no barrier.
+__device__ __forceinline__ int bss_next_df(const BssSmem& s, int y, int n, df::c4* f) {
+  for (; y < n; ++y) {
+    const df::c4 g = s.Dg[y];
+    cplx fz;
+    if (bss_decide(s, y, df::join(g.x, g.y), df::join(g.z, g.w), fz)) {
+      *f = df::csplit(fz.re, fz.im);
+      return y;
+    }
+  }
+  return n;
+}
+
 }  // namespace
 
+// One CTA per configuration (grid-stride over the batch).  In the df path warp 0 decides while
+// the other warps update: after the staging of accepted site x, warp 0 applies the same rank-1
+// update to its own copy of the diagonal (bitwise the values the other warps write into Gs) and
+// decides x+1, x+2, ... until the next acceptance, overlapped with the nx^2 update.
 __global__ void __launch_bounds__(512) k_bss(const BssSlice* __restrict__ slices, int batch,
                                               int maxn, int df_path, double* dlogdet) {
   extern __shared__ __align__(16) char smem_raw[];
   __shared__ df::c4 fdf;
   __shared__ double2 f64;
-  __shared__ int accept[2];  // double-buffered: site x uses accept[x & 1]
+  __shared__ int accept[2];  // FP64 path, double-buffered: site x uses accept[x & 1]
+  __shared__ int next;       // df path: the next accepted site (n: none)
   const BssSmem s = bss_smem(smem_raw, maxn, df_path != 0);
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int c = blockIdx.x; c < batch; c += gridDim.x) {
@@ -117,38 +139,25 @@ __global__ void __launch_bounds__(512) k_bss(const BssSlice* __restrict__ slices
         big |= (mx >= (uint64_t)(1023 + 100) << 52) | (my >= (uint64_t)(1023 + 100) << 52);
         s.Gs[e] = df::csplit(g.x, g.y);
       }
+      for (int i = tid; i < n; i += bd) {
+        const double2 g = q.G[(size_t)i * n + i];
+        s.Dg[i] = df::csplit(g.x, g.y);
+      }
     }
     const bool use_df = df_path && !__syncthreads_or(big);
-    // thread layout of the rank-1 update in the df path: column j, rows i0, i0 + rpp, ...
-    const int rpp = n <= bd ? bd / n : 1;
-    const int j = tid % n, i0 = tid / n;
-    for (int x = 0; x < n; ++x) {
-      if (tid == 0) {
-        double gre, gim;
-        if (use_df) {
-          const df::c4 g = s.Gs[x * n + x];
-          gre = df::join(g.x, g.y);
-          gim = df::join(g.z, g.w);
-        } else {
-          const double2 g = q.G[(size_t)x * n + x];
-          gre = g.x;
-          gim = g.y;
-        }
-        cplx f;
-        const bool a = bss_decide(s, x, gre, gim, f);
-        if (a) {
-          if (use_df) fdf = df::csplit(f.re, f.im);
-          else f64 = make_double2(f.re, f.im);
-        }
-        accept[x & 1] = a;
-      }
+    if (use_df) {
+      // updaters: threads 32.. ; thread layout column j, rows i0, i0 + rpp, ...
+      const int u = tid - 32, rpp = (bd - 32) / n;
+      const int j = u >= 0 ? u % n : 0, i0 = u >= 0 ? u / n : rpp;
+      if (tid == 0) next = bss_next_df(s, 0, n, &fdf);
       __syncthreads();
-      if (!accept[x & 1]) continue;  // uniform: every thread reads the same flag
-      if (use_df) {
-        df::c4* A = (df::c4*)s.a;
-        df::c4* B = (df::c4*)s.b;
+      df::c4* A = (df::c4*)s.a;
+      df::c4* B = (df::c4*)s.b;
+      const df::c4 zero = {0.f, 0.f, 0.f, 0.f};
+      for (;;) {
+        const int x = next;
+        if (x >= n) break;
         const df::c4 f = fdf;
-        const df::c4 zero = {0.f, 0.f, 0.f, 0.f};
         for (int i = tid; i < n; i += bd) {
           df::c4 g = s.Gs[i * n + x];  // G_ix - delta_ix, then a_i = -(delta / r)(G_ix - delta_ix)
           if (i == x) g = df::add_re(g, -1.f);
@@ -156,11 +165,27 @@ __global__ void __launch_bounds__(512) k_bss(const BssSlice* __restrict__ slices
           B[i] = s.Gs[x * n + i];
         }
         __syncthreads();
-        if (i0 < rpp) {
+        if (tid < 32) {
+          for (int i = tid; i < n; i += 32) s.Dg[i] = df::cms(s.Dg[i], A[i], B[i]);
+          __syncwarp();
+          if (tid == 0) next = bss_next_df(s, x + 1, n, &fdf);
+        } else if (i0 < rpp) {
           const df::c4 bj = B[j];
           for (int i = i0; i < n; i += rpp) s.Gs[i * n + j] = df::cms(s.Gs[i * n + j], A[i], bj);
         }
-      } else {
+        __syncthreads();
+      }
+    } else {
+      for (int x = 0; x < n; ++x) {
+        if (tid == 0) {
+          const double2 g = q.G[(size_t)x * n + x];
+          cplx f;
+          const bool a = bss_decide(s, x, g.x, g.y, f);
+          if (a) f64 = make_double2(f.re, f.im);
+          accept[x & 1] = a;
+        }
+        __syncthreads();
+        if (!accept[x & 1]) continue;  // uniform: every thread reads the same flag
         const cplx f = cx(f64.x, f64.y);
         for (int i = tid; i < n; i += bd) {
           const double2 g = q.G[(size_t)i * n + x];
@@ -177,22 +202,31 @@ __global__ void __launch_bounds__(512) k_bss(const BssSlice* __restrict__ slices
           q.G[e] = make_double2(fma(-a.x, b.x, fma(a.y, b.y, g.x)),
                                 fma(-a.x, b.y, fma(-a.y, b.x, g.y)));
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
-    // outputs: field row, decisions, G back to FP64, log r_x of the accepted sites
-    for (int x = tid; x < n; x += bd) {
+    // outputs: field row, decisions, G back to FP64; log|r_x| (k < n) and arg r_x (k >= n) of
+    // the accepted sites on separate threads
+    for (int k = tid; k < 2 * n; k += bd) {
+      const int x = k < n ? k : k - n;
       const int a = s.acc[x];
-      q.acc[x] = a;
-      double lr = 0.0, la = 0.0;
+      double val = 0.0;
       if (a) {
-        q.phi[x] += q.dphi[x];
         const double2 r = s.rs[x];
-        lr = log(hypot(r.x, r.y));
-        la = atan2(r.y, r.x);
+        if (k < n) {
+          const double t = fma(r.x, r.x, r.y * r.y);
+          val = (t > 1e-280 && t < 1e280) ? 0.5 * log(t) : log(hypot(r.x, r.y));
+        } else {
+          val = atan2(r.y, r.x);
+        }
       }
-      s.v[x] = lr;
-      s.vv[x] = la;
+      if (k < n) {
+        q.acc[x] = a;
+        if (a) q.phi[x] += q.dphi[x];
+        s.v[x] = val;
+      } else {
+        s.vv[x] = val;
+      }
     }
     if (use_df) {
       for (int e = tid; e < n * n; e += bd) {
@@ -224,7 +258,7 @@ __global__ void __launch_bounds__(512) k_bss(const BssSlice* __restrict__ slices
 }
 
 size_t bss_smem_bytes(int maxn, bool df_path) {
-  return (df_path ? (size_t)maxn * maxn * sizeof(df::c4) : 0) + (size_t)maxn * 84;
+  return (df_path ? (size_t)maxn * maxn * sizeof(df::c4) : 0) + (size_t)maxn * 100;
 }
 
 int bss_threads(int maxn) { return maxn <= 24 ? 128 : maxn <= 48 ? 256 : 512; }
