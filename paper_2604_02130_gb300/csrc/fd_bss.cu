@@ -62,7 +62,7 @@ __device__ __forceinline__ BssSmem bss_smem(char* base, int maxn, bool df_path) 
   return s;
 }
 
-// The Metropolis decision and delta / r for site x from G_xx (one thread).
+// FP64 path: the Metropolis decision and delta / r for site x from G_xx (one thread).
 __device__ __forceinline__ bool bss_decide(const BssSmem& s, int x, double gre, double gim,
                                            cplx& f) {
   const double2 d = s.dl[x];
@@ -87,14 +87,46 @@ __device__ __forceinline__ bool bss_decide(const BssSmem& s, int x, double gre, 
   return acc;
 }
 
+// df path: the same decision in double-float arithmetic on the FP32 pipes (the FP64 unit would
+// make this serial chain the longest part of a site), from the deciding warp's diagonal.  Where
+// |r|^2 or (u / w)^2 leaves [2^-100, 2^100] it falls back to FP64 on the joined values.
+__device__ __forceinline__ bool bss_decide_df(const BssSmem& s, int x, df::c4& f) {
+  const df::c4 d = ((const df::c4*)s.dl)[x];
+  const df::c4 one = {1.f, 0.f, 0.f, 0.f};
+  const df::c4 r = df::cms(one, d, df::add_re(s.Dg[x], -1.f));  // 1 + delta (1 - G_xx)
+  float th, tl;
+  df::abs2(r, th, tl);
+  const float2 vv = ((const float2*)s.vv)[x];
+  bool acc;
+  if (vv.x >= 0.f && th > 0x1p-100f && th < 0x1p100f) {
+    acc = df::greater(th, tl, vv.x, vv.y);  // (u / w)^2 < |r|^2
+    if (acc) {
+      float yh, yl;
+      df::recip(th, tl, yh, yl);
+      const df::c4 mconj = {-r.x, -r.y, r.z, r.w};
+      const df::c4 zero = {0.f, 0.f, 0.f, 0.f};
+      f = df::scale(df::cms(zero, d, mconj), yh, yl);  // delta conj(r) / |r|^2
+    }
+  } else {
+    const double rre = df::join(r.x, r.y), rim = df::join(r.z, r.w);
+    acc = s.v[x] < sqrt(fma(rre, rre, rim * rim));
+    if (acc) {
+      const cplx fz = cdiv(cx(df::join(d.x, d.y), df::join(d.z, d.w)), cx(rre, rim));
+      f = df::csplit(fz.re, fz.im);
+    }
+  }
+  if (acc) ((df::c4*)s.rs)[x] = r;
+  s.acc[x] = acc;
+  return acc;
+}
+
 // df path: decide sites y, y+1, ... until one is accepted (its delta / r goes to *f); returns
 // that site or n.  Rejected sites change nothing, so they need no barrier.
 __device__ __forceinline__ int bss_next_df(const BssSmem& s, int y, int n, df::c4* f) {
   for (; y < n; ++y) {
-    const df::c4 g = s.Dg[y];
-    cplx fz;
-    if (bss_decide(s, y, df::join(g.x, g.y), df::join(g.z, g.w), fz)) {
-      *f = df::csplit(fz.re, fz.im);
+    df::c4 fz;
+    if (bss_decide_df(s, y, fz)) {
+      *f = fz;
       return y;
     }
   }
@@ -104,10 +136,10 @@ __device__ __forceinline__ int bss_next_df(const BssSmem& s, int y, int n, df::c
 }  // namespace
 
 // One CTA per configuration (grid-stride over the batch).  In the df path warp 0 decides while
-// the other warps update: after the staging of accepted site x, warp 0 applies the same rank-1
-// update to its own copy of the diagonal (bitwise the values the other warps write into Gs) and
-// decides x+1, x+2, ... until the next acceptance, overlapped with the nx^2 update.
-__global__ void __launch_bounds__(512) k_bss(const BssSlice* __restrict__ slices, int batch,
+// warps 1.. update: after the staging of accepted site x, warp 0 applies the same rank-1 update
+// to its own copy of the diagonal (bitwise the values the other warps write into Gs) and decides
+// x+1, x+2, ... until the next acceptance, overlapped with the nx^2 update.
+__global__ void __launch_bounds__(544) k_bss(const BssSlice* __restrict__ slices, int batch,
                                               int maxn, int df_path, double* dlogdet) {
   extern __shared__ __align__(16) char smem_raw[];
   __shared__ df::c4 fdf;
@@ -119,16 +151,6 @@ __global__ void __launch_bounds__(512) k_bss(const BssSlice* __restrict__ slices
   for (int c = blockIdx.x; c < batch; c += gridDim.x) {
     const BssSlice q = slices[c];
     const int n = q.nx;
-    for (int x = tid; x < n; x += bd) {
-      double sn, cs;
-      sincos(q.dphi[x], &sn, &cs);
-      s.dl[x] = make_double2(cs - 1.0, sn);
-      const double v = q.u[x] / q.w[x];
-      const double vv = v * v;
-      s.v[x] = v;
-      s.vv[x] = (vv >= 1e-280 && vv <= 1e280) ? vv : -1.0;
-      s.acc[x] = 0;
-    }
     // df path: G -> shared memory as df pairs, unless an entry is beyond 2^100 (or not finite)
     int big = 0;
     if (df_path) {
@@ -139,12 +161,27 @@ __global__ void __launch_bounds__(512) k_bss(const BssSlice* __restrict__ slices
         big |= (mx >= (uint64_t)(1023 + 100) << 52) | (my >= (uint64_t)(1023 + 100) << 52);
         s.Gs[e] = df::csplit(g.x, g.y);
       }
-      for (int i = tid; i < n; i += bd) {
-        const double2 g = q.G[(size_t)i * n + i];
-        s.Dg[i] = df::csplit(g.x, g.y);
-      }
     }
     const bool use_df = df_path && !__syncthreads_or(big);
+    for (int x = tid; x < n; x += bd) {
+      double sn, cs;
+      sincos(q.dphi[x], &sn, &cs);
+      const double v = q.u[x] / q.w[x];
+      const double vv = v * v;
+      s.v[x] = v;
+      s.acc[x] = 0;
+      if (use_df) {
+        ((df::c4*)s.dl)[x] = df::csplit(cs - 1.0, sn);
+        float2 p = make_float2(-1.f, 0.f);
+        if (vv >= 0x1p-100 && vv <= 0x1p100) df::split(vv, p.x, p.y);
+        ((float2*)s.vv)[x] = p;
+        s.Dg[x] = s.Gs[x * n + x];
+      } else {
+        s.dl[x] = make_double2(cs - 1.0, sn);
+        s.vv[x] = (vv >= 1e-280 && vv <= 1e280) ? vv : -1.0;
+      }
+    }
+    __syncthreads();
     if (use_df) {
       // updaters: threads 32.. ; thread layout column j, rows i0, i0 + rpp, ...
       const int u = tid - 32, rpp = (bd - 32) / n;
@@ -212,12 +249,20 @@ __global__ void __launch_bounds__(512) k_bss(const BssSlice* __restrict__ slices
       const int a = s.acc[x];
       double val = 0.0;
       if (a) {
-        const double2 r = s.rs[x];
-        if (k < n) {
-          const double t = fma(r.x, r.x, r.y * r.y);
-          val = (t > 1e-280 && t < 1e280) ? 0.5 * log(t) : log(hypot(r.x, r.y));
+        double rre, rim;
+        if (use_df) {
+          const df::c4 r = ((const df::c4*)s.rs)[x];
+          rre = df::join(r.x, r.y);
+          rim = df::join(r.z, r.w);
         } else {
-          val = atan2(r.y, r.x);
+          rre = s.rs[x].x;
+          rim = s.rs[x].y;
+        }
+        if (k < n) {
+          const double t = fma(rre, rre, rim * rim);
+          val = (t > 1e-280 && t < 1e280) ? 0.5 * log(t) : log(hypot(rre, rim));
+        } else {
+          val = atan2(rim, rre);
         }
       }
       if (k < n) {
@@ -261,7 +306,9 @@ size_t bss_smem_bytes(int maxn, bool df_path) {
   return (df_path ? (size_t)maxn * maxn * sizeof(df::c4) : 0) + (size_t)maxn * 100;
 }
 
-int bss_threads(int maxn) { return maxn <= 24 ? 128 : maxn <= 48 ? 256 : 512; }
+// df path: 4, 8 or 16 updating warps (a multiple of the SM's four sub-partitions) and the
+// deciding warp; the FP64 path uses them all alike.
+int bss_threads(int maxn) { return 32 + (maxn <= 24 ? 128 : maxn <= 48 ? 256 : 512); }
 
 cudaError_t launch_bss(const BssSlice* slices, int batch, int maxn, double* dlogdet, int grid,
                        cudaStream_t stream) {

@@ -194,6 +194,49 @@ FD_HD c4 cms(c4 g, c4 a, c4 b) {
   return r;
 }
 
+// |r|^2 of a complex df number, as a normalised df pair.
+FD_HD void abs2(c4 r, float& th, float& tl) {
+  float p1, e1, p2, e2, s, e;
+  prod(r.x, r.y, r.x, r.y, p1, e1);
+  prod(r.z, r.w, r.z, r.w, p2, e2);
+  two_sum(p1, p2, s, e);
+  e = add(e, add(e1, e2));
+  renorm(s, e, th, tl);
+}
+
+// 1 / t for a df t > 0 (normal range): the FP32 reciprocal refined by one Newton step in df,
+// y = y0 + y0 (1 - t y0); 1 - t y0 is exact in FP32 because t y0 is within 2^-22 of 1.
+FD_HD void recip(float th, float tl, float& yh, float& yl) {
+#ifdef __CUDA_ARCH__
+  const float y0 = __frcp_rn(th);
+#else
+  const float y0 = 1.0f / th;
+#endif
+  float p, pe;
+  prod(th, tl, y0, 0.f, p, pe);
+  const float e = sub(sub(1.f, p), pe);
+  renorm(y0, mul(y0, e), yh, yl);
+}
+
+// a > b for normalised df pairs (the sign of the df difference).
+FD_HD bool greater(float ah, float al, float bh, float bl) {
+  float s, e;
+  two_sum(ah, -bh, s, e);
+  e = add(e, sub(al, bl));
+  return add(s, e) > 0.f;
+}
+
+// a * y for a complex df a and a real df y.
+FD_HD c4 scale(c4 a, float yh, float yl) {
+  c4 r;
+  float p, e;
+  prod(a.x, a.y, yh, yl, p, e);
+  renorm(p, e, r.x, r.y);
+  prod(a.z, a.w, yh, yl, p, e);
+  renorm(p, e, r.z, r.w);
+  return r;
+}
+
 // g + c with c a plain FP32 value added to the real part.
 FD_HD c4 add_re(c4 g, float c) {
   float s, t;

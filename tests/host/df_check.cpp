@@ -5,6 +5,10 @@
 //   w f               -> d               FP32 -> FP64 on the bit pattern
 //   m g4 a4 b4        -> r4              g - a * b for complex pairs (re hi, re lo, im hi, im lo)
 //   r g4 c            -> r4              g + c on the real part
+//   a r4              -> th tl           |r|^2
+//   q th tl           -> yh yl           1 / t
+//   g ah al bh bl     -> 0 or 1          a > b
+//   c a4 yh yl        -> r4              a * y (complex times real)
 // Compile without FP contraction (-ffp-contract=off) so that the FP32 steps round as written.
 #include <cstdio>
 #include <cstdlib>
@@ -55,6 +59,31 @@ int main() {
       case 'r': {
         const c4 g = read4(&p);
         print4(fd::df::add_re(g, (float)strtod(p, &p)));
+        break;
+      }
+      case 'a': {
+        float th, tl;
+        fd::df::abs2(read4(&p), th, tl);
+        printf("%a %a\n", (double)th, (double)tl);
+        break;
+      }
+      case 'q': {
+        const float th = (float)strtod(p, &p), tl = (float)strtod(p, &p);
+        float yh, yl;
+        fd::df::recip(th, tl, yh, yl);
+        printf("%a %a\n", (double)yh, (double)yl);
+        break;
+      }
+      case 'g': {
+        const float ah = (float)strtod(p, &p), al = (float)strtod(p, &p);
+        const float bh = (float)strtod(p, &p), bl = (float)strtod(p, &p);
+        printf("%d\n", fd::df::greater(ah, al, bh, bl) ? 1 : 0);
+        break;
+      }
+      case 'c': {
+        const c4 a = read4(&p);
+        const float yh = (float)strtod(p, &p), yl = (float)strtod(p, &p);
+        print4(fd::df::scale(a, yh, yl));
         break;
       }
       default:

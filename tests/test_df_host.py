@@ -7,7 +7,10 @@ values are exact rational arithmetic (fractions.Fraction) on the same inputs:
 * widen: exact for normal FP32 values, subnormals flushed to zero;
 * cms (g - a b for complex pairs): error below 2^-43 of |g| + |a||b| per component, including
   cancellations;
-* add_re: the real part gains c with the same bound.
+* add_re: the real part gains c with the same bound;
+* abs2, recip, scale (the decision of a local update in double-float): relative errors below
+  2^-44; greater agrees with the exact comparison wherever the operands differ by more than
+  2^-44 of their size, including pairs that differ only in the low part.
 A planted mistake (the conjugate product) is rejected by the same bound.
 """
 import os
@@ -149,3 +152,48 @@ def test_add_real(df_exe):
         size = abs(Fraction(g[0])) + abs(Fraction(c))
         assert abs(Fraction(r[0]) + Fraction(r[1]) - want) <= Fraction(2) ** -45 * size
         assert r[2] == g[2] and r[3] == g[3]
+
+
+def _fr(h, l):
+    return Fraction(h) + Fraction(l)
+
+
+def test_abs2_recip_scale_greater(df_exe):
+    rng = np.random.default_rng(8)
+    rs = [[*_pair(rng, s), *_pair(rng, s)] for s in np.exp(rng.uniform(-20, 20, size=200))]
+    res = _run(df_exe, ["a %s" % _fmt(r) for r in rs])
+    for r, (th, tl) in zip(rs, res):
+        want = _fr(r[0], r[1]) ** 2 + _fr(r[2], r[3]) ** 2
+        assert abs(_fr(th, tl) - want) <= Fraction(2) ** -44 * want
+    ts = [_pair(rng, s) for s in np.exp(rng.uniform(-40, 40, size=200))]
+    ts = [(abs(h), abs(l) if h >= 0 else -abs(l)) for h, l in ts]
+    res = _run(df_exe, ["q %s %s" % (h.hex(), l.hex()) for h, l in ts])
+    for (h, l), (yh, yl) in zip(ts, res):
+        assert abs(_fr(yh, yl) * _fr(h, l) - 1) <= Fraction(2) ** -44
+    ys = [_pair(rng, s) for s in np.exp(rng.uniform(-5, 5, size=100))]
+    res = _run(df_exe, ["c %s %s %s" % (_fmt(a), y[0].hex(), y[1].hex()) for a, y in zip(rs, ys)])
+    for a, y, r in zip(rs, ys, res):
+        for k in (0, 2):
+            want = _fr(a[k], a[k + 1]) * _fr(*y)
+            assert abs(_fr(r[k], r[k + 1]) - want) <= Fraction(2) ** -44 * abs(want)
+    pairs = []
+    for _ in range(300):
+        a = _pair(rng, 1.0)
+        kind = rng.integers(3)
+        if kind == 0:
+            b = _pair(rng, 1.0)
+        elif kind == 1:  # same high part, different low parts
+            b = (a[0], _f32(a[1] * (1 + rng.normal())))
+        else:  # nearby values
+            d = a[0] + a[1] + rng.normal() * 1e-12 * abs(a[0])
+            b = (_f32(d), _f32(d - _f32(d)))
+        pairs.append((a, b))
+    res = _run(df_exe, ["g %s %s %s %s" % (a[0].hex(), a[1].hex(), b[0].hex(), b[1].hex())
+                        for a, b in pairs])
+    checked = 0
+    for (a, b), (g,) in zip(pairs, res):
+        fa, fb = _fr(*a), _fr(*b)
+        if abs(fa - fb) > Fraction(2) ** -44 * max(abs(fa), abs(fb)):
+            assert bool(g) == (fa > fb)
+            checked += 1
+    assert checked > 200
