@@ -194,21 +194,32 @@ __global__ void __launch_bounds__(544) k_bss(const BssSlice* __restrict__ slices
       for (;;) {
         const int x = next;
         if (x >= n) break;
-        const df::c4 f = fdf;
-        for (int i = tid; i < n; i += bd) {
-          df::c4 g = s.Gs[i * n + x];  // G_ix - delta_ix, then a_i = -(delta / r)(G_ix - delta_ix)
-          if (i == x) g = df::add_re(g, -1.f);
-          A[i] = df::cms(zero, f, g);
-          B[i] = s.Gs[x * n + i];
+        if (u >= 0) {  // staging on the updating warps (the deciding warp's sub-partition is
+                       // the busiest)
+          const df::c4 f = fdf;
+          for (int i = u; i < n; i += bd - 32) {
+            df::c4 g = s.Gs[i * n + x];  // G_ix - delta_ix; a_i = -(delta / r)(G_ix - delta_ix)
+            if (i == x) g = df::add_re(g, -1.f);
+            A[i] = df::cms(zero, f, g);
+            B[i] = s.Gs[x * n + i];
+          }
         }
         __syncthreads();
         if (tid < 32) {
-          for (int i = tid; i < n; i += 32) s.Dg[i] = df::cms(s.Dg[i], A[i], B[i]);
+          // only the sites still to be decided need their diagonal entry
+          for (int i = x + 1 + tid; i < n; i += 32) s.Dg[i] = df::cms(s.Dg[i], A[i], B[i]);
           __syncwarp();
           if (tid == 0) next = bss_next_df(s, x + 1, n, &fdf);
         } else if (i0 < rpp) {
           const df::c4 bj = B[j];
-          for (int i = i0; i < n; i += rpp) s.Gs[i * n + j] = df::cms(s.Gs[i * n + j], A[i], bj);
+          int i = i0;
+          for (; i + rpp < n; i += 2 * rpp) {  // two rows per trip, loads first
+            const int e0 = i * n + j, e1 = e0 + rpp * n;
+            const df::c4 g0 = s.Gs[e0], a0 = A[i], g1 = s.Gs[e1], a1 = A[i + rpp];
+            s.Gs[e0] = df::cms(g0, a0, bj);
+            s.Gs[e1] = df::cms(g1, a1, bj);
+          }
+          if (i < n) s.Gs[i * n + j] = df::cms(s.Gs[i * n + j], A[i], bj);
         }
         __syncthreads();
       }
