@@ -160,11 +160,12 @@ int fd_green_tau(fd_ctx* ctx, int batch, const fd_problem* probs, double* logdet
  * The ratio comes from the matrix determinant lemma, r_x = 1 + (e^{i dphi_x} - 1)(1 - G_xx), and
  * an accepted proposal updates G by Sherman-Morrison (O(nx^2); a rejected one costs O(1)).
  * dlogdet: device, 2*batch float64: sum of log r_x over the accepted sites (re, im wrapped to
- * (-pi, pi]), i.e. the change of log det.  Ratios, decisions and dlogdet are FP64; for the
- * rank-1 updates a launch whose largest nx is <= 110 holds G in shared memory as pairs of FP32
- * values (about 46 significant bits, relative error ~1e-14 per update) and converts it back to
- * FP64 on return; larger nx, or a G with an entry of magnitude >= 2^100, is updated in FP64 in
- * place.  Asynchronous on `stream`; not available through fd_graph_create.  Wrapping G to the
+ * (-pi, pi]), i.e. the change of log det.  A launch whose largest nx is <= 110 holds G in
+ * shared memory as pairs of FP32 values (about 46 significant bits, relative error ~1e-14 per
+ * update) and takes the ratios and decisions in the same pair arithmetic (FP64 where |r|^2 or
+ * (u/w)^2 leaves [2^-100, 2^100]), converting G back to FP64 on return; larger nx, or a G with an
+ * entry of magnitude >= 2^100, runs every step in FP64 with G updated in place.  dlogdet is
+ * summed in FP64.  Asynchronous on `stream`; not available through fd_graph_create.  Wrapping G to the
  * next slice and re-stabilising it every n_stab slices (fd_green / fd_force) are the caller's
  * part of a sweep. */
 typedef struct {

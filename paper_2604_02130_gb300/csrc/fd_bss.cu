@@ -9,13 +9,14 @@
 // Accepted iff u_x < |r| w_x.  A rejected proposal costs O(1), an accepted one O(nx^2) -- the
 // complexity the paper states for BSS updates.  One CTA per configuration.
 //
-// Precision.  Ratios, decisions, delta / r and the change of log det are FP64.  The nx^2 rank-1
-// updates are the bulk of the work, and on this GPU an SM retires FP64 instructions some seventy
-// times slower than FP32 ones, so for nx <= kBssDfMax the slice keeps G in shared memory as
-// double-float pairs (fd_df.cuh, ~46 significant bits) and updates it with FP32 instructions,
-// converting from and back to FP64 once per call.  Larger nx (or a G with entries beyond
-// 2^100, outside the FP32 exponent range the pairs need) runs the same steps in FP64 on G in
-// place in global memory.
+// Precision.  The nx^2 rank-1 updates are the bulk of the work, and on this GPU an SM retires
+// FP64 instructions some seventy times slower than FP32 ones, so for nx <= kBssDfMax the slice
+// keeps G in shared memory as double-float pairs (fd_df.cuh, ~46 significant bits) and updates
+// it with FP32 instructions, converting from and back to FP64 once per call; the ratios,
+// decisions and delta / r use the same pair arithmetic (FP64 where |r|^2 or (u/w)^2 leaves
+// [2^-100, 2^100]).  Larger nx (or a G with entries beyond 2^100, outside the FP32 exponent
+// range the pairs need) runs every step in FP64 on G in place in global memory.  The change of
+// log det is summed in FP64.
 #include "fd_common.cuh"
 #include "fd_df.cuh"
 #include "fd_kernels.h"
