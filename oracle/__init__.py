@@ -26,14 +26,16 @@ Modules:
                       steps 7-9).
     observables    -- fermion number and single-time response traces tr(O G_r) (Section 4.1).
     bss            -- local (BSS) updates of the field at one time slice (Section 3).
+    product_form   -- the slice exponential as a product of n linear factors in the sparse
+                      hopping matrix (Section 8, the intermediate-volume variant).
 
 Parity pins (tests/test_oracle_*.py) tie every module to something other than itself.
 """
 from . import (plain, fermion_matrix, stable, naive, free, force, unequal, observables,  # noqa: F401
-               bss)
+               bss, product_form)
 
 __all__ = ["plain", "fermion_matrix", "stable", "naive", "free", "force", "unequal", "observables",
-           "bss", "wrap_phase"]
+           "bss", "product_form", "wrap_phase"]
 
 
 def wrap_phase(z):
