@@ -6,7 +6,7 @@ beta = 8, Nt = 64, U = 3, n_stab = 8.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec 3xtf32|tf32|fp64]
                     [--workload batch18|cold72|force72|tiny8] [--impl ours|reference]
-                    [--path force|gtau|observables|bss]
+                    [--path force|gtau|observables|bss|sparse]
 
 --path picks what one step computes (default `force`, the headline):
   force        log det + G + force
@@ -14,6 +14,9 @@ beta = 8, Nt = 64, U = 3, n_stab = 8.
   observables  log det + fermion number + response traces tr(A G_t) at every slice (Section 4.1)
   bss          local (BSS) updates of time slice 1, every site proposed once (Section 3); the
                unit is site proposals/s, G_0 comes from an untimed FP64 log det/G call
+  sparse       log det + G with the product-form slices of the intermediate-volume variant
+               (Sections 8-9, n = 4 factors of the sparse hopping matrix, FP64), default
+               workload sparse288; the dense FP64 path with the same E = T_4(K) is timed beside it
 
 The headline is the mixed-precision path (slice products on tensor cores, FP64 QR/assembly);
 the plain FP64 path is measured on the same inputs and reported beside it (`fp64_path`).
@@ -48,6 +51,7 @@ WORKLOAD_TEXT = {
     "cold72": "honeycomb L=6 (Nx=72), beta=64, Nt=512, U=3.5, n_stab=16, 64 configs",
     "force72": "honeycomb L=6 (Nx=72), beta=32, Nt=256, U=3, n_stab=8, 32 configs",
     "tiny8": "honeycomb L=2 (Nx=8), beta=2, Nt=16, U=2, n_stab=4, 1 config",
+    "sparse288": "honeycomb L=12 (Nx=288), kappa=1, beta=8, Nt=64, U=3, n_stab=16, 152 configs",
 }
 
 # what one step computes: Batch outputs, metric, and the text appended to the workload
@@ -59,6 +63,9 @@ PATHS = {
     "observables": {"want": "nferm+response",
                     "metric": "configs/s (log det + n + tr(A G_t) for all t)",
                     "what": "log det + fermion number + response traces tr(A G_t), t=0..Nt-1"},
+    "sparse": {"want": None, "metric": "configs/s (log det + G, product-form slices)",
+               "what": "log det + G with every slice applied as prod_{k=1}^{4} (1 + gamma_k K) "
+                       "diag(e^{i phi_t}), K = delta*kappa*A sparse (3 per row), FP64"},
     "bss": {"want": None, "metric": "site proposals/s (local updates at one time slice)",
             "what": "local (BSS) updates of slice 1, every site proposed once per step "
                     "(dphi ~ N(0, delta*U), u ~ U(0,1), w = 1), G_0 from FP64 log det/G"},
@@ -76,6 +83,12 @@ def _oracle_worker(args):
     from oracle import observables, stable, unequal
 
     p = fi.workload(name, batch=1, first=c)[0]
+    if path == "sparse":
+        from oracle import product_form
+
+        t0 = time.perf_counter()
+        ld, G = product_form.logdet_green(p.A, p.delta, p.kappa, 4, p.phi, p.n_stab)
+        return c, ld, {"G": G}, time.perf_counter() - t0
     if path == "bss":  # step 0's proposals from the G_0 of the workload's field
         dphi, u, w = (a[0] for a in fi.bss_proposals(name, 0, first=c, count=1))
         t0 = time.perf_counter()
@@ -744,6 +757,194 @@ def run_bss(args):
     return 0
 
 
+def run_sparse(args):
+    """--path sparse: one step = one fd_green_sparse call (log det + G of the shard's
+    configurations with the product-form slices, n = 4).  The dense FP64 path on the same
+    arithmetic (E = T_4(K) = sum_{j<=4} K^j / j!) is timed beside it.  A step of sparse288 takes
+    about a second, so at most 10 steps are timed (the line reports the number)."""
+    args.steps = max(1, min(args.steps, 10))
+    ws, rank, local = _dist()
+    import numpy as np
+
+    import fd_inputs as fi
+
+    name = args.workload if args.workload != "batch18" else "sparse288"
+    w_batch = 1 if name == "tiny8" else fi.WORKLOADS[name]["batch"]
+    cores = os.cpu_count() or 1
+    pool = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        pool = _pool(cores)  # spawned before the first CUDA call
+    import torch
+
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2604_02130_gb300 import api, shard
+    from paper_2604_02130_gb300.flops import sparse_fwd_flops
+
+    nfac = 4
+    dev = torch.device("cuda", local)
+    mine = shard.shard_range(rank, w_batch)
+    probs = fi.workload(name, batch=w_batch, first=mine.start)
+    p0 = probs[0]
+    nx, nt, ns = p0.nx, p0.nt, p0.n_stab
+    ctx = api.Context(local)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    phi_host = torch.from_numpy(np.stack([p.phi for p in probs])).pin_memory()
+    phi_dev = phi_host.to(dev)
+    col, val = fi.sparse_rows(p0.A)
+    col_d = torch.from_numpy(col).to(dev)
+    val_d = torch.from_numpy(val * (p0.delta * p0.kappa)).to(dev)
+    q = col.shape[1]
+    sp_probs = [(phi_dev[c], ns) for c in range(w_batch)]
+    hops = [(col_d, val_d)] * w_batch
+
+    def sparse_call():
+        return api.green_sparse(sp_probs, hops, nfac=nfac, ctx=ctx)
+
+    for _ in range(max(3, args.warmup)):
+        sparse_call()
+    barrier()
+    assert all(s == 0 for s in ctx.status(w_batch)), "device status not OK"
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.__enter__()
+    try:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            ld_s, G_s = sparse_call()
+            ev[k][1].record(stream)
+        barrier()
+    finally:
+        clk.__exit__()
+    total_ms = shard.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev)
+    value = w_batch * ws * args.steps / (total_ms * 1e-3)
+    ctx.set_timing(True)
+    flush.zero_()
+    sparse_call()
+    k_ms = ctx.last_kernel_ms()[0]
+    ctx.set_timing(False)
+    ld_s, G_s = sparse_call()
+    barrier()
+
+    # end to end: phi from pinned host memory, log det and G read back
+    G_host = torch.empty((w_batch, nx, nx), dtype=torch.complex128).pin_memory()
+    ld_host = torch.empty((w_batch,), dtype=torch.complex128).pin_memory()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        phi_dev.copy_(phi_host, non_blocking=True)
+        ld_e, G_e = sparse_call()
+        ld_host.copy_(ld_e, non_blocking=True)
+        for c in range(w_batch):
+            G_host[c].copy_(G_e[c], non_blocking=True)
+        ev2[k][1].record(stream)
+    barrier()
+    e2e_ms = shard.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2), dev)
+    e2e = {"value": w_batch * ws * args.steps / (e2e_ms * 1e-3), "unit": "configs/s",
+           "h2d_bytes_per_step": phi_host.numel() * 8,
+           "d2h_bytes_per_step": w_batch * (nx * nx + 1) * 16}
+
+    # the dense FP64 path with the same slice matrix E = T_4(K)
+    K = p0.delta * p0.kappa * p0.A.astype(np.float64)
+    E4 = np.eye(nx)
+    term = np.eye(nx)
+    for j in range(1, nfac + 1):
+        term = term @ K / j
+        E4 = E4 + term
+    E4_d = torch.from_numpy(E4).to(dev)
+    dense = api.Batch(ctx, [(E4_d, None, phi_dev[c], ns) for c in range(w_batch)], "green",
+                      "fp64")
+    for _ in range(max(3, args.warmup)):
+        dense.run()
+    barrier()
+    ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev3[k][0].record(stream)
+        dense.run()
+        ev3[k][1].record(stream)
+    barrier()
+    dense_ms = shard.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev3), dev)
+    dense_plan = dense.plan()
+    agree = max(float((dense.logdet_buf[:, 0] - torch.view_as_real(ld_s)[:, 0]).abs().max()),
+                float(max((a - b).abs().max().item() for a, b in zip(dense.G, G_s))))
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
+
+    fl = sparse_fwd_flops(nx, nt, ns, q, nfac)
+    peak_fp64 = ctx.measure_fp64_peak() / 1e3
+    achieved = fl["total"] * w_batch / (k_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+            "frac": achieved / peak_fp64, "traffic": None, "kernel": "k_fwd_fp64",
+            "kernel_ms": k_ms,
+            "what": "FP64 algorithmic work (product-form slices, QRs, assembly) per launch over "
+                    "the launch's CUDA-event duration",
+            "peak_source": "FP64 DFMA probe over all SMs in this run (fd_measure_fp64_peak)",
+            "flops_per_config": fl}
+    cpu = None
+    err = None
+    if pool is not None:
+        sample = list(range(min(w_batch, cores)))
+        res, dt = oracle_sample(pool, name, sample, "sparse")
+        pool.close()
+        cpu = {"value": len(sample) / dt, "unit": "configs/s", "cores": cores, "kind": "oracle",
+               "sample": "%d of the %d configurations, one per process" % (len(sample), w_batch)}
+        ldc = ld_s.cpu().numpy()
+        e = {"logdet_rel": 0.0, "G_abs_over_maxG2": 0.0}
+        for c, ldr, out, _ in res:
+            d = complex(ldc[c]) - ldr
+            e["logdet_rel"] = max(e["logdet_rel"], max(abs(d.real),
+                                  abs(np.angle(np.exp(1j * d.imag)))) / abs(ldr))
+            e["G_abs_over_maxG2"] = max(e["G_abs_over_maxG2"],
+                                        _scaled_err(G_s[c].cpu().numpy(), out["G"]))
+        e["configs_checked"] = len(res)
+        err = {"fp64": e}
+    line = {
+        "metric": PATHS["sparse"]["metric"],
+        "value": value,
+        "unit": "configs/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": max(3, args.warmup),
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[name] + "; " + PATHS["sparse"]["what"],
+                   "l2": "flushed between timed steps (%d MB write)" % (FLUSH_BYTES >> 20)},
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "dense_fp64_same_E": {"value": w_batch * ws * args.steps / (dense_ms * 1e-3),
+                              "unit": "configs/s", "ms_per_step": dense_ms / args.steps,
+                              "plan": dense_plan, "max_abs_difference": agree},
+        "cpu_baseline": cpu,
+        "error_vs_oracle": err,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -762,6 +963,8 @@ def main():
         return run_reference(args)
     if args.path == "bss":
         return run_bss(args)
+    if args.path == "sparse":
+        return run_sparse(args)
     return run_ours(args)
 
 

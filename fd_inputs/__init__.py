@@ -31,6 +31,7 @@ __all__ = [
     "workload",
     "WORKLOADS",
     "bss_proposals",
+    "sparse_rows",
 ]
 
 
@@ -143,12 +144,14 @@ def make_problem(L: int, nt: int, beta: float, U: float, n_stab: int, seed: int,
 #   batch18    : L=3 (Nx=18), beta=8,  Nt=64,  U=3,   n_stab=8,  256 configs
 #   cold72     : L=6 (Nx=72), beta=64, Nt=512, U=3.5, n_stab=16, 64 configs
 #   force72    : L=6 (Nx=72), beta=32, Nt=256, U=3,   n_stab=8,  32 configs
+#   sparse288  : L=12 (Nx=288), beta=8, Nt=64, U=3,  n_stab=16, 152 configs (intermediate volume)
 #   uneven512  : Nx in {8,...,288} x Nt in {32,...,1024}, delta=1/16, U=3, 512 configs
 WORKLOADS = {
     "tiny8": dict(index=0, L=2, nt=16, beta=2.0, U=2.0, n_stab=4, batch=1),
     "batch18": dict(index=1, L=3, nt=64, beta=8.0, U=3.0, n_stab=8, batch=256),
     "cold72": dict(index=2, L=6, nt=512, beta=64.0, U=3.5, n_stab=16, batch=64),
     "force72": dict(index=3, L=6, nt=256, beta=32.0, U=3.0, n_stab=8, batch=32),
+    "sparse288": dict(index=5, L=12, nt=64, beta=8.0, U=3.0, n_stab=16, batch=152),
 }
 
 UNEVEN_L = (2, 3, 4, 5, 6, 7, 8, 12)
@@ -203,3 +206,21 @@ def bss_proposals(name: str, step: int, first: int = 0, count: int | None = None
     sl = slice(first, first + count)
     return (np.ascontiguousarray(dphi[sl]), np.ascontiguousarray(u[sl]),
             np.ones((count, nx)))
+
+
+def sparse_rows(A: np.ndarray, q: int | None = None):
+    """The non-zero pattern of a (sparse) matrix as fixed-width rows: col (nx, q) int32 and
+    val (nx, q) float64 with row i's entries at [i, 0..q-1]; rows with fewer than q entries are
+    padded with (col = i, val = 0).  For the honeycomb adjacency q = 3."""
+    nx = A.shape[0]
+    rows = [np.flatnonzero(A[i]) for i in range(nx)]
+    width = max(len(r) for r in rows) if q is None else q
+    if any(len(r) > width for r in rows):
+        raise ValueError("a row has more than q entries")
+    col = np.empty((nx, width), dtype=np.int32)
+    val = np.zeros((nx, width))
+    for i, r in enumerate(rows):
+        col[i, :len(r)] = r
+        val[i, :len(r)] = A[i, r]
+        col[i, len(r):] = i
+    return col, val

@@ -181,6 +181,39 @@ typedef struct {
 int fd_bss_update(fd_ctx* ctx, int batch, const fd_bss_slice* slices, double* dlogdet,
                   void* stream);
 
+/* Intermediate-volume variant (Sections 8-9): log det and optionally G with every slice's
+ * hopping factor replaced by the degree-n Taylor polynomial of exp written as a product of
+ * linear factors, B_t = prod_{k=1}^{n} (1 + gamma_k K) diag(e^{i phi_t}), applied matrix-free
+ * with the sparse K -- O(n q nx) per column and slice instead of the dense O(nx^2) -- with the QR
+ * re-orthogonalisation every n_stab slices (the sporadic stabilisation of Section 9) and the
+ * assembly of fd_green.  The factors satisfy prod_k (1 + gamma_k x) = sum_{j<=n} x^j / j!
+ * (fd_taylor_factors), so the result equals fd_green's with E = sum_{j<=n} K^j / j! and differs
+ * from the one with E = exp(K) by O(nt delta^{n+1}) = O(beta delta^n).
+ *   probs  as for fd_green; expA and expA_inv are not read (may be NULL)
+ *   hop    host array of `batch` entries:
+ *            q     entries per row of K, 1 <= q <= 32 (pad short rows with val = 0)
+ *            nfac  n, 1 <= n <= 8 (the paper suggests 4)
+ *            col   device, nx*q int32: the columns of row i's entries at [i*q, i*q + q)
+ *            val   device, nx*q float64: their values K_{i,col} (delta*kappa on the honeycomb
+ *                  lattice)
+ *   G      host array of device pointers, or NULL for log det only
+ * FP64 (DFMA) throughout, one persistent kernel, no time-parallel split; the caller's tables
+ * must stay valid until the call has run.  Not available through fd_graph_create. */
+typedef struct {
+  int32_t q;
+  int32_t nfac;
+  const int32_t* col;
+  const double* val;
+} fd_sparse_hop;
+int fd_green_sparse(fd_ctx* ctx, int batch, const fd_problem* probs, const fd_sparse_hop* hop,
+                    double* logdet, double* const* G, void* stream);
+
+/* The product-form factors of fd_green_sparse for n = 1..8: gamma[2k], gamma[2k+1] = (re, im) of
+ * gamma_k, k = 0..n-1, sorted by (re, im) -- gamma_k = -1/x_k over the roots x_k of
+ * sum_{j<=n} x^j / j! (Weierstrass / Durand-Kerner iteration, then checked by multiplying the
+ * factors out).  Host only; returns FD_ERR_INVALID for n outside [1, 8]. */
+int fd_taylor_factors(int n, double* gamma);
+
 /* Wait for `stream` and copy the per-configuration device status of the LAST call on this
  * context into per_config_status[0..batch-1] (host): FD_OK, FD_ERR_NUMERIC or FD_ERR_TIMEOUT.
  * Returns the worst code seen (FD_OK if all succeeded). */

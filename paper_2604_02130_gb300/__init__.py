@@ -9,12 +9,14 @@ fails loudly if the CUDA library cannot be loaded (there is no CPU fallback).
 from .flops import force_flops, fwd_flops  # noqa: F401
 
 __all__ = ["Context", "Batch", "logdet", "green", "force", "green_tau", "observables",
-           "bss_update", "BssSlices", "FermionLogDet", "fwd_flops", "force_flops"]
+           "bss_update", "BssSlices", "green_sparse", "taylor_factors", "FermionLogDet",
+           "fwd_flops", "force_flops"]
 
 
 def __getattr__(name):
     if name in ("Context", "Batch", "logdet", "green", "force", "green_tau", "observables",
-                "bss_update", "BssSlices", "FermionLogDet", "Result",
+                "bss_update", "BssSlices", "green_sparse", "taylor_factors", "FermionLogDet",
+                "Result",
                 "FdError", "default_context"):
         from . import api
 

@@ -54,6 +54,15 @@ class fd_bss_slice(ctypes.Structure):
     ]
 
 
+class fd_sparse_hop(ctypes.Structure):
+    _fields_ = [
+        ("q", ctypes.c_int32),
+        ("nfac", ctypes.c_int32),
+        ("col", ctypes.c_void_p),
+        ("val", ctypes.c_void_p),
+    ]
+
+
 # (name, restype, argtypes) of every exported function of include/fd.h
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
@@ -69,6 +78,9 @@ SIGNATURES = [
     ("fd_green_tau", _I, [_VP, _I, _PP, _VP, _VP, _VP, _VP, _I, _VP]),
     ("fd_observables", _I, [_VP, _I, _PP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _VP]),
     ("fd_bss_update", _I, [_VP, _I, ctypes.POINTER(fd_bss_slice), _VP, _VP]),
+    ("fd_green_sparse", _I, [_VP, _I, ctypes.POINTER(fd_problem), ctypes.POINTER(fd_sparse_hop),
+                             _VP, ctypes.POINTER(_VP), _VP]),
+    ("fd_taylor_factors", _I, [_I, ctypes.POINTER(ctypes.c_double)]),
     ("fd_status", _I, [_VP, _VP, ctypes.POINTER(_I), _I]),
     ("fd_last_launch_count", _I, [_VP]),
     ("fd_measure_fp64_peak", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),

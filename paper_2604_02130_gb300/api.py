@@ -348,6 +348,60 @@ def observables(problems, operators=None, prec: str = "fp64", with_force: bool =
     return r.logdet.clone(), r.nferm.clone(), r.R, r.F
 
 
+def taylor_factors(n: int) -> List[complex]:
+    """The product-form factors gamma_k fd_green_sparse uses for n factors (fd_taylor_factors):
+    prod_k (1 + gamma_k x) = sum_{j<=n} x^j / j!."""
+    lib = L.load()
+    arr = (ctypes.c_double * 16)()
+    rc = lib.fd_taylor_factors(int(n), arr)
+    if rc != L.FD_OK:
+        raise FdError(rc, "fd_taylor_factors(%d)" % n)
+    return [complex(arr[2 * k], arr[2 * k + 1]) for k in range(n)]
+
+
+def green_sparse(problems, hops, nfac: int = 4, with_green: bool = True,
+                 ctx: Optional[Context] = None, stream=None):
+    """Intermediate-volume variant (Sections 8-9; fd_green_sparse): log det and optionally G with
+    every slice applied as prod_k (1 + gamma_k K) diag(e^{i phi_t}), K sparse.
+
+    problems: sequence of (phi (nt, nx) float64, n_stab); hops: sequence of (col (nx, q) int32,
+    val (nx, q) float64), the entries of K row by row (fd_inputs.sparse_rows); CUDA tensors.
+    Returns (logdet (batch,) complex128, [G (nx, nx) complex128] or None)."""
+    ctx = ctx or default_context()
+    n = len(problems)
+    if len(hops) != n:
+        raise ValueError("one hopping table per configuration")
+    dev = torch.device("cuda", ctx.device)
+    arr = (L.fd_problem * max(1, n))()
+    hop = (L.fd_sparse_hop * max(1, n))()
+    for c, ((phi, n_stab), (col, val)) in enumerate(zip(problems, hops)):
+        if not (phi.is_cuda and phi.dtype == torch.float64 and phi.is_contiguous()):
+            raise ValueError("phi must be a contiguous float64 CUDA tensor")
+        nt, nx = phi.shape
+        if not (col.is_cuda and col.dtype == torch.int32 and col.is_contiguous()
+                and col.dim() == 2 and col.shape[0] == nx):
+            raise ValueError("col must be a contiguous (nx, q) int32 CUDA tensor")
+        if not (val.is_cuda and val.dtype == torch.float64 and val.is_contiguous()
+                and tuple(val.shape) == tuple(col.shape)):
+            raise ValueError("val must be a contiguous float64 CUDA tensor shaped like col")
+        arr[c].nx, arr[c].nt, arr[c].n_stab, arr[c].reserved = nx, nt, int(n_stab), 0
+        arr[c].expA = None
+        arr[c].expA_inv = None
+        arr[c].phi = phi.data_ptr()
+        hop[c].q, hop[c].nfac = int(col.shape[1]), int(nfac)
+        hop[c].col, hop[c].val = col.data_ptr(), val.data_ptr()
+    logdet = torch.empty((max(1, n), 2), dtype=torch.float64, device=dev)
+    G = None
+    Gp = None
+    if with_green:
+        G = [torch.empty((p[0].shape[1], p[0].shape[1]), dtype=torch.complex128, device=dev)
+             for p in problems]
+        Gp = (ctypes.c_void_p * max(1, n))(*[g.data_ptr() for g in G])
+    ctx.check(ctx.lib.fd_green_sparse(ctx.h, n, arr, hop, ctypes.c_void_p(logdet.data_ptr()),
+                                      Gp, _stream_ptr(stream)))
+    return torch.view_as_complex(logdet)[:n], G
+
+
 class BssSlices:
     """A prepared local-update call (fd_bss_update, Section 3) over fixed device buffers.
 

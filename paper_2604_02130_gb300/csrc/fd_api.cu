@@ -1,6 +1,7 @@
 // fd_api.cu -- host runtime behind the C ABI of include/fd.h: context, validation, planning
 // (size classes, shared-memory placement, cost-sorted persistent queues), workspace and launches.
 #include <algorithm>
+#include <complex>
 #include <map>
 #include <cstdarg>
 #include <cstdio>
@@ -49,6 +50,9 @@ struct fd_ctx {
   // local (BSS) slice updates: device copy of the slice table
   fd::BssSlice* d_bss = nullptr;
   size_t bss_cap = 0;
+  // intermediate-volume variant: device copy of the per-configuration sparse hopping tables
+  fd::SparseHop* d_hop = nullptr;
+  size_t hop_cap = 0;
 };
 
 namespace {
@@ -171,7 +175,8 @@ long long tune_key(int kind, int mixed, int three, int nx) {
 // Buffer sets of the kernels ("roles"): log det/G and the force chains (R_FWD), the boundary
 // Green's functions (R_BOUND; R_BOUND2 with the second right-hand side of G(t, 0) beside G_t)
 // and the wraps (R_WRAP); the merge of a time-parallel split (R_MERGE).
-enum Role { R_FWD = 0, R_BOUND = 2, R_WRAP = 3, R_BOUND2 = 4, R_MERGE = 5 };
+// R_FWD_SPARSE: log det/G with the product-form slices (no dense E).
+enum Role { R_FWD = 0, R_BOUND = 2, R_WRAP = 3, R_BOUND2 = 4, R_MERGE = 5, R_FWD_SPARSE = 6 };
 
 // Greedy placement: the buffers touched every slice first, then the per-block ones.
 Layout plan_layout(int n, int role, int budget, int nthreads) {
@@ -182,6 +187,8 @@ Layout plan_layout(int n, int role, int budget, int nthreads) {
   std::vector<std::pair<int, long long>> order;
   if (role == R_FWD)
     order = {{fd::B_E, rm}, {fd::B_X0, cm}, {fd::B_X1, cm}, {fd::B_T0, cm}, {fd::B_T1, cm}};
+  else if (role == R_FWD_SPARSE)
+    order = {{fd::B_X0, cm}, {fd::B_X1, cm}, {fd::B_T0, cm}, {fd::B_T1, cm}};
   else if (role == R_BOUND)
     order = {{fd::B_GA, cm}, {fd::B_GB, cm}};
   else if (role == R_BOUND2)
@@ -345,7 +352,7 @@ fd::MLayout plan_mixed(int n, int role, bool three, int budget, int smem_per_sm)
 }
 
 int validate(fd_ctx* ctx, int batch, const fd_problem* probs, const void* logdet, int prec,
-             bool need_einv) {
+             bool need_einv, bool need_e = true) {
   if (!ctx) return FD_ERR_INVALID;
   if (batch < 0) return fail(ctx, FD_ERR_INVALID, "batch < 0");
   if (batch > 0 && (!probs || !logdet)) return fail(ctx, FD_ERR_INVALID, "null probs or logdet");
@@ -362,7 +369,8 @@ int validate(fd_ctx* ctx, int batch, const fd_problem* probs, const void* logdet
       return fail(ctx, FD_ERR_INVALID, "config %d: nt=%d not a multiple of n_stab=%d", c, p.nt,
                   p.n_stab);
     if (p.reserved != 0) return fail(ctx, FD_ERR_INVALID, "config %d: reserved != 0", c);
-    if (!p.expA || !p.phi) return fail(ctx, FD_ERR_INVALID, "config %d: null expA or phi", c);
+    if ((need_e && !p.expA) || !p.phi)
+      return fail(ctx, FD_ERR_INVALID, "config %d: null expA or phi", c);
     if (need_einv && !p.expA_inv)
       return fail(ctx, FD_ERR_INVALID, "config %d: the force path (F, G(tau, 0), R) needs expA_inv", c);
   }
@@ -447,7 +455,8 @@ bool mixed_phase(fd_ctx* ctx, int n, int role, int which, bool three, int ntasks
   return true;
 }
 
-std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kind, int prec) {
+std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kind, int prec,
+                        bool sparse = false) {
   std::vector<Group> groups;
   std::vector<int> order(batch);
   for (int c = 0; c < batch; ++c) order[c] = c;
@@ -459,7 +468,7 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
     if (na != nb) return na > nb;
     return a < b;
   });
-  const bool mixed = prec != FD_PREC_FP64;
+  const bool mixed = prec != FD_PREC_FP64 && !sparse;
   const bool three = prec == FD_PREC_MIXED_3XTF32;
   int qnext = 0;
   size_t i = 0;
@@ -477,7 +486,7 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
     // most one wave of the chain kernel), computed from the identity in parallel and merged by a
     // stabilised product.
     int target = 1;
-    if (kind == K_FWD && nd < ctx->num_sms) {
+    if (kind == K_FWD && nd < ctx->num_sms && !sparse) {
       // as many segments as one wave of the chain kernel holds
       Phase P0;
       if (!(mixed && mixed_phase(ctx, n, R_FWD, 1, three, nd, P0)))
@@ -503,7 +512,8 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       g.ph.push_back(fp64_phase(ctx, n, R_MERGE, 8, nd));
     } else if (kind == K_FWD) {
       Phase P;
-      if (!(mixed && mixed_phase(ctx, n, R_FWD, 0, three, nd, P))) P = fp64_phase(ctx, n, R_FWD, 0, nd);
+      if (!(mixed && mixed_phase(ctx, n, R_FWD, 0, three, nd, P)))
+        P = fp64_phase(ctx, n, sparse ? R_FWD_SPARSE : R_FWD, 0, nd);
       g.ph.push_back(P);
     } else {
       for (int k = 0; k < nd; ++k) {
@@ -670,6 +680,7 @@ void build_tables(std::vector<Group>& groups, const fd_problem* probs, const Out
                   ? (double2*)(scratch + g.scratch_off + g.slots_bytes + g.fws_off[q])
                   : nullptr;
       d.nseg = g.nseg.empty() ? 0 : g.nseg[q];
+      d.hop = nullptr;
       out[k++] = d;
     }
     g.tA_off = t;
@@ -783,7 +794,7 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
 }
 
 int run(fd_ctx* ctx, int batch, const fd_problem* probs, const Outs& o, int prec, void* stream_,
-        int kind) {
+        int kind, const fd::SparseHop* d_hop = nullptr) {
   cudaStream_t stream = (cudaStream_t)stream_;
   ctx->last_launches = 0;
   ctx->last_batch = batch;
@@ -792,7 +803,7 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, const Outs& o, int prec
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
   // Mixed precision applies to the size classes that fit the tensor-core kernels (nx <= 128 and
   // its operands in shared memory); larger classes run the FP64 kernels (fd_plan_query says so).
-  std::vector<Group> groups = plan(ctx, batch, probs, kind, prec);
+  std::vector<Group> groups = plan(ctx, batch, probs, kind, prec, d_hop != nullptr);
   size_t need = scratch_need(groups);
   const size_t ntasks = task_count(groups);
   int rc = ensure(ctx, (size_t)batch, (size_t)batch * (1 + fd::SF_NUM), queue_count(groups), need,
@@ -803,6 +814,8 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, const Outs& o, int prec
     ctx->staging_pending = false;
   }
   build_tables(groups, probs, o, ctx->scratch, ctx->d_status + batch, ctx->h_desc, ctx->h_tasks);
+  if (d_hop)
+    for (int k = 0; k < batch; ++k) ctx->h_desc[k].hop = d_hop + ctx->h_desc[k].user_index;
   FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(Desc) * batch,
                                cudaMemcpyHostToDevice, stream));
   if (ntasks)
@@ -838,6 +851,69 @@ void graph_free(GraphObj* g) {
   if (g->d_status) cudaFree(g->d_status);
   if (g->scratch) cudaFree(g->scratch);
   delete g;
+}
+
+// Factors of the product form (Section 8): prod_k (1 + gamma_k x) equals the truncated
+// exponential series s_n(x) = sum_{j<=n} x^j / j!, so gamma_k = -1 / x_k over the roots x_k of
+// s_n.  The roots come from the Weierstrass (Durand-Kerner) simultaneous iteration on the monic
+// polynomial n! s_n(x) = sum_j (n!/j!) x^j, then one Newton step each; the factors are accepted
+// only if multiplying them out reproduces 1/j! to 1e-12.  Sorted by (re, im).
+int taylor_factors(int n, std::complex<double>* gamma) {
+  typedef std::complex<double> cd;
+  if (n < 1 || n > FD_SPARSE_NFAC_MAX) return FD_ERR_INVALID;
+  std::vector<double> a(n + 1);  // a[j] = n! / j!
+  for (int j = 0; j <= n; ++j) {
+    double v = 1.0;
+    for (int k = j + 1; k <= n; ++k) v *= k;
+    a[j] = v;
+  }
+  auto poly = [&](cd z) {
+    cd s = a[n];
+    for (int j = n - 1; j >= 0; --j) s = s * z + a[j];
+    return s;
+  };
+  auto dpoly = [&](cd z) {
+    cd s = (double)n * a[n];
+    for (int j = n - 1; j >= 1; --j) s = s * z + (double)j * a[j];
+    return s;
+  };
+  std::vector<cd> z(n);
+  const cd seed(0.4, 0.9);
+  cd w = 1.0;
+  for (int k = 0; k < n; ++k) {
+    z[k] = (0.5 + 0.5 * n) * w;
+    w *= seed;
+  }
+  for (int it = 0; it < 1000; ++it) {
+    double step = 0.0;
+    for (int k = 0; k < n; ++k) {
+      cd den = 1.0;
+      for (int j = 0; j < n; ++j)
+        if (j != k) den *= z[k] - z[j];
+      const cd d = poly(z[k]) / den;
+      z[k] -= d;
+      step = std::max(step, std::abs(d) / std::max(1.0, std::abs(z[k])));
+    }
+    if (step < 1e-15) break;
+  }
+  for (int k = 0; k < n; ++k) z[k] -= poly(z[k]) / dpoly(z[k]);
+  std::vector<cd> g(n);
+  for (int k = 0; k < n; ++k) g[k] = -1.0 / z[k];
+  std::sort(g.begin(), g.end(), [](const cd& x, const cd& y) {
+    return x.real() != y.real() ? x.real() < y.real() : x.imag() < y.imag();
+  });
+  // check: prod_k (1 + g_k x) = sum_j x^j / j!
+  std::vector<cd> c(n + 1, 0.0);
+  c[0] = 1.0;
+  for (int k = 0; k < n; ++k)
+    for (int j = k + 1; j >= 1; --j) c[j] += g[k] * c[j - 1];
+  double inv_fact = 1.0;
+  for (int j = 0; j <= n; ++j) {
+    if (j > 0) inv_fact /= j;
+    if (std::abs(c[j] - inv_fact) > 1e-12) return FD_ERR_NUMERIC;
+  }
+  for (int k = 0; k < n; ++k) gamma[k] = g[k];
+  return FD_OK;
 }
 
 }  // namespace
@@ -880,6 +956,7 @@ void fd_ctx_destroy(fd_ctx* ctx) {
   if (ctx->h_tasks) cudaFreeHost(ctx->h_tasks);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_bss) cudaFree(ctx->d_bss);
+  if (ctx->d_hop) cudaFree(ctx->d_hop);
   if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
   for (auto e : ctx->ev) cudaEventDestroy(e);
   for (auto s : ctx->side) cudaStreamDestroy(s);
@@ -1036,6 +1113,66 @@ int fd_bss_update(fd_ctx* ctx, int batch, const fd_bss_slice* slices, double* dl
   if (ctx->timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[1], stream));
   ctx->last_launches = 1;
   return FD_OK;
+}
+
+int fd_taylor_factors(int n, double* gamma) {
+  if (!gamma) return FD_ERR_INVALID;
+  std::complex<double> g[FD_SPARSE_NFAC_MAX];
+  const int rc = taylor_factors(n, g);
+  if (rc != FD_OK) return rc;
+  for (int k = 0; k < n; ++k) {
+    gamma[2 * k] = g[k].real();
+    gamma[2 * k + 1] = g[k].imag();
+  }
+  return FD_OK;
+}
+
+int fd_green_sparse(fd_ctx* ctx, int batch, const fd_problem* probs, const fd_sparse_hop* hop,
+                    double* logdet, double* const* G, void* stream) {
+  int rc = validate(ctx, batch, probs, logdet, FD_PREC_FP64, false, false);
+  if (rc != FD_OK) return rc;
+  if (batch == 0) return FD_OK;
+  if (!hop) return fail(ctx, FD_ERR_INVALID, "null hop array");
+  std::vector<fd::SparseHop> h(batch);
+  for (int c = 0; c < batch; ++c) {
+    const fd_sparse_hop& s = hop[c];
+    if (s.q < 1 || s.q > 32)
+      return fail(ctx, FD_ERR_INVALID, "config %d: q=%d outside [1,32]", c, s.q);
+    if (s.nfac < 1 || s.nfac > FD_SPARSE_NFAC_MAX)
+      return fail(ctx, FD_ERR_INVALID, "config %d: nfac=%d outside [1,%d]", c, s.nfac,
+                  FD_SPARSE_NFAC_MAX);
+    if (!s.col || !s.val) return fail(ctx, FD_ERR_INVALID, "config %d: null col or val", c);
+    if (G && !G[c]) return fail(ctx, FD_ERR_INVALID, "config %d: null G", c);
+    std::complex<double> g[FD_SPARSE_NFAC_MAX];
+    if (taylor_factors(s.nfac, g) != FD_OK)
+      return fail(ctx, FD_ERR_NUMERIC, "config %d: product-form factors for n=%d", c, s.nfac);
+    fd::SparseHop& d = h[c];
+    memset(&d, 0, sizeof(d));
+    d.col = s.col;
+    d.val = s.val;
+    d.q = s.q;
+    d.nfac = s.nfac;
+    for (int k = 0; k < s.nfac; ++k) d.gamma[k] = make_double2(g[k].real(), g[k].imag());
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  if ((size_t)batch > ctx->hop_cap) {
+    if (ctx->d_hop) {
+      FD_CUDA(ctx, cudaStreamSynchronize(st));
+      cudaFree(ctx->d_hop);
+    }
+    ctx->d_hop = nullptr;
+    const size_t cap = std::max<size_t>(batch, 64);
+    FD_CUDA(ctx, cudaMalloc(&ctx->d_hop, cap * sizeof(fd::SparseHop)));
+    ctx->hop_cap = cap;
+  }
+  // pageable source: the copy is staged before the call returns
+  FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_hop, h.data(), sizeof(fd::SparseHop) * batch,
+                               cudaMemcpyHostToDevice, st));
+  Outs o;
+  o.logdet = logdet;
+  o.G = G;
+  return run(ctx, batch, probs, o, FD_PREC_FP64, stream, K_FWD, ctx->d_hop);
 }
 
 int fd_status(fd_ctx* ctx, void* stream, int* per_config_status, int batch) {

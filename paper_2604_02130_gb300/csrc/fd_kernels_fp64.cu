@@ -68,6 +68,49 @@ __device__ void fwd_slices(int n, const double* E, const double* phi, int s_begi
   }
 }
 
+// Intermediate-volume variant (Sections 8-9): slices s_begin..s_end-1 applied as
+// X <- prod_k (1 + gamma_k K) diag(e^{i phi_s}) X, one pass over X per factor (the field phase is
+// folded into the first pass), K applied matrix-free from its q entries per row: O(n q nx^2)
+// per slice instead of the dense 4 nx^3.  A column index outside [0, nx) marks the
+// configuration FD_ERR_NUMERIC and is skipped.
+__device__ void fwd_slices_sparse(int n, const SparseHop* hop, const double* phi, int s_begin,
+                                  int s_end, double2*& X, double2*& Xo, Small& s) {
+  const int q = hop->q, nfac = hop->nfac;
+  const int* __restrict__ col = hop->col;
+  const double* __restrict__ val = hop->val;
+  for (int t = s_begin; t < s_end; ++t) {
+    cta_phase(n, s.ph, phi + (size_t)t * n, 1.0);
+    __syncthreads();
+    for (int k = 0; k < nfac; ++k) {
+      const double2 g = hop->gamma[k];
+      const bool first = k == 0;
+      for (int e = tid(); e < n * n; e += nthr()) {
+        const int i = e % n, base = e - i;  // column-major: element (i, j) at i + j n
+        double ar = 0.0, ai = 0.0;
+        for (int m = 0; m < q; ++m) {
+          const int c = __ldg(col + i * q + m);
+          const double v = __ldg(val + i * q + m);
+          if ((unsigned)c >= (unsigned)n) {  // a column outside the matrix: flag, skip
+            s.misc[0] = 1;
+            continue;
+          }
+          cplx x = ld(X + base + c);
+          if (first) x = ld(s.ph + c) * x;
+          ar = fma(v, x.re, ar);
+          ai = fma(v, x.im, ai);
+        }
+        cplx y = ld(X + e);
+        if (first) y = ld(s.ph + i) * y;
+        Xo[e] = make_double2(fma(g.x, ar, fma(-g.y, ai, y.re)), fma(g.x, ai, fma(g.y, ar, y.im)));
+      }
+      __syncthreads();
+      double2* tmp = X;
+      X = Xo;
+      Xo = tmp;
+    }
+  }
+}
+
 // Right (backward) product as its adjoint: X <- B_s^H X = diag(e^{-i phi_s}) E X for
 // s = s_hi-1 down to s_lo (0-based rows of phi).
 __device__ void bwd_slices(int n, const double* E, const double* phi, int s_lo, int s_hi,
@@ -133,7 +176,10 @@ __global__ void __launch_bounds__(256) k_fwd_fp64(const Desc* __restrict__ descs
     for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
     __syncthreads();
     for (int b = 0; b < d.nt; b += d.nstab) {
-      fwd_slices(n, B.E, d.phi, b, b + d.nstab, X, Xo, s);
+      if (d.hop)
+        fwd_slices_sparse(n, d.hop, d.phi, b, b + d.nstab, X, Xo, s);
+      else
+        fwd_slices(n, B.E, d.phi, b, b + d.nstab, X, Xo, s);
       cta_reortho(n, X, Xo, T, To, s.logD, s);
       double2* t1 = X; X = Xo; Xo = t1;
       double2* t2 = T; T = To; To = t2;

@@ -14,6 +14,9 @@ Per configuration with n = Nx, blocks nb = Nt / n_stab:
     solve per interior boundary (104/3 n^3; 16 n^3 more when G_t is formed beside it: a second
     right-hand side and product), and one real x complex product 4 n^3 per propagated slice.
   response traces tr(O G_r): 4 n^2 per slice (real O, complex G) on top of the force's G_r.
+  product-form slices (Sections 8-9, q entries per row of K, nf factors): per slice and matrix
+    element 4q + 8 per factor (q real x complex multiply-adds, one complex multiply-add by
+    gamma_k) and 6 (q + 1) for the field phase folded into the first factor.
 """
 from __future__ import annotations
 
@@ -80,3 +83,12 @@ def response_phase_flops(nx: int, nt: int, n_stab: int, mixed: bool) -> dict:
     if not mixed:
         base["C"] = {"fp64": base["C"]["fp64"] + 4.0 * nx * nx * nt, "tensor": 0.0}
     return base
+
+
+def sparse_fwd_flops(nx: int, nt: int, n_stab: int, q: int, nfac: int) -> dict:
+    """log det/G with the product-form slices: the slices above, QR and assembly as fwd_flops."""
+    n2 = float(nx) ** 2
+    slices = (nfac * (4.0 * q + 8.0) + 6.0 * (q + 1)) * n2 * nt
+    f = fwd_flops(nx, nt, n_stab)
+    return {"slices": slices, "qr": f["qr"], "assembly": f["assembly"],
+            "total": slices + f["qr"] + f["assembly"]}

@@ -58,6 +58,39 @@ def test_bss_struct_layout():
     assert _lib.fd_bss_slice.accepted.offset == 48
 
 
+def test_sparse_hop_struct_layout():
+    from paper_2604_02130_gb300 import _lib
+
+    assert ctypes.sizeof(_lib.fd_sparse_hop) == 24
+    assert _lib.fd_sparse_hop.col.offset == 8
+    assert _lib.fd_sparse_hop.val.offset == 16
+
+
+def test_taylor_factors_match_the_oracle(lib):
+    """The library's product-form factors (host code, no GPU: a Weierstrass iteration) against
+    the oracle's, which come from numpy's companion-matrix roots."""
+    import numpy as np
+
+    from oracle import product_form
+
+    from paper_2604_02130_gb300 import _lib
+
+    f = lib.fd_taylor_factors
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    for n in range(1, 9):
+        arr = (ctypes.c_double * 16)()
+        assert f(n, arr) == 0
+        got = [complex(arr[2 * k], arr[2 * k + 1]) for k in range(n)]
+        # the same multiset (conjugate partners may swap places: their real parts tie)
+        for w in product_form.taylor_factors(n):
+            k = int(np.argmin([abs(g - w) for g in got]))
+            assert abs(got.pop(k) - w) < 1e-12, n
+    arr = (ctypes.c_double * 16)()
+    assert f(0, arr) == -1 and f(9, arr) == -1
+    assert _lib.SIGNATURES  # bound like every other export
+
+
 def test_ctx_create_without_gpu_fails_cleanly(lib):
     import torch
 
