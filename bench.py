@@ -188,14 +188,19 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- helpers
 KERNEL_SOURCES = ("fd_common.cuh", "fd_fp64.cuh", "fd_tc.cuh", "fd_kernels_fp64.cu",
                   "fd_kernels_mixed.cu")
+# the files whose code a kernel compiles from, where that is fewer than all of them
+KERNEL_SOURCES_OF = {
+    "k_chain_mixed": ("fd_common.cuh", "fd_fp64.cuh", "fd_tc.cuh", "fd_kernels_mixed.cu"),
+}
 
 
-def _kernel_source_hash():
-    """Hash of the files that define the hot-path kernels (the host runtime and the probes are
-    left out: changing them does not change what a kernel does)."""
+def _kernel_source_hash(kernel=None):
+    """Hash of the files that define a kernel's code (default: all hot-path kernels; the host
+    runtime, the launcher declarations and the probes are left out: changing them does not change
+    what a kernel does)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2604_02130_gb300", "csrc")
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES_OF.get(kernel, KERNEL_SOURCES):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -212,7 +217,7 @@ def _traffic(kernel, workload, prec, step_path="force"):
         if step_path != "force":
             key += "|" + step_path
         e = db.get(key)
-        if e and e.get("source_hash") == _kernel_source_hash():
+        if e and e.get("source_hash") == _kernel_source_hash(kernel):
             return e["dram_bytes_per_launch"]
     except Exception:
         return None

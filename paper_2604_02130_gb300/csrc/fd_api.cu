@@ -680,7 +680,6 @@ void build_tables(std::vector<Group>& groups, const fd_problem* probs, const Out
                   ? (double2*)(scratch + g.scratch_off + g.slots_bytes + g.fws_off[q])
                   : nullptr;
       d.nseg = g.nseg.empty() ? 0 : g.nseg[q];
-      d.hop = nullptr;
       out[k++] = d;
     }
     g.tA_off = t;
@@ -712,7 +711,7 @@ int ensure_side(fd_ctx* ctx, size_t n) {
 // on `stream` itself for a single class, else forked onto side streams and joined back.
 int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_tasks,
             int* d_queue, int* d_status, char* scratch, int batch, cudaStream_t stream,
-            bool timing) {
+            bool timing, const fd::SparseHop* hops = nullptr) {
   const int nq = queue_count(groups);
   FD_CUDA(ctx, cudaMemsetAsync(d_queue, 0, sizeof(int) * nq, stream));
   FD_CUDA(ctx, cudaMemsetAsync(d_status, 0xFF, sizeof(int) * batch, stream));  // pending
@@ -753,7 +752,7 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
           if (P.mixed)
             fd::launch_fwd_mixed(dd, nd, d_queue + qi, d_status, scr, P.ML, P.grid, s);
           else
-            fd::launch_fwd_fp64(dd, nd, d_queue + qi, d_status, scr, P.L, P.grid, s);
+            fd::launch_fwd_fp64(dd, nd, d_queue + qi, d_status, scr, P.L, P.grid, s, hops);
           break;
         case 1:
           if (P.mixed)
@@ -814,8 +813,6 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, const Outs& o, int prec
     ctx->staging_pending = false;
   }
   build_tables(groups, probs, o, ctx->scratch, ctx->d_status + batch, ctx->h_desc, ctx->h_tasks);
-  if (d_hop)
-    for (int k = 0; k < batch; ++k) ctx->h_desc[k].hop = d_hop + ctx->h_desc[k].user_index;
   FD_CUDA(ctx, cudaMemcpyAsync(ctx->d_desc, ctx->h_desc, sizeof(Desc) * batch,
                                cudaMemcpyHostToDevice, stream));
   if (ntasks)
@@ -824,7 +821,7 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, const Outs& o, int prec
   FD_CUDA(ctx, cudaEventRecord(ctx->staging_done, stream));
   ctx->staging_pending = true;
   return enqueue(ctx, groups, ctx->d_desc, ctx->d_tasks, ctx->d_queue, ctx->d_status,
-                 ctx->scratch, batch, stream, ctx->timing);
+                 ctx->scratch, batch, stream, ctx->timing, d_hop);
 }
 
 // A captured call: its own descriptor table, queues, status words and scratch (so later calls

@@ -61,28 +61,6 @@ struct Desc {
   double2* R;          // response traces tr(O G_r), r = 0..nt-1, or null
   int* sync;           // phased path: this configuration's progress flags (SyncFlag), else null
   int nseg;            // time-parallel log det/G: number of segments of the chain (0: not split)
-  const struct SparseHop* hop;  // intermediate-volume variant: product-form slices, else null
-};
-
-// Intermediate-volume variant (Sections 8-9): the hopping factor of a slice applied as
-// prod_k (1 + gamma_k K) with the sparse K (q entries per row, row i at [i*q, i*q + q)).
-#define FD_SPARSE_NFAC_MAX 8
-struct SparseHop {
-  const int* col;
-  const double* val;
-  int q, nfac;
-  double2 gamma[FD_SPARSE_NFAC_MAX];
-};
-
-// One configuration of a local (BSS) slice update (the public fd_bss_slice, device view).
-struct BssSlice {
-  int nx, reserved;
-  double2* G;          // nx*nx row-major, in/out
-  double* phi;         // nx, in/out: the field of the slice
-  const double* dphi;  // nx proposals
-  const double* u;     // nx uniform random numbers
-  const double* w;     // nx other-weight ratios
-  int* acc;            // nx out: accepted
 };
 
 // ---------------------------------------------------------------- overlapped phases

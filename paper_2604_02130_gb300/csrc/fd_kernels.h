@@ -5,9 +5,32 @@
 
 namespace fd {
 
-// FP64 path
+// Intermediate-volume variant (Sections 8-9): the hopping factor of a slice applied as
+// prod_k (1 + gamma_k K) with the sparse K (q entries per row, row i at [i*q, i*q + q)); one
+// entry per configuration, indexed by the user index of the descriptor.
+#define FD_SPARSE_NFAC_MAX 8
+struct SparseHop {
+  const int* col;
+  const double* val;
+  int q, nfac;
+  double2 gamma[FD_SPARSE_NFAC_MAX];
+};
+
+// One configuration of a local (BSS) slice update (the public fd_bss_slice, device view).
+struct BssSlice {
+  int nx, reserved;
+  double2* G;          // nx*nx row-major, in/out
+  double* phi;         // nx, in/out: the field of the slice
+  const double* dphi;  // nx proposals
+  const double* u;     // nx uniform random numbers
+  const double* w;     // nx other-weight ratios
+  int* acc;            // nx out: accepted
+};
+
+// FP64 path.  hops: null, or the product-form tables of the configurations (log det/G only).
 void launch_fwd_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
-                     const Layout& L, int grid, cudaStream_t stream);
+                     const Layout& L, int grid, cudaStream_t stream,
+                     const SparseHop* hops = nullptr);
 // force phases: A chains (2 tasks per configuration: Task.b = 0 forward, 1 backward),
 // B boundary Green's functions, C wraps
 void launch_chain_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,

@@ -151,7 +151,7 @@ __device__ void finish_status(const Desc& d, Small& s, int* status, double re, d
 // ------------------------------------------------------------------ log det and G
 __global__ void __launch_bounds__(256) k_fwd_fp64(const Desc* __restrict__ descs, int ndesc,
                                                    int* queue, int* status, char* scratch,
-                                                   Layout L) {
+                                                   Layout L, const SparseHop* __restrict__ hops) {
   extern __shared__ __align__(16) char smem[];
   char* slotp = scratch + (size_t)blockIdx.x * L.slot_bytes;
   for (;;) {
@@ -175,9 +175,10 @@ __global__ void __launch_bounds__(256) k_fwd_fp64(const Desc* __restrict__ descs
     cta_identity(n, T);
     for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
     __syncthreads();
+    const SparseHop* hop = hops ? hops + d.user_index : nullptr;
     for (int b = 0; b < d.nt; b += d.nstab) {
-      if (d.hop)
-        fwd_slices_sparse(n, d.hop, d.phi, b, b + d.nstab, X, Xo, s);
+      if (hop)
+        fwd_slices_sparse(n, hop, d.phi, b, b + d.nstab, X, Xo, s);
       else
         fwd_slices(n, B.E, d.phi, b, b + d.nstab, X, Xo, s);
       cta_reortho(n, X, Xo, T, To, s.logD, s);
@@ -545,8 +546,9 @@ __global__ void __launch_bounds__(256) k_merge_fp64(const Desc* __restrict__ des
 }
 
 void launch_fwd_fp64(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
-                     const Layout& L, int grid, cudaStream_t stream) {
-  k_fwd_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch, L);
+                     const Layout& L, int grid, cudaStream_t stream, const SparseHop* hops) {
+  k_fwd_fp64<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, ndesc, queue, status, scratch, L,
+                                                         hops);
 }
 void launch_chain_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                        char* scratch, const Layout& L, int grid, cudaStream_t stream) {
