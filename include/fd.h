@@ -28,7 +28,10 @@
  *     inside the context.  A call may grow it with cudaMalloc, which synchronises the device;
  *     fd_reserve() sizes it ahead of time (required before stream capture).
  *   - Every function returns FD_OK (0) or a negative FD_ERR_* code; fd_last_error() gives text.
- *   - A context is not thread-safe; use one per host thread.
+ *   - A context is not thread-safe; use one per host thread.  Its device tables (descriptors,
+ *     queues, status words, scratch, the BSS and sparse-hopping tables) are reused by every call,
+ *     so calls on one context issued to different streams must be ordered with events (or issued
+ *     to one stream); CUDA graphs (fd_graph_create) own separate tables.
  */
 #ifndef FD_H_
 #define FD_H_
