@@ -52,3 +52,28 @@ def test_workload_shapes():
     pairs = {(p.nx, p.nt) for p in u}
     assert len(pairs) == 48
     assert all(abs(p.delta - 1 / 16) < 1e-15 for p in u)
+
+
+def test_sparse_rows_reproduce_the_matrix():
+    A = fi.honeycomb_adjacency(4)
+    col, val = fi.sparse_rows(A)
+    assert col.dtype == np.int32 and col.shape == (32, 3)
+    B = np.zeros_like(A, dtype=float)
+    for i in range(A.shape[0]):
+        for m in range(col.shape[1]):
+            B[i, col[i, m]] += val[i, m]
+    assert np.array_equal(B, A)
+    col4, val4 = fi.sparse_rows(A, 4)  # padded: (col = i, val = 0)
+    assert np.all(col4[:, 3] == np.arange(32)) and np.all(val4[:, 3] == 0)
+    with pytest.raises(ValueError):
+        fi.sparse_rows(A, 2)
+
+
+def test_bss_proposals_law_and_sharding():
+    d, u, w = fi.bss_proposals("batch18", 3)
+    assert d.shape == u.shape == w.shape == (256, 18)
+    assert abs(d.var() / (0.125 * 3.0) - 1.0) < 0.05 and 0.0 <= u.min() and u.max() < 1.0
+    assert np.all(w == 1.0)
+    d2, u2, _ = fi.bss_proposals("batch18", 3, first=100, count=7)
+    assert np.array_equal(d2, d[100:107]) and np.array_equal(u2, u[100:107])
+    assert not np.array_equal(d, fi.bss_proposals("batch18", 4)[0])
