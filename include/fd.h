@@ -217,6 +217,13 @@ int fd_green_sparse(fd_ctx* ctx, int batch, const fd_problem* probs, const fd_sp
  * factors out).  Host only; returns FD_ERR_INVALID for n outside [1, 8]. */
 int fd_taylor_factors(int n, double* gamma);
 
+/* Failure-detection test hook.  With `on`, the phased calls (fd_force, fd_green_tau, and
+ * fd_observables with F or R) skip their chain launch, so the boundary and wrap tasks wait for
+ * checkpoints that never come: each bounded wait gives up after ~4 s without progress, the
+ * kernels return, and every configuration reports FD_ERR_TIMEOUT in fd_status (outputs are then
+ * undefined).  The context stays usable; switch the hook off for normal calls. */
+int fd_debug_skip_chains(fd_ctx* ctx, int on);
+
 /* Wait for `stream` and copy the per-configuration device status of the LAST call on this
  * context into per_config_status[0..batch-1] (host): FD_OK, FD_ERR_NUMERIC or FD_ERR_TIMEOUT.
  * Returns the worst code seen (FD_OK if all succeeded). */

@@ -81,6 +81,7 @@ SIGNATURES = [
     ("fd_green_sparse", _I, [_VP, _I, ctypes.POINTER(fd_problem), ctypes.POINTER(fd_sparse_hop),
                              _VP, ctypes.POINTER(_VP), _VP]),
     ("fd_taylor_factors", _I, [_I, ctypes.POINTER(ctypes.c_double)]),
+    ("fd_debug_skip_chains", _I, [_VP, _I]),
     ("fd_status", _I, [_VP, _VP, ctypes.POINTER(_I), _I]),
     ("fd_last_launch_count", _I, [_VP]),
     ("fd_measure_fp64_peak", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),

@@ -64,6 +64,11 @@ class Context:
         self.lib.fd_status(self.h, _stream_ptr(stream), arr, batch)
         return [arr[i] for i in range(batch)]
 
+    def debug_skip_chains(self, on: bool):
+        """Failure-detection test hook (fd_debug_skip_chains): phased calls skip their chain
+        launch, so the dependent tasks' bounded waits run out and report FD_ERR_TIMEOUT."""
+        self.check(self.lib.fd_debug_skip_chains(self.h, 1 if on else 0))
+
     def last_launch_count(self) -> int:
         return self.lib.fd_last_launch_count(self.h)
 

@@ -53,6 +53,8 @@ struct fd_ctx {
   // intermediate-volume variant: device copy of the per-configuration sparse hopping tables
   fd::SparseHop* d_hop = nullptr;
   size_t hop_cap = 0;
+  // failure-detection test hook: phased calls skip their chain launch (fd_debug_skip_chains)
+  bool debug_skip_chains = false;
 };
 
 namespace {
@@ -743,7 +745,8 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
       char* scr = scratch + g.scratch_off + P.slot_off;
       const int qi = g.qbase + (int)pi;
       if (timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * qi], s));
-      if (P.which == 2 && g.tB.empty()) {  // single-block configurations: no boundary phase
+      if ((P.which == 2 && g.tB.empty()) ||  // single-block configurations: no boundary phase
+          (P.which == 1 && g.kind != K_FWD && ctx->debug_skip_chains)) {
         if (timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * qi + 1], s));
         continue;
       }
@@ -1109,6 +1112,12 @@ int fd_bss_update(fd_ctx* ctx, int batch, const fd_bss_slice* slices, double* dl
   if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
   if (ctx->timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[1], stream));
   ctx->last_launches = 1;
+  return FD_OK;
+}
+
+int fd_debug_skip_chains(fd_ctx* ctx, int on) {
+  if (!ctx) return FD_ERR_INVALID;
+  ctx->debug_skip_chains = on != 0;
   return FD_OK;
 }
 
