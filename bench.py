@@ -52,6 +52,10 @@ WORKLOAD_TEXT = {
     "force72": "honeycomb L=6 (Nx=72), beta=32, Nt=256, U=3, n_stab=8, 32 configs",
     "tiny8": "honeycomb L=2 (Nx=8), beta=2, Nt=16, U=2, n_stab=4, 1 config",
     "sparse288": "honeycomb L=12 (Nx=288), kappa=1, beta=8, Nt=64, U=3, n_stab=16, 152 configs",
+    "uneven512": "uneven batch of 512 configs: honeycomb L in {2,3,4,5,6,7,8,12} (Nx in {8,18,32,"
+                 "50,72,98,128,288}) x Nt in {32,64,128,256,512,1024}, delta=1/16 (beta=Nt/16 in "
+                 "2..64), kappa=1, U=3, phi~N(0,delta*U), n_stab=16, the 48 (Nx, Nt) pairs "
+                 "round-robin (first 32 pairs 11x, last 16 pairs 10x) in a seeded shuffle",
 }
 
 # what one step computes: Batch outputs, metric, and the text appended to the workload
@@ -75,8 +79,13 @@ PATHS = {
 # ----------------------------------------------------------------------------- CPU oracle leg
 def _oracle_worker(args):
     """One configuration through the CPU oracle: stabilised log det and, by path, G and the
-    force, G(tau, 0) for every tau, or the fermion number and the response traces tr(A G_t)."""
-    name, c, path = args
+    force, G(tau, 0) for every tau, or the fermion number and the response traces tr(A G_t).
+    With `rows` (force path) only those force rows are evaluated, each a full stabilised
+    evaluation on the rotated field (the oracle's force is that loop over all Nt rows); the
+    times of log det + G and of the rows are returned apart so that a caller can scale the
+    rows to Nt."""
+    name, c, path = args[:3]
+    rows = args[3] if len(args) > 3 else None
     import fd_inputs as fi
     from oracle import bss
     from oracle import force as oforce
@@ -96,6 +105,14 @@ def _oracle_worker(args):
         return c, total, {"row": row, "acc": acc, "G": G}, time.perf_counter() - t0
     t0 = time.perf_counter()
     ld, G = stable.logdet_green(p.E, p.phi, p.n_stab)
+    t_ld = time.perf_counter() - t0
+    if path == "force" and rows is not None:
+        t1 = time.perf_counter()
+        Fr = oforce.force_rows(p.E, p.phi, p.n_stab, rows)
+        t_rows = time.perf_counter() - t1
+        out = {"G": G, "F_rows": Fr, "t_ld": t_ld, "t_row": t_rows / max(1, len(rows)),
+               "nt": p.nt, "nx": p.nx}
+        return c, ld, out, t_ld + t_rows
     if path == "force":
         out = {"G": G, "F": oforce.force(p.E, p.phi, p.n_stab)}
     elif path == "gtau":
@@ -121,10 +138,56 @@ def _pool(cores):
     return pool
 
 
-def oracle_sample(pool, name, configs, path="force"):
+def oracle_sample(pool, name, configs, path="force", rows=None):
+    """Run the oracle over `configs` in the pool; rows: None, or per configuration the force rows
+    to evaluate (force path only)."""
     t0 = time.perf_counter()
-    res = pool.map(_oracle_worker, [(name, c, path) for c in configs])
+    if rows is None:
+        work = [(name, c, path) for c in configs]
+    else:
+        work = [(name, c, path, r) for c, r in zip(configs, rows)]
+    # longest first, so that the pool's last task is a short one
+    work.sort(key=lambda a: -_oracle_cost(a))
+    res = pool.map(_oracle_worker, work, chunksize=1)
+    res.sort(key=lambda r: r[0])
     return res, time.perf_counter() - t0
+
+
+def _oracle_cost(a):
+    if a[0] != "uneven512":
+        return 0
+    import fd_inputs as fi
+
+    L, nt = fi.uneven_sizes(1, a[1])[0]
+    return (2 * L * L) ** 3 * nt
+
+
+def uneven_sample(indices):
+    """Stratified sample of an uneven batch: the first configuration of every (Nx, Nt) class
+    among `indices`, with one force row (slice Nt/2) each.  Returns (configs, rows, class of
+    every index)."""
+    import fd_inputs as fi
+
+    cls = {}
+    first = {}
+    for c in indices:
+        L, nt = fi.uneven_sizes(1, c)[0]
+        cls[c] = (2 * L * L, nt)
+        first.setdefault(cls[c], c)
+    configs = sorted(first.values())
+    rows = [[cls[c][1] // 2] for c in configs]
+    return configs, rows, cls
+
+
+def uneven_cpu_rate(res, cls, indices, cores):
+    """configs/s of the oracle on the uneven batch `indices`, extrapolated from the stratified
+    sample: a configuration costs its class's log det + G time plus Nt times its class's time
+    per force row, and the configurations are spread over `cores` processes."""
+    per = {}
+    for c, _, out, _ in res:
+        per[(out["nx"], out["nt"])] = out["t_ld"] + out["nt"] * out["t_row"]
+    total = sum(per[cls[c]] for c in indices)
+    return len(indices) / (total / cores), total
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -243,9 +306,11 @@ def run_reference(args):
         name = "sparse288"  # the same default workload as our arm of that path
     if args.path in ("sparse", "bss"):
         args.steps = max(1, min(args.steps, 10))
-    batch = len(fi.workload(name, batch=None)) if name != "tiny8" else 1
     cores = os.cpu_count() or 1
     pool = _pool(cores)
+    if name == "uneven512":
+        return _run_reference_uneven(args, pool, cores)
+    batch = len(fi.workload(name, batch=None)) if name != "tiny8" else 1
     # per-step sample: about 8 configurations per core in all over 20 steps' worth of oracle
     # time, at least one per core, so that any --steps K finishes within a few minutes
     per_step = max(cores, min(8 * cores, (8 * cores * 20) // max(1, args.steps)))
@@ -278,6 +343,47 @@ def run_reference(args):
     return 0
 
 
+def _run_reference_uneven(args, pool, cores):
+    """The oracle on the uneven batch: every step runs the stratified sample (one configuration
+    per (Nx, Nt) class, log det + G in full and one force row) and extrapolates to the batch."""
+    if args.path != "force":
+        raise SystemExit("the uneven workload is measured on the force path")
+    ws = _dist()[0]
+    indices = list(range(512))
+    configs, rows, cls = uneven_sample(indices)
+    small = [k for k, c in enumerate(configs) if cls[c][0] <= 18]
+    for _ in range(args.warmup):
+        oracle_sample(pool, "uneven512", [configs[k] for k in small], "force",
+                      [rows[k] for k in small])
+    rates, totals = [], []
+    for _ in range(args.steps):
+        res, _ = oracle_sample(pool, "uneven512", configs, "force", rows)
+        r, tot = uneven_cpu_rate(res, cls, indices, cores)
+        rates.append(r)
+        totals.append(tot)
+    pool.close()
+    value = len(rates) / sum(1.0 / r for r in rates)  # 512 configurations per step
+    sample = ("one configuration per (Nx, Nt) class (%d classes) per step: log det + G in full and "
+              "one force row (a full stabilised evaluation on the rotated field), scaled to the "
+              "class's Nt rows and to the 512 configurations, spread over %d processes"
+              % (len(configs), cores))
+    line = {
+        "impl": "reference", "metric": PATHS["force"]["metric"], "value": value,
+        "unit": "configs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * 512 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT["uneven512"] + "; " + PATHS["force"]["what"],
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "configs/s", "cores": cores, "kind": "oracle",
+                         "sample": sample,
+                         "cpu_seconds_per_512": statistics.mean(totals)},
+        "e2e": {"value": value, "unit": "configs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- our arm
 def _measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -287,11 +393,12 @@ def _measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def _time_batch(batch, ctx, steps, flush, stream, barrier, sample_clocks, gpu):
+def _time_batch(batch, ctx, steps, flush, stream, barrier, sample_clocks, gpu, timing_runs=5):
     """Time `steps` calls (CUDA events on the launch stream, L2 flushed before each), then a
     separate short pass with per-launch events for the per-kernel roofline.  Per-launch events sit
-    between the launches, so in that pass the phases run one after the other instead of
-    overlapping; the timed steps have no events between launches."""
+    between the launches, so in that pass the phases of a size class run one after the other
+    instead of overlapping (size classes still run side by side on their own streams); the timed
+    steps have no events between launches."""
     import torch
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -314,7 +421,7 @@ def _time_batch(batch, ctx, steps, flush, stream, barrier, sample_clocks, gpu):
             clk.__exit__()
     kernel_ms = []
     ctx.set_timing(True)
-    for _ in range(min(steps, 5)):
+    for _ in range(min(steps, timing_runs)):
         flush.zero_()
         batch.run()
         kernel_ms.append(ctx.last_kernel_ms())
@@ -330,35 +437,80 @@ def _scaled_err(a, ref):
     return float(np.abs(a - ref).max()) / max(1.0, float(np.abs(ref).max())) ** 2
 
 
-def _errors(batch, res, path="force"):
+def _errors(batch, res, path="force", pos=None):
+    """Errors of the GPU results against the oracle's on the sampled configurations (pos maps a
+    configuration index to its position in the batch; identity by default)."""
     import numpy as np
 
     ld = batch.logdet_buf.cpu().numpy()
     e_ld = 0.0
     e = {}
+    per_nx = {}
     for c, ldr, out, _ in res:
-        g = complex(ld[c, 0], ld[c, 1])
+        k = c if pos is None else pos[c]
+        g = complex(ld[k, 0], ld[k, 1])
         dim = abs(np.angle(np.exp(1j * (g.imag - ldr.imag))))
-        e_ld = max(e_ld, max(abs(g.real - ldr.real), dim) / abs(ldr))
+        el = max(abs(g.real - ldr.real), dim) / abs(ldr)
+        e_ld = max(e_ld, el)
         if path == "force":
-            e["G_abs_over_maxG2"] = max(e.get("G_abs_over_maxG2", 0.0),
-                                        _scaled_err(batch.G[c].cpu().numpy(), out["G"]))
-            e["F_abs_over_maxF2"] = max(e.get("F_abs_over_maxF2", 0.0),
-                                        _scaled_err(batch.F[c].cpu().numpy(), out["F"]))
+            eg = _scaled_err(batch.G[k].cpu().numpy(), out["G"])
+            e["G_abs_over_maxG2"] = max(e.get("G_abs_over_maxG2", 0.0), eg)
+            if "F_rows" in out:
+                Fk = batch.F[k].cpu().numpy()
+                ef = max(float(np.abs(Fk[r] - v).max()) / max(1.0, float(np.abs(v).max())) ** 2
+                         for r, v in out["F_rows"].items())
+                e["F_rows_abs_over_maxF2"] = max(e.get("F_rows_abs_over_maxF2", 0.0), ef)
+                # Im F = 1/2 on every entry (particle-hole symmetry of the bipartite lattice)
+                e["ImF_minus_half_max"] = max(e.get("ImF_minus_half_max", 0.0),
+                                              float(np.abs(Fk.imag - 0.5).max()))
+                nx = out["nx"]
+                d = per_nx.setdefault(str(nx), {"logdet_rel": 0.0, "G": 0.0, "F_rows": 0.0})
+                d["logdet_rel"] = max(d["logdet_rel"], el)
+                d["G"] = max(d["G"], eg)
+                d["F_rows"] = max(d["F_rows"], ef)
+            else:
+                e["F_abs_over_maxF2"] = max(e.get("F_abs_over_maxF2", 0.0),
+                                            _scaled_err(batch.F[k].cpu().numpy(), out["F"]))
         elif path == "gtau":
-            gt = batch.Gtau[c].cpu().numpy()
+            gt = batch.Gtau[k].cpu().numpy()
             e["Gtau_abs_over_max2"] = max(
                 [e.get("Gtau_abs_over_max2", 0.0)] +
                 [_scaled_err(gt[t], out["Gtau"][t]) for t in range(gt.shape[0])])
         else:
-            nf = complex(*batch.nferm_buf[c].cpu().numpy())
+            nf = complex(*batch.nferm_buf[k].cpu().numpy())
             e["nferm_abs_over_maxG2"] = max(e.get("nferm_abs_over_maxG2", 0.0),
                                             abs(nf - out["nferm"]) / max(1.0, out["gmax"]) ** 2)
             e["R_abs_over_max"] = max(e.get("R_abs_over_max", 0.0),
-                                      float(np.abs(batch.R[c].cpu().numpy() - out["R"]).max())
+                                      float(np.abs(batch.R[k].cpu().numpy() - out["R"]).max())
                                       / max(1.0, float(np.abs(out["R"]).max())))
     e.update({"logdet_rel": e_ld, "configs_checked": len(res)})
+    if per_nx:
+        e["per_nx"] = per_nx
     return e
+
+
+PHASE_OF_KERNEL = {1: "A", 2: "B", 3: "C"}
+KERNEL_NAME = {0: "k_fwd_", 1: "k_chain_", 2: "k_boundary_", 3: "k_wrap_", 8: "k_merge_"}
+
+
+def launch_flops(plan, probs, phase_flops):
+    """Algorithmic (FP64-pipe, tensor) flops of every launch of the plan: the phase of the
+    launch summed over the configurations of its size class, split by where the launch runs
+    (a launch on the FP64 kernels counts its products as FP64 work)."""
+    out = []
+    for rec in plan:
+        k = rec["kernel"]
+        which, mixed = k % 4 if k < 8 else 8, k >= 4 and k < 8
+        ph = PHASE_OF_KERNEL.get(which)
+        f64 = tns = 0.0
+        if ph:
+            for p in probs:
+                if p.nx == rec["nx"]:
+                    pf = phase_flops(p.nx, p.nt, p.n_stab, mixed)[ph]
+                    f64 += pf["fp64"]
+                    tns += pf["tensor"]
+        out.append((f64, tns))
+    return out
 
 
 def run_ours(args):
@@ -368,7 +520,7 @@ def run_ours(args):
     import fd_inputs as fi
 
     name = args.workload
-    w_batch = 1 if name == "tiny8" else fi.WORKLOADS[name]["batch"]
+    uneven = name == "uneven512"
     cores = os.cpu_count() or 1
     pool = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -385,53 +537,77 @@ def run_ours(args):
                                               response_phase_flops)
 
     dev = torch.device("cuda", local)
-    mine = shard.shard_range(rank, w_batch)  # disjoint configuration indices per rank
-    probs = fi.workload(name, batch=w_batch, first=mine.start)
-    nx, nt, ns = probs[0].nx, probs[0].nt, probs[0].n_stab
-    # inputs resident on the device: one phi buffer for the batch; E, E^{-1} shared
-    phi_host = torch.from_numpy(np.stack([p.phi for p in probs])).pin_memory()
+    if uneven:
+        # the first 512 x ranks configurations of the uneven sequence, split by cost (LPT)
+        per_rank = 512
+        sizes = fi.uneven_sizes(per_rank * ws)
+        mine = shard.lpt_partition([(2 * L * L) ** 3 * nt for L, nt in sizes], ws)[rank]
+        probs = [fi.workload(name, batch=1, first=c)[0] for c in mine]
+    else:
+        per_rank = 1 if name == "tiny8" else fi.WORKLOADS[name]["batch"]
+        mine = list(shard.shard_range(rank, per_rank))  # disjoint configuration indices
+        probs = fi.workload(name, batch=per_rank, first=mine[0])
+    n_mine = len(probs)
+    n_total = per_rank * ws
+    pos = {c: k for k, c in enumerate(mine)}
+    # inputs resident on the device: one phi buffer for the batch (one host copy for e2e);
+    # E, E^{-1} (and A, the operator of the response traces) once per lattice
+    lat = {}
+    for p in probs:
+        if id(p.E) not in lat:
+            lat[id(p.E)] = tuple(torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+                                 for a in (p.E, p.Einv, p.A))
+    counts = [p.nt * p.nx for p in probs]
+    phi_host = torch.empty(sum(counts), dtype=torch.float64).pin_memory()
+    o = 0
+    for p, k in zip(probs, counts):
+        phi_host[o:o + k] = torch.from_numpy(np.ascontiguousarray(p.phi).ravel())
+        o += k
     phi_dev = phi_host.to(dev)
-    E = torch.from_numpy(probs[0].E).to(dev)
-    Einv = torch.from_numpy(probs[0].Einv).to(dev)
-    A = torch.from_numpy(probs[0].A).to(dev)  # operator of the response traces
+    phis, o = [], 0
+    for p, k in zip(probs, counts):
+        phis.append(phi_dev[o:o + k].view(p.nt, p.nx))
+        o += k
     spec = PATHS[args.path]
     ctx = api.Context(local)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    slow = uneven  # steps of seconds: fewer untimed and per-launch passes
+    timing_runs = 2 if slow else 5
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def make(prec):
-        ops = [A] * len(probs) if args.path == "observables" else None
-        b = api.Batch(ctx, [(E, Einv, phi_dev[c], p.n_stab) for c, p in enumerate(probs)],
-                      spec["want"], prec, ops)
+    def make(prec, warm):
+        ops = [lat[id(p.E)][2] for p in probs] if args.path == "observables" else None
+        b = api.Batch(ctx, [(lat[id(p.E)][0], lat[id(p.E)][1], phis[c], p.n_stab)
+                            for c, p in enumerate(probs)], spec["want"], prec, ops)
         b.reserve()
-        for _ in range(max(3, args.warmup)):
+        for _ in range(warm):
             b.run()
         barrier()
-        assert all(s == 0 for s in b.status()), "device status not OK"
+        st = b.status()
+        assert all(x == 0 for x in st), "device status not OK: %s" % (
+            [(c, x) for c, x in enumerate(st) if x][:8],)
         return b
 
     def allmax(x):
         return shard.max_over_ranks(x, dev)
 
-    n_total = w_batch * ws
     phase_flops = {"force": force_phase_flops, "gtau": gtau_phase_flops,
                    "observables": response_phase_flops}[args.path]
 
-    def step_flops(mixed):
-        pf = phase_flops(nx, nt, ns, mixed)
-        return sum(v["fp64"] + v["tensor"] for v in pf.values())
-
     # ---- headline path: device-resident timing, L2 flushed between steps
-    batch = make(args.prec)
+    warm = max(3, args.warmup)
+    batch = make(args.prec, warm)
     plan = batch.plan()
-    head = _time_batch(batch, ctx, args.steps, flush, stream, barrier, True, local)
+    lf = launch_flops(plan, probs, phase_flops)
+    flops_step = sum(a + b for a, b in lf)
+    head = _time_batch(batch, ctx, args.steps, flush, stream, barrier, True, local, timing_runs)
     total_ms = allmax(head["total_ms"])
-    value = shard.aggregate_rate(w_batch, ws, args.steps, total_ms)
+    value = n_total * args.steps / (total_ms * 1e-3)
 
     # ---- end to end through the public API: pinned host inputs in, results out
     outs = {"force": [batch.logdet_buf, batch.G_flat, batch.F_flat],
@@ -461,66 +637,72 @@ def run_ours(args):
     fp64 = None
     b64 = None
     if args.prec != "fp64" and not args.no_fp64_path:
-        b64 = make("fp64")
-        r64 = _time_batch(b64, ctx, max(3, args.steps // 2), flush, stream, barrier, False, local)
-        ms64 = allmax(r64["total_ms"]) / max(3, args.steps // 2)
+        steps64 = 2 if slow else max(3, args.steps // 2)
+        b64 = make("fp64", 1 if slow else 3)
+        plan64 = b64.plan()
+        r64 = _time_batch(b64, ctx, steps64, flush, stream, barrier, False, local,
+                          1 if slow else 5)
+        ms64 = allmax(r64["total_ms"]) / steps64
+        lf64 = launch_flops(plan64, probs, phase_flops)
+        km64 = [statistics.mean(k[i] for k in r64["kernel_ms"]) for i in range(len(plan64))]
         fp64 = {"value": n_total / (ms64 * 1e-3), "unit": "configs/s", "ms_per_step": ms64,
-                "tflops": step_flops(False) * n_total / (ms64 * 1e-3) / 1e12,
-                "kernel_ms": [statistics.mean(k[i] for k in r64["kernel_ms"]) for i in range(3)]}
+                "steps": steps64,
+                "tflops": sum(a + b for a, b in lf64) * n_total / n_mine / (ms64 * 1e-3) / 1e12,
+                "kernel_ms": {"%s%d" % (KERNEL_NAME.get(r["kernel"] % 4 if r["kernel"] < 8
+                                                        else 8, "k"), r["nx"]): m
+                              for r, m in zip(plan64, km64)}}
 
     if rank != 0:
         torch.distributed.destroy_process_group()
         return 0
 
-    # ---- roofline: the step is three launches (chains, boundary Green's functions, wraps);
-    #      the longest one is reported.  Per-launch durations from CUDA events on the launch
-    #      stream.
+    # ---- roofline of the longest launch.  Per-launch durations from CUDA events on the
+    #      launch streams.
     peaks, peak_src = _measured_peaks()
     peak_fp64 = ctx.measure_fp64_peak() / 1e3
     tf32_peak = peaks["bf16_tflops"] / 2.0
-    mixed = args.prec != "fp64"
-    pf = phase_flops(nx, nt, ns, mixed)
-    per_launch = [statistics.mean(k[i] for k in head["kernel_ms"]) for i in range(3)]
-    kinds = [p["kernel"] for p in plan]
-    names = [("k_chain_", "k_boundary_", "k_wrap_")[i] + ("mixed" if kinds[i] >= 4 else "fp64")
-             for i in range(3)]
+    per_launch = [statistics.mean(k[i] for k in head["kernel_ms"]) for i in range(len(plan))]
     phases = []
-    for i, key in enumerate("ABC"):
+    for i, rec in enumerate(plan):
+        k = rec["kernel"]
+        nm = KERNEL_NAME.get(k % 4 if k < 8 else 8, "k_") + ("mixed" if 4 <= k < 8 else "fp64")
         ms = per_launch[i]
-        f64 = pf[key]["fp64"] * w_batch / (ms * 1e-3) / 1e12
-        tns = pf[key]["tensor"] * w_batch / (ms * 1e-3) / 1e12
-        phases.append({"kernel": names[i], "ms": ms, "fp64_tflops": f64,
-                       "fp64_frac": f64 / peak_fp64, "tensor_tflops": tns,
+        f64 = lf[i][0] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+        tns = lf[i][1] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+        phases.append({"kernel": nm, "nx": rec["nx"], "configs": rec["configs"], "ms": ms,
+                       "fp64_tflops": f64, "fp64_frac": f64 / peak_fp64, "tensor_tflops": tns,
                        "tensor_frac": tns / tf32_peak})
-    dom = max(range(3), key=lambda i: per_launch[i])
+    dom = max(range(len(plan)), key=lambda i: per_launch[i])
     k_ms = per_launch[dom]
-    what = {0: "the chain kernel (QRs, assembly%s)" % ("" if mixed else ", slice products"),
-            1: "the boundary kernel (boundary Green's functions: GEMMs, LU, solves)",
-            2: "the wrap kernel (%s)" % ("wrap products" if args.path != "gtau"
-                                         else "slice propagation of G(tau,0)")}[dom]
-    if phases[dom]["fp64_tflops"] > 0 or phases[dom]["tensor_tflops"] == 0:
-        achieved = phases[dom]["fp64_tflops"]
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp64,
+    dk = plan[dom]["kernel"] % 4
+    what = {0: "the log det/G kernel", 1: "the chain kernel (slice products, QRs, assembly)",
+            2: "the boundary kernel (boundary Green's functions: GEMMs, LU, solves)",
+            3: "the wrap kernel (%s)" % ("wrap products" if args.path != "gtau"
+                                         else "slice propagation of G(tau,0)")}.get(dk, "")
+    what += " of the Nx=%d size class" % plan[dom]["nx"]
+    P = phases[dom]
+    if P["fp64_tflops"] > 0 or P["tensor_tflops"] == 0:
+        roof = {"bound": "alu", "achieved": P["fp64_tflops"], "peak": peak_fp64,
+                "unit": "TFLOP/s", "frac": P["fp64_tflops"] / peak_fp64,
                 "what": "FP64 algorithmic work of %s per launch over its CUDA-event duration"
                         % what,
                 "peak_source": "FP64 DFMA probe over all SMs in this run (fd_measure_fp64_peak)"}
     else:
-        achieved = phases[dom]["tensor_tflops"]
-        roof = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                "frac": achieved / tf32_peak,
+        roof = {"bound": "tensor", "achieved": P["tensor_tflops"], "peak": tf32_peak,
+                "unit": "TFLOP/s", "frac": P["tensor_tflops"] / tf32_peak,
                 "what": "tensor-core work of %s per launch over its CUDA-event duration" % what,
                 "peak_source": "%s bf16 dense x 1/2 (TF32:BF16 nominal ratio)" % peak_src}
-    roof.update({"traffic": _traffic(names[dom], name, args.prec, args.path),
-                 "kernel": names[dom], "kernel_ms": k_ms,
+    roof.update({"traffic": _traffic(P["kernel"], name, args.prec, args.path),
+                 "kernel": P["kernel"], "kernel_ms": k_ms,
                  "kernel_ms_from": "a separate pass with CUDA events between the launches "
-                                   "(phases one after the other; in the timed steps they overlap)",
+                                   "(phases of a size class one after the other; in the timed "
+                                   "steps they overlap)",
                  "fp64_issue_cycles": dict(zip(("one_lane", "full_warp", "one_of_8_warps"),
                                                ctx.measure_fp64_issue())),
                  "phases": phases})
-    if mixed and phases[dom]["tensor_tflops"] > 0 and roof["bound"] == "alu":
-        roof["tensor"] = {"achieved": phases[dom]["tensor_tflops"], "peak": tf32_peak,
-                          "unit": "TFLOP/s", "frac": phases[dom]["tensor_tflops"] / tf32_peak,
+    if P["tensor_tflops"] > 0 and roof["bound"] == "alu":
+        roof["tensor"] = {"achieved": P["tensor_tflops"], "peak": tf32_peak,
+                          "unit": "TFLOP/s", "frac": P["tensor_tflops"] / tf32_peak,
                           "what": "tensor-core work of the same kernel (a product counted once, "
                                   "not x3 for split TF32)",
                           "peak_source": "%s bf16 dense x 1/2 (TF32:BF16 nominal ratio)"
@@ -530,15 +712,28 @@ def run_ours(args):
     cpu = None
     err = None
     if pool is not None:
-        sample = list(range(min(w_batch, 8 * cores)))
-        res, dt = oracle_sample(pool, name, sample, args.path)
+        if uneven:
+            configs, rows, cls = uneven_sample(mine)
+            res, dt = oracle_sample(pool, name, configs, args.path, rows)
+            rate, tot = uneven_cpu_rate(res, cls, mine, cores)
+            cpu = {"value": rate, "unit": "configs/s", "cores": cores, "kind": "oracle",
+                   "sample": "one configuration per (Nx, Nt) class (%d classes): log det + G in "
+                             "full and one force row (a full stabilised evaluation on the "
+                             "rotated field), scaled to the class's Nt rows and to the %d "
+                             "configurations, spread over %d processes"
+                             % (len(configs), n_mine, cores),
+                   "cpu_seconds_per_step": tot, "sample_wall_s": dt}
+        else:
+            sample = list(range(min(n_mine, 8 * cores)))
+            res, dt = oracle_sample(pool, name, sample, args.path)
+            cpu = {"value": len(sample) / dt, "unit": "configs/s", "cores": cores,
+                   "kind": "oracle",
+                   "sample": "%d of the %d configurations (%s), one per process"
+                             % (len(sample), n_mine, spec["what"])}
         pool.close()
-        cpu = {"value": len(sample) / dt, "unit": "configs/s", "cores": cores, "kind": "oracle",
-               "sample": "%d of the %d configurations (%s), one per process"
-                         % (len(sample), w_batch, spec["what"])}
-        err = {args.prec: _errors(batch, res, args.path)}
+        err = {args.prec: _errors(batch, res, args.path, pos)}
         if b64 is not None:
-            err["fp64"] = _errors(b64, res, args.path)
+            err["fp64"] = _errors(b64, res, args.path, pos)
 
     line = {
         "metric": spec["metric"],
@@ -546,7 +741,7 @@ def run_ours(args):
         "unit": "configs/s",
         "n_gpus": ws,
         "steps": args.steps,
-        "warmup": max(3, args.warmup),
+        "warmup": warm,
         "ms_per_step": total_ms / args.steps,
         "higher_is_better": True,
         "scaling": "weak",
@@ -556,7 +751,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD_TEXT[name] + "; " + spec["what"], "prec": args.prec,
                    "plan": plan,
                    "l2": "flushed between timed steps (%d MB write)" % (FLUSH_BYTES >> 20)},
-        "tflops": step_flops(mixed) * n_total * args.steps / (total_ms * 1e-3) / 1e12,
+        "tflops": flops_step * n_total * args.steps / n_mine / (total_ms * 1e-3) / 1e12,
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roof,
@@ -957,17 +1152,23 @@ def run_sparse(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 5 for uneven512, else 500)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--prec", choices=("fp64", "tf32", "3xtf32"), default="3xtf32")
-    ap.add_argument("--workload", choices=tuple(WORKLOAD_TEXT), default="batch18")
+    ap.add_argument("--workload", choices=tuple(WORKLOAD_TEXT), default=None,
+                    help="default uneven512 (force path), batch18 (other paths), sparse288 (sparse)")
     ap.add_argument("--path", choices=tuple(PATHS), default="force",
                     help="what one step computes (default: log det + G + force)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true",
                     help="skip the FP64-path measurement reported beside the mixed path")
     args = ap.parse_args()
+    if args.workload is None:
+        args.workload = "uneven512" if args.path == "force" else "batch18"
+    if args.steps is None:
+        args.steps = 5 if args.workload == "uneven512" else 500
     if args.impl == "reference":
         return run_reference(args)
     if args.path == "bss":

@@ -158,19 +158,22 @@ UNEVEN_L = (2, 3, 4, 5, 6, 7, 8, 12)
 UNEVEN_NT = (32, 64, 128, 256, 512, 1024)
 
 
-def _uneven(batch: int = 512, n_stab: int = 16) -> List[Problem]:
+def uneven_sizes(batch: int = 512, first: int = 0) -> List[tuple]:
+    """(L, Nt) of configurations first .. first+batch-1 of the uneven sequence (no fields drawn)."""
+    pairs = [(L, nt) for L in UNEVEN_L for nt in UNEVEN_NT]
+    order = [pairs[i % len(pairs)] for i in range(512)]
+    perm = np.random.default_rng(1004).permutation(len(order))
+    return [order[perm[c % 512]] for c in range(first, first + batch)]
+
+
+def _uneven(batch: int = 512, n_stab: int = 16, first: int = 0) -> List[Problem]:
+    """Configurations first .. first+batch-1 of the uneven sequence.  Every run of 512
+    consecutive indices (k*512 .. k*512+511) holds the 48 (L, Nt) pairs round-robin -- the first
+    32 pairs 11 times, the other 16 pairs 10 times -- in the order of one seeded shuffle; the field
+    of index c is drawn from seed (1004, c), so later runs repeat the size mix with new fields."""
     seed = 1004
-    pairs = [(L, nt) for L in UNEVEN_L for nt in UNEVEN_NT]  # 48 pairs
-    order = []
-    i = 0
-    while len(order) < batch:
-        order.append(pairs[i % len(pairs)])
-        i += 1
-    rng = np.random.default_rng(seed)
-    perm = rng.permutation(len(order))
     probs = []
-    for c, k in enumerate(perm):
-        L, nt = order[k]
+    for c, (L, nt) in zip(range(first, first + batch), uneven_sizes(batch, first)):
         beta = nt / 16.0
         probs.append(make_problem(L, nt, beta, 3.0, min(n_stab, nt), seed, c))
     return probs
@@ -181,7 +184,7 @@ def workload(name: str, batch: int | None = None, n_stab: int | None = None,
     """The configurations of a named workload (optionally ``batch`` of them, starting at
     configuration index ``first``; shards of a multi-GPU run use disjoint index ranges)."""
     if name == "uneven512":
-        return _uneven(batch or 512, n_stab or 16)
+        return _uneven(512 if batch is None else batch, n_stab or 16, first)
     w = WORKLOADS[name]
     b = w["batch"] if batch is None else batch
     ns = w["n_stab"] if n_stab is None else n_stab

@@ -311,6 +311,19 @@ int fd_measure_fp64_peak(fd_ctx* ctx, double* gflops);
  * issue independent DFMAs (the SM's shared FP64 pipe).  Synchronous. */
 int fd_measure_fp64_issue(fd_ctx* ctx, double* cycles);
 
+/* Self-check of the hand-written FP64 refinements that the serial QR and LU steps use in place
+ * of IEEE division and square root (an FP32 hardware estimate refined by Newton or by
+ * Householder's third-order iteration; Section 7's QR re-orthogonalisation is where they run).
+ * For each argument i (x, y, z: device, n float64 each) writes 16 float64 to out[16 i ..]
+ * (device): 0 rcp64(x), 1 CUDA's correctly rounded 1/x, 2 rsqrt64(x), 3 CUDA's 1/sqrt(x) as
+ * two correctly rounded operations, 4 sqrt64(x), 5 CUDA's correctly rounded sqrt(x); then the
+ * Householder reflector of a column with leading entry x + i y and squared norm z below it:
+ * 6, 7 alpha = -(x/|x|) sqrt(|x|^2 + z), 8, 9 1/c = conj(x) / (|x| (|x| + sqrt(|x|^2 + z))),
+ * 10 tau = 1 + |x| / sqrt(|x|^2 + z), 11 1 if the column is zero; 12..15 zero.  Runs on the
+ * current device, asynchronously on `stream`.  Returns FD_OK, FD_ERR_INVALID or FD_ERR_CUDA. */
+int fd_check_fp64_refinements(const double* x, const double* y, const double* z, int n,
+                              double* out, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * fd_logdet_noalloc: log det (and optionally G) without any memory allocation.
  * The paper has no counterpart; this entry point exists for callers that cannot allocate

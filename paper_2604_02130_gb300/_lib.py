@@ -86,6 +86,7 @@ SIGNATURES = [
     ("fd_last_launch_count", _I, [_VP]),
     ("fd_measure_fp64_peak", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
     ("fd_measure_fp64_issue", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    ("fd_check_fp64_refinements", _I, [_VP, _VP, _VP, _I, _VP, _VP]),
     ("fd_set_timing", _I, [_VP, _I]),
     ("fd_last_kernel_ms", _I, [_VP, ctypes.POINTER(ctypes.c_double), _I]),
     ("fd_logdet_noalloc", _I, [_I, _PP, _VP, _VP, _VP, _VP]),

@@ -469,21 +469,44 @@ def bss_update(G: Sequence[torch.Tensor], phi_rows: Sequence[torch.Tensor],
 
 
 class FermionLogDet(torch.autograd.Function):
-    """log det(1 + B_Nt...B_1) of one configuration as a differentiable function of phi.
+    """log det(1 + B_Nt...B_1) as a differentiable function of the field phi, for one
+    configuration (phi of shape (nt, nx), complex128 scalar out) or a batch sharing E
+    (phi of shape (batch, nt, nx), (batch,) out).
 
-    forward(phi, E, Einv, n_stab, prec) -> complex128 scalar.  The backward pass uses the
-    adjoint force sweep (fd_force): with F = d logdet / d phi (complex, holomorphic in phi),
-    torch's convention for a real input gives grad_phi = Re(conj(grad_out) * F)."""
+    forward(phi, E, Einv, n_stab, prec) runs fd_logdet only: no checkpoints are kept.  The
+    backward pass runs the adjoint force sweep (fd_force), which recomputes the stabilised
+    checkpoints every n_stab slices from the field instead of storing partial products, and
+    returns torch's gradient for a real input, grad_phi = Re(conj(grad_out) * F) with
+    F = d logdet / d phi (Section 4, Eq. response_result).  A forward under torch.no_grad(), or
+    with a phi that does not require a gradient, therefore costs one log det call."""
+
+    @staticmethod
+    def _problems(phi, E, Einv, n_stab):
+        phis = phi.detach()
+        phis = (phis if phis.dim() == 3 else phis.unsqueeze(0)).contiguous()
+        return phis, [(E, Einv, phis[k], n_stab) for k in range(phis.shape[0])]
 
     @staticmethod
     def forward(ctx_, phi, E, Einv, n_stab, prec="fp64"):
+        if phi.dim() not in (2, 3):
+            raise ValueError("phi must be (nt, nx) or (batch, nt, nx)")
         c = default_context()
-        r = Batch(c, [(E, Einv, phi.detach().contiguous(), n_stab)], "force", prec).run()
-        ctx_.save_for_backward(r.F[0])
-        return r.logdet[0].clone()
+        phis, probs = FermionLogDet._problems(phi, E, Einv, n_stab)
+        r = Batch(c, probs, "logdet", prec).run()
+        ctx_.save_for_backward(phis)
+        ctx_.E, ctx_.Einv, ctx_.n_stab, ctx_.prec = E, Einv, n_stab, prec
+        ctx_.batched = phi.dim() == 3
+        out = r.logdet.clone()
+        return out if ctx_.batched else out[0]
 
     @staticmethod
     def backward(ctx_, grad_out):
-        (F,) = ctx_.saved_tensors
-        g = (grad_out.conj() * F).real
-        return g, None, None, None, None
+        (phis,) = ctx_.saved_tensors
+        if ctx_.Einv is None:
+            raise ValueError("the gradient needs E^{-1} (Einv)")
+        probs = [(ctx_.E, ctx_.Einv, phis[k], ctx_.n_stab) for k in range(phis.shape[0])]
+        r = Batch(default_context(), probs, "force", ctx_.prec).run()
+        F = torch.stack(r.F)
+        g = grad_out if ctx_.batched else grad_out.reshape(1)
+        grad = (g.conj().view(-1, 1, 1) * F).real
+        return (grad if ctx_.batched else grad[0]), None, None, None, None

@@ -1515,6 +1515,14 @@ int fd_measure_fp64_issue(fd_ctx* ctx, double* cycles) {
   return FD_OK;
 }
 
+int fd_check_fp64_refinements(const double* x, const double* y, const double* z, int n,
+                              double* out, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y || !z || !out))) return FD_ERR_INVALID;
+  return fd::run_refine_check(x, y, z, n, out, (cudaStream_t)stream) == cudaSuccess
+             ? FD_OK
+             : FD_ERR_CUDA;
+}
+
 int fd_measure_fp64_peak(fd_ctx* ctx, double* gflops) {
   if (!ctx || !gflops) return FD_ERR_INVALID;
   FD_CUDA(ctx, cudaSetDevice(ctx->device));

@@ -70,5 +70,8 @@ cudaError_t launch_bss(const BssSlice* slices, int batch, int maxn, double* dlog
 // FP64 throughput probe
 cudaError_t run_fp64_probe(int grid, int threads, int iters, double* out, cudaStream_t stream);
 cudaError_t run_fp64_issue(double* out3);
+// self-check of the FP64 refinements beside CUDA's IEEE operations (16 values per argument)
+cudaError_t run_refine_check(const double* x, const double* y, const double* z, int n,
+                             double* out, cudaStream_t stream);
 
 }  // namespace fd

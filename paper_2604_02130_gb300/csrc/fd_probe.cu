@@ -2,6 +2,7 @@
 //
 // Every thread runs 8 independent chains of dependent DFMAs; the result is written so the
 // compiler cannot drop the work.  GFLOP/s = 2 * grid * threads * iters * 8 / time.
+#include "fd_fp64.cuh"
 #include "fd_kernels.h"
 
 namespace fd {
@@ -93,6 +94,40 @@ cudaError_t run_fp64_issue(double* out3) {
   cudaFree(d_out);
   cudaFree(sink);
   return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+// Self-check of the hand-written FP64 refinements used by the QR and LU steps (rcp64, rsqrt64,
+// sqrt64 and reflector_math), each beside CUDA's correctly rounded IEEE operations on the same
+// argument: out[16 i + k] for argument i --
+//   0 rcp64(x)   1 __drcp_rn(x)   2 rsqrt64(x)   3 __drcp_rn(__dsqrt_rn(x))   4 sqrt64(x)
+//   5 __dsqrt_rn(x)   6, 7 alpha   8, 9 1/c   10 tau   11 zero flag  of reflector_math(x + i y, z)
+//   12..15 zero.
+__global__ void k_refine_check(const double* x, const double* y, const double* z, int n,
+                               double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = x[i];
+  double* o = out + 16 * (size_t)i;
+  o[0] = rcp64(a);
+  o[1] = __drcp_rn(a);
+  o[2] = rsqrt64(a);
+  o[3] = __drcp_rn(__dsqrt_rn(a));
+  o[4] = sqrt64(a);
+  o[5] = __dsqrt_rn(a);
+  const Refl r = reflector_math(cx(a, y[i]), z[i]);
+  o[6] = r.alpha.re;
+  o[7] = r.alpha.im;
+  o[8] = r.cinv.re;
+  o[9] = r.cinv.im;
+  o[10] = r.tau;
+  o[11] = r.zero ? 1.0 : 0.0;
+  for (int k = 12; k < 16; ++k) o[k] = 0.0;
+}
+
+cudaError_t run_refine_check(const double* x, const double* y, const double* z, int n,
+                             double* out, cudaStream_t stream) {
+  if (n > 0) k_refine_check<<<(n + 127) / 128, 128, 0, stream>>>(x, y, z, n, out);
+  return cudaGetLastError();
 }
 
 }  // namespace fd

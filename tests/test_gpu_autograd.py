@@ -64,3 +64,35 @@ def test_gradient_matches_finite_differences_of_the_forward():
             vals.append(complex(api.FermionLogDet.apply(q, E, Einv, p.n_stab).item()).real)
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(fd - g[t, x]) < 1e-6 * max(1.0, abs(g[t, x])), (t, x, fd, g[t, x])
+
+
+def test_batched_gradient_and_lazy_forward():
+    """A batch of fields through one call: the forward runs the log det kernels only (no force
+    sweep, no checkpoints); the backward's force sweep gives every configuration's gradient."""
+    from paper_2604_02130_gb300 import api
+
+    probs = [fi.make_problem(3, 32, 4.0, 3.0, 8, 1201, c) for c in range(5)]
+    E, Einv, _ = _tensors(probs[0])
+    phi0 = torch.stack([_tensors(p)[2] for p in probs])
+    ctx = api.default_context()
+    ref_plan = api.Batch(ctx, [(E, Einv, phi0[k], 8) for k in range(5)], "logdet").plan()
+    with torch.no_grad():
+        ld = api.FermionLogDet.apply(phi0, E, Einv, 8)
+    torch.cuda.synchronize()
+    # the log det plan's launches only (chain segments and merge, or one log det kernel)
+    assert ctx.last_launch_count() == len(ref_plan)
+    assert all(r["kernel"] % 4 in (0, 1) or r["kernel"] == 8 for r in ref_plan)
+    phi = phi0.clone().requires_grad_(True)
+    ld2 = api.FermionLogDet.apply(phi, E, Einv, 8)
+    assert torch.equal(ld, ld2.detach())
+    w = torch.tensor([0.5 - 0.25j, 1.0, -2.0 + 1j, 0.0, 1j], dtype=torch.complex128,
+                     device=phi.device)
+    (ld2 * w).real.sum().backward()  # torch hands backward grad_out = conj(w)
+    torch.cuda.synchronize()
+    g = phi.grad.cpu().numpy()
+    for c, p in enumerate(probs):
+        ref_ld, _ = stable.logdet_green(p.E, p.phi, p.n_stab)
+        assert logdet_err(complex(ld[c].item()), ref_ld) <= LOGDET_RTOL_FP64
+        F = oforce.force(p.E, p.phi, p.n_stab)
+        want = (w[c].item() * F).real  # d Re(w logdet) / d phi = Re(w F)
+        assert np.abs(g[c] - want).max() <= F_ATOL_FP64, c

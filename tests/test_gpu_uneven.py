@@ -1,0 +1,110 @@
+"""Full-size parity of the uneven workload: 512 configurations of Nx = 8..288 and Nt = 32..1024
+(delta = 1/16, so beta = Nt/16 reaches 64), log det + G + force in one call, as bench.py times
+it.  One configuration of every (Nx, Nt) class is compared with the oracle (log det, every entry
+of G, one force row: a full stabilised evaluation on the rotated field); every one of the 512
+configurations is held to the exact invariants of the bipartite lattice (Im log det = 1/2 sum phi
+mod pi, Re G_xx = 1/2, Im F = 1/2)."""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import fd_inputs as fi
+
+from gpu_helpers import MIXED_TOL, g_scaled_err, logdet_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# FP64 path: log det to the stated 1e-8 relative target; G and F rows to 1e-10 max(1, max|G|)^2
+# (a relative perturbation of the product moves G by -G dP G).
+FP64_LOGDET = 1e-8
+FP64_SCALED = 1e-10
+
+
+def _oracle(args):
+    c, row = args
+    from oracle import force as oforce
+    from oracle import stable
+
+    p = fi.workload("uneven512", batch=1, first=c)[0]
+    ld, G = stable.logdet_green(p.E, p.phi, p.n_stab)
+    return c, ld, G, oforce.force_rows(p.E, p.phi, p.n_stab, [row])[row]
+
+
+@pytest.fixture(scope="module")
+def sample():
+    sizes = fi.uneven_sizes(512)
+    first = {}
+    for c, (L, nt) in enumerate(sizes):
+        first.setdefault((2 * L * L, nt), c)
+    work = sorted(((c, nt // 2) for (nx, nt), c in first.items()),
+                  key=lambda a: -(2 * sizes[a[0]][0] ** 2) ** 3 * sizes[a[0]][1])
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(min(len(work), os.cpu_count() or 1)) as pool:
+            res = pool.map(_oracle, work, chunksize=1)
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {c: (ld, G, (row, Fr)) for (c, ld, G, Fr), (_, row) in zip(res, work)}
+
+
+@pytest.fixture(scope="module")
+def batch_inputs():
+    from gpu_helpers import to_dev
+
+    probs = fi.workload("uneven512")
+    dev = torch.device("cuda", 0)
+    lat = {}
+    tens = []
+    for p in probs:
+        if id(p.E) not in lat:
+            lat[id(p.E)] = (torch.from_numpy(p.E).to(dev), torch.from_numpy(p.Einv).to(dev))
+        tens.append((*lat[id(p.E)], torch.from_numpy(p.phi).to(dev), p.n_stab))
+    return probs, tens
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "fp64"])
+def test_uneven512_full_size(prec, sample, batch_inputs):
+    from paper_2604_02130_gb300 import api
+
+    probs, tens = batch_inputs
+    ctx = api.Context(0)
+    b = api.Batch(ctx, tens, "force+green", prec)
+    r = b.run()
+    torch.cuda.synchronize()
+    st = b.status()
+    assert all(s == 0 for s in st), [(c, s) for c, s in enumerate(st) if s][:8]
+    ld = r.logdet.cpu().numpy()
+    # invariants on every configuration
+    tol_inv = 1e-8 if prec == "fp64" else 5e-4
+    for c, p in enumerate(probs):
+        q = (ld[c].imag - 0.5 * p.phi.sum()) / np.pi
+        assert abs(q - round(q)) < 1e-8 * max(1.0, abs(ld[c])), (c, p.nx, p.nt)
+        G = r.G[c].cpu().numpy()
+        F = r.F[c].cpu().numpy()
+        scale = max(1.0, float(np.abs(G).max())) ** 2
+        assert np.abs(np.diag(G).real - 0.5).max() <= tol_inv * scale, (c, p.nx, p.nt)
+        assert np.abs(F.imag - 0.5).max() <= tol_inv * scale, (c, p.nx, p.nt)
+    # one configuration per (Nx, Nt) class against the oracle
+    for c, (ref_ld, ref_G, (row, ref_F)) in sample.items():
+        G = r.G[c].cpu().numpy()
+        F = r.F[c][row].cpu().numpy()
+        if prec == "fp64":
+            assert logdet_err(complex(ld[c]), ref_ld) <= FP64_LOGDET, (c, probs[c].nx)
+            assert g_scaled_err(G, ref_G) <= FP64_SCALED, (c, probs[c].nx, probs[c].nt)
+            assert np.abs(F - ref_F).max() <= FP64_SCALED * max(1.0, np.abs(ref_G).max()) ** 2
+        else:
+            tol = MIXED_TOL["3xtf32"]
+            assert logdet_err(complex(ld[c]), ref_ld) <= tol["logdet_rel"], (c, probs[c].nx)
+            assert g_scaled_err(G, ref_G) <= tol["G_scaled"], (c, probs[c].nx, probs[c].nt)
+            assert (np.abs(F - ref_F).max() / max(1.0, np.abs(ref_G).max()) ** 2
+                    <= tol["F_scaled"]), (c, probs[c].nx, probs[c].nt)
+    ctx.close()
