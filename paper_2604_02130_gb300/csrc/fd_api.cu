@@ -107,9 +107,11 @@ struct Outs {
 // One launch of a size class.  which: 0 log det/G, 1 force chains, 2 boundary G, 3 wraps.
 struct Phase {
   int which;
-  int mixed;  // 1: tcgen05 kernel (ML), 0: FP64 kernel (L)
+  int mixed;  // 1: tcgen05 kernel (ML, or BL when big), 0: FP64 kernel (L)
+  int big = 0;  // 1: streamed tcgen05 kernel (operands in global memory, BL)
   Layout L;
   fd::MLayout ML;
+  fd::BLayout BL{};
   int nthreads, smem, grid, occ;
   long long slot_bytes;
   size_t slot_off;  // byte offset of this launch's CTA slots in the group's scratch
@@ -131,6 +133,11 @@ struct Group {
   std::vector<size_t> fws_off;   // force: per configuration, bytes from the group's FWork base
   size_t fws_bytes;
   std::vector<int> nseg;         // time-parallel log det/G: segments per configuration (or empty)
+  // streamed tensor-core phases: chunked TF32 copies of the distinct E (and E^{-1}) matrices
+  std::vector<const double*> prep_src;
+  size_t prep_off = 0;   // byte offset from the group's scratch base
+  size_t prep_each = 0;  // bytes per prepared matrix (hi and lo planes)
+  int prep_Ma = 0, prep_Kp = 0, prep_three = 0;
   int qbase;                     // first queue counter of the group
   int grid;                      // largest grid of the phases (reported)
   int occ;
@@ -457,6 +464,102 @@ bool mixed_phase(fd_ctx* ctx, int n, int role, int which, bool three, int ntasks
   return true;
 }
 
+// Streamed tensor-core kernels (size classes whose operands do not fit the shared-memory tensor
+// tiles): chunked operands in global memory, a shared-memory pipeline of as many stages as fit
+// (at least two), TMEM for one 128-row tile of the product.  Returns smem_bytes = 0 if not even
+// two stages fit.
+fd::BLayout plan_big(fd_ctx* ctx, int n, bool three, bool wrap) {
+  fd::BLayout B;
+  memset(&B, 0, sizeof(B));
+  B.n = n;
+  B.three = three ? 1 : 0;
+  B.Kp = (n + 15) & ~15;
+  B.Ne = B.Kp;
+  B.Ma = (n + 127) & ~127;
+  B.Mc = (2 * n + 127) & ~127;
+  const int nb16 = (2 * n + 15) & ~15;
+  B.npass = (nb16 + 287) / 288;
+  B.Nw = ((nb16 + B.npass - 1) / B.npass + 15) & ~15;
+  B.Nb = B.npass * B.Nw;
+  B.nthreads = 256;
+  B.num_sms = ctx->num_sms;
+  const int nbmax = wrap ? B.Nw : B.Ne;
+  const int a_slab = 128 * 64, b_slab = nbmax * 64;
+  B.a_lo = a_slab;
+  B.b_hi = 2 * a_slab;
+  B.b_lo = B.b_hi + b_slab;
+  B.stage_bytes = (int)(((long long)2 * (a_slab + b_slab) + 1023) & ~1023LL);
+  const long long small = wrap ? 0 : round16(fd::small_bytes(n));
+  const long long rest = small + round16(16LL * n) + round16(8LL * n) + 256;
+  const long long room = (long long)ctx->max_smem_optin - rest;
+  const int S = (int)std::min<long long>(4, room / B.stage_bytes);
+  if (S < 2) return B;  // smem_bytes = 0: does not fit
+  B.nstages = S;
+  long long o = (long long)S * B.stage_bytes;
+  B.small_off = (int)o;
+  o += small;
+  B.ph_off = (int)o;
+  o += round16(16LL * n);
+  B.dg_off = (int)o;
+  o += round16(8LL * n);
+  B.bar_off = (int)o;
+  o += 8LL * (2 * S + 1) + 4 + 16;
+  B.smem_bytes = (int)((o + 127) & ~127LL);
+  B.tmem_cols = 32;
+  while (B.tmem_cols < nbmax) B.tmem_cols <<= 1;
+  const long long cm = 16LL * n * n;
+  long long g = 0;
+  if (wrap) {
+    const long long bsz = 2LL * B.Nb * B.Kp * 4;  // hi and lo planes
+    B.b1_off = g;
+    g += (bsz + 255) & ~255LL;
+    B.b2_off = g;
+    g += (bsz + 255) & ~255LL;
+  } else {
+    B.a_off = g;
+    g += (2LL * B.Mc * B.Kp * 4 + 255) & ~255LL;
+    B.xc_off = g;
+    g += (cm + 255) & ~255LL;
+    B.xn_off = g;
+    g += (cm + 255) & ~255LL;
+    B.t0_off = g;
+    g += (cm + 255) & ~255LL;
+    B.t1_off = g;
+    g += (cm + 255) & ~255LL;
+  }
+  B.slot_bytes = std::max(256LL, g);
+  return B;
+}
+
+bool big_phase(fd_ctx* ctx, int n, bool wrap, bool three, int ntasks, Phase& P) {
+  fd::BLayout B = plan_big(ctx, n, three, wrap);
+  if (B.smem_bytes == 0) return false;
+  memset(&P.L, 0, sizeof(P.L));
+  memset(&P.ML, 0, sizeof(P.ML));
+  P.which = wrap ? 3 : 1;
+  P.mixed = 1;
+  P.big = 1;
+  P.BL = B;
+  P.nthreads = B.nthreads;
+  P.smem = B.smem_bytes;
+  const int by_smem = std::max(1, (ctx->smem_per_sm + 1024) / (B.smem_bytes + 1024));
+  P.occ = std::max(1, std::min(by_smem, 512 / B.tmem_cols));
+  P.grid = std::max(1, std::min(ntasks, ctx->num_sms * P.occ));
+  P.slot_bytes = B.slot_bytes;
+  P.ntasks = ntasks;
+  return true;
+}
+
+// The chain phase of a size class on the tensor cores (the shared-memory tile, else the
+// streamed kernel), or false.
+bool tensor_chain(fd_ctx* ctx, int n, int which, bool three, int ntasks, Phase& P) {
+  if (mixed_phase(ctx, n, R_FWD, which, three, ntasks, P)) {
+    P.big = 0;
+    return true;
+  }
+  return big_phase(ctx, n, false, three, ntasks, P);
+}
+
 std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kind, int prec,
                         bool sparse = false) {
   std::vector<Group> groups;
@@ -491,7 +594,7 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
     if (kind == K_FWD && nd < ctx->num_sms && !sparse) {
       // as many segments as one wave of the chain kernel holds
       Phase P0;
-      if (!(mixed && mixed_phase(ctx, n, R_FWD, 1, three, nd, P0)))
+      if (!(mixed && tensor_chain(ctx, n, 1, three, nd, P0)))
         P0 = fp64_phase(ctx, n, R_FWD, 1, nd);
       const int slots = ctx->num_sms * std::max(1, P0.occ);
       while (target < 16 && 2 * target * nd <= slots) target *= 2;
@@ -508,14 +611,20 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
         g.fws_bytes += (fd::FWork::elems(n, nb + 1, false) * 16 + 255) & ~(size_t)255;
       }
       Phase A;
-      if (!(mixed && mixed_phase(ctx, n, R_FWD, 1, three, (int)g.tA.size(), A)))
+      if (!(mixed && tensor_chain(ctx, n, 1, three, (int)g.tA.size(), A)))
         A = fp64_phase(ctx, n, R_FWD, 1, (int)g.tA.size());
       g.ph.push_back(A);
       g.ph.push_back(fp64_phase(ctx, n, R_MERGE, 8, nd));
     } else if (kind == K_FWD) {
       Phase P;
-      if (!(mixed && mixed_phase(ctx, n, R_FWD, 0, three, nd, P)))
+      if (mixed && mixed_phase(ctx, n, R_FWD, 0, three, nd, P)) {
+        P.big = 0;
+      } else if (mixed && big_phase(ctx, n, false, three, nd, P)) {
+        // the streamed chain kernel runs the forward chains (no checkpoints)
+        for (int k = 0; k < nd; ++k) g.tA.push_back(fd::Task{k, 0});
+      } else {
         P = fp64_phase(ctx, n, sparse ? R_FWD_SPARSE : R_FWD, 0, nd);
+      }
       g.ph.push_back(P);
     } else {
       for (int k = 0; k < nd; ++k) {
@@ -542,18 +651,41 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
         return chain_cost(a) > chain_cost(b);
       });
       Phase A, C;
-      if (!(mixed && mixed_phase(ctx, n, R_FWD, 1, three, 2 * nd, A)))
+      if (!(mixed && tensor_chain(ctx, n, 1, three, 2 * nd, A)))
         A = fp64_phase(ctx, n, R_FWD, 1, 2 * nd);
       const bool two_rhs = (kind & K_GTAU) && (kind & (K_FORCE | K_RESP));
       Phase B = fp64_phase(ctx, n, two_rhs ? R_BOUND2 : R_BOUND, 2,
                            std::max(1, (int)g.tB.size()));
-      // the tensor-core wrap kernel covers the force rows; G(tau, 0) wraps run in FP64
+      // the tensor-core wrap kernels cover the force rows (the shared-memory one also the
+      // response traces); G(tau, 0) wraps run in FP64
       const bool mixed_wrap = mixed && !(kind & K_GTAU);
-      if (!(mixed_wrap && mixed_phase(ctx, n, R_WRAP, 3, three, (int)g.tC.size(), C)))
-        C = fp64_phase(ctx, n, R_WRAP, 3, (int)g.tC.size());
+      const int ntC = (int)g.tC.size();
+      if (mixed_wrap && mixed_phase(ctx, n, R_WRAP, 3, three, ntC, C))
+        C.big = 0;
+      else if (!(mixed_wrap && !(kind & K_RESP) && big_phase(ctx, n, true, three, ntC, C)))
+        C = fp64_phase(ctx, n, R_WRAP, 3, ntC);
       g.ph.push_back(A);
       g.ph.push_back(B);
       g.ph.push_back(C);
+    }
+    // streamed tensor-core phases read chunked TF32 copies of the class's distinct matrices
+    bool big_chain = false, big_wrap = false;
+    for (auto& P : g.ph) {
+      if (P.big && P.which == 3) big_wrap = true;
+      else if (P.big) big_chain = true;
+    }
+    if (big_chain || big_wrap) {
+      const fd::BLayout& BL = g.ph[0].big ? g.ph[0].BL : g.ph.back().BL;
+      g.prep_Ma = BL.Ma;
+      g.prep_Kp = BL.Kp;
+      g.prep_three = BL.three;
+      g.prep_each = ((size_t)2 * BL.Ma * BL.Kp * 4 + 255) & ~(size_t)255;
+      for (int c : g.idx) {
+        const double* mats[2] = {probs[c].expA, big_wrap ? probs[c].expA_inv : nullptr};
+        for (const double* mtx : mats)
+          if (mtx && std::find(g.prep_src.begin(), g.prep_src.end(), mtx) == g.prep_src.end())
+            g.prep_src.push_back(mtx);
+      }
     }
     g.slots_bytes = 0;
     g.grid = 0;
@@ -636,6 +768,8 @@ size_t scratch_need(std::vector<Group>& groups) {
     g.scratch_off = off;
     off += g.slots_bytes + g.fws_bytes;
     off = (off + 255) & ~(size_t)255;
+    g.prep_off = off - g.scratch_off;
+    off += g.prep_src.size() * g.prep_each;
   }
   return off;
 }
@@ -682,6 +816,12 @@ void build_tables(std::vector<Group>& groups, const fd_problem* probs, const Out
                   ? (double2*)(scratch + g.scratch_off + g.slots_bytes + g.fws_off[q])
                   : nullptr;
       d.nseg = g.nseg.empty() ? 0 : g.nseg[q];
+      d.Ec = d.Eic = nullptr;
+      for (size_t i = 0; i < g.prep_src.size(); ++i) {
+        const float* dst = (const float*)(scratch + g.scratch_off + g.prep_off + i * g.prep_each);
+        if (g.prep_src[i] == p.expA) d.Ec = dst;
+        if (g.prep_src[i] == p.expA_inv) d.Eic = dst;
+      }
       out[k++] = d;
     }
     g.tA_off = t;
@@ -740,6 +880,21 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
     cudaStream_t s = fork ? ctx->side[gi % nside] : stream;
     const Desc* dd = d_desc + g.desc_off;
     const int nd = (int)g.idx.size();
+    for (size_t i0 = 0; i0 < g.prep_src.size(); i0 += FD_BIG_PREP_MAX) {
+      fd::BigPrep bp;
+      memset(&bp, 0, sizeof(bp));
+      bp.n = g.nx;
+      bp.Ma = g.prep_Ma;
+      bp.Kp = g.prep_Kp;
+      bp.three = g.prep_three;
+      bp.count = (int)std::min<size_t>(FD_BIG_PREP_MAX, g.prep_src.size() - i0);
+      for (int i = 0; i < bp.count; ++i) {
+        bp.item[i].src = g.prep_src[i0 + i];
+        bp.item[i].dst = (float*)(scratch + g.scratch_off + g.prep_off + (i0 + i) * g.prep_each);
+      }
+      FD_CUDA(ctx, fd::launch_prep_big(bp, s));
+      ctx->last_launches++;
+    }
     for (size_t pi = 0; pi < g.ph.size(); ++pi) {
       const Phase& P = g.ph[pi];
       char* scr = scratch + g.scratch_off + P.slot_off;
@@ -750,7 +905,7 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
         if (timing) FD_CUDA(ctx, cudaEventRecord(ctx->ev[2 * qi + 1], s));
         continue;
       }
-      switch (P.which) {
+      switch (P.big ? -P.which : P.which) {
         case 0:
           if (P.mixed)
             fd::launch_fwd_mixed(dd, nd, d_queue + qi, d_status, scr, P.ML, P.grid, s);
@@ -767,6 +922,14 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
           break;
         case 8:
           fd::launch_merge_fp64(dd, nd, d_queue + qi, d_status, scr, P.L, P.grid, s);
+          break;
+        case -1:  // streamed tensor-core chains (force, segments, or log det/G)
+          fd::launch_chain_big(dd, d_tasks + g.tA_off, (int)g.tA.size(), d_queue + qi, d_status,
+                               scr, P.BL, P.grid, s);
+          break;
+        case -3:
+          fd::launch_wrap_big(dd, d_tasks + g.tC_off, (int)g.tC.size(), d_queue + qi, d_status,
+                              scr, P.BL, P.grid, s, !timing);
           break;
         case 2:
           fd::launch_boundary_fp64(dd, d_tasks + g.tB_off, (int)g.tB.size(), d_queue + qi,
@@ -935,7 +1098,8 @@ int fd_ctx_create(fd_ctx** out, int device) {
   cudaDeviceGetAttribute(&ctx->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
   if (cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming) != cudaSuccess ||
       fd::set_smem_fp64(ctx->max_smem_optin) != cudaSuccess ||
-      fd::set_smem_mixed(ctx->max_smem_optin) != cudaSuccess) {
+      fd::set_smem_mixed(ctx->max_smem_optin) != cudaSuccess ||
+      fd::set_smem_big(ctx->max_smem_optin) != cudaSuccess) {
     delete ctx;
     return FD_ERR_CUDA;
   }
@@ -1476,7 +1640,7 @@ int fd_plan_query(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int
       if (k >= max_groups) continue;
       int* o = info + 8 * k++;
       o[0] = g.nx;
-      o[1] = P.which + (P.mixed ? 4 : 0);
+      o[1] = P.which + (P.mixed ? 4 : 0) + (P.big ? 16 : 0);
       o[2] = P.nthreads;
       o[3] = P.smem;
       o[4] = P.grid;

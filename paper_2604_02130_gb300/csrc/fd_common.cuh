@@ -61,6 +61,10 @@ struct Desc {
   double2* R;          // response traces tr(O G_r), r = 0..nt-1, or null
   int* sync;           // phased path: this configuration's progress flags (SyncFlag), else null
   int nseg;            // time-parallel log det/G: number of segments of the chain (0: not split)
+  // streamed tensor-core kernels (nx above one tile): E and E^{-1} as chunked TF32 operands
+  // (hi at the pointer, lo after it; see BLayout), prepared once per call; else null
+  const float* Ec;
+  const float* Eic;
 };
 
 // ---------------------------------------------------------------- overlapped phases
@@ -248,6 +252,38 @@ struct MLayout {
   // force only
   long long g_off[4];    // G_lo, G_hi, G_a, G_b (complex128 n*n each)
   long long ws_bytes;    // slot bytes before the checkpoints
+};
+
+// Layout of the streamed tensor-core kernels (matrices larger than one tensor-core tile).  Every
+// operand lives in global memory in a chunked K-major layout -- K in chunks of 16, then 8-row
+// groups, then the four core matrices (8 rows x 4 TF32) along K -- so that the rows of one
+// chunk form one contiguous slab that a single bulk copy moves into a shared-memory stage.
+//   chains (slice products):  (E Y)^T = Y^T E,  A = Y^T (Mc rows: column j of Y as rows 2j (Re)
+//                             and 2j+1 (Im)), B = E (Ne rows), accumulator 128 x Ne per M-tile
+//   wraps:  W = M1 Z (A = M1, rows of E padded to Ma; B = Z as rows 2j+part, K = rows of Z), then
+//           G = W M2 as C[c, 2r+part] = sum_k M2[c, k] W_part[r, k] (A = M2, B = W by rows),
+//           the B rows split into npass passes of Nw rows (TMEM columns)
+// Byte offsets into dynamic shared memory unless stated otherwise.
+struct BLayout {
+  int nthreads, num_sms, smem_bytes;
+  int n;
+  int Kp;          // K padded to a multiple of 16 (= Ne)
+  int Ne;          // rows of E as the chains' B operand (n padded to 16)
+  int Ma;          // rows of E / E^{-1} as the wraps' A operand (n padded to 128) = rows of the
+                   // prepared chunked copies
+  int Mc;          // rows of the chains' A operand (2n padded to 128)
+  int Nw, npass;   // wraps: B rows per pass (a multiple of 16, at most 288) and passes
+  int Nb;          // wraps: B rows allocated (npass * Nw >= 2n)
+  int three;       // split TF32 (hi + lo, 3 MMAs per product)
+  int nstages, stage_bytes;
+  int a_lo, b_hi, b_lo;  // offsets inside a stage
+  int small_off, ph_off, dg_off, bar_off;
+  int tmem_cols;
+  // CTA scratch slot (bytes from the slot base)
+  long long a_off;                       // chains: A operand, hi then lo (Mc * Kp floats each)
+  long long xc_off, xn_off, t0_off, t1_off;  // chains: FP64 n x n complex
+  long long b1_off, b2_off;              // wraps: B operands, hi then lo (Nb * Kp floats each)
+  long long slot_bytes;
 };
 
 // status codes written per configuration (device side); the host pre-fills ST_PENDING and the

@@ -62,6 +62,26 @@ cudaError_t set_smem_mixed(int bytes);
 int occupancy_mixed(int which, int nthreads, int smem_bytes);  // -1 on error
 cudaError_t attrs_mixed(int which, cudaFuncAttributes* a);
 
+// streamed tensor-core path (matrices larger than one shared-memory tile): chunked TF32
+// copies of the call's distinct E / E^{-1} (rows padded to Ma), then the chains and wraps
+#define FD_BIG_PREP_MAX 16
+struct BigPrepItem {
+  const double* src;  // n x n row-major FP64
+  float* dst;         // hi (Ma * Kp floats), then lo
+};
+struct BigPrep {
+  BigPrepItem item[FD_BIG_PREP_MAX];
+  int count, n, Ma, Kp, three;
+};
+cudaError_t launch_prep_big(const BigPrep& P, cudaStream_t stream);
+void launch_chain_big(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
+                      char* scratch, const BLayout& L, int grid, cudaStream_t stream);
+void launch_wrap_big(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
+                     char* scratch, const BLayout& L, int grid, cudaStream_t stream, bool pdl);
+cudaError_t set_smem_big(int bytes);
+// kernel ids: 1 chains, 3 wraps
+cudaError_t attrs_big(int which, cudaFuncAttributes* a);
+
 // local (BSS) slice updates (one CTA per configuration; G in shared memory as double-float
 // pairs when maxn is small enough, else FP64 in place)
 cudaError_t launch_bss(const BssSlice* slices, int batch, int maxn, double* dlogdet, int grid,

@@ -112,6 +112,31 @@ __device__ __forceinline__ bool mbar_wait(void* mbar, uint32_t parity, long long
   }
 }
 
+// Arrive on an mbarrier (one arrival) and add `bytes` to the transaction count the current phase
+// waits for (the bulk copies that complete on it).
+__device__ __forceinline__ void mbar_arrive_expect_tx(void* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// ---------------------------------------------------------------- bulk copies (async proxy)
+// Global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) that
+// completes on `mbar` (complete_tx).
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_global, uint32_t bytes,
+                                         void* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst_smem)),
+      "l"(src_global), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
+// Order this thread's earlier generic-proxy global writes before later async-proxy accesses
+// (bulk copies that read them).
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- TMEM -> registers
 // 32 lanes x 16 consecutive 32-bit columns: thread t of the warp gets lane (base + t).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
