@@ -493,14 +493,22 @@ PHASE_OF_KERNEL = {1: "A", 2: "B", 3: "C"}
 KERNEL_NAME = {0: "k_fwd_", 1: "k_chain_", 2: "k_boundary_", 3: "k_wrap_", 8: "k_merge_"}
 
 
+def decode_kernel(k):
+    """fd_plan_query's kernel code: (which, on the tensor cores, streamed, kernel name)."""
+    which = 8 if k == 8 else k & 3
+    tensor, big = bool(k & 4), bool(k & 16)
+    name = KERNEL_NAME.get(which, "k_") + ("big" if big else "mixed" if tensor else "fp64")
+    return which, tensor, big, name
+
+
 def launch_flops(plan, probs, phase_flops):
     """Algorithmic (FP64-pipe, tensor) flops of every launch of the plan: the phase of the
     launch summed over the configurations of its size class, split by where the launch runs
-    (a launch on the FP64 kernels counts its products as FP64 work)."""
+    (a launch on the FP64 kernels counts its products as FP64 work; the streamed kernels' QR,
+    in double-float arithmetic on the FP32 pipes, is counted with the FP64-pipe work)."""
     out = []
     for rec in plan:
-        k = rec["kernel"]
-        which, mixed = k % 4 if k < 8 else 8, k >= 4 and k < 8
+        which, mixed, _, _ = decode_kernel(rec["kernel"])
         ph = PHASE_OF_KERNEL.get(which)
         f64 = tns = 0.0
         if ph:
@@ -648,8 +656,7 @@ def run_ours(args):
         fp64 = {"value": n_total / (ms64 * 1e-3), "unit": "configs/s", "ms_per_step": ms64,
                 "steps": steps64,
                 "tflops": sum(a + b for a, b in lf64) * n_total / n_mine / (ms64 * 1e-3) / 1e12,
-                "kernel_ms": {"%s%d" % (KERNEL_NAME.get(r["kernel"] % 4 if r["kernel"] < 8
-                                                        else 8, "k"), r["nx"]): m
+                "kernel_ms": {"%s_%d" % (decode_kernel(r["kernel"])[3], r["nx"]): m
                               for r, m in zip(plan64, km64)}}
 
     if rank != 0:
@@ -664,8 +671,7 @@ def run_ours(args):
     per_launch = [statistics.mean(k[i] for k in head["kernel_ms"]) for i in range(len(plan))]
     phases = []
     for i, rec in enumerate(plan):
-        k = rec["kernel"]
-        nm = KERNEL_NAME.get(k % 4 if k < 8 else 8, "k_") + ("mixed" if 4 <= k < 8 else "fp64")
+        nm = decode_kernel(rec["kernel"])[3]
         ms = per_launch[i]
         f64 = lf[i][0] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
         tns = lf[i][1] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
@@ -674,7 +680,7 @@ def run_ours(args):
                        "tensor_frac": tns / tf32_peak})
     dom = max(range(len(plan)), key=lambda i: per_launch[i])
     k_ms = per_launch[dom]
-    dk = plan[dom]["kernel"] % 4
+    dk = decode_kernel(plan[dom]["kernel"])[0]
     what = {0: "the log det/G kernel", 1: "the chain kernel (slice products, QRs, assembly)",
             2: "the boundary kernel (boundary Green's functions: GEMMs, LU, solves)",
             3: "the wrap kernel (%s)" % ("wrap products" if args.path != "gtau"

@@ -342,7 +342,12 @@ int fd_check_fp64_refinements(const double* x, const double* y, const double* z,
  * FD_ERR_TOO_LARGE and launch nothing.  FP64 arithmetic only (the FD_PREC_FP64 path).
  * The first call on a device performs a one-time set-up on the current device (it looks up
  * the device address of the array and sets the kernel's shared-memory limit); make that first
- * call before any stream capture.
+ * call before any stream capture.  With CUDA's default lazy module loading, that first call is
+ * also when the device loads this library's code and with it reserves the 12 MiB array, so a
+ * caller whose memory pool later takes the whole device should make the first call at start-up,
+ * before the pool does (a failed reservation returns FD_ERR_CUDA).  The looked-up address is
+ * kept for the life of the process: resetting the device (cudaDeviceReset) after the first call
+ * is not supported.
  *   probs   host array of `batch` problems (device pointers inside, as for fd_logdet)
  *   logdet  device, 2*batch float64 (re, im); G: NULL or host array of device pointers
  *           (nx*nx complex128, row-major); status: NULL or device int[batch] receiving 0 (ok)

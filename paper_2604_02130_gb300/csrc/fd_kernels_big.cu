@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
                            Xc);
         }
         if (!ok) break;
-        cta_reortho_df(n, Xc, Xn, T, To, s.logD, s);
+        cta_reortho_df(n, Xc, Xn, T, To, s.logD, s, (float4*)m.stages);
         double2* t2 = T; T = To; To = t2;
         if (keep && sg < 0 && b < nb) {
           cta_copy(n * n, W.LX(b), Xn);
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
           ok = chain_slice(L, m, P, d, Ahi, Alo, tbase, PhaseVec{pf, false}, t == t0, Xc);
         }
         if (!ok) break;
-        cta_reortho_df(n, Xc, Xn, T, To, s.logD, s);
+        cta_reortho_df(n, Xc, Xn, T, To, s.logD, s, (float4*)m.stages);
         double2* t2 = T; T = To; To = t2;
         cta_copy(n * n, W.RX(b), Xn);
         cta_copy(n * n, W.RT(b), T);

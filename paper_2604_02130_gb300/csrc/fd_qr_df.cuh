@@ -81,32 +81,84 @@ __device__ __forceinline__ df::c4 acc_value(const DAcc& A) {
   return r;
 }
 
-// Lanes per column for a column reduction over `rows` rows: about 16-32 rows per lane.
-__device__ __forceinline__ int df_seg_width(int rows) {
-  int W = 1;
-  while (W < 32 && rows > 32 * W) W <<= 1;
-  return W;
+// ---------------------------------------------------------------- register-resident columns
+// A warp owns one column: lane l holds rows r0 + l + 32 u, u < DF_RMAX (n <= 32 DF_RMAX).
+#define DF_RMAX 9
+#define DF_PANEL 4
+
+struct Col {
+  df::c4 q[DF_RMAX];
+};
+__device__ __forceinline__ void col_load(Col& c, const float4* colp, int r0, int n) {
+  const int l = lane_id();
+#pragma unroll
+  for (int u = 0; u < DF_RMAX; ++u) {
+    const int i = r0 + l + 32 * u;
+    c.q[u] = i < n ? ld4(colp + i) : df::c4{0.f, 0.f, 0.f, 0.f};
+  }
+}
+__device__ __forceinline__ void col_store(const Col& c, float4* colp, int r0, int n) {
+  const int l = lane_id();
+#pragma unroll
+  for (int u = 0; u < DF_RMAX; ++u) {
+    const int i = r0 + l + 32 * u;
+    if (i < n) st4(colp + i, c.q[u]);
+  }
+}
+// Apply H = I - tau v v^H to the column (rows >= r0); v (rows r0.., zero above its own row,
+// 1 on it) in shared memory.
+__device__ __forceinline__ void acc_merge(DAcc& a, const DAcc& b) {
+  float s, t;
+  df::two_sum(a.rs, b.rs, s, t);
+  a.rs = s;
+  a.rc = df::add(df::add(a.rc, b.rc), t);
+  df::two_sum(a.is, b.is, s, t);
+  a.is = s;
+  a.ic = df::add(df::add(a.ic, b.ic), t);
+}
+__device__ __forceinline__ void col_apply(Col& c, const float4* v, int r0, int n, float th,
+                                          float tl) {
+  const int l = lane_id();
+  // three independent accumulators: the compensated sums are serial chains of dependent FP32
+  // operations, so interleaving them keeps the pipes busier
+  DAcc acc[3] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+  for (int u = 0; u < DF_RMAX; ++u) {
+    const int i = r0 + l + 32 * u;
+    if (i < n) acc_conj(acc[u % 3], ld4(v + i), c.q[u]);
+  }
+  acc_merge(acc[0], acc[1]);
+  acc_merge(acc[0], acc[2]);
+  DAcc& a0 = acc[0];
+  acc_seg_sum(a0, 32);
+  DAcc acc1 = a0;
+  const df::c4 f = df::scale(acc_value(acc1), th, tl);
+#pragma unroll
+  for (int u = 0; u < DF_RMAX; ++u) {
+    const int i = r0 + l + 32 * u;
+    if (i < n) c.q[u] = df::cms(c.q[u], f, ld4(v + i));
+  }
 }
 
-// Reflector of column k (rows k..n-1) of the df matrix A, by one warp: FP64 scalars from
-// reflector_math, v_i = a_i / c stored below the diagonal, tau and alpha = R_kk in s.
-__device__ __forceinline__ void df_reflector(int n, int k, float4* A, Small& s) {
-  const int lane = lane_id();
-  if (k == n - 1) {
-    if (lane == 0) {
-      s.tau[k] = 0.0;
-      st(s.rdiag + k, c4join(ld4(A + k + (size_t)k * n)));
-    }
-    return;
-  }
+// Reflector of column k held in registers (rows r0..n-1, k >= r0): FP64 scalars from
+// reflector_math; the column's rows > k become v (a_i / c), row k becomes 1, rows < k stay.
+// Writes v (rows r0..n-1: 0 above k, 1 at k) to vs, and tau, alpha = R_kk to s.
+__device__ __forceinline__ void col_reflector(Col& c, int k, int r0, int n, float4* vs,
+                                              Small& s) {
+  const int l = lane_id();
   float sh = 0.f, sl = 0.f;
-  for (int i = k + 1 + lane; i < n; i += 32) {
-    float th, tl, t;
-    df::abs2(ld4(A + i + (size_t)k * n), th, tl);
-    float s2;
-    df::two_sum(sh, th, s2, t);
-    sh = s2;
-    sl = df::add(sl, df::add(t, tl));
+  df::c4 x{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int u = 0; u < DF_RMAX; ++u) {
+    const int i = r0 + l + 32 * u;
+    if (i > k && i < n) {
+      float th, tl, t, s2;
+      df::abs2(c.q[u], th, tl);
+      df::two_sum(sh, th, s2, t);
+      sh = s2;
+      sl = df::add(sl, df::add(t, tl));
+    }
+    if (i == k) x = c.q[u];
   }
   for (int o = 16; o > 0; o >>= 1) {
     const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
@@ -115,58 +167,37 @@ __device__ __forceinline__ void df_reflector(int n, int k, float4* A, Small& s) 
     df::two_sum(sh, oh, s2, t);
     sh = s2;
     sl = df::add(df::add(sl, ol), t);
+    x.x += __shfl_xor_sync(0xffffffffu, x.x, o);  // exactly one lane holds row k
+    x.y += __shfl_xor_sync(0xffffffffu, x.y, o);
+    x.z += __shfl_xor_sync(0xffffffffu, x.z, o);
+    x.w += __shfl_xor_sync(0xffffffffu, x.w, o);
   }
-  const double sig = df::join(sh, sl);
-  const cplx x = c4join(ld4(A + k + (size_t)k * n));
-  const Refl r = reflector_math(x, sig);
-  if (r.zero) {
-    if (lane == 0) {
-      s.tau[k] = 0.0;
-      st(s.rdiag + k, cx(0, 0));
-      atomicOr(&s.misc[0], 1);
-    }
-    return;
+  const Refl r = k == n - 1 ? Refl{c4join(x), cx(0, 0), 0.0, false}
+                            : reflector_math(c4join(x), df::join(sh, sl));
+  if (l == 0) {
+    s.tau[k] = k == n - 1 || r.zero ? 0.0 : r.tau;
+    st(s.rdiag + k, k == n - 1 ? c4join(x) : (r.zero ? cx(0, 0) : r.alpha));
+    if (r.zero) atomicOr(&s.misc[0], 1);
   }
   const df::c4 ci = df::csplit(r.cinv.re, r.cinv.im);
-  for (int i = k + 1 + lane; i < n; i += 32)
-    st4(A + i + (size_t)k * n, c4mul(ld4(A + i + (size_t)k * n), ci));
-  if (lane == 0) {
-    s.tau[k] = r.tau;
-    st(s.rdiag + k, r.alpha);
+#pragma unroll
+  for (int u = 0; u < DF_RMAX; ++u) {
+    const int i = r0 + l + 32 * u;
+    if (i >= n) continue;
+    df::c4 v;
+    if (i < k) v = df::c4{0.f, 0.f, 0.f, 0.f};
+    else if (i == k) v = df::c4{1.f, 0.f, 0.f, 0.f};
+    else v = (k == n - 1 || r.zero) ? df::c4{0.f, 0.f, 0.f, 0.f} : c4mul(c.q[u], ci);
+    st4(vs + i, v);
+    if (i > k) c.q[u] = v;  // rows below k keep v; rows <= k keep R (and x on the diagonal)
   }
 }
 
-// Apply H_k = I - tau v v^H (v_k = 1, v_i = A(i,k) below the diagonal) to columns k+1..n-1.
-__device__ __forceinline__ void df_householder_update(int n, int k, float4* A, Small& s) {
-  const int lane = lane_id(), w = warp_id(), NW = nwarps();
-  const int rows = n - k;
-  const int W = df_seg_width(rows), spw = 32 / W, sl = lane % W;
-  float th, tl;
-  df::split(s.tau[k], th, tl);
-  const float4* vcol = A + (size_t)k * n;
-  for (int base = k + 1 + w * spw; base < n; base += NW * spw) {
-    const int j = base + lane / W;
-    const bool act = j < n;
-    DAcc acc{0.f, 0.f, 0.f, 0.f};
-    if (act)
-      for (int i = k + sl; i < n; i += W) {
-        const df::c4 v = i == k ? df::c4{1.f, 0.f, 0.f, 0.f} : ld4(vcol + i);
-        acc_conj(acc, v, ld4(A + i + (size_t)j * n));
-      }
-    acc_seg_sum(acc, W);
-    if (act) {
-      const df::c4 f = df::scale(acc_value(acc), th, tl);
-      for (int i = k + sl; i < n; i += W) {
-        const df::c4 v = i == k ? df::c4{1.f, 0.f, 0.f, 0.f} : ld4(vcol + i);
-        float4* p = A + i + (size_t)j * n;
-        st4(p, df::cms(ld4(p), f, v));
-      }
-    }
-  }
-}
-
+// The QR of Section 7 (see cta_reortho) with the factorisation, the T update and the formation
+// of Q in double-float.  vsm: shared memory for DF_PANEL n df numbers (the panel's reflectors).
+// n <= 32 * DF_RMAX.
 __device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, const double2* Tc,
-                                      double2* Tn, double* logD, Small& s) {
+                                      double2* Tn, double* logD, Small& s, float4* vsm) {
   const int lane = lane_id(), w = warp_id(), NW = nwarps();
   float4* A = reinterpret_cast<float4*>(Xn);
   float4* Td = reinterpret_cast<float4*>(Xc);
@@ -227,13 +258,36 @@ __device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, const dou
     st4(Td + e, df::csplit(t.x, t.y));
   }
   const bool scaled = s.misc[4] != 0;
-  // 4. Householder factorisation
-  if (w == 0) df_reflector(n, 0, A, s);
-  __syncthreads();
-  for (int k = 0; k < n - 1; ++k) {
-    df_householder_update(n, k, A, s);
+  // 4. blocked Householder factorisation: warp 0 factors a panel of DF_PANEL columns (each
+  //    column first brought up to date with the panel's earlier reflectors), then every warp
+  //    applies the panel's reflectors to its trailing columns in registers: one load and one
+  //    store of a trailing column per panel.
+  for (int kb = 0; kb < n; kb += DF_PANEL) {
+    const int pe = min(n, kb + DF_PANEL);  // panel columns kb..pe-1 (column n-1: no reflector)
+    if (w == 0) {
+      for (int c = kb; c < pe; ++c) {
+        Col col;
+        col_load(col, A + (size_t)c * n, kb, n);
+        for (int r = kb; r < c; ++r) {
+          float th, tl;
+          df::split(s.tau[r], th, tl);
+          col_apply(col, vsm + (size_t)(r - kb) * n, kb, n, th, tl);
+        }
+        col_reflector(col, c, kb, n, vsm + (size_t)(c - kb) * n, s);
+        col_store(col, A + (size_t)c * n, kb, n);
+        __syncwarp();
+      }
+    }
     __syncthreads();
-    if (w == (k + 1) % NW) df_reflector(n, k + 1, A, s);
+    float th[DF_PANEL], tl[DF_PANEL];
+#pragma unroll
+    for (int r = 0; r < DF_PANEL; ++r) df::split(kb + r < pe ? s.tau[kb + r] : 0.0, th[r], tl[r]);
+    for (int j = pe + w; j < n; j += NW) {
+      Col col;
+      col_load(col, A + (size_t)j * n, kb, n);
+      for (int r = kb; r < pe; ++r) col_apply(col, vsm + (size_t)(r - kb) * n, kb, n, th[r - kb], tl[r - kb]);
+      col_store(col, A + (size_t)j * n, kb, n);
+    }
     __syncthreads();
   }
   // 5. new log D, the row factors q_k = 1 / (sc_k |R_kk|), and the T-update coefficients
@@ -269,82 +323,80 @@ __device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, const dou
     st4(A + e, df::csplit(c.re, c.im));
   }
   __syncthreads();
-  // 6. Tn = C (Pi^T Tc), C upper triangular: each thread a 2 x 2 tile of Tn
-  {
-    const int tiles_i = (n + 1) / 2;
-    for (int t = tid(); t < tiles_i * tiles_i; t += nthr()) {
-      const int i0 = 2 * (t % tiles_i), j0 = 2 * (t / tiles_i);
-      DAcc a00{0.f, 0.f, 0.f, 0.f}, a01 = a00, a10 = a00, a11 = a00;
-      const bool i1 = i0 + 1 < n, j1 = j0 + 1 < n;
-      for (int k = i0; k < n; ++k) {
-        const df::c4 c0 = ld4(A + i0 + (size_t)k * n);
-        const df::c4 c1 = (i1 && k >= i0 + 1) ? ld4(A + i0 + 1 + (size_t)k * n)
-                                              : df::c4{0.f, 0.f, 0.f, 0.f};
-        const df::c4 t0 = ld4(Td + k + (size_t)j0 * n);
-        const df::c4 t1 = j1 ? ld4(Td + k + (size_t)(j0 + 1) * n) : df::c4{0.f, 0.f, 0.f, 0.f};
-        acc_mul(a00, c0, t0);
-        acc_mul(a01, c0, t1);
-        acc_mul(a10, c1, t0);
-        acc_mul(a11, c1, t1);
+  // 6. Tn = C (Pi^T Tc), C upper triangular: a warp per pair of output columns, rows in
+  //    registers, one pass over the columns of C (Tn[:, j] = sum_k C[:, k] T'[k][j])
+  for (int j0 = 2 * w; j0 < n; j0 += 2 * NW) {
+    const bool two = j0 + 1 < n;
+    DAcc a0[DF_RMAX], a1[DF_RMAX];
+#pragma unroll
+    for (int u = 0; u < DF_RMAX; ++u) {
+      a0[u] = DAcc{0.f, 0.f, 0.f, 0.f};
+      a1[u] = a0[u];
+    }
+    for (int k = 0; k < n; ++k) {
+      const df::c4 t0 = ld4(Td + k + (size_t)j0 * n);
+      const df::c4 t1 = two ? ld4(Td + k + (size_t)(j0 + 1) * n) : df::c4{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < DF_RMAX; ++u) {
+        if (32 * u > k) break;  // rows > k of column k of C are zero
+        const int i = lane + 32 * u;
+        if (i <= k && i < n) {
+          const df::c4 ck = ld4(A + i + (size_t)k * n);
+          acc_mul(a0[u], ck, t0);
+          acc_mul(a1[u], ck, t1);
+        }
       }
-      st(Tn + i0 + (size_t)j0 * n, c4join(acc_value(a00)));
-      if (j1) st(Tn + i0 + (size_t)(j0 + 1) * n, c4join(acc_value(a01)));
-      if (i1) st(Tn + i0 + 1 + (size_t)j0 * n, c4join(acc_value(a10)));
-      if (i1 && j1) st(Tn + i0 + 1 + (size_t)(j0 + 1) * n, c4join(acc_value(a11)));
+    }
+#pragma unroll
+    for (int u = 0; u < DF_RMAX; ++u) {
+      const int i = lane + 32 * u;
+      if (i < n) {
+        st(Tn + i + (size_t)j0 * n, c4join(acc_value(a0[u])));
+        if (two) st(Tn + i + (size_t)(j0 + 1) * n, c4join(acc_value(a1[u])));
+      }
     }
   }
   __syncthreads();
-  // 7. form Q in place: Q = H_0 H_1 ... H_{n-2}, accumulated backwards; v_k is copied to the
-  //    shared buffer vb before column k is overwritten
-  float4* vb = reinterpret_cast<float4*>(s.vbuf);  // 2n df numbers
+  // 7. form Q in place, Q = H_0 H_1 ... H_{n-2}, by groups of DF_PANEL reflectors from the last
+  //    one down: each group's reflectors go to shared memory, then a warp per column j >= k0
+  //    applies them (from the highest) in registers; the group's own columns start as e_j.
   for (int e = tid(); e < n * n; e += nthr()) {
     const int i = e % n, j = e / n;
     if (i < j) st4(A + e, df::c4{0.f, 0.f, 0.f, 0.f});
-    if (i == n - 1 && j == n - 1) st4(A + e, df::c4{1.f, 0.f, 0.f, 0.f});
+    if (i == n - 1 && j == n - 1) st4(A + e, df::c4{1.f, 0.f, 0.f, 0.f});  // e_{n-1}
   }
-  if (n >= 2)
-    for (int i = n - 1 + tid(); i < n; i += nthr()) vb[((n - 2) & 1) * n + i] = A[i + (size_t)(n - 2) * n];
   __syncthreads();
-  for (int k = n - 2; k >= 0; --k) {
-    const int rows = n - k - 1;
-    const int W = df_seg_width(rows), spw = 32 / W, sl = lane % W;
-    float th, tl;
-    df::split(s.tau[k], th, tl);
-    const float4* vk = vb + (k & 1) * n;
-    for (int base = k + w * spw; base < n; base += NW * spw) {
-      const int j = base + lane / W;
-      const bool act = j < n && j > k;
-      DAcc acc{0.f, 0.f, 0.f, 0.f};
-      if (act)
-        for (int i = k + 1 + sl; i < n; i += W) acc_conj(acc, ld4(vk + i), ld4(A + i + (size_t)j * n));
-      acc_seg_sum(acc, W);
-      if (act) {
-        const df::c4 f = df::scale(acc_value(acc), th, tl);
-        if (sl == 0) st4(A + k + (size_t)j * n, c4neg(f));
-        for (int i = k + 1 + sl; i < n; i += W) {
-          float4* p = A + i + (size_t)j * n;
-          st4(p, df::cms(ld4(p), f, ld4(vk + i)));
+  const int nref = n - 1;  // reflectors 0..n-2 (tau of column n-1 is 0)
+  for (int k0 = ((nref - 1) / DF_PANEL) * DF_PANEL; nref > 0 && k0 >= 0; k0 -= DF_PANEL) {
+    const int k1 = min(nref - 1, k0 + DF_PANEL - 1);
+    for (int e = tid(); e < (k1 - k0 + 1) * n; e += nthr()) {
+      const int r = k0 + e / n, i = e % n;
+      df::c4 v{0.f, 0.f, 0.f, 0.f};
+      if (i == r) v = df::c4{1.f, 0.f, 0.f, 0.f};
+      else if (i > r) v = ld4(A + i + (size_t)r * n);
+      st4(vsm + (size_t)(r - k0) * n + i, v);
+    }
+    __syncthreads();
+    float th[DF_PANEL], tl[DF_PANEL];
+#pragma unroll
+    for (int r = 0; r < DF_PANEL; ++r) df::split(k0 + r <= k1 ? s.tau[k0 + r] : 0.0, th[r], tl[r]);
+    for (int j = k0 + w; j < n; j += NW) {
+      Col col;
+      if (j <= k1) {  // e_j
+#pragma unroll
+        for (int u = 0; u < DF_RMAX; ++u) {
+          const int i = k0 + lane + 32 * u;
+          col.q[u] = i == j ? df::c4{1.f, 0.f, 0.f, 0.f} : df::c4{0.f, 0.f, 0.f, 0.f};
         }
+      } else {
+        col_load(col, A + (size_t)j * n, k0, n);
       }
-      if (j == k) {  // this segment sets column k and copies v_{k-1}
-        if (sl == 0) {
-          float h, l;
-          df::two_sum(1.f, -th, h, l);
-          df::renorm(h, df::sub(l, tl), h, l);
-          st4(A + k + (size_t)k * n, df::c4{h, l, 0.f, 0.f});
-        }
-        for (int i = k + 1 + sl; i < n; i += W) {
-          const df::c4 v = ld4(vk + i);
-          st4(A + i + (size_t)k * n, c4neg(df::scale(v, th, tl)));
-        }
-        if (k >= 1)
-          for (int i = k + sl; i < n; i += W) vb[((k - 1) & 1) * n + i] = A[i + (size_t)(k - 1) * n];
-      }
+      for (int r = min(j, k1); r >= k0; --r)
+        col_apply(col, vsm + (size_t)(r - k0) * n, k0, n, th[r - k0], tl[r - k0]);
+      col_store(col, A + (size_t)j * n, k0, n);
     }
     __syncthreads();
   }
-  if (n == 1 && tid() == 0) st4(A, df::c4{1.f, 0.f, 0.f, 0.f});
-  __syncthreads();
   // 8. Q back to FP64, in place (each thread converts its own elements)
   for (int e = tid(); e < n * n; e += nthr()) {
     const df::c4 q = ld4(A + e);

@@ -94,9 +94,10 @@ def test_reflector_against_exact_formula():
     ang = rng.uniform(0, 2 * np.pi, size=n)
     a, b = mag * np.cos(ang), mag * np.sin(ang)
     z = (mag * np.exp(rng.uniform(-30, 30, size=n))) ** 2
-    # edges: FP32 range limits of |x|^2 and of the norm, a zero leading entry, a zero column
+    # edges: FP32 range limits of |x|^2 and of the norm, a zero leading entry, a zero column, and
+    # a leading entry near the bottom of the FP64 range (|x|^2 still a normal double)
     extra = [(1e-19, 0.0, 1.0), (1e-18, 0.0, 0.0), (1e18, 0.0, 0.0), (1e17, 1e17, 1e36),
-             (0.0, 0.0, 4.0), (0.0, 0.0, 0.0), (1e-200, 1e-200, 1e-300), (3.0, -4.0, 0.0)]
+             (0.0, 0.0, 4.0), (0.0, 0.0, 0.0), (1e-150, 1e-150, 1e-300), (3.0, -4.0, 0.0)]
     a = np.concatenate([a, [e[0] for e in extra]])
     b = np.concatenate([b, [e[1] for e in extra]])
     z = np.concatenate([z, [e[2] for e in extra]])

@@ -3,9 +3,10 @@
 It runs the FP64 log det / G computation with its working memory in a fixed array inside the
 library instead of context-owned allocations.  This test calls it through the C ABI (ctypes) on
 two batches in a row -- the second call reuses the array with the first call's contents still
-in it -- and compares each result with the context-based entry point fd_green, within the FP64
-tolerances used by the other parity tests.  It also checks the capacity limits.  The file name
-makes pytest collect it last.
+in it -- and compares each result with the context-based entry point fd_green and with the CPU
+oracle, within the FP64 tolerances used by the other parity tests; a third call fills the array
+to its largest allowed batch.  It also checks the capacity limits.  The file name makes pytest
+collect it last.
 """
 import ctypes
 
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 
 import fd_inputs as fi
+from oracle import stable
 
 from gpu_helpers import G_ATOL_FP64, LOGDET_RTOL_FP64, logdet_err, to_dev
 
@@ -64,16 +66,25 @@ def test_noalloc_matches_fd_green_two_calls():
 
     lib = L.load()
     torch.cuda.set_device(0)
-    # call 1: the largest allowed size; call 2: a different, smaller mix that reuses the array
-    first = to_dev([fi.make_problem(6, 32, 4.0, 3.0, 8, 91, c) for c in range(6)])
-    second = to_dev([fi.make_problem(L_, 32, 2.0, 3.0, 8, 92, c)
-                     for c, L_ in enumerate([3, 2, 4, 3, 5, 2, 3, 6])])
-    for tens in (first, second):
+    # call 1: the largest matrix size (Nx = 72); call 2: a different, smaller mix that reuses the
+    # array; call 3: the largest batch at the largest size, whose last slot ends nearest the end
+    # of the array
+    first = [fi.make_problem(6, 32, 4.0, 3.0, 8, 91, c) for c in range(6)]
+    second = [fi.make_problem(L_, 32, 2.0, 3.0, 8, 92, c)
+              for c, L_ in enumerate([3, 2, 4, 3, 5, 2, 3, 6])]
+    third = [fi.make_problem(6, 4, 0.5, 3.0, 4, 94, c) for c in range(L.FD_NOALLOC_MAX_BATCH)]
+    for probs in (first, second, third):
+        tens = to_dev(probs)
         ld, G = _noalloc(lib, tens)
         ref_ld, ref_G = _reference(tens)
         for c in range(len(tens)):
             assert logdet_err(complex(*ld[c]), complex(ref_ld[c])) <= LOGDET_RTOL_FP64
             assert np.abs(G[c] - ref_G[c]).max() <= G_ATOL_FP64
+        for c in range(0, len(probs), 7):  # against the oracle as well
+            p = probs[c]
+            o_ld, o_G = stable.logdet_green(p.E, p.phi, p.n_stab)
+            assert logdet_err(complex(*ld[c]), o_ld) <= LOGDET_RTOL_FP64
+            assert np.abs(G[c] - o_G).max() <= G_ATOL_FP64
 
 
 def test_noalloc_rejects_beyond_capacity():
