@@ -33,9 +33,16 @@ def logdet_err(gpu: complex, ref: complex) -> float:
 # sensitivity of (1 + P)^{-1} to a relative perturbation of P grows like |G|^2 when 1 + P is
 # nearly singular (single configurations reach max|G| ~ 200).
 MIXED_TOL = {
-    "3xtf32": {"logdet_rel": 5e-5, "logdet_cond": 2e-5, "G_scaled": 1e-3, "F_scaled": 1e-3},
-    "tf32": {"logdet_rel": 1e-1, "logdet_cond": 4e-2, "G_scaled": 2e-1, "F_scaled": 2e-1},
+    "3xtf32": {"logdet_rel": 5e-5, "logdet_cond": 2e-5, "G_scaled": 1e-3, "F_scaled": 1e-3,
+               "F_scaled_cold": 5e-3},
+    "tf32": {"logdet_rel": 1e-1, "logdet_cond": 4e-2, "G_scaled": 2e-1, "F_scaled": 2e-1,
+             "F_scaled_cold": 5e-1},
 }
+# F_scaled_cold: force rows at beta up to 64 with 16-slice blocks, relative to max|G_t|^2 of the
+# row's Green's function.  The block products are TF32 pairs (~22 bits per element), so their
+# small singular directions lose accuracy in proportion to the block's condition number
+# (e^{6 delta kappa n_stab}); measured up to 1.2e-3 on the 512 configurations of the uneven
+# workload (beta = 2..64), against 1e-4 and below at beta <= 8.
 
 
 def mixed_logdet_ok(gpu: complex, ref: complex, max_g: float, prec: str) -> bool:
