@@ -531,6 +531,39 @@ fd::BLayout plan_big(fd_ctx* ctx, int n, bool three, bool wrap) {
   return B;
 }
 
+// Boundary Green's functions of the mixed force for the streamed size classes (double-float):
+// the small-vector area and the queue slot in shared memory, three n x n df matrices per slot.
+bool big_boundary_phase(fd_ctx* ctx, int n, int ntasks, Phase& P) {
+  fd::BLayout B;
+  memset(&B, 0, sizeof(B));
+  B.n = n;
+  B.nthreads = 256;
+  B.num_sms = ctx->num_sms;
+  B.small_off = 0;
+  B.bar_off = (int)round16(fd::small_bytes(n));
+  B.smem_bytes = (int)((B.bar_off + 16 + 127) & ~127LL);
+  B.b1_off = 0;
+  B.slot_bytes = (3LL * n * n * 16 + 255) & ~255LL;
+  memset(&P.L, 0, sizeof(P.L));
+  memset(&P.ML, 0, sizeof(P.ML));
+  P.which = 2;
+  P.mixed = 0;
+  P.big = 1;
+  P.BL = B;
+  P.nthreads = 256;
+  P.smem = B.smem_bytes;
+  cudaFuncAttributes fa;
+  int by_regs = 1;
+  if (fd::attrs_big(2, &fa) == cudaSuccess && fa.numRegs > 0)
+    by_regs = std::max(1, 65536 / (((fa.numRegs * 32 + 255) / 256) * 256 * 8));
+  const int by_smem = std::max(1, (ctx->smem_per_sm + 1024) / (B.smem_bytes + 1024));
+  P.occ = std::max(1, std::min(by_regs, by_smem));
+  P.grid = std::max(1, std::min(ntasks, ctx->num_sms * P.occ));
+  P.slot_bytes = B.slot_bytes;
+  P.ntasks = ntasks;
+  return true;
+}
+
 bool big_phase(fd_ctx* ctx, int n, bool wrap, bool three, int ntasks, Phase& P) {
   fd::BLayout B = plan_big(ctx, n, three, wrap);
   if (B.smem_bytes == 0) return false;
@@ -664,6 +697,9 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
         C.big = 0;
       else if (!(mixed_wrap && !(kind & K_RESP) && big_phase(ctx, n, true, three, ntC, C)))
         C = fp64_phase(ctx, n, R_WRAP, 3, ntC);
+      // the mixed force of a streamed class: boundary Green's functions in double-float
+      if (C.big && A.big && kind == K_FORCE)
+        big_boundary_phase(ctx, n, std::max(1, (int)g.tB.size()), B);
       g.ph.push_back(A);
       g.ph.push_back(B);
       g.ph.push_back(C);
@@ -926,6 +962,10 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
         case -1:  // streamed tensor-core chains (force, segments, or log det/G)
           fd::launch_chain_big(dd, d_tasks + g.tA_off, (int)g.tA.size(), d_queue + qi, d_status,
                                scr, P.BL, P.grid, s);
+          break;
+        case -2:
+          fd::launch_boundary_big(dd, d_tasks + g.tB_off, (int)g.tB.size(), d_queue + qi,
+                                  d_status, scr, P.BL, P.grid, s, !timing);
           break;
         case -3:
           fd::launch_wrap_big(dd, d_tasks + g.tC_off, (int)g.tC.size(), d_queue + qi, d_status,

@@ -78,8 +78,12 @@ void launch_chain_big(const Desc* descs, const Task* tasks, int ntasks, int* que
                       char* scratch, const BLayout& L, int grid, cudaStream_t stream);
 void launch_wrap_big(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                      char* scratch, const BLayout& L, int grid, cudaStream_t stream, bool pdl);
+// mixed force, streamed classes: boundary Green's functions in double-float
+void launch_boundary_big(const Desc* descs, const Task* tasks, int ntasks, int* queue,
+                         int* status, char* scratch, const BLayout& L, int grid,
+                         cudaStream_t stream, bool pdl);
 cudaError_t set_smem_big(int bytes);
-// kernel ids: 1 chains, 3 wraps
+// kernel ids: 1 chains, 2 boundary Green's functions, 3 wraps
 cudaError_t attrs_big(int which, cudaFuncAttributes* a);
 
 // local (BSS) slice updates (one CTA per configuration; G in shared memory as double-float

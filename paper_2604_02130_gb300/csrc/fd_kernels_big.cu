@@ -25,6 +25,7 @@
 //   wrap's Z = D G D^* (or D^* G D) by columns.  No product needs a transposed write.
 #include <algorithm>
 
+#include "fd_bound_df.cuh"
 #include "fd_fp64.cuh"
 #include "fd_kernels.h"
 #include "fd_qr_df.cuh"
@@ -466,7 +467,8 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
                            Xc);
         }
         if (!ok) break;
-        cta_reortho_df(n, Xc, Xn, T, To, s.logD, s, (float4*)m.stages);
+        cta_reortho_df(n, Xc, Xn, T, To, s.logD, s, (float4*)m.stages,
+                       L.nstages * L.stage_bytes / 16);
         double2* t2 = T; T = To; To = t2;
         if (keep && sg < 0 && b < nb) {
           cta_copy(n * n, W.LX(b), Xn);
@@ -515,7 +517,8 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
           ok = chain_slice(L, m, P, d, Ahi, Alo, tbase, PhaseVec{pf, false}, t == t0, Xc);
         }
         if (!ok) break;
-        cta_reortho_df(n, Xc, Xn, T, To, s.logD, s, (float4*)m.stages);
+        cta_reortho_df(n, Xc, Xn, T, To, s.logD, s, (float4*)m.stages,
+                       L.nstages * L.stage_bytes / 16);
         double2* t2 = T; T = To; To = t2;
         cta_copy(n * n, W.RX(b), Xn);
         cta_copy(n * n, W.RT(b), T);
@@ -661,6 +664,42 @@ __global__ void __launch_bounds__(256, 1) k_wrap_big(const Desc* __restrict__ de
   if (warp_id() == 0) tc::tmem_dealloc(tbase, (uint32_t)L.tmem_cols);
 }
 
+// ------------------------------------------------------------------ boundary Green's functions
+// Phase B of the mixed force for the streamed size classes: G_{(b-1) ns} of block b from the left
+// checkpoint b-1 and the right checkpoint b, in double-float (fd_bound_df.cuh); three n x n df
+// work matrices in the CTA's slot.
+__global__ void __launch_bounds__(256) k_boundary_big(const Desc* __restrict__ descs,
+                                                      const Task* __restrict__ tasks, int ntasks,
+                                                      int* queue, int* status, char* scratch,
+                                                      BLayout L) {
+  extern __shared__ __align__(1024) char smem[];
+  char* slot = scratch + (size_t)blockIdx.x * L.slot_bytes;
+  int* qs = (int*)(smem + L.bar_off);
+  const int n = L.n;
+  float4* H = (float4*)(slot + L.b1_off);
+  float4* Mb = H + (size_t)n * n;
+  float4* Wb = Mb + (size_t)n * n;
+  allow_dependents();
+  for (;;) {
+    const int q = grab_b(queue, qs);
+    if (q >= ntasks) break;
+    const Task tk = tasks[q];
+    const Desc d = descs[tk.desc];
+    const int nb = d.nt / d.nstab, b = tk.b;
+    const FWork W{d.fws, n, nb};
+    if (d.sync && !cta_wait_flags(d.sync, b - 1, nb - b + 1, 0, qs + 1) && tid() == 0)
+      atomicMax(status + d.user_index, ST_TIMEOUT);
+    Small s = carve_small(smem + L.small_off, n);
+    if (tid() == 0) s.misc[0] = 0;
+    __syncthreads();
+    boundary_green_df(n, W.LX(b - 1), W.LT(b - 1), W.LD(b - 1), W.RX(b), W.RT(b), W.RD(b), H, Mb,
+                      Wb, W.Gb(b), s);
+    if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
+    __syncthreads();
+    if (tid() == 0 && d.sync) flag_add(d.sync + SF_BND, 1);
+  }
+}
+
 // ------------------------------------------------------------------ operand preparation
 // Chunked TF32 copies (hi, then lo) of the distinct E and E^{-1} matrices of a call, rows padded
 // to Ma (one item per blockIdx.y).
@@ -699,20 +738,29 @@ void launch_chain_big(const Desc* descs, const Task* tasks, int ntasks, int* que
   k_chain_big<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue, status,
                                                            scratch, L);
 }
+void launch_boundary_big(const Desc* descs, const Task* tasks, int ntasks, int* queue,
+                         int* status, char* scratch, const BLayout& L, int grid,
+                         cudaStream_t stream, bool pdl) {
+  launch_maybe_pdl(k_boundary_big, grid, L.nthreads, L.smem_bytes, stream, pdl, descs, tasks,
+                   ntasks, queue, status, scratch, L);
+}
 void launch_wrap_big(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                      char* scratch, const BLayout& L, int grid, cudaStream_t stream, bool pdl) {
   launch_maybe_pdl(k_wrap_big, grid, L.nthreads, L.smem_bytes, stream, pdl, descs, tasks, ntasks,
                    queue, status, scratch, L);
 }
 cudaError_t set_smem_big(int bytes) {
-  for (const void* k : {(const void*)k_chain_big, (const void*)k_wrap_big}) {
+  for (const void* k : {(const void*)k_chain_big, (const void*)k_wrap_big,
+                        (const void*)k_boundary_big}) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 cudaError_t attrs_big(int which, cudaFuncAttributes* a) {
-  return cudaFuncGetAttributes(a, which == 3 ? (const void*)k_wrap_big : (const void*)k_chain_big);
+  return cudaFuncGetAttributes(a, which == 3   ? (const void*)k_wrap_big
+                                  : which == 2 ? (const void*)k_boundary_big
+                                               : (const void*)k_chain_big);
 }
 
 }  // namespace fd

@@ -84,7 +84,7 @@ __device__ __forceinline__ df::c4 acc_value(const DAcc& A) {
 // ---------------------------------------------------------------- register-resident columns
 // A warp owns one column: lane l holds rows r0 + l + 32 u, u < DF_RMAX (n <= 32 DF_RMAX).
 #define DF_RMAX 9
-#define DF_PANEL 4
+#define DF_PANEL 8
 
 struct Col {
   df::c4 q[DF_RMAX];
@@ -194,10 +194,11 @@ __device__ __forceinline__ void col_reflector(Col& c, int k, int r0, int n, floa
 }
 
 // The QR of Section 7 (see cta_reortho) with the factorisation, the T update and the formation
-// of Q in double-float.  vsm: shared memory for DF_PANEL n df numbers (the panel's reflectors).
-// n <= 32 * DF_RMAX.
+// of Q in double-float.  vsm: shared memory for vcap df numbers, at least DF_PANEL n (the
+// panel's reflectors; the T update stages blocks of columns of C in it).  n <= 32 * DF_RMAX.
 __device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, const double2* Tc,
-                                      double2* Tn, double* logD, Small& s, float4* vsm) {
+                                      double2* Tn, double* logD, Small& s, float4* vsm,
+                                      int vcap) {
   const int lane = lane_id(), w = warp_id(), NW = nwarps();
   float4* A = reinterpret_cast<float4*>(Xn);
   float4* Td = reinterpret_cast<float4*>(Xc);
@@ -323,37 +324,55 @@ __device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, const dou
     st4(A + e, df::csplit(c.re, c.im));
   }
   __syncthreads();
-  // 6. Tn = C (Pi^T Tc), C upper triangular: a warp per pair of output columns, rows in
-  //    registers, one pass over the columns of C (Tn[:, j] = sum_k C[:, k] T'[k][j])
-  for (int j0 = 2 * w; j0 < n; j0 += 2 * NW) {
-    const bool two = j0 + 1 < n;
-    DAcc a0[DF_RMAX], a1[DF_RMAX];
-#pragma unroll
-    for (int u = 0; u < DF_RMAX; ++u) {
-      a0[u] = DAcc{0.f, 0.f, 0.f, 0.f};
-      a1[u] = a0[u];
-    }
-    for (int k = 0; k < n; ++k) {
-      const df::c4 t0 = ld4(Td + k + (size_t)j0 * n);
-      const df::c4 t1 = two ? ld4(Td + k + (size_t)(j0 + 1) * n) : df::c4{0.f, 0.f, 0.f, 0.f};
+  // 6. Tn = C (Pi^T Tc), C upper triangular: in rounds, each warp owns a pair of output columns
+  //    with its rows in registers (Tn[:, j] = sum_k C[:, k] T'[k][j]); the columns of C pass
+  //    through shared memory in blocks of kbs, staged by the whole CTA once per round
+  {
+    const int kbs = max(1, min(32, vcap / n));
+    for (int r0 = 0; r0 < n; r0 += 2 * NW) {
+      const int j0 = r0 + 2 * w;
+      const bool one = j0 < n, two = j0 + 1 < n;
+      DAcc a0[DF_RMAX], a1[DF_RMAX];
 #pragma unroll
       for (int u = 0; u < DF_RMAX; ++u) {
-        if (32 * u > k) break;  // rows > k of column k of C are zero
-        const int i = lane + 32 * u;
-        if (i <= k && i < n) {
-          const df::c4 ck = ld4(A + i + (size_t)k * n);
-          acc_mul(a0[u], ck, t0);
-          acc_mul(a1[u], ck, t1);
+        a0[u] = DAcc{0.f, 0.f, 0.f, 0.f};
+        a1[u] = a0[u];
+      }
+      for (int k0 = 0; k0 < n; k0 += kbs) {
+        const int kn = min(kbs, n - k0);
+        for (int e = tid(); e < kn * n; e += nthr()) {
+          const int k = k0 + e / n, i = e % n;
+          vsm[e] = i <= k ? A[i + (size_t)k * n] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-      }
-    }
+        __syncthreads();
+        if (one)
+          for (int k = k0; k < k0 + kn; ++k) {
+            const df::c4 t0 = ld4(Td + k + (size_t)j0 * n);
+            const df::c4 t1 = two ? ld4(Td + k + (size_t)(j0 + 1) * n)
+                                  : df::c4{0.f, 0.f, 0.f, 0.f};
+            const float4* ck = vsm + (size_t)(k - k0) * n;
 #pragma unroll
-    for (int u = 0; u < DF_RMAX; ++u) {
-      const int i = lane + 32 * u;
-      if (i < n) {
-        st(Tn + i + (size_t)j0 * n, c4join(acc_value(a0[u])));
-        if (two) st(Tn + i + (size_t)(j0 + 1) * n, c4join(acc_value(a1[u])));
+            for (int u = 0; u < DF_RMAX; ++u) {
+              if (32 * u > k) break;  // rows > k of column k of C are zero
+              const int i = lane + 32 * u;
+              if (i <= k && i < n) {
+                const df::c4 c = ld4(ck + i);
+                acc_mul(a0[u], c, t0);
+                acc_mul(a1[u], c, t1);
+              }
+            }
+          }
+        __syncthreads();
       }
+      if (one)
+#pragma unroll
+        for (int u = 0; u < DF_RMAX; ++u) {
+          const int i = lane + 32 * u;
+          if (i < n) {
+            st(Tn + i + (size_t)j0 * n, c4join(acc_value(a0[u])));
+            if (two) st(Tn + i + (size_t)(j0 + 1) * n, c4join(acc_value(a1[u])));
+          }
+        }
     }
   }
   __syncthreads();
