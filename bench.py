@@ -437,9 +437,11 @@ def _scaled_err(a, ref):
     return float(np.abs(a - ref).max()) / max(1.0, float(np.abs(ref).max())) ** 2
 
 
-def _errors(batch, res, path="force", pos=None):
+def _errors(batch, res, path="force", pos=None, scale_batch=None):
     """Errors of the GPU results against the oracle's on the sampled configurations (pos maps a
-    configuration index to its position in the batch; identity by default)."""
+    configuration index to its position in the batch; identity by default).  scale_batch: the
+    FP64 path's batch, whose force rows give each row's conditioning max(1, max_x |G_t,xx|)^2
+    for the scaled Im F = 1/2 invariant."""
     import numpy as np
 
     ld = batch.logdet_buf.cpu().numpy()
@@ -460,9 +462,14 @@ def _errors(batch, res, path="force", pos=None):
                 ef = max(float(np.abs(Fk[r] - v).max()) / max(1.0, float(np.abs(v).max())) ** 2
                          for r, v in out["F_rows"].items())
                 e["F_rows_abs_over_maxF2"] = max(e.get("F_rows_abs_over_maxF2", 0.0), ef)
-                # Im F = 1/2 on every entry (particle-hole symmetry of the bipartite lattice)
-                e["ImF_minus_half_max"] = max(e.get("ImF_minus_half_max", 0.0),
-                                              float(np.abs(Fk.imag - 0.5).max()))
+                # Im F = 1/2 on every entry (particle-hole symmetry of the bipartite lattice),
+                # relative to the conditioning of each row's G_t
+                if scale_batch is not None:
+                    F64 = scale_batch.F[k].cpu().numpy()
+                    rs = np.maximum(1.0, np.abs(1.0 + 1j * F64).max(axis=1)) ** 2
+                    e["ImF_minus_half_over_maxGt2"] = max(
+                        e.get("ImF_minus_half_over_maxGt2", 0.0),
+                        float((np.abs(Fk.imag - 0.5).max(axis=1) / rs).max()))
                 nx = out["nx"]
                 d = per_nx.setdefault(str(nx), {"logdet_rel": 0.0, "G": 0.0, "F_rows": 0.0})
                 d["logdet_rel"] = max(d["logdet_rel"], el)
@@ -578,6 +585,21 @@ def run_ours(args):
         o += k
     spec = PATHS[args.path]
     ctx = api.Context(local)
+    tuned = None
+    if args.tune_nstab:
+        # the QR interval of every (Nx, Nt) class from the tuner on the class's first
+        # configuration: the fastest candidate within the budget against FP64
+        tuned = {}
+        for c, p in enumerate(probs):
+            key = "%dx%d" % (p.nx, p.nt)
+            if key not in tuned:
+                cands = [k for k in (4, 8, 16, 32, 64) if p.nt % k == 0]
+                best, errs, ms = ctx.tune_nstab((lat[id(p.E)][0], lat[id(p.E)][1], phis[c],
+                                                 p.n_stab), cands, args.tune_nstab, args.prec,
+                                                stats=True)
+                tuned[key] = {"n_stab": best or p.n_stab, "candidates": cands, "err": errs,
+                              "ms": ms}
+            p.n_stab = tuned[key]["n_stab"]
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     slow = uneven  # steps of seconds: fewer untimed and per-launch passes
@@ -737,9 +759,9 @@ def run_ours(args):
                    "sample": "%d of the %d configurations (%s), one per process"
                              % (len(sample), n_mine, spec["what"])}
         pool.close()
-        err = {args.prec: _errors(batch, res, args.path, pos)}
+        err = {args.prec: _errors(batch, res, args.path, pos, b64)}
         if b64 is not None:
-            err["fp64"] = _errors(b64, res, args.path, pos)
+            err["fp64"] = _errors(b64, res, args.path, pos, b64)
 
     line = {
         "metric": spec["metric"],
@@ -754,8 +776,10 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32+f64", "3xtf32": "3xtf32+f64"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[name] + "; " + spec["what"], "prec": args.prec,
-                   "plan": plan,
+        "config": {"workload": WORKLOAD_TEXT[name] + "; " + spec["what"]
+                               + ("; n_stab tuned per (Nx, Nt) class within %g of FP64"
+                                  % args.tune_nstab if tuned else ""),
+                   "prec": args.prec, "plan": plan, "nstab_tuned": tuned,
                    "l2": "flushed between timed steps (%d MB write)" % (FLUSH_BYTES >> 20)},
         "tflops": flops_step * n_total * args.steps / n_mine / (total_ms * 1e-3) / 1e12,
         "e2e": e2e,
@@ -1167,6 +1191,9 @@ def main():
                     help="default uneven512 (force path), batch18 (other paths), sparse288 (sparse)")
     ap.add_argument("--path", choices=tuple(PATHS), default="force",
                     help="what one step computes (default: log det + G + force)")
+    ap.add_argument("--tune-nstab", type=float, default=None, metavar="BUDGET",
+                    help="pick n_stab per (Nx, Nt) class with the tuner (fd_tune_nstab_stats): "
+                         "the fastest of 4..64 whose log det and G stay within BUDGET of FP64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true",
                     help="skip the FP64-path measurement reported beside the mixed path")

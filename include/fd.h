@@ -57,9 +57,11 @@ enum {
 };
 
 /* Arithmetic of the slice products.  QR re-orthogonalisation, scale separation, assembly,
- * boundary Green's functions and all outputs are FP64 in every mode.  The mixed modes apply to
- * configurations with nx <= 128 (one tensor-core tile: M = 128 rows, N = 2*nx <= 256 TMEM
- * columns); larger nx in the same call run on the FP64 kernels (see fd_plan_query). */
+ * boundary Green's functions and all outputs are FP64 in every mode (in the mixed modes, the
+ * size classes whose tensor-core operands do not fit in shared memory -- nx 98..288 in split
+ * TF32 -- stream their operands from global memory and run the O(nx^3) parts of the QR and of
+ * the force's boundary Green's functions in double-float arithmetic, hi + lo FP32 pairs with
+ * about 46 significant bits, keeping FP64 scalars, inputs and outputs; see fd_plan_query). */
 enum {
   FD_PREC_FP64 = 0,        /* everything in FP64 (DFMA) */
   FD_PREC_MIXED_TF32 = 1,  /* slice GEMMs on tcgen05 tensor cores, TF32 operands, FP32 accumulate */
@@ -255,16 +257,23 @@ int fd_last_launch_count(const fd_ctx* ctx);
  * after a warm-up, FP64 or mixed as `prec` says), and keeps the faster choice per launch in the
  * context's plan cache, which later plans (calls, graphs, fd_plan_query) use.
  * Synchronous; allocates and frees its own trial outputs.
- * fd_tune_nstab picks, for one configuration, the largest QR interval among `candidates`
- * (each must divide nt) whose log det at precision `prec` stays within `rel_budget`
- * (|d Re|, |d Im mod 2pi| over max(1, |logdet|)) of an FP64 run with the smallest candidate;
- * *best = 0 if none does.  The Section 9 proposal of stabilising every beta_0/delta slices with
- * beta_0 ~ 10 is the regime this explores.  Synchronous.
+ * fd_tune_nstab picks, for one configuration, the QR interval among `candidates` (each must
+ * divide nt) whose log det + G call at precision `prec` is fastest (CUDA-event time of the call
+ * after a warm-up; ties to the larger interval) among those whose error stays within
+ * `rel_budget` of an FP64 run with the smallest candidate -- the error being the larger of the
+ * log det error (|d Re|, |d Im mod 2pi| over max(1, |logdet|)) and the G error (max |dG_ij| over
+ * max(1, max|G|)^2); *best = 0 if none does.  Section 9's proposal of stabilising every
+ * beta_0/delta slices with beta_0 ~ 10 is the regime this explores: fewer QRs cost accuracy in
+ * the mixed path (its block products lose the small singular directions in proportion to the
+ * block's condition number).  fd_tune_nstab_stats also writes each candidate's error and time
+ * (err, ms: ncand doubles each, host, may be NULL).  Synchronous; allocates its trial outputs.
  * fd_tune_save / fd_tune_load write / read the plan cache as a JSON list (one object per size
  * class: gpu, kind, mixed, three, nx, threads); load returns the number of entries read. */
 int fd_tune(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec, int reps);
 int fd_tune_nstab(fd_ctx* ctx, const fd_problem* prob, const int* candidates, int ncand,
                   double rel_budget, int prec, int* best);
+int fd_tune_nstab_stats(fd_ctx* ctx, const fd_problem* prob, const int* candidates, int ncand,
+                        double rel_budget, int prec, int* best, double* err, double* ms);
 int fd_tune_save(fd_ctx* ctx, const char* path);
 int fd_tune_load(fd_ctx* ctx, const char* path);
 
@@ -284,10 +293,12 @@ int fd_graph_destroy(fd_ctx* ctx, void* graph);
 
 /* The launch plan a call with these arguments would use, without launching anything: one
  * record of 8 ints per kernel launch in info[8*g .. 8*g+7]:
- *   nx, kernel (+4 when it runs on the tensor cores): 0 log det/G, 1 chains (force: forward and
- *   backward products, two tasks per configuration; time-parallel log det/G: segment products),
- *   2 block-boundary Green's functions, 3 wraps and force rows, 8 merge of the segment products
- *   and assembly (FP64);  threads per CTA, dynamic shared memory bytes, grid (persistent CTAs),
+ *   nx, kernel (+4 when it runs on the tensor cores, +16 for the kernels that stream their
+ *   operands from global memory and use double-float QRs and boundary Green's functions):
+ *   0 log det/G, 1 chains (force: forward and backward products, two tasks per configuration;
+ *   time-parallel log det/G: segment products; streamed log det/G: one forward chain per
+ *   configuration), 2 block-boundary Green's functions, 3 wraps and force rows, 8 merge of the
+ *   segment products and assembly (FP64);  threads per CTA, dynamic shared memory bytes, grid (persistent CTAs),
  *   resident CTAs per SM, scratch KiB per CTA, tasks of the launch.
  * Returns the number of launches (>= 0, records beyond max_groups are not written) or a
  * negative FD_ERR_* code.  Synchronous, host only (queries the device's occupancy limits). */

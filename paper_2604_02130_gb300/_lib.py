@@ -97,6 +97,9 @@ SIGNATURES = [
     ("fd_tune", _I, [_VP, _I, _PP, _I, _I, _I]),
     ("fd_tune_nstab", _I, [_VP, _PP, ctypes.POINTER(_I), _I, ctypes.c_double, _I,
                            ctypes.POINTER(_I)]),
+    ("fd_tune_nstab_stats", _I, [_VP, _PP, ctypes.POINTER(_I), _I, ctypes.c_double, _I,
+                                 ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)]),
     ("fd_tune_save", _I, [_VP, ctypes.c_char_p]),
     ("fd_tune_load", _I, [_VP, ctypes.c_char_p]),
 ]

@@ -83,15 +83,22 @@ class Context:
         return [arr[i] for i in range(n)]
 
     def tune_nstab(self, problem: Tuple, candidates: Sequence[int], rel_budget: float,
-                   prec: str = "3xtf32") -> int:
-        """Largest QR interval among candidates within rel_budget of FP64 (fd_tune_nstab)."""
+                   prec: str = "3xtf32", stats: bool = False):
+        """The fastest QR interval among candidates whose log det and G stay within rel_budget of
+        FP64 (fd_tune_nstab_stats); 0 if none does.  With stats, also returns each candidate's
+        error and time: (best, [err], [ms])."""
         E, Einv, phi, _ = problem
         p = L.fd_problem(phi.shape[1], phi.shape[0], int(candidates[0]), 0, E.data_ptr(),
                          Einv.data_ptr() if Einv is not None else None, phi.data_ptr())
         cand = (ctypes.c_int * len(candidates))(*candidates)
         best = ctypes.c_int()
-        self.check(self.lib.fd_tune_nstab(self.h, ctypes.byref(p), cand, len(candidates),
-                                          rel_budget, L.PRECISIONS[prec], ctypes.byref(best)))
+        err = (ctypes.c_double * len(candidates))()
+        ms = (ctypes.c_double * len(candidates))()
+        self.check(self.lib.fd_tune_nstab_stats(self.h, ctypes.byref(p), cand, len(candidates),
+                                                rel_budget, L.PRECISIONS[prec],
+                                                ctypes.byref(best), err, ms))
+        if stats:
+            return best.value, list(err), list(ms)
         return best.value
 
     def tune_save(self, path: str):

@@ -1006,8 +1006,9 @@ int run(fd_ctx* ctx, int batch, const fd_problem* probs, const Outs& o, int prec
   ctx->last_status = nullptr;
   if (batch == 0) return FD_OK;
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
-  // Mixed precision applies to the size classes that fit the tensor-core kernels (nx <= 128 and
-  // its operands in shared memory); larger classes run the FP64 kernels (fd_plan_query says so).
+  // Mixed precision: size classes whose operands fit in shared memory run the tensor-core
+  // kernels of fd_kernels_mixed.cu, larger ones the streamed kernels of fd_kernels_big.cu
+  // (fd_plan_query says which).
   std::vector<Group> groups = plan(ctx, batch, probs, kind, prec, d_hop != nullptr);
   size_t need = scratch_need(groups);
   const size_t ntasks = task_count(groups);
@@ -1578,8 +1579,8 @@ int fd_tune(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int prec,
   return result;
 }
 
-int fd_tune_nstab(fd_ctx* ctx, const fd_problem* prob, const int* candidates, int ncand,
-                  double rel_budget, int prec, int* best) {
+int fd_tune_nstab_stats(fd_ctx* ctx, const fd_problem* prob, const int* candidates, int ncand,
+                        double rel_budget, int prec, int* best, double* err, double* ms) {
   if (!ctx || !prob || !candidates || ncand < 1 || !best) return FD_ERR_INVALID;
   *best = 0;
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -1590,36 +1591,77 @@ int fd_tune_nstab(fd_ctx* ctx, const fd_problem* prob, const int* candidates, in
                   candidates[i], prob->nt);
     nmin = std::min(nmin, candidates[i]);
   }
+  const int n = prob->nx;
+  const size_t gn = (size_t)n * n;
   double* d_ld = nullptr;
+  double* d_g = nullptr;
   FD_CUDA(ctx, cudaMalloc(&d_ld, sizeof(double) * 2));
+  FD_CUDA(ctx, cudaMalloc(&d_g, sizeof(double) * 2 * gn));
+  std::vector<double> gref(2 * gn), got(2 * gn);
+  double* gp[1] = {d_g};
+  Outs o;
+  o.logdet = d_ld;
+  o.G = gp;
   // reference: FP64 with the smallest candidate interval
   fd_problem p = *prob;
   p.n_stab = nmin;
-  Outs o;
-  o.logdet = d_ld;
   int rc = run(ctx, 1, &p, o, FD_PREC_FP64, nullptr, K_FWD);
   double ref[2] = {0, 0};
   if (rc == FD_OK) {
     cudaDeviceSynchronize();
     cudaMemcpy(ref, d_ld, sizeof(ref), cudaMemcpyDeviceToHost);
+    cudaMemcpy(gref.data(), d_g, sizeof(double) * 2 * gn, cudaMemcpyDeviceToHost);
   }
+  double gmax = 1.0;
+  for (size_t e = 0; e < gn; ++e) gmax = std::max(gmax, hypot(gref[2 * e], gref[2 * e + 1]));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
   int chosen = 0;
+  float best_ms = 0.f;
   for (int i = 0; i < ncand && rc == FD_OK; ++i) {
     p.n_stab = candidates[i];
-    rc = run(ctx, 1, &p, o, prec, nullptr, K_FWD);
+    rc = run(ctx, 1, &p, o, prec, nullptr, K_FWD);  // warm-up (plans and sizes the workspace)
     if (rc != FD_OK) break;
-    double got[2];
-    cudaDeviceSynchronize();
-    cudaMemcpy(got, d_ld, sizeof(got), cudaMemcpyDeviceToHost);
-    double dre = fabs(got[0] - ref[0]);
-    double dim = fabs(remainder(got[1] - ref[1], 2.0 * 3.14159265358979323846));
-    double scale = std::max(1.0, hypot(ref[0], ref[1]));
-    if (std::max(dre, dim) / scale <= rel_budget && candidates[i] > chosen) chosen = candidates[i];
+    cudaEventRecord(e0, 0);
+    rc = run(ctx, 1, &p, o, prec, nullptr, K_FWD);
+    cudaEventRecord(e1, 0);
+    if (rc != FD_OK) break;
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    double g2[2];
+    cudaMemcpy(g2, d_ld, sizeof(g2), cudaMemcpyDeviceToHost);
+    cudaMemcpy(got.data(), d_g, sizeof(double) * 2 * gn, cudaMemcpyDeviceToHost);
+    const double dre = fabs(g2[0] - ref[0]);
+    const double dim = fabs(remainder(g2[1] - ref[1], 2.0 * 3.14159265358979323846));
+    double e_ld = std::max(dre, dim) / std::max(1.0, hypot(ref[0], ref[1]));
+    double e_g = 0.0;
+    for (size_t e = 0; e < gn; ++e)
+      e_g = std::max(e_g, hypot(got[2 * e] - gref[2 * e], got[2 * e + 1] - gref[2 * e + 1]));
+    e_g /= gmax * gmax;
+    const double e_all = std::max(e_ld, e_g);
+    if (err) err[i] = e_all;
+    if (ms) ms[i] = t;
+    if (e_all <= rel_budget &&
+        (chosen == 0 || t < best_ms || (t == best_ms && candidates[i] > chosen))) {
+      chosen = candidates[i];
+      best_ms = t;
+    }
   }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   cudaFree(d_ld);
+  cudaFree(d_g);
   if (rc != FD_OK) return rc;
   *best = chosen;
   return FD_OK;
+}
+
+int fd_tune_nstab(fd_ctx* ctx, const fd_problem* prob, const int* candidates, int ncand,
+                  double rel_budget, int prec, int* best) {
+  return fd_tune_nstab_stats(ctx, prob, candidates, ncand, rel_budget, prec, best, nullptr,
+                             nullptr);
 }
 
 int fd_tune_save(fd_ctx* ctx, const char* path) {
