@@ -688,7 +688,15 @@ def run_ours(args):
     # ---- roofline of the longest launch.  Per-launch durations from CUDA events on the
     #      launch streams.
     peaks, peak_src = _measured_peaks()
-    peak_fp64 = ctx.measure_fp64_peak() / 1e3
+    # the FP64 DFMA probe, repeated for about a second with the clocks sampled meanwhile
+    clk64 = ClockSampler(local)
+    clk64.__enter__()
+    try:
+        probe = [ctx.measure_fp64_peak() / 1e3 for _ in range(4)]
+    finally:
+        clk64.__exit__()
+    peak_fp64 = max(probe)
+    probe_clocks = clk64.summary()
     tf32_peak = peaks["bf16_tflops"] / 2.0
     per_launch = [statistics.mean(k[i] for k in head["kernel_ms"]) for i in range(len(plan))]
     phases = []
@@ -714,7 +722,8 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": P["fp64_tflops"] / peak_fp64,
                 "what": "FP64 algorithmic work of %s per launch over its CUDA-event duration"
                         % what,
-                "peak_source": "FP64 DFMA probe over all SMs in this run (fd_measure_fp64_peak)"}
+                "peak_source": "FP64 DFMA probe over all SMs in this run (fd_measure_fp64_peak, "
+                               "best of 4), clocks during the probe: %s" % json.dumps(probe_clocks)}
     else:
         roof = {"bound": "tensor", "achieved": P["tensor_tflops"], "peak": tf32_peak,
                 "unit": "TFLOP/s", "frac": P["tensor_tflops"] / tf32_peak,

@@ -494,6 +494,9 @@ fd::BLayout plan_big(fd_ctx* ctx, int n, bool three, bool wrap) {
   const long long room = (long long)ctx->max_smem_optin - rest;
   const int S = (int)std::min<long long>(4, room / B.stage_bytes);
   if (S < 2) return B;  // smem_bytes = 0: does not fit
+  // the chains' double-float QR works in the stages: a panel of 16 reflectors, its T and Gram
+  // matrices and the GEMM tiles (df numbers of 16 bytes)
+  if (!wrap && (long long)S * B.stage_bytes < 16LL * (16LL * n + 2 * 256 + 4352)) return B;
   B.nstages = S;
   long long o = (long long)S * B.stage_bytes;
   B.small_off = (int)o;
@@ -540,7 +543,8 @@ bool big_boundary_phase(fd_ctx* ctx, int n, int ntasks, Phase& P) {
   B.nthreads = 256;
   B.num_sms = ctx->num_sms;
   B.small_off = 0;
-  B.bar_off = (int)round16(fd::small_bytes(n));
+  B.ph_off = (int)round16(fd::small_bytes(n));  // the df GEMM tiles (2048 df numbers)
+  B.bar_off = B.ph_off + 2048 * 16;
   B.smem_bytes = (int)((B.bar_off + 16 + 127) & ~127LL);
   B.b1_off = 0;
   B.slot_bytes = (3LL * n * n * 16 + 255) & ~255LL;

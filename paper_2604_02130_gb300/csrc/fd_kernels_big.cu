@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(256) k_boundary_big(const Desc* __restrict__ d
     if (tid() == 0) s.misc[0] = 0;
     __syncthreads();
     boundary_green_df(n, W.LX(b - 1), W.LT(b - 1), W.LD(b - 1), W.RX(b), W.RT(b), W.RD(b), H, Mb,
-                      Wb, W.Gb(b), s);
+                      Wb, W.Gb(b), s, (float4*)(smem + L.ph_off));
     if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     __syncthreads();
     if (tid() == 0 && d.sync) flag_add(d.sync + SF_BND, 1);

@@ -81,10 +81,73 @@ __device__ __forceinline__ df::c4 acc_value(const DAcc& A) {
   return r;
 }
 
+__device__ __forceinline__ df::c4 df_of(double2 v) { return df::csplit(v.x, v.y); }
+__device__ __forceinline__ df::c4 df_conj(df::c4 a) { return df::c4{a.x, a.y, -a.z, -a.w}; }
+
+// C (m x p) = A (m x K) B (K x p) in df with the operands staged through shared memory: BM x BN
+// output tiles (64 x 64, or 16 x 256 for a short-and-wide product), K in chunks of 16; 256
+// threads, each a 4 x 4 block of outputs with compensated accumulators.  A(i, k) = aload(i, k),
+// B(k, j) = bload(k, j) (called once per element per tile, inside the bounds), epi(i, j, c4)
+// stores an output element.  sm: shared memory for 16 (BM + BN) df numbers (32 KB for 64 x 64,
+// 68 KB for 16 x 256).  upper_a: A is upper triangular (its K chunks below a tile's rows are
+// skipped).  All threads of the CTA call it (blockDim.x == 256).
+template <int BM = 64, int BN = 64, class ALoad, class BLoad, class Epi>
+__device__ inline void df_gemm_tiled(int m, int p, int K, const ALoad& aload, const BLoad& bload,
+                                     const Epi& epi, float4* sm, bool upper_a = false) {
+  static_assert(BM * BN == 4096, "256 threads of 4 x 4 outputs");
+  float4* As = sm;            // [16][BM]: As[k * BM + i]
+  float4* Bs = sm + 16 * BM;  // [16][BN]: Bs[k * BN + j]
+  const int t = tid();
+  const int tx = t % (BN / 4), ty = t / (BN / 4);  // output columns 4 tx.., rows 4 ty..
+  for (int i0 = 0; i0 < m; i0 += BM)
+    for (int j0 = 0; j0 < p; j0 += BN) {
+      DAcc acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = DAcc{0.f, 0.f, 0.f, 0.f};
+      // an upper triangular A (A(i, k) = 0 for k < i) contributes nothing below the tile's rows
+      for (int k0 = upper_a ? (i0 / 16) * 16 : 0; k0 < K; k0 += 16) {
+        __syncthreads();
+        for (int e = t; e < 16 * BM; e += 256) {
+          const int kk = e / BM, r = e % BM;
+          const int i = i0 + r, k = k0 + kk;
+          st4(As + e, (i < m && k < K) ? aload(i, k) : df::c4{0.f, 0.f, 0.f, 0.f});
+        }
+        for (int e = t; e < 16 * BN; e += 256) {
+          const int kk = e / BN, r = e % BN;
+          const int j = j0 + r, k = k0 + kk;
+          st4(Bs + e, (j < p && k < K) ? bload(k, j) : df::c4{0.f, 0.f, 0.f, 0.f});
+        }
+        __syncthreads();
+        const int kn = min(16, K - k0);
+        for (int kk = 0; kk < kn; ++kk) {
+          df::c4 av[4], bv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) av[a] = ld4(As + kk * BM + 4 * ty + a);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) bv[b] = ld4(Bs + kk * BN + 4 * tx + b);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc_mul(acc[a][b], av[a], bv[b]);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = i0 + 4 * ty + a, j = j0 + 4 * tx + b;
+          if (i < m && j < p) epi(i, j, acc_value(acc[a][b]));
+        }
+    }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- register-resident columns
 // A warp owns one column: lane l holds rows r0 + l + 32 u, u < DF_RMAX (n <= 32 DF_RMAX).
 #define DF_RMAX 9
-#define DF_PANEL 8
+#define DF_PANEL 16
 
 struct Col {
   df::c4 q[DF_RMAX];
@@ -193,10 +256,97 @@ __device__ __forceinline__ void col_reflector(Col& c, int k, int r0, int n, floa
   }
 }
 
+// T of the block reflector H_0 H_1 ... H_{np-1} = I - V T V^H of np consecutive reflectors
+// (forward, column-wise: T upper triangular, T_jj = tau_j, T(0:j, j) = -tau_j T(0:j, 0:j)
+// (V(:, 0:j)^H v_j)).  V(r, j) = vs[j * n + r] for rows r0..n-1 (zero above row r0 + j, 1 on it).
+// Tw, Sg: shared memory, DF_PANEL^2 df numbers each (column-major, leading dimension DF_PANEL).
+__device__ inline void df_block_t(int np, int r0, int n, const float4* vs, const double* tau,
+                                  float4* Tw, float4* Sg) {
+  const int lane = lane_id(), w = warp_id(), NW = nwarps();
+  // Gram entries S(i, j) = v_i^H v_j, i < j
+  for (int pr = w; pr < np * np; pr += NW) {
+    const int i = pr % np, j = pr / np;
+    if (i >= j) continue;
+    DAcc acc{0.f, 0.f, 0.f, 0.f};
+    for (int r = r0 + j + lane; r < n; r += 32)  // v_j is zero above row r0 + j
+      acc_conj(acc, ld4(vs + (size_t)i * n + r), ld4(vs + (size_t)j * n + r));
+    acc_seg_sum(acc, 32);
+    if (lane == 0) st4(Sg + i + j * DF_PANEL, acc_value(acc));
+  }
+  __syncthreads();
+  if (w == 0) {
+    for (int j = 0; j < np; ++j) {
+      float th, tl;
+      df::split(tau[j], th, tl);
+      if (lane < j) {  // T(i, j) = -tau_j sum_{k=i}^{j-1} T(i, k) S(k, j)
+        DAcc acc{0.f, 0.f, 0.f, 0.f};
+        for (int k = lane; k < j; ++k)
+          acc_mul(acc, ld4(Tw + lane + k * DF_PANEL), ld4(Sg + k + j * DF_PANEL));
+        st4(Tw + lane + j * DF_PANEL, c4neg(df::scale(acc_value(acc), th, tl)));
+      }
+      if (lane == 0) st4(Tw + j + j * DF_PANEL, df::c4{th, tl, 0.f, 0.f});
+      if (lane > j && lane < DF_PANEL) st4(Tw + lane + j * DF_PANEL, df::c4{0.f, 0.f, 0.f, 0.f});
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// Apply the block reflector of np reflectors (vs, Tw as for df_block_t, rows r0..n-1) to columns
+// c0..n-1 of the df matrix A (rows r0..n-1): A <- (I - V Tw' V^H) A with Tw' = Tw^H (adjoint:
+// the factorisation's H_{np-1}...H_0) or Tw (the formation of Q's H_0...H_{np-1}).  Wg: global
+// scratch for DF_PANEL x (n - c0) df numbers; gsm: shared memory for the GEMM tiles.
+__device__ inline void df_apply_block(int np, int r0, int c0, int n, const float4* vs,
+                                      const float4* Tw, bool adjoint, float4* A, float4* Wg,
+                                      float4* gsm) {
+  const int m = n - r0, p = n - c0;
+  if (p <= 0) return;
+  // W = V^H A(r0:, c0:)   (np x p)
+  df_gemm_tiled<16, 256>(
+      np, p, m, [&](int i, int k) { return df_conj(ld4(vs + (size_t)i * n + r0 + k)); },
+      [&](int k, int j) { return ld4(A + r0 + k + (size_t)(c0 + j) * n); },
+      [&](int i, int j, df::c4 v) { st4(Wg + i + (size_t)j * DF_PANEL, v); }, gsm);
+  // W <- Tw' W, a thread per column
+  for (int j = tid(); j < p; j += nthr()) {
+    df::c4 wv[DF_PANEL];
+#pragma unroll
+    for (int k = 0; k < DF_PANEL; ++k)
+      wv[k] = k < np ? ld4(Wg + k + (size_t)j * DF_PANEL) : df::c4{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < DF_PANEL; ++i) {
+      if (i >= np) break;
+      DAcc acc{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < DF_PANEL; ++k) {
+        if (k >= np) break;
+        if (adjoint ? (k <= i) : (k >= i)) {  // T^H lower, T upper triangular
+          const df::c4 tk = adjoint ? df_conj(ld4(Tw + k + i * DF_PANEL)) : ld4(Tw + i + k * DF_PANEL);
+          acc_mul(acc, tk, wv[k]);
+        }
+      }
+      st4(Wg + i + (size_t)j * DF_PANEL, acc_value(acc));
+    }
+  }
+  __syncthreads();
+  // A(r0:, c0:) -= V W
+  const df::c4 one{1.f, 0.f, 0.f, 0.f};
+  df_gemm_tiled<64, 64>(
+      m, p, np, [&](int i, int k) { return ld4(vs + (size_t)k * n + r0 + i); },
+      [&](int k, int j) { return ld4(Wg + k + (size_t)j * DF_PANEL); },
+      [&](int i, int j, df::c4 v) {
+        float4* q = A + r0 + i + (size_t)(c0 + j) * n;
+        st4(q, df::cms(ld4(q), v, one));
+      },
+      gsm);
+}
+
 // The QR of Section 7 (see cta_reortho) with the factorisation, the T update and the formation
-// of Q in double-float.  vsm: shared memory for vcap df numbers, at least DF_PANEL n (the
-// panel's reflectors; the T update stages blocks of columns of C in it).  n <= 32 * DF_RMAX.
-__device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, const double2* Tc,
+// of Q in double-float, the O(n^3) work in shared-memory tiled df GEMMs on block reflectors
+// (compact WY form) of DF_PANEL reflectors.  vsm: shared memory for vcap >= DF_PANEL (n + 2
+// DF_PANEL) + 4352 df numbers (the panel's reflectors, its T and Gram matrices, the GEMM tiles).
+// Tc is consumed: after its rows are gathered in df into Xc, its memory holds the block
+// reflectors' DF_PANEL x n intermediate products.  n <= 32 * DF_RMAX.
+__device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, double2* Tc,
                                       double2* Tn, double* logD, Small& s, float4* vsm,
                                       int vcap) {
   const int lane = lane_id(), w = warp_id(), NW = nwarps();
@@ -260,9 +410,13 @@ __device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, const dou
   }
   const bool scaled = s.misc[4] != 0;
   // 4. blocked Householder factorisation: warp 0 factors a panel of DF_PANEL columns (each
-  //    column first brought up to date with the panel's earlier reflectors), then every warp
-  //    applies the panel's reflectors to its trailing columns in registers: one load and one
-  //    store of a trailing column per panel.
+  //    column first brought up to date with the panel's earlier reflectors, in registers), then
+  //    the panel's block reflector I - V T V^H updates the trailing columns by two tiled GEMMs
+  float4* Vs = vsm;                                  // DF_PANEL x n
+  float4* Tw = vsm + (size_t)DF_PANEL * n;           // DF_PANEL^2
+  float4* Sg = Tw + DF_PANEL * DF_PANEL;             // DF_PANEL^2
+  float4* gsm = Sg + DF_PANEL * DF_PANEL;            // GEMM tiles
+  float4* Wg = reinterpret_cast<float4*>(Tc);        // DF_PANEL x n, global
   for (int kb = 0; kb < n; kb += DF_PANEL) {
     const int pe = min(n, kb + DF_PANEL);  // panel columns kb..pe-1 (column n-1: no reflector)
     if (w == 0) {
@@ -272,24 +426,18 @@ __device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, const dou
         for (int r = kb; r < c; ++r) {
           float th, tl;
           df::split(s.tau[r], th, tl);
-          col_apply(col, vsm + (size_t)(r - kb) * n, kb, n, th, tl);
+          col_apply(col, Vs + (size_t)(r - kb) * n, kb, n, th, tl);
         }
-        col_reflector(col, c, kb, n, vsm + (size_t)(c - kb) * n, s);
+        col_reflector(col, c, kb, n, Vs + (size_t)(c - kb) * n, s);
         col_store(col, A + (size_t)c * n, kb, n);
         __syncwarp();
       }
     }
     __syncthreads();
-    float th[DF_PANEL], tl[DF_PANEL];
-#pragma unroll
-    for (int r = 0; r < DF_PANEL; ++r) df::split(kb + r < pe ? s.tau[kb + r] : 0.0, th[r], tl[r]);
-    for (int j = pe + w; j < n; j += NW) {
-      Col col;
-      col_load(col, A + (size_t)j * n, kb, n);
-      for (int r = kb; r < pe; ++r) col_apply(col, vsm + (size_t)(r - kb) * n, kb, n, th[r - kb], tl[r - kb]);
-      col_store(col, A + (size_t)j * n, kb, n);
+    if (pe < n) {
+      df_block_t(pe - kb, kb, n, Vs, s.tau + kb, Tw, Sg);
+      df_apply_block(pe - kb, kb, pe, n, Vs, Tw, true, A, Wg, gsm);
     }
-    __syncthreads();
   }
   // 5. new log D, the row factors q_k = 1 / (sc_k |R_kk|), and the T-update coefficients
   //    C_kj = R'_kj sc_j q_k (j > k), C_kk = R_kk / |R_kk|, FP64, stored back in df
@@ -324,61 +472,15 @@ __device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, const dou
     st4(A + e, df::csplit(c.re, c.im));
   }
   __syncthreads();
-  // 6. Tn = C (Pi^T Tc), C upper triangular: in rounds, each warp owns a pair of output columns
-  //    with its rows in registers (Tn[:, j] = sum_k C[:, k] T'[k][j]); the columns of C pass
-  //    through shared memory in blocks of kbs, staged by the whole CTA once per round
-  {
-    const int kbs = max(1, min(32, vcap / n));
-    for (int r0 = 0; r0 < n; r0 += 2 * NW) {
-      const int j0 = r0 + 2 * w;
-      const bool one = j0 < n, two = j0 + 1 < n;
-      DAcc a0[DF_RMAX], a1[DF_RMAX];
-#pragma unroll
-      for (int u = 0; u < DF_RMAX; ++u) {
-        a0[u] = DAcc{0.f, 0.f, 0.f, 0.f};
-        a1[u] = a0[u];
-      }
-      for (int k0 = 0; k0 < n; k0 += kbs) {
-        const int kn = min(kbs, n - k0);
-        for (int e = tid(); e < kn * n; e += nthr()) {
-          const int k = k0 + e / n, i = e % n;
-          vsm[e] = i <= k ? A[i + (size_t)k * n] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        __syncthreads();
-        if (one)
-          for (int k = k0; k < k0 + kn; ++k) {
-            const df::c4 t0 = ld4(Td + k + (size_t)j0 * n);
-            const df::c4 t1 = two ? ld4(Td + k + (size_t)(j0 + 1) * n)
-                                  : df::c4{0.f, 0.f, 0.f, 0.f};
-            const float4* ck = vsm + (size_t)(k - k0) * n;
-#pragma unroll
-            for (int u = 0; u < DF_RMAX; ++u) {
-              if (32 * u > k) break;  // rows > k of column k of C are zero
-              const int i = lane + 32 * u;
-              if (i <= k && i < n) {
-                const df::c4 c = ld4(ck + i);
-                acc_mul(a0[u], c, t0);
-                acc_mul(a1[u], c, t1);
-              }
-            }
-          }
-        __syncthreads();
-      }
-      if (one)
-#pragma unroll
-        for (int u = 0; u < DF_RMAX; ++u) {
-          const int i = lane + 32 * u;
-          if (i < n) {
-            st(Tn + i + (size_t)j0 * n, c4join(acc_value(a0[u])));
-            if (two) st(Tn + i + (size_t)(j0 + 1) * n, c4join(acc_value(a1[u])));
-          }
-        }
-    }
-  }
-  __syncthreads();
+  // 6. Tn = C (Pi^T Tc), C upper triangular, one tiled df GEMM
+  df_gemm_tiled<64, 64>(
+      n, n, n,
+      [&](int i, int k) { return i <= k ? ld4(A + i + (size_t)k * n) : df::c4{0.f, 0.f, 0.f, 0.f}; },
+      [&](int k, int j) { return ld4(Td + k + (size_t)j * n); },
+      [&](int i, int j, df::c4 v) { st(Tn + i + (size_t)j * n, c4join(v)); }, gsm, true);
   // 7. form Q in place, Q = H_0 H_1 ... H_{n-2}, by groups of DF_PANEL reflectors from the last
-  //    one down: each group's reflectors go to shared memory, then a warp per column j >= k0
-  //    applies them (from the highest) in registers; the group's own columns start as e_j.
+  //    one down: a group's reflectors go to shared memory, its own columns become e_j, and its
+  //    block reflector I - V T V^H is applied to columns k0..n-1 (rows k0..n-1)
   for (int e = tid(); e < n * n; e += nthr()) {
     const int i = e % n, j = e / n;
     if (i < j) st4(A + e, df::c4{0.f, 0.f, 0.f, 0.f});
@@ -387,34 +489,22 @@ __device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, const dou
   __syncthreads();
   const int nref = n - 1;  // reflectors 0..n-2 (tau of column n-1 is 0)
   for (int k0 = ((nref - 1) / DF_PANEL) * DF_PANEL; nref > 0 && k0 >= 0; k0 -= DF_PANEL) {
-    const int k1 = min(nref - 1, k0 + DF_PANEL - 1);
-    for (int e = tid(); e < (k1 - k0 + 1) * n; e += nthr()) {
+    const int k1 = min(nref - 1, k0 + DF_PANEL - 1), np = k1 - k0 + 1;
+    for (int e = tid(); e < np * n; e += nthr()) {
       const int r = k0 + e / n, i = e % n;
       df::c4 v{0.f, 0.f, 0.f, 0.f};
       if (i == r) v = df::c4{1.f, 0.f, 0.f, 0.f};
       else if (i > r) v = ld4(A + i + (size_t)r * n);
-      st4(vsm + (size_t)(r - k0) * n + i, v);
+      st4(Vs + (size_t)(r - k0) * n + i, v);
     }
     __syncthreads();
-    float th[DF_PANEL], tl[DF_PANEL];
-#pragma unroll
-    for (int r = 0; r < DF_PANEL; ++r) df::split(k0 + r <= k1 ? s.tau[k0 + r] : 0.0, th[r], tl[r]);
-    for (int j = k0 + w; j < n; j += NW) {
-      Col col;
-      if (j <= k1) {  // e_j
-#pragma unroll
-        for (int u = 0; u < DF_RMAX; ++u) {
-          const int i = k0 + lane + 32 * u;
-          col.q[u] = i == j ? df::c4{1.f, 0.f, 0.f, 0.f} : df::c4{0.f, 0.f, 0.f, 0.f};
-        }
-      } else {
-        col_load(col, A + (size_t)j * n, k0, n);
-      }
-      for (int r = min(j, k1); r >= k0; --r)
-        col_apply(col, vsm + (size_t)(r - k0) * n, k0, n, th[r - k0], tl[r - k0]);
-      col_store(col, A + (size_t)j * n, k0, n);
+    for (int e = tid(); e < np * (n - k0); e += nthr()) {
+      const int j = k0 + e / (n - k0), i = k0 + e % (n - k0);
+      st4(A + i + (size_t)j * n, i == j ? df::c4{1.f, 0.f, 0.f, 0.f} : df::c4{0.f, 0.f, 0.f, 0.f});
     }
     __syncthreads();
+    df_block_t(np, k0, n, Vs, s.tau + k0, Tw, Sg);
+    df_apply_block(np, k0, k0, n, Vs, Tw, false, A, Wg, gsm);
   }
   // 8. Q back to FP64, in place (each thread converts its own elements)
   for (int e = tid(); e < n * n; e += nthr()) {

@@ -39,9 +39,9 @@ MIXED_TOL = {
              "F_scaled_cold": 5e-1},
 }
 # F_scaled_cold: force rows at beta up to 64 with 16-slice blocks, relative to max|G_t|^2 of the
-# row's Green's function.  The block products are TF32 pairs (~22 bits per element), so their
-# small singular directions lose accuracy in proportion to the block's condition number
-# (e^{6 delta kappa n_stab}); measured up to 1.2e-3 on the 512 configurations of the uneven
+# row's Green's function.  Each slice product rounds to a TF32 pair (~22 bits per element) and
+# the rounding accumulates over the slices (and, for long blocks, grows with the block's condition
+# number e^{6 delta kappa n_stab}); measured up to 1.2e-3 on the 512 configurations of the uneven
 # workload (beta = 2..64), against 1e-4 and below at beta <= 8.
 
 
