@@ -226,6 +226,22 @@ int fd_taylor_factors(int n, double* gamma);
  * undefined).  The context stays usable; switch the hook off for normal calls. */
 int fd_debug_skip_chains(fd_ctx* ctx, int on);
 
+/* Time-parallel force chains.  A force call (fd_force, or fd_observables with F only) runs two
+ * chains per configuration, the forward one (left checkpoints, then log det and G_0) and the
+ * backward one (right checkpoints); with the chains split at the middle block h = nb/2 each runs
+ * as two halves in parallel, the second halves from the identity, and the boundary phase merges
+ * a second half's checkpoint with the first half's last one before the boundary Green's function
+ * (Section 7's stabilised product of two factored matrices, in FP64) and forms log det and G_0
+ * from the forward halves.  The merges cost about one chain's QRs per configuration, so the split
+ * pays only where whole chains would leave SMs idle.  mode -1 (default): split in FP64 when
+ * 4 * batch <= the SM count; 0: never; 1: every configuration with at least 4 blocks.  Size
+ * classes that the mixed path runs on the streamed kernels (Nx above the shared-memory tile) are
+ * never split: their double-float boundary kernel cannot hold the merge's row scaling, which
+ * spans beta/2 times the hopping bandwidth (e^{-96} at beta = 32), within the FP32 exponent range.
+ * A merge whose second-half factor spans more than e^700 marks the configuration FD_ERR_NUMERIC.
+ * Results agree with the unsplit chains to rounding.  Returns FD_ERR_INVALID for another mode. */
+int fd_set_force_split(fd_ctx* ctx, int mode);
+
 /* Wait for `stream` and copy the per-configuration device status of the LAST call on this
  * context into per_config_status[0..batch-1] (host): FD_OK, FD_ERR_NUMERIC or FD_ERR_TIMEOUT.
  * Returns the worst code seen (FD_OK if all succeeded). */

@@ -82,6 +82,7 @@ SIGNATURES = [
                              _VP, ctypes.POINTER(_VP), _VP]),
     ("fd_taylor_factors", _I, [_I, ctypes.POINTER(ctypes.c_double)]),
     ("fd_debug_skip_chains", _I, [_VP, _I]),
+    ("fd_set_force_split", _I, [_VP, _I]),
     ("fd_status", _I, [_VP, _VP, ctypes.POINTER(_I), _I]),
     ("fd_last_launch_count", _I, [_VP]),
     ("fd_measure_fp64_peak", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),

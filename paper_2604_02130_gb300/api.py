@@ -69,6 +69,12 @@ class Context:
         launch, so the dependent tasks' bounded waits run out and report FD_ERR_TIMEOUT."""
         self.check(self.lib.fd_debug_skip_chains(self.h, 1 if on else 0))
 
+    def set_force_split(self, mode: int) -> None:
+        """Time-parallel force chains (fd_set_force_split): -1 automatic (FP64 calls with
+        4 * batch <= SMs split every configuration's chains at the middle block), 0 never, 1 every
+        configuration with at least 4 blocks (streamed mixed size classes are never split)."""
+        self.check(self.lib.fd_set_force_split(self.h, int(mode)))
+
     def last_launch_count(self) -> int:
         return self.lib.fd_last_launch_count(self.h)
 

@@ -55,6 +55,9 @@ struct fd_ctx {
   size_t hop_cap = 0;
   // failure-detection test hook: phased calls skip their chain launch (fd_debug_skip_chains)
   bool debug_skip_chains = false;
+  // force chains split at the middle block: -1 when one chain outlasts an SM's share, 0 never,
+  // 1 every configuration with at least 4 blocks (fd_set_force_split)
+  int force_split = -1;
 };
 
 namespace {
@@ -109,6 +112,7 @@ struct Phase {
   int which;
   int mixed;  // 1: tcgen05 kernel (ML, or BL when big), 0: FP64 kernel (L)
   int big = 0;  // 1: streamed tcgen05 kernel (operands in global memory, BL)
+  int merge = 0;  // boundary phase: the variant that merges split chains' checkpoints
   Layout L;
   fd::MLayout ML;
   fd::BLayout BL{};
@@ -133,6 +137,7 @@ struct Group {
   std::vector<size_t> fws_off;   // force: per configuration, bytes from the group's FWork base
   size_t fws_bytes;
   std::vector<int> nseg;         // time-parallel log det/G: segments per configuration (or empty)
+  std::vector<int> fsplit;       // force: block at which each configuration's chains split (0: not)
   // streamed tensor-core phases: chunked TF32 copies of the distinct E (and E^{-1}) matrices
   std::vector<const double*> prep_src;
   size_t prep_off = 0;   // byte offset from the group's scratch base
@@ -183,9 +188,18 @@ long long tune_key(int kind, int mixed, int three, int nx) {
 
 // Buffer sets of the kernels ("roles"): log det/G and the force chains (R_FWD), the boundary
 // Green's functions (R_BOUND; R_BOUND2 with the second right-hand side of G(t, 0) beside G_t)
-// and the wraps (R_WRAP); the merge of a time-parallel split (R_MERGE).
+// and the wraps (R_WRAP); the merge of a time-parallel split (R_MERGE); boundary Green's
+// functions that first merge a split chain's checkpoints (R_BOUNDM).
 // R_FWD_SPARSE: log det/G with the product-form slices (no dense E).
-enum Role { R_FWD = 0, R_BOUND = 2, R_WRAP = 3, R_BOUND2 = 4, R_MERGE = 5, R_FWD_SPARSE = 6 };
+enum Role {
+  R_FWD = 0,
+  R_BOUND = 2,
+  R_WRAP = 3,
+  R_BOUND2 = 4,
+  R_MERGE = 5,
+  R_FWD_SPARSE = 6,
+  R_BOUNDM = 7
+};
 
 // Greedy placement: the buffers touched every slice first, then the per-block ones.
 Layout plan_layout(int n, int role, int budget, int nthreads) {
@@ -204,6 +218,8 @@ Layout plan_layout(int n, int role, int budget, int nthreads) {
     order = {{fd::B_GA, cm}, {fd::B_GB, 2 * cm}};
   else if (role == R_MERGE)
     order = {{fd::B_X0, cm}, {fd::B_X1, cm}, {fd::B_T0, cm}, {fd::B_T1, cm}, {fd::B_GA, cm}};
+  else if (role == R_BOUNDM)
+    order = {{fd::B_GA, cm}, {fd::B_GB, cm}, {fd::B_X0, cm}, {fd::B_T0, cm}};
   else
     order = {{fd::B_E, rm}, {fd::B_EINV, rm}, {fd::B_GA, cm}, {fd::B_GB, cm}};
   long long used = round16(fd::small_bytes(n)) + 16;  // small vectors + queue slot
@@ -496,7 +512,7 @@ fd::BLayout plan_big(fd_ctx* ctx, int n, bool three, bool wrap) {
   if (S < 2) return B;  // smem_bytes = 0: does not fit
   // the chains' double-float QR works in the stages: a panel of 16 reflectors, its T and Gram
   // matrices and the GEMM tiles (df numbers of 16 bytes)
-  if (!wrap && (long long)S * B.stage_bytes < 16LL * (16LL * n + 2 * 256 + 4352)) return B;
+  if (!wrap && (long long)S * B.stage_bytes < 16LL * fd::big_qr_vcap(n)) return B;
   B.nstages = S;
   long long o = (long long)S * B.stage_bytes;
   B.small_off = (int)o;
@@ -543,8 +559,8 @@ bool big_boundary_phase(fd_ctx* ctx, int n, int ntasks, Phase& P) {
   B.nthreads = 256;
   B.num_sms = ctx->num_sms;
   B.small_off = 0;
-  B.ph_off = (int)round16(fd::small_bytes(n));  // the df GEMM tiles (2048 df numbers)
-  B.bar_off = B.ph_off + 2048 * 16;
+  B.ph_off = (int)round16(fd::small_bytes(n));  // the df GEMM tiles
+  B.bar_off = B.ph_off + fd::big_bound_tiles() * 16;
   B.smem_bytes = (int)((B.bar_off + 16 + 127) & ~127LL);
   B.b1_off = 0;
   B.slot_bytes = (3LL * n * n * 16 + 255) & ~255LL;
@@ -612,6 +628,21 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
   });
   const bool mixed = prec != FD_PREC_FP64 && !sparse;
   const bool three = prec == FD_PREC_MIXED_3XTF32;
+  // Force chains split at the middle block (ChainSpan): the halves run in parallel and the
+  // boundary phase pays one merge (a product and a QR) per checkpoint of a second half, about a
+  // chain's worth of QRs in all.  That pays where the chains alone would leave SMs idle: in
+  // FP64 (QR-bound chains) when all the halves fit in one wave (4 batch <= SMs); measured on
+  // 32 configurations of Nx = 72, beta = 32: 118 -> 95 ms, while 64 configurations at beta = 64
+  // and the mixed path (tensor-core slices, FP64 merges) lose.  Classes whose boundary kernel
+  // is the double-float one (streamed mixed classes) are never split (fd_kernels_big.cu).
+  std::vector<char> split_c(batch, 0);
+  if (kind == K_FORCE && !sparse && ctx->force_split != 0) {
+    const bool auto_ok = prec == FD_PREC_FP64 && 4 * batch <= ctx->num_sms;
+    for (int c = 0; c < batch; ++c) {
+      const int nb = probs[c].nt / probs[c].n_stab;
+      split_c[c] = nb >= 4 && (ctx->force_split > 0 || auto_ok);
+    }
+  }
   int qnext = 0;
   size_t i = 0;
   while (i < order.size()) {
@@ -664,23 +695,41 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       }
       g.ph.push_back(P);
     } else {
+      // streamed mixed classes (double-float boundary kernel) keep whole chains
+      Phase A0;
+      const bool streamed = mixed && !mixed_phase(ctx, n, R_FWD, 1, three, 2 * nd, A0) &&
+                            big_phase(ctx, n, false, three, 2 * nd, A0);
+      bool any_split = false;
       for (int k = 0; k < nd; ++k) {
         const int c = g.idx[k];
         const int nb = probs[c].nt / probs[c].n_stab;
-        g.tA.push_back(fd::Task{k, 0});
-        g.tA.push_back(fd::Task{k, 1});
+        const int h = split_c[c] && !streamed ? nb / 2 : 0;
+        g.fsplit.push_back(h);
+        any_split |= h > 0;
+        g.tA.push_back(fd::Task{k, fd::CT_FWD});
+        g.tA.push_back(fd::Task{k, fd::CT_BWD});
+        if (h) {
+          g.tA.push_back(fd::Task{k, fd::CT_FWD2});
+          g.tA.push_back(fd::Task{k, fd::CT_BWD2});
+        }
         for (int b = 2; b <= nb; ++b) g.tB.push_back(fd::Task{k, b});
+        if (h) g.tB.push_back(fd::Task{k, 1});  // G_0 and log det from the halves
         for (int b = 1; b <= nb; ++b) g.tC.push_back(fd::Task{k, b});
         g.fws_off.push_back(g.fws_bytes);
-        g.fws_bytes += (fd::FWork::elems(n, nb, (kind & K_GTAU) != 0, (kind & K_RESP) != 0) * 16 +
-                        255) & ~(size_t)255;
+        g.fws_bytes += (fd::FWork::elems(n, nb, (kind & K_GTAU) != 0, (kind & K_RESP) != 0,
+                                         h > 0) * 16 + 255) & ~(size_t)255;
       }
       // chains longest first (LPT): a forward chain carries one more QR and the assembly, so for
       // equal configurations all forward chains go out before the backward ones and the SMs that
       // receive an extra chain get a short one
       auto chain_cost = [&](const fd::Task& t) {
         const fd_problem& p = probs[g.idx[t.desc]];
-        const long long nb = p.nt / p.n_stab;
+        const long long nb = p.nt / p.n_stab, h = g.fsplit[t.desc];
+        if (h) {
+          const long long blocks = t.b == fd::CT_FWD ? h
+                                   : t.b == fd::CT_BWD2 ? h - 1 : nb - h;
+          return blocks * p.n_stab + 16 * blocks;
+        }
         return t.b == 0 ? (long long)p.nt + 16 * (nb + 1)
                         : (long long)(p.nt - p.n_stab) + 16 * (nb - 1);
       };
@@ -688,11 +737,14 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
         return chain_cost(a) > chain_cost(b);
       });
       Phase A, C;
-      if (!(mixed && tensor_chain(ctx, n, 1, three, 2 * nd, A)))
-        A = fp64_phase(ctx, n, R_FWD, 1, 2 * nd);
+      const int ntA = (int)g.tA.size();
+      if (!(mixed && tensor_chain(ctx, n, 1, three, ntA, A))) A = fp64_phase(ctx, n, R_FWD, 1, ntA);
       const bool two_rhs = (kind & K_GTAU) && (kind & (K_FORCE | K_RESP));
-      Phase B = fp64_phase(ctx, n, two_rhs ? R_BOUND2 : R_BOUND, 2,
-                           std::max(1, (int)g.tB.size()));
+      Phase B = any_split ? fp64_phase(ctx, n, R_BOUNDM, 9, std::max(1, (int)g.tB.size()))
+                          : fp64_phase(ctx, n, two_rhs ? R_BOUND2 : R_BOUND, 2,
+                                       std::max(1, (int)g.tB.size()));
+      B.which = 2;
+      B.merge = any_split ? 1 : 0;
       // the tensor-core wrap kernels cover the force rows (the shared-memory one also the
       // response traces); G(tau, 0) wraps run in FP64
       const bool mixed_wrap = mixed && !(kind & K_GTAU);
@@ -856,6 +908,7 @@ void build_tables(std::vector<Group>& groups, const fd_problem* probs, const Out
                   ? (double2*)(scratch + g.scratch_off + g.slots_bytes + g.fws_off[q])
                   : nullptr;
       d.nseg = g.nseg.empty() ? 0 : g.nseg[q];
+      d.fsplit = g.fsplit.empty() ? 0 : g.fsplit[q];
       d.Ec = d.Eic = nullptr;
       for (size_t i = 0; i < g.prep_src.size(); ++i) {
         const float* dst = (const float*)(scratch + g.scratch_off + g.prep_off + i * g.prep_each);
@@ -977,7 +1030,7 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
           break;
         case 2:
           fd::launch_boundary_fp64(dd, d_tasks + g.tB_off, (int)g.tB.size(), d_queue + qi,
-                                   d_status, scr, P.L, P.grid, s, !timing);
+                                   d_status, scr, P.L, P.grid, s, !timing, P.merge != 0);
           break;
         default:
           if (P.mixed)
@@ -1327,6 +1380,12 @@ int fd_bss_update(fd_ctx* ctx, int batch, const fd_bss_slice* slices, double* dl
 int fd_debug_skip_chains(fd_ctx* ctx, int on) {
   if (!ctx) return FD_ERR_INVALID;
   ctx->debug_skip_chains = on != 0;
+  return FD_OK;
+}
+
+int fd_set_force_split(fd_ctx* ctx, int mode) {
+  if (!ctx || mode < -1 || mode > 1) return FD_ERR_INVALID;
+  ctx->force_split = mode;
   return FD_OK;
 }
 

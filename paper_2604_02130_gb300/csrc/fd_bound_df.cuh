@@ -12,133 +12,6 @@
 
 namespace fd {
 
-// C(:, j) = sum_k A(:, k) B(k, j), a warp per pair of output columns, the rows of the pair in
-// registers (lane l: rows l + 32 u); A(i, k) = acol(k)[i] (a column loader), B(k, j) = bel(k, j).
-// epi(i, j, c4) stores an output element.  n <= 32 DF_RMAX.
-template <class ACol, class BEl, class Epi>
-__device__ __forceinline__ void df_gemm_pairs(int n, const ACol& acol, const BEl& bel,
-                                              const Epi& epi) {
-  const int lane = lane_id(), w = warp_id(), NW = nwarps();
-  for (int j0 = 2 * w; j0 < n; j0 += 2 * NW) {
-    const bool two = j0 + 1 < n;
-    DAcc a0[DF_RMAX], a1[DF_RMAX];
-#pragma unroll
-    for (int u = 0; u < DF_RMAX; ++u) {
-      a0[u] = DAcc{0.f, 0.f, 0.f, 0.f};
-      a1[u] = a0[u];
-    }
-    for (int k = 0; k < n; ++k) {
-      const df::c4 b0 = bel(k, j0);
-      const df::c4 b1 = two ? bel(k, j0 + 1) : df::c4{0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int u = 0; u < DF_RMAX; ++u) {
-        const int i = lane + 32 * u;
-        if (i < n) {
-          const df::c4 a = acol(k, i);
-          acc_mul(a0[u], a, b0);
-          acc_mul(a1[u], a, b1);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < DF_RMAX; ++u) {
-      const int i = lane + 32 * u;
-      if (i < n) {
-        epi(i, j0, acc_value(a0[u]));
-        if (two) epi(i, j0 + 1, acc_value(a1[u]));
-      }
-    }
-  }
-}
-
-// LU factorisation with partial pivoting of the df matrix A (n x n, column-major), the same row
-// operations on the nr columns of B, then B <- U^{-1} B: on return B = A^{-1} B_in.  Pivots on
-// FP32 magnitudes; a zero pivot flags s.misc[0] and continues with 1.
-__device__ inline void cta_lu_solve_df(int n, float4* A, float4* B, int nr, Small& s) {
-  const int lane = lane_id(), w = warp_id();
-  float4* piv = reinterpret_cast<float4*>(s.vbuf);  // reciprocal pivots (df), n of 2n slots
-  for (int k = 0; k < n; ++k) {
-    if (w == 0) {
-      float best = -1.f;
-      int bi = k;
-      for (int i = k + lane; i < n; i += 32) {
-        const float4 v = A[i + (size_t)k * n];
-        const float m = v.x * v.x + v.z * v.z;
-        if (m > best) {
-          best = m;
-          bi = i;
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
-      }
-      if (bi != k) {
-        for (int j = lane; j < n; j += 32) {
-          const float4 t = A[k + (size_t)j * n];
-          A[k + (size_t)j * n] = A[bi + (size_t)j * n];
-          A[bi + (size_t)j * n] = t;
-        }
-        for (int j = lane; j < nr; j += 32) {
-          const float4 t = B[k + (size_t)j * n];
-          B[k + (size_t)j * n] = B[bi + (size_t)j * n];
-          B[bi + (size_t)j * n] = t;
-        }
-      }
-      __syncwarp();
-      df::c4 p = ld4(A + k + (size_t)k * n);
-      float th, tl;
-      df::abs2(p, th, tl);
-      if (!(th > 0.f)) {
-        if (lane == 0) atomicOr(&s.misc[0], 1);
-        p = df::c4{1.f, 0.f, 0.f, 0.f};
-        th = 1.f;
-        tl = 0.f;
-      }
-      float yh, yl;
-      df::recip(th, tl, yh, yl);
-      const df::c4 pinv = df::scale(df_conj(p), yh, yl);
-      if (lane == 0) st4(piv + k, pinv);
-      for (int i = k + 1 + lane; i < n; i += 32)
-        st4(A + i + (size_t)k * n, c4mul(ld4(A + i + (size_t)k * n), pinv));
-    }
-    __syncthreads();
-    const int m = n - k - 1;
-    const int cols = m + nr;
-    for (int e = tid(); e < m * cols; e += nthr()) {
-      const int i = k + 1 + e % m, c = e / m;
-      const df::c4 l = ld4(A + i + (size_t)k * n);
-      float4* p = c < m ? A + i + (size_t)(k + 1 + c) * n : B + i + (size_t)(c - m) * n;
-      const df::c4 r = c < m ? ld4(A + k + (size_t)(k + 1 + c) * n) : ld4(B + k + (size_t)(c - m) * n);
-      st4(p, df::cms(ld4(p), l, r));
-    }
-    __syncthreads();
-  }
-  // back substitution with U's columns pre-scaled by the reciprocal pivots
-  for (int e = tid(); e < n * n; e += nthr()) {
-    const int i = e % n, k = e / n;
-    if (i < k) st4(A + e, c4mul(ld4(A + e), ld4(piv + k)));
-  }
-  __syncthreads();
-  for (int k = n - 1; k >= 1; --k) {
-    for (int e = tid(); e < k * nr; e += nthr()) {
-      const int i = e % k, j = e / k;
-      float4* p = B + i + (size_t)j * n;
-      st4(p, df::cms(ld4(p), ld4(A + i + (size_t)k * n), ld4(B + k + (size_t)j * n)));
-    }
-    __syncthreads();
-  }
-  for (int e = tid(); e < n * nr; e += nthr()) {
-    const int i = e % n;
-    st4(B + e, c4mul(ld4(B + e), ld4(piv + i)));
-  }
-  __syncthreads();
-}
-
 // Blocked LU with partial pivoting of the df matrix A (n x n, column-major), applied to the nr
 // columns of B, then B <- U^{-1} B: on return B = A^{-1} B_in.  Panels of DF_LU_P columns are
 // factored column by column (pivot search on FP32 magnitudes, full-row swaps of A and B); the
@@ -236,20 +109,12 @@ __device__ inline void cta_lu_solve_blocked_df(int n, float4* A, float4* B, int 
     if (pe < n) {
       const int m = n - pe;
       auto l21 = [&](int i, int k) { return ld4(A + pe + i + (size_t)(kb + k) * n); };
-      df_gemm_tiled(
+      df_gemm_sub_tiled(
           m, m, pe - kb, l21, [&](int k, int j) { return ld4(A + kb + k + (size_t)(pe + j) * n); },
-          [&](int i, int j, df::c4 v) {
-            float4* q = A + pe + i + (size_t)(pe + j) * n;
-            st4(q, df::cms(ld4(q), v, one));
-          },
-          sm);
-      df_gemm_tiled(
+          [&](int i, int j) { return A + pe + i + (size_t)(pe + j) * n; }, sm);
+      df_gemm_sub_tiled(
           m, nr, pe - kb, l21, [&](int k, int j) { return ld4(B + kb + k + (size_t)j * n); },
-          [&](int i, int j, df::c4 v) {
-            float4* q = B + pe + i + (size_t)j * n;
-            st4(q, df::cms(ld4(q), v, one));
-          },
-          sm);
+          [&](int i, int j) { return B + pe + i + (size_t)j * n; }, sm);
     }
   }
   // back substitution: B <- U^{-1} B by blocks from the last one
@@ -275,14 +140,10 @@ __device__ inline void cta_lu_solve_blocked_df(int n, float4* A, float4* B, int 
     }
     __syncthreads();
     if (kb > 0)
-      df_gemm_tiled(
+      df_gemm_sub_tiled(
           kb, nr, pe - kb, [&](int i, int k) { return ld4(A + i + (size_t)(kb + k) * n); },
           [&](int k, int j) { return ld4(B + kb + k + (size_t)j * n); },
-          [&](int i, int j, df::c4 v) {
-            float4* q = B + i + (size_t)j * n;
-            st4(q, df::cms(ld4(q), v, one));
-          },
-          sm);
+          [&](int i, int j) { return B + i + (size_t)j * n; }, sm);
   }
   __syncthreads();
 }
@@ -324,18 +185,20 @@ __device__ inline void boundary_green_df(int n, const double2* XL, const double2
         st4(Mb + i + (size_t)j * n, df::scale(v, sh, sl));
       },
       sm);
-  // M += diag(c) T_L T_R^H diag(d)
-  df_gemm_tiled(
-      n, n, n, [&](int i, int k) { return df_of(TL[i + (size_t)k * n]); },
-      [&](int k, int j) { return df_conj(df_of(TR[j + (size_t)k * n])); },
-      [&](int i, int j, df::c4 v) {
+  // M += diag(c) T_L T_R^H diag(d), as M -= (-diag(c) T_L) (T_R^H diag(d))
+  df_gemm_sub_tiled(
+      n, n, n,
+      [&](int i, int k) {
         float sh, sl;
-        df::split(s.sc[i] * s.sd[j], sh, sl);
-        float4* p = Mb + i + (size_t)j * n;
-        const df::c4 t = df::scale(v, sh, sl);
-        st4(p, df::cms(ld4(p), c4neg(t), df::c4{1.f, 0.f, 0.f, 0.f}));
+        df::split(-s.sc[i], sh, sl);
+        return df::scale(df_of(TL[i + (size_t)k * n]), sh, sl);
       },
-      sm);
+      [&](int k, int j) {
+        float sh, sl;
+        df::split(s.sd[j], sh, sl);
+        return df::scale(df_conj(df_of(TR[j + (size_t)k * n])), sh, sl);
+      },
+      [&](int i, int j) { return Mb + i + (size_t)j * n; }, sm);
   // W <- M^{-1} W
   cta_lu_solve_blocked_df(n, Mb, Wb, n, s, sm);
   // G = X_R diag(b) W
@@ -351,5 +214,6 @@ __device__ inline void boundary_green_df(int n, const double2* XL, const double2
       },
       sm);
 }
+
 
 }  // namespace fd

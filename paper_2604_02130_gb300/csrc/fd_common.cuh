@@ -61,6 +61,7 @@ struct Desc {
   double2* R;          // response traces tr(O G_r), r = 0..nt-1, or null
   int* sync;           // phased path: this configuration's progress flags (SyncFlag), else null
   int nseg;            // time-parallel log det/G: number of segments of the chain (0: not split)
+  int fsplit;          // force: chains split at block h = fsplit (0: not split; see ChainSpan)
   // streamed tensor-core kernels (nx above one tile): E and E^{-1} as chunked TF32 operands
   // (hi at the pointer, lo after it; see BLayout), prepared once per call; else null
   const float* Ec;
@@ -73,10 +74,12 @@ struct Desc {
 // still runs) and each task waits only for the data it reads, through per-configuration progress
 // flags written with release and read with acquire semantics at GPU scope.
 enum SyncFlag {
-  SF_FWD = 0,  // forward chain: left checkpoints 1..v written; nb once G_0 (= G) is written
-  SF_BWD = 1,  // backward chain: v right checkpoints written (blocks nb, nb-1, ...)
-  SF_BND = 2,  // boundary Green's functions written (count)
-  SF_NUM = 4   // ints per configuration (padding)
+  SF_FWD = 0,   // forward chain: left checkpoints 1..v written; nb once G_0 (= G) is written
+  SF_BWD = 1,   // backward chain: v right checkpoints written (blocks nb, nb-1, ...)
+  SF_BND = 2,   // boundary Green's functions written (count)
+  SF_FWD2 = 3,  // split chains: v local left products of the second forward half written
+  SF_BWD2 = 4,  // split chains: v local right products of the second backward half written
+  SF_NUM = 8    // ints per configuration (padding)
 };
 // A wait gives up after this many cycles without any change of the configuration's flags
 // (~4 s at 2 GHz; one checkpoint interval of the largest supported size takes well under that).
@@ -118,19 +121,21 @@ __device__ __forceinline__ int flag_load(const int* f) {
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
   return v;
 }
-// CTA-wide wait until flags[SF_FWD] >= fwd, flags[SF_BWD] >= bwd and flags[SF_BND] >= bnd.
-// Thread 0 polls; it gives up (false) after FD_SYNC_WAIT_CYCLES without progress of the flags.
-// `bcast` is a shared int.
+// CTA-wide wait until flags[SF_FWD] >= fwd, flags[SF_BWD] >= bwd, flags[SF_BND] >= bnd,
+// flags[SF_FWD2] >= fwd2 and flags[SF_BWD2] >= bwd2.  Thread 0 polls; it gives up (false) after
+// FD_SYNC_WAIT_CYCLES without progress of the flags.  `bcast` is a shared int.
 __device__ __forceinline__ bool cta_wait_flags(const int* flags, int fwd, int bwd, int bnd,
-                                               volatile int* bcast) {
+                                               volatile int* bcast, int fwd2 = 0, int bwd2 = 0) {
   if (threadIdx.x == 0) {
     long long t0 = clock64();
     int ok = 1, last = -1;
     for (;;) {
       const int f0 = flag_load(flags + SF_FWD), f1 = flag_load(flags + SF_BWD),
                 f2 = flag_load(flags + SF_BND);
-      if (f0 >= fwd && f1 >= bwd && f2 >= bnd) break;
-      const int sum = f0 + f1 + f2;
+      const int f3 = fwd2 > 0 ? flag_load(flags + SF_FWD2) : 0,
+                f4 = bwd2 > 0 ? flag_load(flags + SF_BWD2) : 0;
+      if (f0 >= fwd && f1 >= bwd && f2 >= bnd && f3 >= fwd2 && f4 >= bwd2) break;
+      const int sum = f0 + f1 + f2 + f3 + f4;
       const long long now = clock64();
       if (sum != last) {
         last = sum;
@@ -161,9 +166,11 @@ struct FWork {
   int n, nb;
   __host__ __device__ static size_t stride(int n) { return (size_t)2 * n * n + (n + 1) / 2; }
   // gt: room for the boundary values G((b-1) ns, 0) of the unequal-time Green's function
-  __host__ __device__ static size_t elems(int n, int nb, bool gt, bool op = false) {
+  // split: room for the second forward half's full product (force chains split at a block)
+  __host__ __device__ static size_t elems(int n, int nb, bool gt, bool op = false,
+                                          bool split = false) {
     return (size_t)2 * (nb - 1) * stride(n) + (size_t)(gt ? 2 : 1) * nb * n * n +
-           (op ? ((size_t)n * n + 3) / 4 : 0);
+           (op ? ((size_t)n * n + 3) / 4 : 0) + (split ? stride(n) : 0);
   }
   __device__ double2* LX(int b) const { return base + (size_t)(b - 1) * stride(n); }
   __device__ double2* LT(int b) const { return LX(b) + (size_t)n * n; }
@@ -180,6 +187,10 @@ struct FWork {
     return b == 1 ? Gb(1)
                   : base + (size_t)2 * (nb - 1) * stride(n) + (size_t)(nb + b - 1) * n * n;
   }
+  // split force chains (no G(tau, 0), no O): the product of blocks h+1..nb from the identity
+  __device__ double2* SX() const { return base + (size_t)2 * (nb - 1) * stride(n) + (size_t)nb * n * n; }
+  __device__ double2* ST() const { return SX() + (size_t)n * n; }
+  __device__ double* SD() const { return (double*)(SX() + (size_t)2 * n * n); }
   // O (row-major) in FP32, after the G(tau, 0) values when those are kept (gt)
   __device__ float* OF(bool gt) const {
     return (float*)(base + (size_t)2 * (nb - 1) * stride(n) + (size_t)(gt ? 2 : 1) * nb * n * n);
@@ -191,6 +202,33 @@ struct Task {
   int desc;  // index into the launch's descriptor array
   int b;     // block, 1-based
 };
+
+// Chain tasks (Task.b of the chain launch): 0 forward chain, 1 backward chain, 2 + s segment s
+// of a time-parallel log det/G split, and the second halves of force chains split at block h.
+enum ChainCode { CT_FWD = 0, CT_BWD = 1, CT_SEG = 2, CT_FWD2 = 64, CT_BWD2 = 65 };
+
+// Blocks of a force chain task, forward ascending from `first` to `last`, backward descending.
+// Unsplit (h = 0): forward 1..nb with the assembly at the end (log det, G_0), backward nb..2.
+// Split at h (Desc.fsplit): forward 1..h, its second half h+1..nb from the identity (local
+// products L'_b = B_{b ns}...B_{h ns+1}, the full one in FWork::SX), backward nb..h+1, its second
+// half h..2 from the identity (local right products).  The boundary phase merges a local product
+// with the first half's last checkpoint (L_b = L'_b L_h, R_b = R'_b R_{h+1}) and forms G_0 and
+// log det from L'_nb L_h.  The progress flag counts the checkpoints written, in chain order.
+struct ChainSpan {
+  bool fwd;
+  int first, last;
+  int flag;       // SyncFlag index
+  bool assemble;  // unsplit forward chain: log det and G_0 at the end
+  __device__ int count(int b) const { return fwd ? b - first + 1 : first - b + 1; }
+};
+__device__ __forceinline__ ChainSpan chain_span(int code, int nb, int h) {
+  switch (code) {
+    case CT_FWD2: return ChainSpan{true, h + 1, nb, SF_FWD2, false};
+    case CT_BWD2: return ChainSpan{false, h, 2, SF_BWD2, false};
+    case CT_BWD: return ChainSpan{false, nb, h > 0 ? h + 1 : 2, SF_BWD, false};
+    default: return ChainSpan{true, 1, h > 0 ? h : nb, SF_FWD, h == 0};
+  }
+}
 
 // Where each working matrix lives: shared memory (offset in bytes from the dynamic smem base)
 // or the CTA's global scratch slot (offset in bytes from the slot base).  Each persistent CTA

@@ -935,4 +935,41 @@ __device__ __forceinline__ double wrap_pi(double x) {
   return y;
 }
 
+// ---------------------------------------------------------------- product of two UDV factors
+// Section 7's stabilised product of two factored matrices, Xs Ds Ts (acting later) times
+// Xa Da Ta:  Xs Ds Ts Xa Da Ta = Xs [Ds Ts Xa] Da Ta  with  Xc = e^{-m} Ds (Ts Xa),
+// m = max log Ds, re-factored by the pre-pivoted QR (Xc Da Ta = Q D' T'), so that
+// X = Xs Q, log D = log D' + m, T = T'.  The row scaling e^{log Ds - m} is formed: a factor whose
+// log D spans more than 700 marks the configuration (misc[0]) instead of losing rows silently.
+// X = Xs Q is a product of two Householder products (det X = +1).  Scratch: Xc, Q (n^2 each);
+// X, T, logD receive the result (X may alias Xa, logD may alias lDa; T may not alias Ta).
+__device__ inline void cta_merge(int n, const double2* Xs, const double2* Ts, const double* lDs,
+                                 const double2* Xa, const double2* Ta, const double* lDa,
+                                 double2* Xc, double2* Q, double2* X, double2* T, double* logD,
+                                 Small& s) {
+  if (warp_id() == 0) {
+    double mx = -INFINITY;
+    for (int k = lane_id(); k < n; k += 32) mx = fmax(mx, lDs[k]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane_id() == 0) s.red[9] = mx;
+  }
+  __syncthreads();
+  const double m = s.red[9];
+  for (int k = tid(); k < n; k += nthr()) {
+    const double e = lDs[k] - m;
+    if (e < -700.0) atomicOr(&s.misc[0], 1);  // the row scaling would underflow
+    s.sa[k] = exp(e);
+    logD[k] = lDa[k];
+  }
+  __syncthreads();
+  const double* sa = s.sa;
+  cta_gemm<false>(n, CMat{Ts, 1, n}, CMat{Xa, 1, n},
+                  [&](int i, int j, cplx v) { st(Xc + i + j * n, sa[i] * v); });
+  cta_reortho(n, Xc, Q, Ta, T, logD, s);
+  for (int k = tid(); k < n; k += nthr()) logD[k] += m;
+  cta_gemm<false>(n, CMat{Xs, 1, n}, CMat{Q, 1, n},
+                  [&](int i, int j, cplx v) { st(X + i + j * n, v); });
+  __syncthreads();
+}
+
 }  // namespace fd

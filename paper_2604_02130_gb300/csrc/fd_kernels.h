@@ -36,9 +36,10 @@ void launch_fwd_fp64(const Desc* descs, int ndesc, int* queue, int* status, char
 void launch_chain_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                        char* scratch, const Layout& L, int grid, cudaStream_t stream);
 // pdl: launch as a programmatic dependent of the previous kernel (tasks wait on the flags)
+// merge: the variant that merges split chains' checkpoints first (attrs/occupancy: which 9)
 void launch_boundary_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue,
                           int* status, char* scratch, const Layout& L, int grid,
-                          cudaStream_t stream, bool pdl);
+                          cudaStream_t stream, bool pdl, bool merge);
 void launch_wrap_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                       char* scratch, const Layout& L, int grid, cudaStream_t stream, bool pdl);
 // time-parallel log det/G: merge of the segment products and assembly (kernel id 8)
@@ -85,6 +86,10 @@ void launch_boundary_big(const Desc* descs, const Task* tasks, int ntasks, int* 
 cudaError_t set_smem_big(int bytes);
 // kernel ids: 1 chains, 2 boundary Green's functions, 3 wraps
 cudaError_t attrs_big(int which, cudaFuncAttributes* a);
+// df numbers of shared memory: the streamed chains' df QR at size n, the boundary Green's
+// function's GEMM tiles
+int big_qr_vcap(int n);
+int big_bound_tiles();
 
 // local (BSS) slice updates (one CTA per configuration; G in shared memory as double-float
 // pairs when maxn is small enough, else FP64 in place)

@@ -435,9 +435,11 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
     if (q >= ntasks) break;
     const Task tk = tasks[q];
     const Desc d = descs[tk.desc];
-    const bool fwd = tk.b != 1;
-    const int sg = tk.b - 2;
+    // Task.b: a ChainCode (forward/backward chain, its second half, or a log det/G segment)
     const int ns = d.nstab, nb = d.nt / d.nstab;
+    const int sg = (tk.b >= CT_SEG && tk.b < CT_FWD2) ? tk.b - CT_SEG : -1;
+    const ChainSpan sp = chain_span(tk.b, nb, d.fsplit);
+    const bool fwd = sg >= 0 || sp.fwd;
     const FWork W{d.fws, n, nb};
     const bool keep = d.fws != nullptr;
     Small s = carve_small(smem + L.small_off, n);
@@ -450,7 +452,8 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
     for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
     __syncthreads();
     if (fwd) {
-      const int kb = sg >= 0 ? nb / d.nseg : nb, b_first = sg >= 0 ? sg * kb + 1 : 1;
+      const int kb = sg >= 0 ? nb / d.nseg : sp.last - sp.first + 1;
+      const int b_first = sg >= 0 ? sg * kb + 1 : sp.first;
       for (int b = b_first; b < b_first + kb && ok; ++b) {
         const int t0 = (b - 1) * ns;
         phase32(n, pf, d.phi + (size_t)t0 * n, 1.f);
@@ -470,18 +473,21 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
         cta_reortho_df(n, Xc, Xn, T, To, s.logD, s, (float4*)m.stages,
                        L.nstages * L.stage_bytes / 16);
         double2* t2 = T; T = To; To = t2;
-        if (keep && sg < 0 && b < nb) {
-          cta_copy(n * n, W.LX(b), Xn);
-          cta_copy(n * n, W.LT(b), T);
-          for (int k = tid(); k < n; k += nthr()) W.LD(b)[k] = s.logD[k];
+        if (keep && sg < 0 && (b < nb || !sp.assemble)) {  // a split half's product: SX
+          cta_copy(n * n, b < nb ? W.LX(b) : W.SX(), Xn);
+          cta_copy(n * n, b < nb ? W.LT(b) : W.ST(), T);
+          double* ldst = b < nb ? W.LD(b) : W.SD();
+          for (int k = tid(); k < n; k += nthr()) ldst[k] = s.logD[k];
           __syncthreads();
-          if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, b);
+          if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
         }
       }
       if (ok && sg >= 0) {  // segment result in the checkpoint storage of block sg+1
         cta_copy(n * n, W.LX(sg + 1), Xn);
         cta_copy(n * n, W.LT(sg + 1), T);
         for (int k = tid(); k < n; k += nthr()) W.LD(sg + 1)[k] = s.logD[k];
+        if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
+      } else if (ok && !sp.assemble) {
         if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
       } else if (ok) {
         double2* G0 = keep ? W.Gb(1) : To;  // To is free after the last swap
@@ -506,9 +512,10 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
         if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, nb);
       }
     } else {
-      for (int b = nb; b >= 2 && ok; --b) {
+      for (int b = sp.first; b >= sp.last && ok; --b) {
         const int t0 = (b - 1) * ns;
-        fill_cols(n, L.Mc, L.Kp, b == nb ? nullptr : Xn, none, none, Ahi, Alo, L.three != 0);
+        fill_cols(n, L.Mc, L.Kp, b == sp.first ? nullptr : Xn, none, none, Ahi, Alo,
+                  L.three != 0);
         publish_for_copies();
         for (int t = b * ns - 1; t >= t0 && ok; --t) {
           phase32(n, pf, d.phi + (size_t)t * n, -1.f);
@@ -524,14 +531,14 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
         cta_copy(n * n, W.RT(b), T);
         for (int k = tid(); k < n; k += nthr()) W.RD(b)[k] = s.logD[k];
         __syncthreads();
-        if (tid() == 0 && d.sync) flag_store(d.sync + SF_BWD, nb - b + 1);
+        if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
       }
       if (ok && tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     }
     if (!ok) {
       if (tid() == 0) {
         atomicMax(status + d.user_index, ST_TIMEOUT);
-        if (d.sync) flag_store(d.sync + (fwd ? SF_FWD : SF_BWD), nb);
+        if (d.sync) flag_store(d.sync + (sg >= 0 ? SF_FWD : sp.flag), nb);
       }
       break;
     }
@@ -667,11 +674,14 @@ __global__ void __launch_bounds__(256, 1) k_wrap_big(const Desc* __restrict__ de
 // ------------------------------------------------------------------ boundary Green's functions
 // Phase B of the mixed force for the streamed size classes: G_{(b-1) ns} of block b from the left
 // checkpoint b-1 and the right checkpoint b, in double-float (fd_bound_df.cuh); three n x n df
-// work matrices in the CTA's slot.
-__global__ void __launch_bounds__(256) k_boundary_big(const Desc* __restrict__ descs,
-                                                      const Task* __restrict__ tasks, int ntasks,
-                                                      int* queue, int* status, char* scratch,
-                                                      BLayout L) {
+// work matrices in the CTA's slot.  (Split chains are not planned for these classes: merging a
+// second half's checkpoint forms a row scaling that spans beta/2 times the hopping bandwidth,
+// beyond the FP32 exponent range of double-float numbers at the low temperatures these sizes
+// run at; the FP64 boundary kernel merges within FP64's range.)
+__global__ void __launch_bounds__(256, 2) k_boundary_big(const Desc* __restrict__ descs,
+                                                         const Task* __restrict__ tasks,
+                                                         int ntasks, int* queue, int* status,
+                                                         char* scratch, BLayout L) {
   extern __shared__ __align__(1024) char smem[];
   char* slot = scratch + (size_t)blockIdx.x * L.slot_bytes;
   int* qs = (int*)(smem + L.bar_off);
@@ -699,6 +709,11 @@ __global__ void __launch_bounds__(256) k_boundary_big(const Desc* __restrict__ d
     if (tid() == 0 && d.sync) flag_add(d.sync + SF_BND, 1);
   }
 }
+
+// Shared memory (df numbers): the df QR (its panel, T and Gram matrices and GEMM tiles) and the
+// boundary Green's function (64 x 64 GEMM tiles).
+int big_qr_vcap(int n) { return DF_PANEL * (n + 2 * DF_PANEL) + DF_TILE_ELEMS(16, 256); }
+int big_bound_tiles() { return DF_TILE_ELEMS(64, 64); }
 
 // ------------------------------------------------------------------ operand preparation
 // Chunked TF32 copies (hi, then lo) of the distinct E and E^{-1} matrices of a call, rows padded

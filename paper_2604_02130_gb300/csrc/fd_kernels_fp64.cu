@@ -227,12 +227,12 @@ __device__ void wrap_backward(int n, const double* E, const double* Einv, const 
 }
 
 // ------------------------------------------------------------------ force, phase A
-// Two independent chains per configuration (task q: configuration q/2, direction q%2).
+// Two independent chains per configuration, four when they are split (ChainSpan):
 //   forward : X D T <- B_t ... B_1 with a QR every n_stab slices; left checkpoints after blocks
 //             1..nb-1; at the end log det and G_0 = G (also the boundary G of block 1).
 //   backward: the right products as adjoints, X_R D_R T_R <- B_{t+1}^H ... B_Nt^H, a QR every
 //             n_stab slices; right checkpoints at t = (b-1) n_stab for blocks b = nb..2.
-__global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ descs,
+__global__ void __launch_bounds__(256, 3) k_chain_fp64(const Desc* __restrict__ descs,
                                                      const Task* __restrict__ tasks, int ntasks,
                                                      int* queue, int* status, char* scratch,
                                                      Layout L) {
@@ -245,10 +245,11 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
     if (q >= ntasks) return;
     const Task tk = tasks[q];
     const Desc d = descs[tk.desc];
-    // Task.b: 0 forward chain, 1 backward chain, 2 + s segment s of a time-parallel split
-    const bool fwd = tk.b != 1;
-    const int sg = tk.b - 2;
-    const int n = d.nx, ns = d.nstab, nb = d.nt / d.nstab;
+    // Task.b: a ChainCode (forward/backward chain, its second half, or a log det/G segment)
+    const int ns = d.nstab, nb = d.nt / d.nstab;
+    const int sg = (tk.b >= CT_SEG && tk.b < CT_FWD2) ? tk.b - CT_SEG : -1;
+    const ChainSpan sp = chain_span(tk.b, nb, d.fsplit);
+    const int n = d.nx;
     const FWork W{d.fws, n, nb};
     Small s = carve_small(smem + L.small_off, n);
     if (tid() == 0) {
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
     cta_identity(n, T);
     for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
     __syncthreads();
-    if (fwd && sg >= 0) {
+    if (sg >= 0) {
       // one segment of the chain from the identity: blocks sg*kb+1 .. (sg+1)*kb, result in
       // the checkpoint storage of block sg+1 (merged by k_merge_fp64)
       const int kb = nb / d.nseg, b_first = sg * kb + 1;
@@ -279,41 +280,46 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
       cta_copy(n * n, W.LT(sg + 1), T);
       for (int k = tid(); k < n; k += nthr()) W.LD(sg + 1)[k] = s.logD[k];
       if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
-    } else if (fwd) {
-      for (int b = 1; b <= nb; ++b) {
+    } else if (sp.fwd) {
+      for (int b = sp.first; b <= sp.last; ++b) {
         fwd_slices(n, B.E, d.phi, (b - 1) * ns, b * ns, X, Xo, s);
         cta_reortho(n, X, Xo, T, To, s.logD, s);
         double2* t1 = X; X = Xo; Xo = t1;
         double2* t2 = T; T = To; To = t2;
-        if (b < nb) {
-          cta_copy(n * n, W.LX(b), X);
-          cta_copy(n * n, W.LT(b), T);
-          for (int k = tid(); k < n; k += nthr()) W.LD(b)[k] = s.logD[k];
+        if (b < nb || !sp.assemble) {  // left checkpoint b (the split half's full product: SX)
+          cta_copy(n * n, b < nb ? W.LX(b) : W.SX(), X);
+          cta_copy(n * n, b < nb ? W.LT(b) : W.ST(), T);
+          double* ldst = b < nb ? W.LD(b) : W.SD();
+          for (int k = tid(); k < n; k += nthr()) ldst[k] = s.logD[k];
           __syncthreads();
-          if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, b);
+          if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
         }
       }
-      cta_assemble(n, X, T, s.logD, Xo, To, s, s.red + 2, s.red + 3);
-      const double re = s.red[2], im = wrap_pi(s.red[3]);
-      if (tid() == 0) {
-        d.logdet[0] = re;
-        d.logdet[1] = im;
+      if (sp.assemble) {
+        cta_assemble(n, X, T, s.logD, Xo, To, s, s.red + 2, s.red + 3);
+        const double re = s.red[2], im = wrap_pi(s.red[3]);
+        if (tid() == 0) {
+          d.logdet[0] = re;
+          d.logdet[1] = im;
+        }
+        cta_copy(n * n, W.Gb(1), To);
+        if (d.G) write_green(n, To, d.G);
+        if (d.Gt) write_green(n, To, d.Gt);  // G(0, 0) = G
+        if (d.nf) cta_fermion_number(n, To, d.nf);
+        if (d.O) {  // FP32 copy of the response operator for the tensor-core wraps
+          float* of = W.OF(d.Gt != nullptr);
+          for (int e = tid(); e < n * n; e += nthr()) of[e] = (float)d.O[e];
+        }
+        __syncthreads();
+        if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, nb);  // G_0 written
+        if (tid() == 0)
+          atomicMax(status + d.user_index,
+                    (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
+      } else if (tid() == 0 && s.misc[0]) {
+        atomicMax(status + d.user_index, ST_NUMERIC);
       }
-      cta_copy(n * n, W.Gb(1), To);
-      if (d.G) write_green(n, To, d.G);
-      if (d.Gt) write_green(n, To, d.Gt);  // G(0, 0) = G
-      if (d.nf) cta_fermion_number(n, To, d.nf);
-      if (d.O) {  // FP32 copy of the response operator for the tensor-core wraps
-        float* of = W.OF(d.Gt != nullptr);
-        for (int e = tid(); e < n * n; e += nthr()) of[e] = (float)d.O[e];
-      }
-      __syncthreads();
-      if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, nb);  // G_0 written
-      if (tid() == 0)
-        atomicMax(status + d.user_index,
-                  (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
     } else {
-      for (int b = nb; b >= 2; --b) {
+      for (int b = sp.first; b >= sp.last; --b) {
         bwd_slices(n, B.E, d.phi, (b - 1) * ns, b * ns, X, Xo, s);
         cta_reortho(n, X, Xo, T, To, s.logD, s);
         double2* t1 = X; X = Xo; Xo = t1;
@@ -322,7 +328,7 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
         cta_copy(n * n, W.RT(b), T);
         for (int k = tid(); k < n; k += nthr()) W.RD(b)[k] = s.logD[k];
         __syncthreads();
-        if (tid() == 0 && d.sync) flag_store(d.sync + SF_BWD, nb - b + 1);
+        if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
       }
       if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     }
@@ -332,7 +338,12 @@ __global__ void __launch_bounds__(256) k_chain_fp64(const Desc* __restrict__ des
 
 // ------------------------------------------------------------------ force, phase B
 // Boundary Green's function of block b (b = 2..nb): G_{(b-1)ns} from the left checkpoint b-1
-// and the right checkpoint b (Section 7 steps 7-9 with t1 = t2; Section 5.3).
+// and the right checkpoint b (Section 7 steps 7-9 with t1 = t2; Section 5.3).  With the chains
+// split at block h (ChainSpan) a left checkpoint beyond h is first merged with L_h and a right
+// one below h+1 with R_{h+1} (cta_merge), and task b = 1 forms the full product L'_nb L_h, the
+// assembly (log det, G_0) and the outputs of the forward chain.
+// MERGE: the variant for calls with split chains (the plain one keeps its register budget).
+template <bool MERGE>
 __global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ descs,
                                                         const Task* __restrict__ tasks,
                                                         int ntasks, int* queue, int* status,
@@ -346,10 +357,13 @@ __global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ 
     if (q >= ntasks) return;
     const Task tk = tasks[q];
     const Desc d = descs[tk.desc];
-    const int n = d.nx, nb = d.nt / d.nstab, b = tk.b;
+    const int n = d.nx, nb = d.nt / d.nstab, b = tk.b, h = MERGE ? d.fsplit : 0;
     const FWork W{d.fws, n, nb};
-    // left checkpoint b-1 and right checkpoint b
-    if (d.sync && !cta_wait_flags(d.sync, b - 1, nb - b + 1, 0, slot + 1) && tid() == 0)
+    // inputs: left checkpoint b-1 (merged when beyond h), right checkpoint b (merged below h+1)
+    const bool ml = h > 0 && b - 1 > h, mr = h > 0 && b >= 2 && b <= h;
+    const int wf = b == 1 ? h : (ml ? h : b - 1), wf2 = b == 1 ? nb - h : (ml ? b - 1 - h : 0);
+    const int wb = b == 1 ? 0 : (mr ? nb - h : nb - b + 1), wb2 = mr ? h - b + 1 : 0;
+    if (d.sync && !cta_wait_flags(d.sync, wf, wb, 0, slot + 1, wf2, wb2) && tid() == 0)
       atomicMax(status + d.user_index, ST_TIMEOUT);
     Small s = carve_small(smem + L.small_off, n);
     if (tid() == 0) {
@@ -360,8 +374,44 @@ __global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ 
     double2* Ma = (double2*)place(smem, slotp, L, B_GA);
     double2* Mb = (double2*)place(smem, slotp, L, B_GB);
     __syncthreads();
-    boundary_green(n, false, W.LX(b - 1), W.LT(b - 1), W.LD(b - 1), W.RX(b), W.RT(b), W.RD(b),
-                   Ma, Mb, (d.F || d.R) ? W.Gb(b) : nullptr, s, d.Gt ? W.GT(b) : nullptr);
+    if (MERGE && b == 1) {  // split chains: G_0 and log det from the full product L'_nb L_h
+      double2* X = (double2*)place(smem, slotp, L, B_X0);
+      double2* T = (double2*)place(smem, slotp, L, B_T0);
+      cta_merge(n, W.SX(), W.ST(), W.SD(), W.LX(h), W.LT(h), W.LD(h), Ma, Mb, X, T, s.logD, s);
+      cta_assemble(n, X, T, s.logD, Ma, Mb, s, s.red + 2, s.red + 3);
+      const double pi = 3.14159265358979323846;  // det X = +1 after the merge
+      const double re = s.red[2], im = wrap_pi(s.red[3] - ((n - 1) & 1 ? pi : 0.0));
+      if (tid() == 0) {
+        d.logdet[0] = re;
+        d.logdet[1] = im;
+      }
+      cta_copy(n * n, W.Gb(1), Mb);
+      if (d.G) write_green(n, Mb, d.G);
+      if (d.nf) cta_fermion_number(n, Mb, d.nf);
+      __syncthreads();
+      if (tid() == 0) {
+        atomicMax(status + d.user_index,
+                  (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
+        if (d.sync) flag_store(d.sync + SF_FWD, nb);  // G_0 written
+      }
+      __syncthreads();
+      continue;
+    }
+    const double2 *XL = W.LX(b - 1), *TL = W.LT(b - 1), *XR = W.RX(b), *TR = W.RT(b);
+    const double *DL = W.LD(b - 1), *DR = W.RD(b);
+    if (MERGE && (ml || mr)) {
+      double2* X = (double2*)place(smem, slotp, L, B_X0);
+      double2* T = (double2*)place(smem, slotp, L, B_T0);
+      if (ml) {
+        cta_merge(n, XL, TL, DL, W.LX(h), W.LT(h), W.LD(h), Ma, Mb, X, T, s.logD, s);
+        XL = X; TL = T; DL = s.logD;
+      } else {
+        cta_merge(n, XR, TR, DR, W.RX(h + 1), W.RT(h + 1), W.RD(h + 1), Ma, Mb, X, T, s.logD, s);
+        XR = X; TR = T; DR = s.logD;
+      }
+    }
+    boundary_green(n, false, XL, TL, DL, XR, TR, DR, Ma, Mb, (d.F || d.R) ? W.Gb(b) : nullptr, s,
+                   d.Gt ? W.GT(b) : nullptr);
     if (d.Gt) write_green(n, W.GT(b), d.Gt + (size_t)(b - 1) * d.nstab * n * n);
     if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     __syncthreads();
@@ -467,15 +517,12 @@ __global__ void __launch_bounds__(256) k_wrap_fp64(const Desc* __restrict__ desc
 }
 
 // ------------------------------------------------------------------ time-parallel log det/G
-// Merge of the nseg segment products of one configuration (Section 7's stabilised product of two
-// UDV factors, applied segment by segment) and the assembly.  With the accumulated product
-// Xa Da Ta and the next segment Xs Ds Ts (acting later):
-//   Xs Ds Ts Xa Da Ta = Xs [Ds Ts Xa] Da Ta,  Xc = e^{-m} Ds (Ts Xa),  m = max log Ds,
-// re-factored by the pre-pivoted QR (Xc Da Ta = Q D' T'), so X <- Xs Q, D <- e^m D', T <- T'.
-// The row scaling by Ds is formed (e^{logDs - m} <= 1): a segment's log D must span less than
-// 700 (else FD_ERR_NUMERIC) -- beta per segment up to ~100 at kappa = 1 on this lattice.
-// After a merge X = Xs Q is a product of two Householder products: det X = +1 (the assembly
-// assumes (-1)^{n-1}, right for S = 1).
+// Merge of the nseg segment products of one configuration (cta_merge: Section 7's stabilised
+// product of two UDV factors, applied segment by segment, the accumulated product Xa Da Ta
+// acting first) and the assembly.  A segment's log D must span less than 700 (else
+// FD_ERR_NUMERIC) -- beta per segment up to ~100 at kappa = 1 on this lattice.  After a merge
+// X = Xs Q is a product of two Householder products: det X = +1 (the assembly assumes
+// (-1)^{n-1}, right for S = 1).
 __global__ void __launch_bounds__(256) k_merge_fp64(const Desc* __restrict__ descs, int ndesc,
                                                      int* queue, int* status, char* scratch,
                                                      Layout L) {
@@ -504,30 +551,9 @@ __global__ void __launch_bounds__(256) k_merge_fp64(const Desc* __restrict__ des
     for (int k = tid(); k < n; k += nthr()) s.logD[k] = W.LD(1)[k];
     __syncthreads();
     for (int sg = 1; sg < S; ++sg) {
-      const double* lds = W.LD(sg + 1);
-      if (warp_id() == 0) {
-        double mx = -INFINITY;
-        for (int k = lane_id(); k < n; k += 32) mx = fmax(mx, lds[k]);
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane_id() == 0) s.red[9] = mx;
-      }
-      __syncthreads();
-      const double m = s.red[9];
-      for (int k = tid(); k < n; k += nthr()) {
-        const double e = lds[k] - m;
-        if (e < -700.0) atomicOr(&s.misc[0], 1);  // the row scaling would underflow
-        s.sa[k] = exp(e);
-      }
-      __syncthreads();
-      const double* sa = s.sa;
-      cta_gemm<false>(n, CMat{W.LT(sg + 1), 1, n}, CMat{Xa, 1, n},
-                      [&](int i, int j, cplx v) { st(Xc + i + j * n, sa[i] * v); });
-      cta_reortho(n, Xc, Xn, Ta, Tn, s.logD, s);
-      for (int k = tid(); k < n; k += nthr()) s.logD[k] += m;
-      cta_gemm<false>(n, CMat{W.LX(sg + 1), 1, n}, CMat{Xn, 1, n},
-                      [&](int i, int j, cplx v) { st(Xa + i + j * n, v); });
+      cta_merge(n, W.LX(sg + 1), W.LT(sg + 1), W.LD(sg + 1), Xa, Ta, s.logD, Xc, Xn, Xa, Tn,
+                s.logD, s);
       double2* t = Ta; Ta = Tn; Tn = t;
-      __syncthreads();
     }
     cta_assemble(n, Xa, Ta, s.logD, Xc, Xn, s, s.red + 2, s.red + 3);
     const double pi = 3.14159265358979323846;
@@ -557,9 +583,13 @@ void launch_chain_fp64(const Desc* descs, const Task* tasks, int ntasks, int* qu
 }
 void launch_boundary_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue,
                           int* status, char* scratch, const Layout& L, int grid,
-                          cudaStream_t stream, bool pdl) {
-  launch_maybe_pdl(k_boundary_fp64, grid, L.nthreads, L.smem_bytes, stream, pdl, descs, tasks,
-                   ntasks, queue, status, scratch, L);
+                          cudaStream_t stream, bool pdl, bool merge) {
+  if (merge)
+    launch_maybe_pdl(k_boundary_fp64<true>, grid, L.nthreads, L.smem_bytes, stream, pdl, descs,
+                     tasks, ntasks, queue, status, scratch, L);
+  else
+    launch_maybe_pdl(k_boundary_fp64<false>, grid, L.nthreads, L.smem_bytes, stream, pdl, descs,
+                     tasks, ntasks, queue, status, scratch, L);
 }
 void launch_wrap_fp64(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                       char* scratch, const Layout& L, int grid, cudaStream_t stream, bool pdl) {
@@ -574,7 +604,8 @@ void launch_merge_fp64(const Desc* descs, int ndesc, int* queue, int* status, ch
 static const void* fp64_kernel(int which) {
   switch (which) {
     case 1: return (const void*)k_chain_fp64;
-    case 2: return (const void*)k_boundary_fp64;
+    case 2: return (const void*)k_boundary_fp64<false>;
+    case 9: return (const void*)k_boundary_fp64<true>;
     case 3: return (const void*)k_wrap_fp64;
     case 8: return (const void*)k_merge_fp64;
     default: return (const void*)k_fwd_fp64;
@@ -588,8 +619,8 @@ int occupancy_fp64(int which, int nthreads, int smem_bytes) {
 }
 cudaError_t set_smem_fp64(int bytes) {
   for (const void* k : {(const void*)k_fwd_fp64, (const void*)k_chain_fp64,
-                        (const void*)k_boundary_fp64, (const void*)k_wrap_fp64,
-                        (const void*)k_merge_fp64}) {
+                        (const void*)k_boundary_fp64<false>, (const void*)k_boundary_fp64<true>,
+                        (const void*)k_wrap_fp64, (const void*)k_merge_fp64}) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,

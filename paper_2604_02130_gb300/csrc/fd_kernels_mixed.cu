@@ -394,10 +394,11 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
     if (q >= ntasks) break;
     const Task tk = tasks[q];
     const Desc d = descs[tk.desc];
-    // Task.b: 0 forward chain, 1 backward chain, 2 + s segment s of a time-parallel split
-    const bool fwd = tk.b != 1;
-    const int sg = tk.b - 2;
+    // Task.b: a ChainCode (forward/backward chain, its second half, or a log det/G segment)
     const int ns = d.nstab, nb = d.nt / d.nstab;
+    const int sg = (tk.b >= CT_SEG && tk.b < CT_FWD2) ? tk.b - CT_SEG : -1;
+    const ChainSpan sp = chain_span(tk.b, nb, d.fsplit);
+    const bool fwd = sg >= 0 || sp.fwd;
     const FWork W{d.fws, n, nb};
     Small s = carve_small(smem + L.small_off, n);
     float2* pf = (float2*)s.ph;  // FP32 phases: two halves of n
@@ -412,7 +413,8 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
     bool ok = true;
     if (fwd) {
       // a segment of a time-parallel split runs blocks sg*kb+1 .. (sg+1)*kb from the identity
-      const int kb = sg >= 0 ? nb / d.nseg : nb, b_first = sg >= 0 ? sg * kb + 1 : 1;
+      const int kb = sg >= 0 ? nb / d.nseg : sp.last - sp.first + 1;
+      const int b_first = sg >= 0 ? sg * kb + 1 : sp.first;
       for (int b = b_first; b < b_first + kb && ok; ++b) {
         const int t0 = (b - 1) * ns;
         cta_phase32(n, pf, d.phi + (size_t)t0 * n, 1.f);
@@ -428,18 +430,21 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
         if (!ok) break;
         cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
         double2* t2 = T; T = To; To = t2;
-        if (sg < 0 && b < nb) {
-          cta_copy(n * n, W.LX(b), m.Xn);
-          cta_copy(n * n, W.LT(b), T);
-          for (int k = tid(); k < n; k += nthr()) W.LD(b)[k] = s.logD[k];
+        if (sg < 0 && (b < nb || !sp.assemble)) {  // checkpoint (a split half's product: SX)
+          cta_copy(n * n, b < nb ? W.LX(b) : W.SX(), m.Xn);
+          cta_copy(n * n, b < nb ? W.LT(b) : W.ST(), T);
+          double* ldst = b < nb ? W.LD(b) : W.SD();
+          for (int k = tid(); k < n; k += nthr()) ldst[k] = s.logD[k];
           __syncthreads();
-          if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, b);
+          if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
         }
       }
       if (ok && sg >= 0) {  // segment result in the checkpoint storage of block sg+1
         cta_copy(n * n, W.LX(sg + 1), m.Xn);
         cta_copy(n * n, W.LT(sg + 1), T);
         for (int k = tid(); k < n; k += nthr()) W.LD(sg + 1)[k] = s.logD[k];
+        if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
+      } else if (ok && !sp.assemble) {
         if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
       } else if (ok) {
         double2* G0 = W.Gb(1);
@@ -464,9 +469,9 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
         if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, nb);  // G_0 written
       }
     } else {
-      for (int b = nb; b >= 2 && ok; --b) {
+      for (int b = sp.first; b >= sp.last && ok; --b) {
         const int t0 = (b - 1) * ns;
-        fill_b2(L, m, b == nb ? nullptr : m.Xn, one, one);
+        fill_b2(L, m, b == sp.first ? nullptr : m.Xn, one, one);
         for (int t = b * ns - 1; t >= t0; --t) {
           const bool last = t == t0;
           cta_phase32(n, pf, d.phi + (size_t)t * n, -1.f);
@@ -484,7 +489,7 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
         cta_copy(n * n, W.RT(b), T);
         for (int k = tid(); k < n; k += nthr()) W.RD(b)[k] = s.logD[k];
         __syncthreads();
-        if (tid() == 0 && d.sync) flag_store(d.sync + SF_BWD, nb - b + 1);
+        if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
       }
       if (ok && tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     }
@@ -492,7 +497,7 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
       if (tid() == 0) {
         atomicMax(status + d.user_index, ST_TIMEOUT);
         // release the dependent tasks (their inputs are invalid; the status says so)
-        if (d.sync) flag_store(d.sync + (fwd ? SF_FWD : SF_BWD), nb);
+        if (d.sync) flag_store(d.sync + (sg >= 0 ? SF_FWD : sp.flag), nb);
       }
       break;
     }

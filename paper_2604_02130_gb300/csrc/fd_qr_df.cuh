@@ -86,19 +86,31 @@ __device__ __forceinline__ df::c4 df_conj(df::c4 a) { return df::c4{a.x, a.y, -a
 
 // C (m x p) = A (m x K) B (K x p) in df with the operands staged through shared memory: BM x BN
 // output tiles (64 x 64, or 16 x 256 for a short-and-wide product), K in chunks of 16; 256
-// threads, each a 4 x 4 block of outputs with compensated accumulators.  A(i, k) = aload(i, k),
-// B(k, j) = bload(k, j) (called once per element per tile, inside the bounds), epi(i, j, c4)
-// stores an output element.  sm: shared memory for 16 (BM + BN) df numbers (32 KB for 64 x 64,
-// 68 KB for 16 x 256).  upper_a: A is upper triangular (its K chunks below a tile's rows are
-// skipped).  All threads of the CTA call it (blockDim.x == 256).
-template <int BM = 64, int BN = 64, class ALoad, class BLoad, class Epi>
-__device__ inline void df_gemm_tiled(int m, int p, int K, const ALoad& aload, const BLoad& bload,
-                                     const Epi& epi, float4* sm, bool upper_a = false) {
+// threads, each a 4 x 4 block of outputs with compensated accumulators.  The threads run along
+// the rows first (rows ty + TY a, columns tx + TX b): the epilogue's loads and stores of a
+// column-major output are contiguous across neighbouring threads.  A(i, k) = aload(i, k) is
+// staged with i fastest and B(k, j) = bload(k, j) with k fastest, so column-major operands in
+// global memory are read contiguously; each thread issues its loads of a chunk together before
+// storing them to shared memory (one memory latency per chunk, not one per element), and the B
+// tile's rows are padded by one df number so that those stores avoid bank conflicts.  Both
+// loaders are called once per element per tile, inside the bounds.
+//   df_gemm_tiled: epi(i, j, c4) stores an output element.
+//   df_gemm_sub_tiled: C(i, j) -= (A B)(i, j) in place at caddr(i, j) (a df number), the old
+//   values of a thread's block loaded together before the update.
+// sm: shared memory for DF_TILE_ELEMS(BM, BN) df numbers.  upper_a: A is upper triangular (its K
+// chunks below a tile's rows are skipped).  All threads of the CTA call it (blockDim.x == 256).
+#define DF_TILE_ELEMS(BM, BN) (16 * ((BM) + (BN) + 1))
+template <int BM, int BN, bool SUB, class ALoad, class BLoad, class Epi>
+__device__ inline void df_gemm_core(int m, int p, int K, const ALoad& aload, const BLoad& bload,
+                                    const Epi& epi, float4* sm, bool upper_a) {
   static_assert(BM * BN == 4096, "256 threads of 4 x 4 outputs");
+  constexpr int TY = BM / 4, TX = BN / 4, BS = BN + 1;
+  constexpr int NA = 16 * BM / 256, NB = 16 * BN / 256, GB = NB < 8 ? NB : 8;
   float4* As = sm;            // [16][BM]: As[k * BM + i]
-  float4* Bs = sm + 16 * BM;  // [16][BN]: Bs[k * BN + j]
+  float4* Bs = sm + 16 * BM;  // [16][BS]: Bs[k * BS + j]
   const int t = tid();
-  const int tx = t % (BN / 4), ty = t / (BN / 4);  // output columns 4 tx.., rows 4 ty..
+  const int ty = t % TY, tx = t / TY;
+  const df::c4 zero{0.f, 0.f, 0.f, 0.f};
   for (int i0 = 0; i0 < m; i0 += BM)
     for (int j0 = 0; j0 < p; j0 += BN) {
       DAcc acc[4][4];
@@ -109,39 +121,89 @@ __device__ inline void df_gemm_tiled(int m, int p, int K, const ALoad& aload, co
       // an upper triangular A (A(i, k) = 0 for k < i) contributes nothing below the tile's rows
       for (int k0 = upper_a ? (i0 / 16) * 16 : 0; k0 < K; k0 += 16) {
         __syncthreads();
-        for (int e = t; e < 16 * BM; e += 256) {
-          const int kk = e / BM, r = e % BM;
-          const int i = i0 + r, k = k0 + kk;
-          st4(As + e, (i < m && k < K) ? aload(i, k) : df::c4{0.f, 0.f, 0.f, 0.f});
+        {
+          df::c4 ra[NA];
+#pragma unroll
+          for (int u = 0; u < NA; ++u) {
+            const int e = t + 256 * u, kk = e / BM, r = e % BM;
+            const int i = i0 + r, k = k0 + kk;
+            ra[u] = (i < m && k < K) ? aload(i, k) : zero;
+          }
+#pragma unroll
+          for (int u = 0; u < NA; ++u) st4(As + t + 256 * u, ra[u]);
         }
-        for (int e = t; e < 16 * BN; e += 256) {
-          const int kk = e / BN, r = e % BN;
-          const int j = j0 + r, k = k0 + kk;
-          st4(Bs + e, (j < p && k < K) ? bload(k, j) : df::c4{0.f, 0.f, 0.f, 0.f});
+#pragma unroll
+        for (int g = 0; g < NB; g += GB) {
+          df::c4 rb[GB];
+#pragma unroll
+          for (int u = 0; u < GB; ++u) {
+            const int e = t + 256 * (g + u), kk = e % 16, r = e / 16;
+            const int j = j0 + r, k = k0 + kk;
+            rb[u] = (j < p && k < K) ? bload(k, j) : zero;
+          }
+#pragma unroll
+          for (int u = 0; u < GB; ++u) {
+            const int e = t + 256 * (g + u), kk = e % 16, r = e / 16;
+            st4(Bs + kk * BS + r, rb[u]);
+          }
         }
         __syncthreads();
         const int kn = min(16, K - k0);
         for (int kk = 0; kk < kn; ++kk) {
           df::c4 av[4], bv[4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) av[a] = ld4(As + kk * BM + 4 * ty + a);
+          for (int a = 0; a < 4; ++a) av[a] = ld4(As + kk * BM + ty + TY * a);
 #pragma unroll
-          for (int b = 0; b < 4; ++b) bv[b] = ld4(Bs + kk * BN + 4 * tx + b);
+          for (int b = 0; b < 4; ++b) bv[b] = ld4(Bs + kk * BS + tx + TX * b);
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc_mul(acc[a][b], av[a], bv[b]);
         }
       }
+      if constexpr (SUB) {
+        const df::c4 one{1.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+        for (int b0 = 0; b0 < 4; b0 += 2) {
+          df::c4 old[2][4];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int i = i0 + 4 * ty + a, j = j0 + 4 * tx + b;
-          if (i < m && j < p) epi(i, j, acc_value(acc[a][b]));
+          for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              const int i = i0 + ty + TY * a, j = j0 + tx + TX * (b0 + b);
+              old[b][a] = (i < m && j < p) ? ld4(epi(i, j)) : zero;
+            }
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              const int i = i0 + ty + TY * a, j = j0 + tx + TX * (b0 + b);
+              if (i < m && j < p) st4(epi(i, j), df::cms(old[b][a], acc_value(acc[a][b0 + b]), one));
+            }
         }
+      } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = i0 + ty + TY * a, j = j0 + tx + TX * b;
+            if (i < m && j < p) epi(i, j, acc_value(acc[a][b]));
+          }
+      }
     }
   __syncthreads();
+}
+template <int BM = 64, int BN = 64, class ALoad, class BLoad, class Epi>
+__device__ __forceinline__ void df_gemm_tiled(int m, int p, int K, const ALoad& aload,
+                                              const BLoad& bload, const Epi& epi, float4* sm,
+                                              bool upper_a = false) {
+  df_gemm_core<BM, BN, false>(m, p, K, aload, bload, epi, sm, upper_a);
+}
+template <int BM = 64, int BN = 64, class ALoad, class BLoad, class CAddr>
+__device__ __forceinline__ void df_gemm_sub_tiled(int m, int p, int K, const ALoad& aload,
+                                                  const BLoad& bload, const CAddr& caddr,
+                                                  float4* sm) {
+  df_gemm_core<BM, BN, true>(m, p, K, aload, bload, caddr, sm, false);
 }
 
 // ---------------------------------------------------------------- register-resident columns
@@ -329,21 +391,17 @@ __device__ inline void df_apply_block(int np, int r0, int c0, int n, const float
   }
   __syncthreads();
   // A(r0:, c0:) -= V W
-  const df::c4 one{1.f, 0.f, 0.f, 0.f};
-  df_gemm_tiled<64, 64>(
+  df_gemm_sub_tiled<64, 64>(
       m, p, np, [&](int i, int k) { return ld4(vs + (size_t)k * n + r0 + i); },
       [&](int k, int j) { return ld4(Wg + k + (size_t)j * DF_PANEL); },
-      [&](int i, int j, df::c4 v) {
-        float4* q = A + r0 + i + (size_t)(c0 + j) * n;
-        st4(q, df::cms(ld4(q), v, one));
-      },
-      gsm);
+      [&](int i, int j) { return A + r0 + i + (size_t)(c0 + j) * n; }, gsm);
 }
 
 // The QR of Section 7 (see cta_reortho) with the factorisation, the T update and the formation
 // of Q in double-float, the O(n^3) work in shared-memory tiled df GEMMs on block reflectors
 // (compact WY form) of DF_PANEL reflectors.  vsm: shared memory for vcap >= DF_PANEL (n + 2
-// DF_PANEL) + 4352 df numbers (the panel's reflectors, its T and Gram matrices, the GEMM tiles).
+// DF_PANEL) + DF_TILE_ELEMS(16, 256) df numbers (the panel's reflectors, its T and Gram
+// matrices, the GEMM tiles).
 // Tc is consumed: after its rows are gathered in df into Xc, its memory holds the block
 // reflectors' DF_PANEL x n intermediate products.  n <= 32 * DF_RMAX.
 __device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, double2* Tc,
