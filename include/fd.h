@@ -228,18 +228,24 @@ int fd_debug_skip_chains(fd_ctx* ctx, int on);
 
 /* Time-parallel force chains.  A force call (fd_force, or fd_observables with F only) runs two
  * chains per configuration, the forward one (left checkpoints, then log det and G_0) and the
- * backward one (right checkpoints); with the chains split at the middle block h = nb/2 each runs
- * as two halves in parallel, the second halves from the identity, and the boundary phase merges
- * a second half's checkpoint with the first half's last one before the boundary Green's function
- * (Section 7's stabilised product of two factored matrices, in FP64) and forms log det and G_0
- * from the forward halves.  The merges cost about one chain's QRs per configuration, so the split
- * pays only where whole chains would leave SMs idle.  mode -1 (default): split in FP64 when
- * 4 * batch <= the SM count; 0: never; 1: every configuration with at least 4 blocks.  Size
- * classes that the mixed path runs on the streamed kernels (Nx above the shared-memory tile) are
- * never split: their double-float boundary kernel cannot hold the merge's row scaling, which
- * spans beta/2 times the hopping bandwidth (e^{-96} at beta = 32), within the FP32 exponent range.
- * A merge whose second-half factor spans more than e^700 marks the configuration FD_ERR_NUMERIC.
- * Results agree with the unsplit chains to rounding.  Returns FD_ERR_INVALID for another mode. */
+ * backward one (right checkpoints), so a long chain is serial work on one SM.  Two decompositions
+ * (Section 7's stabilised product of two factored matrices joins the pieces):
+ *  - halves (size classes whose boundary Green's functions run in FP64: the FP64 path, and the
+ *    mixed path's shared-memory classes): each chain runs as two halves in parallel, the second
+ *    from the identity; the boundary phase merges a second half's checkpoint with the first
+ *    half's last one (FP64) and forms log det and G_0 from the forward halves.  A merge whose
+ *    left factor spans more than e^700 marks the configuration FD_ERR_NUMERIC.
+ *  - segments (the mixed path's streamed classes, Nx above the shared-memory tile): S segments
+ *    of about 8 blocks (4..8 segments, a power of two dividing the block count) run from the
+ *    identity in parallel, their prefixes are formed in order by double-float merges, and the
+ *    segments are re-run from their exact prefixes, so every checkpoint is final.  A segment
+ *    whose log D spans more than e^76 (beyond the double-float exponent range once squared)
+ *    marks the configuration FD_ERR_NUMERIC.
+ * mode -1 (default): halves in FP64 when 4 * batch <= the SM count; segments for a streamed
+ * configuration whose chain would outlast an SM's share of all the call's chains (cost
+ * nx^3 (nt + 150 nt / n_stab)).  0: never.  1: halves for every eligible configuration with at
+ * least 4 blocks, segments of at least 4 blocks (S >= 4) for every streamed one that has them.
+ * Results agree with the whole chains to rounding.  Returns FD_ERR_INVALID for another mode. */
 int fd_set_force_split(fd_ctx* ctx, int mode);
 
 /* Wait for `stream` and copy the per-configuration device status of the LAST call on this

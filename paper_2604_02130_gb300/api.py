@@ -70,9 +70,9 @@ class Context:
         self.check(self.lib.fd_debug_skip_chains(self.h, 1 if on else 0))
 
     def set_force_split(self, mode: int) -> None:
-        """Time-parallel force chains (fd_set_force_split): -1 automatic (FP64 calls with
-        4 * batch <= SMs split every configuration's chains at the middle block), 0 never, 1 every
-        configuration with at least 4 blocks (streamed mixed size classes are never split)."""
+        """Time-parallel force chains (fd_set_force_split): -1 automatic (halves for FP64
+        calls with 4 * batch <= SMs, segments for long chains of the mixed path's streamed size
+        classes), 0 never, 1 wherever the configuration has enough blocks."""
         self.check(self.lib.fd_set_force_split(self.h, int(mode)))
 
     def last_launch_count(self) -> int:

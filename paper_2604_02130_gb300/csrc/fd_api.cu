@@ -138,6 +138,7 @@ struct Group {
   size_t fws_bytes;
   std::vector<int> nseg;         // time-parallel log det/G: segments per configuration (or empty)
   std::vector<int> fsplit;       // force: block at which each configuration's chains split (0: not)
+  std::vector<int> fseg;         // force, streamed classes: segments per chain (0: whole chains)
   // streamed tensor-core phases: chunked TF32 copies of the distinct E (and E^{-1}) matrices
   std::vector<const double*> prep_src;
   size_t prep_off = 0;   // byte offset from the group's scratch base
@@ -643,6 +644,29 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       split_c[c] = nb >= 4 && (ctx->force_split > 0 || auto_ok);
     }
   }
+  // Segmented chains (SegPlan) for the streamed mixed classes, whose boundary kernel reads only
+  // final checkpoints: S = nb / 8 segments (a power of two, 4..FD_SEG_MAX, dividing nb) where
+  // one chain would outlast an SM's share of all the call's chains -- a chain of nt slices costs
+  // ~nx^3 (nt + 150 nt / n_stab), a QR about as much as 150 slice products.  The critical path
+  // becomes 2 nb / S blocks and S - 2 merges; the work grows by the re-run segments.
+  std::vector<int> seg_c(batch, 0);
+  if (kind == K_FORCE && !sparse && prec != FD_PREC_FP64 && ctx->force_split != 0) {
+    auto ccost = [&](const fd_problem& p) {
+      const double n3 = (double)p.nx * p.nx * p.nx;
+      return n3 * ((double)p.nt + 150.0 * p.nt / p.n_stab);
+    };
+    double tot = 0.0;
+    for (int c = 0; c < batch; ++c) tot += 2.0 * ccost(probs[c]);
+    const double share = tot / std::max(1, ctx->num_sms);
+    for (int c = 0; c < batch; ++c) {
+      const int nb = probs[c].nt / probs[c].n_stab;
+      // forced: segments of at least 4 blocks; automatic: of about 8
+      int S = 1;
+      const int mmin = ctx->force_split > 0 ? 4 : 8;
+      while (2 * S <= FD_SEG_MAX && nb % (2 * S) == 0 && nb / (2 * S) >= mmin) S *= 2;
+      if (S >= 4 && (ctx->force_split > 0 || ccost(probs[c]) > share)) seg_c[c] = S;
+    }
+  }
   int qnext = 0;
   size_t i = 0;
   while (i < order.size()) {
@@ -700,24 +724,46 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       const bool streamed = mixed && !mixed_phase(ctx, n, R_FWD, 1, three, 2 * nd, A0) &&
                             big_phase(ctx, n, false, three, 2 * nd, A0);
       bool any_split = false;
+      std::vector<fd::Task> seg_p1, seg_pre, seg_p2, seg_B, seg_C;
       for (int k = 0; k < nd; ++k) {
         const int c = g.idx[k];
         const int nb = probs[c].nt / probs[c].n_stab;
         const int h = split_c[c] && !streamed ? nb / 2 : 0;
+        const int S = streamed ? seg_c[c] : 0;
         g.fsplit.push_back(h);
+        g.fseg.push_back(S);
         any_split |= h > 0;
-        g.tA.push_back(fd::Task{k, fd::CT_FWD});
-        g.tA.push_back(fd::Task{k, fd::CT_BWD});
+        if (S) {
+          // pass 1, the two prefix tasks, pass 2 (queued in that order across configurations)
+          for (int sg = 0; sg <= S - 2; ++sg) {
+            seg_p1.push_back(fd::Task{k, fd::CT_SFA + sg});
+            seg_p1.push_back(fd::Task{k, fd::CT_SBA + sg});
+          }
+          seg_pre.push_back(fd::Task{k, fd::CT_SFP});
+          seg_pre.push_back(fd::Task{k, fd::CT_SBP});
+          for (int sg = 1; sg <= S - 1; ++sg) {
+            seg_p2.push_back(fd::Task{k, fd::CT_SFB + sg});
+            seg_p2.push_back(fd::Task{k, fd::CT_SBB + sg});
+          }
+        } else {
+          g.tA.push_back(fd::Task{k, fd::CT_FWD});
+          g.tA.push_back(fd::Task{k, fd::CT_BWD});
+        }
         if (h) {
           g.tA.push_back(fd::Task{k, fd::CT_FWD2});
           g.tA.push_back(fd::Task{k, fd::CT_BWD2});
         }
-        for (int b = 2; b <= nb; ++b) g.tB.push_back(fd::Task{k, b});
-        if (h) g.tB.push_back(fd::Task{k, 1});  // G_0 and log det from the halves
-        for (int b = 1; b <= nb; ++b) g.tC.push_back(fd::Task{k, b});
+        // a segmented configuration's checkpoints come last: its boundary and wrap tasks go to
+        // the end of their queues (a wait that sees no progress for ~4 s gives up)
+        std::vector<fd::Task>& tb = S ? seg_B : g.tB;
+        std::vector<fd::Task>& tc = S ? seg_C : g.tC;
+        for (int b = 2; b <= nb; ++b) tb.push_back(fd::Task{k, b});
+        if (h) tb.push_back(fd::Task{k, 1});  // G_0 and log det from the halves
+        for (int b = 1; b <= nb; ++b) tc.push_back(fd::Task{k, b});
+        const int extra = h > 0 ? 1 : S > 0 ? 2 * (S - 2) : 0;
         g.fws_off.push_back(g.fws_bytes);
         g.fws_bytes += (fd::FWork::elems(n, nb, (kind & K_GTAU) != 0, (kind & K_RESP) != 0,
-                                         h > 0) * 16 + 255) & ~(size_t)255;
+                                         extra) * 16 + 255) & ~(size_t)255;
       }
       // chains longest first (LPT): a forward chain carries one more QR and the assembly, so for
       // equal configurations all forward chains go out before the backward ones and the SMs that
@@ -736,6 +782,20 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       std::stable_sort(g.tA.begin(), g.tA.end(), [&](const fd::Task& a, const fd::Task& b) {
         return chain_cost(a) > chain_cost(b);
       });
+      // segmented chains: every task waits only for tasks queued before it (pass 1, then the
+      // prefixes, then the whole chains, then pass 2 by segment)
+      std::stable_sort(seg_p2.begin(), seg_p2.end(), [](const fd::Task& a, const fd::Task& b) {
+        return (a.b & 15) < (b.b & 15);
+      });
+      if (!seg_p1.empty()) {
+        std::vector<fd::Task> all = seg_p1;
+        all.insert(all.end(), seg_pre.begin(), seg_pre.end());
+        all.insert(all.end(), g.tA.begin(), g.tA.end());
+        all.insert(all.end(), seg_p2.begin(), seg_p2.end());
+        g.tA.swap(all);
+        g.tB.insert(g.tB.end(), seg_B.begin(), seg_B.end());
+        g.tC.insert(g.tC.end(), seg_C.begin(), seg_C.end());
+      }
       Phase A, C;
       const int ntA = (int)g.tA.size();
       if (!(mixed && tensor_chain(ctx, n, 1, three, ntA, A))) A = fp64_phase(ctx, n, R_FWD, 1, ntA);
@@ -909,6 +969,7 @@ void build_tables(std::vector<Group>& groups, const fd_problem* probs, const Out
                   : nullptr;
       d.nseg = g.nseg.empty() ? 0 : g.nseg[q];
       d.fsplit = g.fsplit.empty() ? 0 : g.fsplit[q];
+      d.fseg = g.fseg.empty() ? 0 : g.fseg[q];
       d.Ec = d.Eic = nullptr;
       for (size_t i = 0; i < g.prep_src.size(); ++i) {
         const float* dst = (const float*)(scratch + g.scratch_off + g.prep_off + i * g.prep_each);

@@ -62,6 +62,7 @@ struct Desc {
   int* sync;           // phased path: this configuration's progress flags (SyncFlag), else null
   int nseg;            // time-parallel log det/G: number of segments of the chain (0: not split)
   int fsplit;          // force: chains split at block h = fsplit (0: not split; see ChainSpan)
+  int fseg;            // force, streamed kernels: S segments per chain (0: not segmented; SegPlan)
   // streamed tensor-core kernels (nx above one tile): E and E^{-1} as chunked TF32 operands
   // (hi at the pointer, lo after it; see BLayout), prepared once per call; else null
   const float* Ec;
@@ -79,8 +80,16 @@ enum SyncFlag {
   SF_BND = 2,   // boundary Green's functions written (count)
   SF_FWD2 = 3,  // split chains: v local left products of the second forward half written
   SF_BWD2 = 4,  // split chains: v local right products of the second backward half written
-  SF_NUM = 8    // ints per configuration (padding)
+  // segmented chains (SegPlan), + k for segment k < FD_SEG_MAX:
+  SF_SEGF = 8,   // final left checkpoints written inside forward segment k (count)
+  SF_SEGB = 16,  // final right checkpoints written inside backward segment k (count)
+  SF_PREF = 24,  // prefix L_{k m} (the first checkpoint of forward segment k) formed by a merge
+  SF_PREB = 32,  // suffix R_{nb - k m + 1} formed by a merge
+  SF_LSF = 40,   // local product of forward segment k (from the identity) written
+  SF_LSB = 48,   // local product of backward segment k written
+  SF_NUM = 56    // ints per configuration
 };
+#define FD_SEG_MAX 8
 // A wait gives up after this many cycles without any change of the configuration's flags
 // (~4 s at 2 GHz; one checkpoint interval of the largest supported size takes well under that).
 #define FD_SYNC_WAIT_CYCLES (8LL * 1000 * 1000 * 1000)
@@ -121,6 +130,39 @@ __device__ __forceinline__ int flag_load(const int* f) {
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
   return v;
 }
+// CTA-wide wait until flags[idx[i]] >= thr[i] for i < np (np <= 4); as cta_wait_flags.
+__device__ __forceinline__ bool cta_wait_pairs(const int* flags, const int* idx, const int* thr,
+                                               int np, volatile int* bcast) {
+  if (threadIdx.x == 0) {
+    long long t0 = clock64();
+    int ok = 1, last = -1;
+    for (;;) {
+      int sum = 0, done = 1;
+      for (int i = 0; i < np; ++i) {
+        const int f = flag_load(flags + idx[i]);
+        sum += f;
+        done &= f >= thr[i];
+      }
+      if (done) break;
+      const long long now = clock64();
+      if (sum != last) {
+        last = sum;
+        t0 = now;
+      } else if (now - t0 > FD_SYNC_WAIT_CYCLES) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(256);
+    }
+    __threadfence();
+    *bcast = ok;
+  }
+  __syncthreads();
+  const bool ok = *bcast != 0;
+  __syncthreads();
+  return ok;
+}
+
 // CTA-wide wait until flags[SF_FWD] >= fwd, flags[SF_BWD] >= bwd, flags[SF_BND] >= bnd,
 // flags[SF_FWD2] >= fwd2 and flags[SF_BWD2] >= bwd2.  Thread 0 polls; it gives up (false) after
 // FD_SYNC_WAIT_CYCLES without progress of the flags.  `bcast` is a shared int.
@@ -166,11 +208,12 @@ struct FWork {
   int n, nb;
   __host__ __device__ static size_t stride(int n) { return (size_t)2 * n * n + (n + 1) / 2; }
   // gt: room for the boundary values G((b-1) ns, 0) of the unequal-time Green's function
-  // split: room for the second forward half's full product (force chains split at a block)
+  // extra: room for that many more (X, T, log D) factors after the boundary Green's functions
+  // (force only: the split chains' second forward half, the segmented chains' local products)
   __host__ __device__ static size_t elems(int n, int nb, bool gt, bool op = false,
-                                          bool split = false) {
+                                          int extra = 0) {
     return (size_t)2 * (nb - 1) * stride(n) + (size_t)(gt ? 2 : 1) * nb * n * n +
-           (op ? ((size_t)n * n + 3) / 4 : 0) + (split ? stride(n) : 0);
+           (op ? ((size_t)n * n + 3) / 4 : 0) + (size_t)extra * stride(n);
   }
   __device__ double2* LX(int b) const { return base + (size_t)(b - 1) * stride(n); }
   __device__ double2* LT(int b) const { return LX(b) + (size_t)n * n; }
@@ -187,10 +230,16 @@ struct FWork {
     return b == 1 ? Gb(1)
                   : base + (size_t)2 * (nb - 1) * stride(n) + (size_t)(nb + b - 1) * n * n;
   }
-  // split force chains (no G(tau, 0), no O): the product of blocks h+1..nb from the identity
-  __device__ double2* SX() const { return base + (size_t)2 * (nb - 1) * stride(n) + (size_t)nb * n * n; }
-  __device__ double2* ST() const { return SX() + (size_t)n * n; }
-  __device__ double* SD() const { return (double*)(SX() + (size_t)2 * n * n); }
+  // extra factors of the force (no G(tau, 0), no O): i = 0 the split chains' product of blocks
+  // h+1..nb; the segmented chains' local products
+  __device__ double2* XX(int i) const {
+    return base + (size_t)2 * (nb - 1) * stride(n) + (size_t)nb * n * n + (size_t)i * stride(n);
+  }
+  __device__ double2* XT(int i) const { return XX(i) + (size_t)n * n; }
+  __device__ double* XD(int i) const { return (double*)(XX(i) + (size_t)2 * n * n); }
+  __device__ double2* SX() const { return XX(0); }
+  __device__ double2* ST() const { return XT(0); }
+  __device__ double* SD() const { return XD(0); }
   // O (row-major) in FP32, after the G(tau, 0) values when those are kept (gt)
   __device__ float* OF(bool gt) const {
     return (float*)(base + (size_t)2 * (nb - 1) * stride(n) + (size_t)(gt ? 2 : 1) * nb * n * n);
@@ -228,6 +277,34 @@ __device__ __forceinline__ ChainSpan chain_span(int code, int nb, int h) {
     case CT_BWD: return ChainSpan{false, nb, h > 0 ? h + 1 : 2, SF_BWD, false};
     default: return ChainSpan{true, 1, h > 0 ? h : nb, SF_FWD, h == 0};
   }
+}
+
+// Segmented chains (Desc.fseg = S, the streamed kernels): forward segment k covers blocks
+// k m + 1 .. (k+1) m (m = nb / S), backward segment k blocks nb - k m down to nb - (k+1) m + 1.
+// Pass 1 runs segments from the identity in parallel: segment 0 writes its final checkpoints,
+// segments 1..S-2 only their local product (FWork::XX).  A prefix task then forms the prefixes
+// L_{k m} = (local product of segment k-1) L_{(k-1) m}, k = 2..S-1, in order (a short
+// sequential chain of merges whose left factor spans only m blocks) and writes each as that
+// checkpoint.  Pass 2 re-runs segments 1..S-1 from their exact prefix, writing their final
+// checkpoints (all but the last, which the next prefix forms); the last forward segment ends
+// with the assembly.  Backward in mirror image, with suffixes R_{nb - k m + 1} (the last
+// backward segment stops at block 2 and writes R_2).  Chain task codes:
+// pass 1 (CT_SFA/CT_SBA + k, k = 0..S-2), pass 2 (CT_SFB/CT_SBB + k, k = 1..S-1), and one
+// prefix task per direction (CT_SFP/CT_SBP) that forms L_{2m}, ..., L_{(S-1)m} in order.
+enum SegCode { CT_SFA = 96, CT_SFB = 112, CT_SBA = 128, CT_SBB = 144, CT_SFP = 160, CT_SBP = 161 };
+// Which flag shows a final left checkpoint L_c (c = 1..nb-1) or right checkpoint R_c
+// (c = 2..nb), and the value it must reach.
+__device__ __forceinline__ void seg_left_ready(int c, int m, int& idx, int& thr) {
+  const int k = (c - 1) / m, j = c - k * m;
+  if (k == 0) { idx = SF_SEGF; thr = j; }
+  else if (j < m) { idx = SF_SEGF + k; thr = j; }
+  else { idx = SF_PREF + k + 1; thr = 1; }
+}
+__device__ __forceinline__ void seg_right_ready(int c, int nb, int m, int& idx, int& thr) {
+  const int k = (nb - c) / m, j = nb - c + 1 - k * m;
+  if (k == 0) { idx = SF_SEGB; thr = j; }
+  else if (j < m) { idx = SF_SEGB + k; thr = j; }
+  else { idx = SF_PREB + k + 1; thr = 1; }
 }
 
 // Where each working matrix lives: shared memory (offset in bytes from the dynamic smem base)

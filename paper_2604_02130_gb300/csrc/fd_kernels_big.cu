@@ -399,10 +399,11 @@ __device__ bool chain_slice(const BLayout& L, const BigSmem& m, BigPipe& P, cons
 }
 
 // ------------------------------------------------------------------ chains
-// Task.b: 0 forward chain, 1 backward chain, 2 + s segment s of a time-parallel log det/G split.
-// Forward: slices with QR every n_stab, left checkpoints (when the configuration has a force
-// workspace), assembly -> log det, G (and G(0,0), the fermion number, O in FP32 as asked).
-// Backward: the right products as adjoints X_R <- D_s^* E X_R, QR, right checkpoints.
+// Task.b: a ChainCode (forward chain, backward chain, a log det/G segment) or a SegCode (the
+// segmented chains of SegPlan).  Forward: slices with QR every n_stab, left checkpoints (when the
+// configuration has a force workspace), assembly -> log det, G (and G(0,0), the fermion number,
+// O in FP32 as asked).  Backward: the right products as adjoints X_R <- D_s^* E X_R, QR, right
+// checkpoints.  The chain state between blocks is (Xn = Q of the last QR, T, log D).
 __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ descs,
                                                       const Task* __restrict__ tasks, int ntasks,
                                                       int* queue, int* status, char* scratch,
@@ -427,6 +428,8 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
   double2* T = (double2*)(slot + L.t0_off);
   double2* To = (double2*)(slot + L.t1_off);
   float2* pf = (float2*)(smem + L.ph_off);  // FP32 phases, two halves of n
+  float4* qsm = (float4*)m.stages;          // the df QR's shared memory (the idle stages)
+  const int qcap = L.nstages * L.stage_bytes / 16;
   const PhaseVec none{nullptr, false};
   allow_dependents();
   bool ok = true;
@@ -435,11 +438,7 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
     if (q >= ntasks) break;
     const Task tk = tasks[q];
     const Desc d = descs[tk.desc];
-    // Task.b: a ChainCode (forward/backward chain, its second half, or a log det/G segment)
     const int ns = d.nstab, nb = d.nt / d.nstab;
-    const int sg = (tk.b >= CT_SEG && tk.b < CT_FWD2) ? tk.b - CT_SEG : -1;
-    const ChainSpan sp = chain_span(tk.b, nb, d.fsplit);
-    const bool fwd = sg >= 0 || sp.fwd;
     const FWork W{d.fws, n, nb};
     const bool keep = d.fws != nullptr;
     Small s = carve_small(smem + L.small_off, n);
@@ -451,94 +450,189 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
     cta_identity(n, T);
     for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
     __syncthreads();
-    if (fwd) {
-      const int kb = sg >= 0 ? nb / d.nseg : sp.last - sp.first + 1;
-      const int b_first = sg >= 0 ? sg * kb + 1 : sp.first;
-      for (int b = b_first; b < b_first + kb && ok; ++b) {
-        const int t0 = (b - 1) * ns;
-        phase32(n, pf, d.phi + (size_t)t0 * n, 1.f);
+    // one forward block b: its slices on the tensor cores, then the QR (the state advances)
+    auto fwd_block = [&](int b, bool from_id) -> bool {
+      const int t0 = (b - 1) * ns;
+      phase32(n, pf, d.phi + (size_t)t0 * n, 1.f);
+      __syncthreads();
+      fill_cols(n, L.Mc, L.Kp, from_id ? nullptr : Xn, PhaseVec{pf, false}, none, Ahi, Alo,
+                L.three != 0);
+      publish_for_copies();
+      for (int t = t0; t < t0 + ns; ++t) {
+        const bool last = t + 1 == t0 + ns;
+        float2* phn = pf + ((t - t0 + 1) & 1) * n;
+        if (!last) phase32(n, phn, d.phi + (size_t)(t + 1) * n, 1.f);
         __syncthreads();
-        fill_cols(n, L.Mc, L.Kp, b == b_first ? nullptr : Xn, PhaseVec{pf, false}, none, Ahi,
-                  Alo, L.three != 0);
-        publish_for_copies();
-        for (int t = t0; t < t0 + ns && ok; ++t) {
-          const bool last = t + 1 == t0 + ns;
-          float2* phn = pf + ((t - t0 + 1) & 1) * n;
-          if (!last) phase32(n, phn, d.phi + (size_t)(t + 1) * n, 1.f);
-          __syncthreads();
-          ok = chain_slice(L, m, P, d, Ahi, Alo, tbase, last ? none : PhaseVec{phn, false}, last,
-                           Xc);
-        }
-        if (!ok) break;
-        cta_reortho_df(n, Xc, Xn, T, To, s.logD, s, (float4*)m.stages,
-                       L.nstages * L.stage_bytes / 16);
-        double2* t2 = T; T = To; To = t2;
-        if (keep && sg < 0 && (b < nb || !sp.assemble)) {  // a split half's product: SX
-          cta_copy(n * n, b < nb ? W.LX(b) : W.SX(), Xn);
-          cta_copy(n * n, b < nb ? W.LT(b) : W.ST(), T);
-          double* ldst = b < nb ? W.LD(b) : W.SD();
-          for (int k = tid(); k < n; k += nthr()) ldst[k] = s.logD[k];
-          __syncthreads();
-          if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
-        }
+        if (!chain_slice(L, m, P, d, Ahi, Alo, tbase, last ? none : PhaseVec{phn, false}, last,
+                         Xc))
+          return false;
       }
-      if (ok && sg >= 0) {  // segment result in the checkpoint storage of block sg+1
-        cta_copy(n * n, W.LX(sg + 1), Xn);
-        cta_copy(n * n, W.LT(sg + 1), T);
-        for (int k = tid(); k < n; k += nthr()) W.LD(sg + 1)[k] = s.logD[k];
-        if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
-      } else if (ok && !sp.assemble) {
-        if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
-      } else if (ok) {
-        double2* G0 = keep ? W.Gb(1) : To;  // To is free after the last swap
-        cta_assemble(n, Xn, T, s.logD, Xc, G0, s, s.red + 2, s.red + 3);
-        const double re = s.red[2], im = wrap_pi(s.red[3]);
-        if (tid() == 0) {
-          d.logdet[0] = re;
-          d.logdet[1] = im;
-          atomicMax(status + d.user_index,
-                    (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
-        }
-        if (d.G)
-          for (int e = tid(); e < n * n; e += nthr()) d.G[e] = G0[(e / n) + (e % n) * n];
-        if (d.Gt)
-          for (int e = tid(); e < n * n; e += nthr()) d.Gt[e] = G0[(e / n) + (e % n) * n];
-        if (d.nf) cta_fermion_number(n, G0, d.nf);
-        if (keep && d.O) {
-          float* of = W.OF(d.Gt != nullptr);
-          for (int e = tid(); e < n * n; e += nthr()) of[e] = (float)d.O[e];
-        }
+      cta_reortho_df(n, Xc, Xn, T, To, s.logD, s, qsm, qcap);
+      double2* t2 = T; T = To; To = t2;
+      return true;
+    };
+    // one backward block b (right products as adjoints)
+    auto bwd_block = [&](int b, bool from_id) -> bool {
+      const int t0 = (b - 1) * ns;
+      fill_cols(n, L.Mc, L.Kp, from_id ? nullptr : Xn, none, none, Ahi, Alo, L.three != 0);
+      publish_for_copies();
+      for (int t = b * ns - 1; t >= t0; --t) {
+        phase32(n, pf, d.phi + (size_t)t * n, -1.f);
         __syncthreads();
-        if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, nb);
+        // the block's last product goes out in FP64 (with its phase) for the QR
+        if (!chain_slice(L, m, P, d, Ahi, Alo, tbase, PhaseVec{pf, false}, t == t0, Xc))
+          return false;
+      }
+      cta_reortho_df(n, Xc, Xn, T, To, s.logD, s, qsm, qcap);
+      double2* t2 = T; T = To; To = t2;
+      return true;
+    };
+    auto store_state = [&](double2* x, double2* t, double* dl) {
+      cta_copy(n * n, x, Xn);
+      cta_copy(n * n, t, T);
+      for (int k = tid(); k < n; k += nthr()) dl[k] = s.logD[k];
+      __syncthreads();
+    };
+    auto load_state = [&](const double2* x, const double2* t, const double* dl) {
+      cta_copy(n * n, Xn, x);
+      cta_copy(n * n, T, t);
+      for (int k = tid(); k < n; k += nthr()) s.logD[k] = dl[k];
+      __syncthreads();
+    };
+    // the end of the forward chain: log det, G_0 and the outputs
+    auto assemble_out = [&]() {
+      double2* G0 = keep ? W.Gb(1) : To;  // To is free after the last swap
+      cta_assemble(n, Xn, T, s.logD, Xc, G0, s, s.red + 2, s.red + 3);
+      const double re = s.red[2], im = wrap_pi(s.red[3]);
+      if (tid() == 0) {
+        d.logdet[0] = re;
+        d.logdet[1] = im;
+        atomicMax(status + d.user_index,
+                  (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
+      }
+      if (d.G)
+        for (int e = tid(); e < n * n; e += nthr()) d.G[e] = G0[(e / n) + (e % n) * n];
+      if (d.Gt)
+        for (int e = tid(); e < n * n; e += nthr()) d.Gt[e] = G0[(e / n) + (e % n) * n];
+      if (d.nf) cta_fermion_number(n, G0, d.nf);
+      if (keep && d.O) {
+        float* of = W.OF(d.Gt != nullptr);
+        for (int e = tid(); e < n * n; e += nthr()) of[e] = (float)d.O[e];
+      }
+      __syncthreads();
+      if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, nb);
+    };
+    auto numeric_status = [&]() {
+      if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
+    };
+    int fail_flag[3] = {-1, -1, -1};  // flags a failed task releases (set to nb)
+    if (tk.b >= CT_SFA) {
+      // ---- segmented chains (SegPlan)
+      const int S = d.fseg, mb = nb / S;
+      const bool pre = tk.b >= CT_SFP;
+      const int code = pre ? tk.b : (tk.b & ~15), k = pre ? 0 : (tk.b & 15);
+      const bool fw = pre ? tk.b == CT_SFP : (code == CT_SFA || code == CT_SFB);
+      const int FSEG = fw ? SF_SEGF : SF_SEGB, FPRE = fw ? SF_PREF : SF_PREB;
+      const int FLS = fw ? SF_LSF : SF_LSB;
+      // checkpoint c of this direction, the prefix checkpoint of segment kk, local product kk
+      auto ckx = [&](int c) { return fw ? W.LX(c) : W.RX(c); };
+      auto ckt = [&](int c) { return fw ? W.LT(c) : W.RT(c); };
+      auto ckd = [&](int c) { return fw ? W.LD(c) : W.RD(c); };
+      auto pre_c = [&](int kk) { return fw ? kk * mb : nb - kk * mb + 1; };
+      auto loc = [&](int kk) { return (fw ? 0 : S - 2) + kk - 1; };
+      if (pre) {
+        fail_flag[0] = FPRE + S - 1;
+        for (int kk = 2; kk < S; ++kk) {
+          const int wi[2] = {FLS + kk - 1, kk == 2 ? FSEG : FPRE + kk - 1};
+          const int wt[2] = {1, kk == 2 ? mb : 1};
+          if (!cta_wait_pairs(d.sync, wi, wt, 2, m.qslot + 1) && tid() == 0)
+            atomicMax(status + d.user_index, ST_TIMEOUT);
+          const int a = pre_c(kk - 1), c = pre_c(kk), li = loc(kk - 1);
+          cta_merge_df(n, W.XX(li), W.XT(li), W.XD(li), ckx(a), ckt(a), ckd(a), Xc, Xn, T, To,
+                       ckx(c), s.logD, s, qsm, qcap);
+          cta_copy(n * n, ckt(c), To);
+          for (int e = tid(); e < n; e += nthr()) ckd(c)[e] = s.logD[e];
+          __syncthreads();
+          if (tid() == 0) flag_store(d.sync + FPRE + kk, 1);
+        }
+        numeric_status();
+      } else {
+        const bool pass2 = code == CT_SFB || code == CT_SBB;
+        const int first = fw ? k * mb + 1 : nb - k * mb;
+        const int last = fw ? (k + 1) * mb : max(2, nb - (k + 1) * mb + 1);
+        fail_flag[0] = FSEG + k;
+        fail_flag[1] = pass2 ? (fw && k == S - 1 ? SF_FWD : -1) : FLS + k;
+        if (pass2) {
+          const int wi[1] = {k == 1 ? FSEG : FPRE + k}, wt[1] = {k == 1 ? mb : 1};
+          if (!cta_wait_pairs(d.sync, wi, wt, 1, m.qslot + 1) && tid() == 0)
+            atomicMax(status + d.user_index, ST_TIMEOUT);
+          const int c = pre_c(k);
+          load_state(ckx(c), ckt(c), ckd(c));
+        }
+        const int step = fw ? 1 : -1;
+        for (int b = first; ok; b += step) {
+          ok = fw ? fwd_block(b, !pass2 && b == first) : bwd_block(b, !pass2 && b == first);
+          if (!ok) break;
+          const bool lastb = b == last;
+          // final checkpoints: pass 1 of segment 0, and pass 2 but for a segment's last block
+          // (formed by the next prefix) and the forward chain's end (the assembly)
+          if ((!pass2 && k == 0) || (pass2 && !(lastb && k < S - 1) && !(fw && b == nb))) {
+            store_state(ckx(b), ckt(b), ckd(b));
+            if (tid() == 0) flag_store(d.sync + FSEG + k, fw ? b - first + 1 : first - b + 1);
+          }
+          if (lastb) break;
+        }
+        if (ok && !pass2 && k > 0) {  // pass 1: the segment's local product
+          const int li = loc(k);
+          store_state(W.XX(li), W.XT(li), W.XD(li));
+          if (tid() == 0) flag_store(d.sync + FLS + k, 1);
+        }
+        if (ok && fw && pass2 && k == S - 1) assemble_out();
+        else if (ok) numeric_status();
       }
     } else {
-      for (int b = sp.first; b >= sp.last && ok; --b) {
-        const int t0 = (b - 1) * ns;
-        fill_cols(n, L.Mc, L.Kp, b == sp.first ? nullptr : Xn, none, none, Ahi, Alo,
-                  L.three != 0);
-        publish_for_copies();
-        for (int t = b * ns - 1; t >= t0 && ok; --t) {
-          phase32(n, pf, d.phi + (size_t)t * n, -1.f);
-          __syncthreads();
-          // the block's last product goes out in FP64 (with its phase) for the QR
-          ok = chain_slice(L, m, P, d, Ahi, Alo, tbase, PhaseVec{pf, false}, t == t0, Xc);
+      // ---- whole chains, split halves, or log det/G segments
+      const int sg = (tk.b >= CT_SEG && tk.b < CT_FWD2) ? tk.b - CT_SEG : -1;
+      const ChainSpan sp = chain_span(tk.b, nb, d.fsplit);
+      const bool fwd = sg >= 0 || sp.fwd;
+      fail_flag[0] = sg >= 0 ? SF_FWD : sp.flag;
+      if (fwd) {
+        const int kb = sg >= 0 ? nb / d.nseg : sp.last - sp.first + 1;
+        const int b_first = sg >= 0 ? sg * kb + 1 : sp.first;
+        for (int b = b_first; b < b_first + kb && ok; ++b) {
+          ok = fwd_block(b, b == b_first);
+          if (!ok) break;
+          if (keep && sg < 0 && (b < nb || !sp.assemble)) {  // a split half's product: SX
+            if (b < nb) store_state(W.LX(b), W.LT(b), W.LD(b));
+            else store_state(W.SX(), W.ST(), W.SD());
+            if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
+          }
         }
-        if (!ok) break;
-        cta_reortho_df(n, Xc, Xn, T, To, s.logD, s, (float4*)m.stages,
-                       L.nstages * L.stage_bytes / 16);
-        double2* t2 = T; T = To; To = t2;
-        cta_copy(n * n, W.RX(b), Xn);
-        cta_copy(n * n, W.RT(b), T);
-        for (int k = tid(); k < n; k += nthr()) W.RD(b)[k] = s.logD[k];
-        __syncthreads();
-        if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
+        if (ok && sg >= 0) {  // segment result in the checkpoint storage of block sg+1
+          store_state(W.LX(sg + 1), W.LT(sg + 1), W.LD(sg + 1));
+          numeric_status();
+        } else if (ok && !sp.assemble) {
+          numeric_status();
+        } else if (ok) {
+          assemble_out();
+        }
+      } else {
+        for (int b = sp.first; b >= sp.last && ok; --b) {
+          ok = bwd_block(b, b == sp.first);
+          if (!ok) break;
+          store_state(W.RX(b), W.RT(b), W.RD(b));
+          if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
+        }
+        if (ok) numeric_status();
       }
-      if (ok && tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     }
     if (!ok) {
       if (tid() == 0) {
         atomicMax(status + d.user_index, ST_TIMEOUT);
-        if (d.sync) flag_store(d.sync + (sg >= 0 ? SF_FWD : sp.flag), nb);
+        // release the dependent tasks (their inputs are invalid; the status says so)
+        if (d.sync)
+          for (int i = 0; i < 3; ++i)
+            if (fail_flag[i] >= 0) flag_store(d.sync + fail_flag[i], nb);
       }
       break;
     }
@@ -674,10 +768,11 @@ __global__ void __launch_bounds__(256, 1) k_wrap_big(const Desc* __restrict__ de
 // ------------------------------------------------------------------ boundary Green's functions
 // Phase B of the mixed force for the streamed size classes: G_{(b-1) ns} of block b from the left
 // checkpoint b-1 and the right checkpoint b, in double-float (fd_bound_df.cuh); three n x n df
-// work matrices in the CTA's slot.  (Split chains are not planned for these classes: merging a
-// second half's checkpoint forms a row scaling that spans beta/2 times the hopping bandwidth,
-// beyond the FP32 exponent range of double-float numbers at the low temperatures these sizes
-// run at; the FP64 boundary kernel merges within FP64's range.)
+// work matrices in the CTA's slot.  Every checkpoint it reads is final (whole or segmented
+// chains; the split chains of ChainSpan, which leave merges to this phase, are not planned for
+// these classes: merging a second half's checkpoint forms a row scaling that spans beta/2 times
+// the hopping bandwidth, beyond the FP32 exponent range of double-float numbers at low
+// temperature).
 __global__ void __launch_bounds__(256, 2) k_boundary_big(const Desc* __restrict__ descs,
                                                          const Task* __restrict__ tasks,
                                                          int ntasks, int* queue, int* status,
@@ -697,8 +792,17 @@ __global__ void __launch_bounds__(256, 2) k_boundary_big(const Desc* __restrict_
     const Desc d = descs[tk.desc];
     const int nb = d.nt / d.nstab, b = tk.b;
     const FWork W{d.fws, n, nb};
-    if (d.sync && !cta_wait_flags(d.sync, b - 1, nb - b + 1, 0, qs + 1) && tid() == 0)
-      atomicMax(status + d.user_index, ST_TIMEOUT);
+    bool waited = true;
+    if (d.sync && d.fseg) {  // segmented chains: the flags of the two checkpoints' segments
+      const int mb = nb / d.fseg;
+      int wi[2], wt[2];
+      seg_left_ready(b - 1, mb, wi[0], wt[0]);
+      seg_right_ready(b, nb, mb, wi[1], wt[1]);
+      waited = cta_wait_pairs(d.sync, wi, wt, 2, qs + 1);
+    } else if (d.sync) {
+      waited = cta_wait_flags(d.sync, b - 1, nb - b + 1, 0, qs + 1);
+    }
+    if (!waited && tid() == 0) atomicMax(status + d.user_index, ST_TIMEOUT);
     Small s = carve_small(smem + L.small_off, n);
     if (tid() == 0) s.misc[0] = 0;
     __syncthreads();

@@ -572,4 +572,60 @@ __device__ inline void cta_reortho_df(int n, double2* Xc, double2* Xn, double2* 
   __syncthreads();
 }
 
+// The stabilised product of two factored matrices (cta_merge) with its O(n^3) work in
+// double-float: Xs Ds Ts (acting later) times Xa Da Ta = Xs [Ds Ts Xa] Da Ta, the bracket
+// Xc = e^{-c} Ds (Ts Xa) as a tiled df GEMM (c = the mid-range of log Ds, so that Xc's rows lie
+// within e^{+-span/2}), re-factored by the pre-pivoted QR of cta_reortho_df (the column scaling
+// Da never formed), then X = Xs Q by a second GEMM and log D += c.  The df numbers carry FP32's
+// exponent range and the QR squares its entries, so a left factor whose log D spans more than
+// DF_MERGE_SPAN marks the configuration (misc[0]) instead of losing its small rows.  FP64 inputs
+// and outputs; Ta is copied to Tw (the QR consumes its T input).  Scratch: Xc, Xn (Q), Tw; the
+// result in X, Tn, logD.  sm: the QR's shared memory (vcap df numbers).
+#define DF_MERGE_SPAN 76.0
+__device__ inline void cta_merge_df(int n, const double2* Xs, const double2* Ts, const double* lDs,
+                                    const double2* Xa, const double2* Ta, const double* lDa,
+                                    double2* Xc, double2* Xn, double2* Tw, double2* Tn, double2* X,
+                                    double* logD, Small& s, float4* sm, int vcap) {
+  if (warp_id() == 0) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int k = lane_id(); k < n; k += 32) {
+      lo = fmin(lo, lDs[k]);
+      hi = fmax(hi, lDs[k]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane_id() == 0) {
+      s.red[9] = 0.5 * (lo + hi);
+      if (!(hi - lo <= DF_MERGE_SPAN)) atomicOr(&s.misc[0], 1);
+    }
+  }
+  __syncthreads();
+  const double c = s.red[9];
+  for (int k = tid(); k < n; k += nthr()) {
+    s.sa[k] = exp(lDs[k] - c);
+    logD[k] = lDa[k];
+  }
+  for (int e = tid(); e < n * n; e += nthr()) Tw[e] = Ta[e];
+  __syncthreads();
+  df_gemm_tiled(
+      n, n, n, [&](int i, int k) { return df_of(Ts[i + (size_t)k * n]); },
+      [&](int k, int j) { return df_of(Xa[k + (size_t)j * n]); },
+      [&](int i, int j, df::c4 v) {
+        const double a = s.sa[i];
+        Xc[i + (size_t)j * n] = make_double2(a * df::join(v.x, v.y), a * df::join(v.z, v.w));
+      },
+      sm);
+  cta_reortho_df(n, Xc, Xn, Tw, Tn, logD, s, sm, vcap);
+  for (int k = tid(); k < n; k += nthr()) logD[k] += c;
+  df_gemm_tiled(
+      n, n, n, [&](int i, int k) { return df_of(Xs[i + (size_t)k * n]); },
+      [&](int k, int j) { return df_of(Xn[k + (size_t)j * n]); },
+      [&](int i, int j, df::c4 v) {
+        X[i + (size_t)j * n] = make_double2(df::join(v.x, v.y), df::join(v.z, v.w));
+      },
+      sm);
+}
+
 }  // namespace fd

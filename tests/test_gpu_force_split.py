@@ -1,10 +1,11 @@
-"""Time-parallel force chains (fd_set_force_split): each chain of a configuration runs as two
-halves in parallel, the boundary phase merges a second half's checkpoint with the first half's
-last one (Section 7's stabilised product of two factored matrices, FP64) and forms log det and
-G_0 from the forward halves.  Compared with the unsplit chains and with the CPU oracle, every
-entry, in FP64 (buffers in shared memory and in global scratch) and for the mixed path's
-shared-memory tensor-core class; odd block counts; streamed mixed classes stay unsplit; the
-automatic rule on the force workloads."""
+"""Time-parallel force chains (fd_set_force_split).  Halves: each chain of a configuration runs
+as two halves in parallel, the boundary phase merges a second half's checkpoint with the first
+half's last one (Section 7's stabilised product of two factored matrices, FP64) and forms log det
+and G_0 from the forward halves.  Segments (the mixed path's streamed size classes): segments run
+from the identity, their prefixes are formed by double-float merges and the segments re-run from
+them.  Compared with the whole chains and with the CPU oracle, every entry, in FP64 (buffers in
+shared memory and in global scratch) and in both mixed modes; odd block counts; short streamed
+chains stay whole; the automatic rule on the force workloads."""
 import numpy as np
 import pytest
 
@@ -91,15 +92,38 @@ def test_split_mixed_against_oracle(ctx):
             assert float(np.abs(F.imag - 0.5).max()) <= tol["F_scaled"] * scale
 
 
-def test_streamed_mixed_class_stays_unsplit(ctx):
+def test_streamed_mixed_class_short_chains_stay_whole(ctx):
     from paper_2604_02130_gb300 import api
 
     # Nx = 98 in the mixed path runs the streamed kernels (double-float boundary): never split
+    # in halves, and 8 blocks are too few for segments of at least 4 blocks (S >= 4)
     probs = [fi.make_problem(7, 64, 8.0, 3.0, 8, 98, c) for c in range(2)]
     ctx.set_force_split(1)
     plan = api.Batch(ctx, to_dev(probs), "force+green", "3xtf32").plan()
     ctx.set_force_split(-1)
     assert _chain_tasks(plan) == 2 * len(probs)
+
+
+# Nx = 98, nb = 16 blocks.  Split TF32 runs it on the streamed kernels: forced segments S = 4 of
+# 4 blocks -- pass 1 (3 + 3 tasks), two prefix tasks, pass 2 (3 + 3) per configuration.  Plain
+# TF32 fits the shared-memory tile: halves with FP64 merges (4 tasks per configuration).
+@pytest.mark.parametrize("prec,kernels,per", [("3xtf32", [21, 18, 23], 14), ("tf32", [5, 2, 7], 4)])
+def test_segmented_streamed_chains(ctx, prec, kernels, per):
+    tol = MIXED_TOL[prec]
+    probs = [fi.make_problem(7, 128, 8.0, 3.0, 8, 100, c) for c in range(2)]
+    plan1, ld1, G1, F1 = _run(ctx, probs, prec, 1)
+    _, ld0, G0, F0 = _run(ctx, probs, prec, 0)
+    assert [g["kernel"] for g in plan1] == kernels
+    assert _chain_tasks(plan1) == per * len(probs)
+    for c, p in enumerate(probs):
+        ref_ld, ref_G = stable.logdet_green(p.E, p.phi, p.n_stab)
+        ref_F = oforce.force(p.E, p.phi, p.n_stab)
+        gmax = float(np.abs(ref_G).max())
+        scale = max(1.0, gmax) ** 2
+        for ld, G, F in ((ld1[c], G1[c], F1[c]), (ld0[c], G0[c], F0[c])):
+            assert mixed_logdet_ok(complex(ld), ref_ld, gmax, prec), (c, ld, ref_ld)
+            assert g_scaled_err(G, ref_G) <= tol["G_scaled"], c
+            assert float(np.abs(F - ref_F).max()) / scale <= tol["F_scaled"], c
 
 
 def test_split_fp64_streamed_class(ctx):
@@ -130,3 +154,10 @@ def test_split_rule_on_force_workloads(ctx):
     n0 = tasks("force72", "fp64")
     ctx.set_force_split(-1)
     assert n0 == 2 * 32
+    # uneven512, mixed: the Nx = 288 chains of Nt = 512 (32 blocks, S = 4) and Nt = 1024 (64
+    # blocks, S = 8) are segmented, the shorter ones stay whole
+    per = {512: 6 + 2 + 6, 1024: 14 + 2 + 14}
+    want = sum(per.get(nt, 2) for L, nt in fi.uneven_sizes(512) if L == 12)
+    plan = api.Batch(ctx, to_dev(fi.workload("uneven512")), "force+green", "3xtf32").plan()
+    got = [g["configs"] for g in plan if g["nx"] == 288 and g["kernel"] % 4 == 1]
+    assert got == [want]
