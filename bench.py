@@ -249,11 +249,14 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- helpers
-KERNEL_SOURCES = ("fd_common.cuh", "fd_fp64.cuh", "fd_tc.cuh", "fd_kernels_fp64.cu",
-                  "fd_kernels_mixed.cu")
+KERNEL_SOURCES = ("fd_common.cuh", "fd_fp64.cuh", "fd_tc.cuh", "fd_df.cuh", "fd_qr_df.cuh",
+                  "fd_bound_df.cuh", "fd_kernels_fp64.cu", "fd_kernels_mixed.cu",
+                  "fd_kernels_big.cu")
 # the files whose code a kernel compiles from, where that is fewer than all of them
 KERNEL_SOURCES_OF = {
     "k_chain_mixed": ("fd_common.cuh", "fd_fp64.cuh", "fd_tc.cuh", "fd_kernels_mixed.cu"),
+    "k_chain_big": ("fd_common.cuh", "fd_fp64.cuh", "fd_tc.cuh", "fd_df.cuh", "fd_qr_df.cuh",
+                    "fd_bound_df.cuh", "fd_kernels_big.cu"),
 }
 
 
@@ -497,6 +500,7 @@ def _errors(batch, res, path="force", pos=None, scale_batch=None):
 
 
 PHASE_OF_KERNEL = {1: "A", 2: "B", 3: "C"}
+DF_INSTR_PER_FLOP = 6
 KERNEL_NAME = {0: "k_fwd_", 1: "k_chain_", 2: "k_boundary_", 3: "k_wrap_", 8: "k_merge_"}
 
 
@@ -698,16 +702,31 @@ def run_ours(args):
     peak_fp64 = max(probe)
     probe_clocks = clk64.summary()
     tf32_peak = peaks["bf16_tflops"] / 2.0
+    # The streamed kernels' QR, boundary LU and products run in double-float on the FP32 pipes:
+    # their peak is the FP32 issue rate of all SMs at the timed region's median SM clock over
+    # DF_INSTR_PER_FLOP instructions per algorithmic flop (a compensated complex multiply-add,
+    # 8 flops, is 4 double-float products of 12 FP32 instructions each: 48 / 8 = 6).
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = (head["clocks"] or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_df = n_sms * 128 * clk_mhz * 1e6 / DF_INSTR_PER_FLOP / 1e12
+    peak_df_src = ("%d SMs x 128 FP32 lanes x %.0f MHz (median SM clock in the timed region) / "
+                   "%d FP32 instructions per double-float flop" % (n_sms, clk_mhz,
+                                                                  DF_INSTR_PER_FLOP))
     per_launch = [statistics.mean(k[i] for k in head["kernel_ms"]) for i in range(len(plan))]
     phases = []
     for i, rec in enumerate(plan):
-        nm = decode_kernel(rec["kernel"])[3]
+        _, _, big, nm = decode_kernel(rec["kernel"])
         ms = per_launch[i]
         f64 = lf[i][0] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
         tns = lf[i][1] / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
-        phases.append({"kernel": nm, "nx": rec["nx"], "configs": rec["configs"], "ms": ms,
-                       "fp64_tflops": f64, "fp64_frac": f64 / peak_fp64, "tensor_tflops": tns,
-                       "tensor_frac": tns / tf32_peak})
+        ph = {"kernel": nm, "nx": rec["nx"], "configs": rec["configs"], "ms": ms}
+        if big:  # double-float work on the FP32 pipes
+            ph.update({"df_tflops": f64, "df_frac": f64 / peak_df})
+        else:
+            ph.update({"fp64_tflops": f64, "fp64_frac": f64 / peak_fp64})
+        ph.update({"tensor_tflops": tns, "tensor_frac": tns / tf32_peak, "_alu": f64,
+                   "_big": big})
+        phases.append(ph)
     dom = max(range(len(plan)), key=lambda i: per_launch[i])
     k_ms = per_launch[dom]
     dk = decode_kernel(plan[dom]["kernel"])[0]
@@ -717,9 +736,16 @@ def run_ours(args):
                                          else "slice propagation of G(tau,0)")}.get(dk, "")
     what += " of the Nx=%d size class" % plan[dom]["nx"]
     P = phases[dom]
-    if P["fp64_tflops"] > 0 or P["tensor_tflops"] == 0:
-        roof = {"bound": "alu", "achieved": P["fp64_tflops"], "peak": peak_fp64,
-                "unit": "TFLOP/s", "frac": P["fp64_tflops"] / peak_fp64,
+    if P["_alu"] > 0 and P["_big"]:
+        roof = {"bound": "alu", "achieved": P["_alu"], "peak": peak_df, "unit": "TFLOP/s",
+                "frac": P["_alu"] / peak_df,
+                "what": "algorithmic QR, assembly and boundary work (FP64-class flops, computed "
+                        "in double-float on the FP32 pipes) of %s per launch over its CUDA-event "
+                        "duration" % what,
+                "peak_source": peak_df_src}
+    elif P["_alu"] > 0 or P["tensor_tflops"] == 0:
+        roof = {"bound": "alu", "achieved": P["_alu"], "peak": peak_fp64,
+                "unit": "TFLOP/s", "frac": P["_alu"] / peak_fp64,
                 "what": "FP64 algorithmic work of %s per launch over its CUDA-event duration"
                         % what,
                 "peak_source": "FP64 DFMA probe over all SMs in this run (fd_measure_fp64_peak, "
@@ -731,12 +757,17 @@ def run_ours(args):
                 "peak_source": "%s bf16 dense x 1/2 (TF32:BF16 nominal ratio)" % peak_src}
     roof.update({"traffic": _traffic(P["kernel"], name, args.prec, args.path),
                  "kernel": P["kernel"], "kernel_ms": k_ms,
-                 "kernel_ms_from": "a separate pass with CUDA events between the launches "
-                                   "(phases of a size class one after the other; in the timed "
-                                   "steps they overlap)",
+                 "kernel_ms_from": "a separate pass with CUDA events between the launches, "
+                                   "every launch alone (in the timed steps the size classes run "
+                                   "concurrently and the phases overlap)",
                  "fp64_issue_cycles": dict(zip(("one_lane", "full_warp", "one_of_8_warps"),
                                                ctx.measure_fp64_issue())),
-                 "phases": phases})
+                 "fp64_peak": {"value": peak_fp64, "unit": "TFLOP/s",
+                               "source": "FP64 DFMA probe over all SMs (best of 4), clocks "
+                                         "during the probe: %s" % json.dumps(probe_clocks)},
+                 "df_peak": {"value": peak_df, "unit": "TFLOP/s", "source": peak_df_src},
+                 "phases": [{k: v for k, v in ph.items() if not k.startswith("_")}
+                            for ph in phases]})
     if P["tensor_tflops"] > 0 and roof["bound"] == "alu":
         roof["tensor"] = {"achieved": P["tensor_tflops"], "peak": tf32_peak,
                           "unit": "TFLOP/s", "frac": P["tensor_tflops"] / tf32_peak,

@@ -328,9 +328,11 @@ int fd_plan_query(fd_ctx* ctx, int batch, const fd_problem* probs, int what, int
                   int max_groups);
 
 /* Per-launch timing.  With timing on, every kernel launch of a call is bracketed by CUDA events
- * recorded on the call's stream.  fd_last_kernel_ms waits for them and writes the durations (ms)
- * of the last call's launches, in launch order, to ms[0..max-1]; it returns how many it wrote
- * (>= 0) or a negative FD_ERR_* code. */
+ * recorded on the call's stream, and the launches run one after another (size classes are not
+ * forked onto side streams and later phases do not start early), so each duration is that
+ * kernel's alone.  fd_last_kernel_ms waits for them and writes the durations (ms) of the last
+ * call's launches, in launch order, to ms[0..max-1]; it returns how many it wrote (>= 0) or a
+ * negative FD_ERR_* code. */
 int fd_set_timing(fd_ctx* ctx, int on);
 int fd_last_kernel_ms(fd_ctx* ctx, double* ms, int max);
 

@@ -1021,7 +1021,9 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
     }
     ctx->ev_used = 2 * nq;
   }
-  const bool fork = groups.size() > 1;
+  // with per-launch timing the size classes run one after another on the call's stream, so each
+  // duration is that kernel's alone (as a profiler's serialised launch list sees it)
+  const bool fork = groups.size() > 1 && !timing;
   const size_t nside = std::min<size_t>(groups.size(), 8);
   if (fork) {
     int rc = ensure_side(ctx, nside);
