@@ -113,6 +113,7 @@ struct Phase {
   int mixed;  // 1: tcgen05 kernel (ML, or BL when big), 0: FP64 kernel (L)
   int big = 0;  // 1: streamed tcgen05 kernel (operands in global memory, BL)
   int merge = 0;  // boundary phase: the variant that merges split chains' checkpoints
+  int seg = 0;    // shared-memory mixed chain phase: the variant with segmented-chain tasks
   Layout L;
   fd::MLayout ML;
   fd::BLayout BL{};
@@ -644,11 +645,12 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       split_c[c] = nb >= 4 && (ctx->force_split > 0 || auto_ok);
     }
   }
-  // Segmented chains (SegPlan) for the streamed mixed classes, whose boundary kernel reads only
-  // final checkpoints: S = nb / 8 segments (a power of two, 4..FD_SEG_MAX, dividing nb) where
-  // one chain would outlast an SM's share of all the call's chains -- a chain of nt slices costs
-  // ~nx^3 (nt + 150 nt / n_stab), a QR about as much as 150 slice products.  The critical path
-  // becomes 2 nb / S blocks and S - 2 merges; the work grows by the re-run segments.
+  // Segmented chains (SegPlan) for the mixed path: S = nb / 8 segments (a power of two,
+  // 4..FD_SEG_MAX, dividing nb) where one chain would outlast 1.5 times an SM's share of all the
+  // call's chains -- a chain of nt slices costs ~nx^3 (nt + 150 nt / n_stab), a QR about as much
+  // as 150 slice products, and re-running the segments adds up to half a chain of work.  The
+  // critical path becomes 2 nb / S blocks and S - 2 merges (double-float in the streamed
+  // classes, FP64 in the shared-memory ones); the boundary phase reads final checkpoints.
   std::vector<int> seg_c(batch, 0);
   if (kind == K_FORCE && !sparse && prec != FD_PREC_FP64 && ctx->force_split != 0) {
     auto ccost = [&](const fd_problem& p) {
@@ -664,7 +666,7 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       int S = 1;
       const int mmin = ctx->force_split > 0 ? 4 : 8;
       while (2 * S <= FD_SEG_MAX && nb % (2 * S) == 0 && nb / (2 * S) >= mmin) S *= 2;
-      if (S >= 4 && (ctx->force_split > 0 || ccost(probs[c]) > share)) seg_c[c] = S;
+      if (S >= 4 && (ctx->force_split > 0 || ccost(probs[c]) > 1.5 * share)) seg_c[c] = S;
     }
   }
   int qnext = 0;
@@ -719,7 +721,7 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       }
       g.ph.push_back(P);
     } else {
-      // streamed mixed classes (double-float boundary kernel) keep whole chains
+      // streamed mixed classes (double-float boundary kernel): no halves
       Phase A0;
       const bool streamed = mixed && !mixed_phase(ctx, n, R_FWD, 1, three, 2 * nd, A0) &&
                             big_phase(ctx, n, false, three, 2 * nd, A0);
@@ -728,8 +730,9 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       for (int k = 0; k < nd; ++k) {
         const int c = g.idx[k];
         const int nb = probs[c].nt / probs[c].n_stab;
-        const int h = split_c[c] && !streamed ? nb / 2 : 0;
-        const int S = streamed ? seg_c[c] : 0;
+        // segments where planned, else halves (FP64 joins: not for the streamed classes)
+        const int S = mixed ? seg_c[c] : 0;
+        const int h = split_c[c] && !streamed && S == 0 ? nb / 2 : 0;
         g.fsplit.push_back(h);
         g.fseg.push_back(S);
         any_split |= h > 0;
@@ -798,13 +801,24 @@ std::vector<Group> plan(fd_ctx* ctx, int batch, const fd_problem* probs, int kin
       }
       Phase A, C;
       const int ntA = (int)g.tA.size();
-      if (!(mixed && tensor_chain(ctx, n, 1, three, ntA, A))) A = fp64_phase(ctx, n, R_FWD, 1, ntA);
+      bool any_seg = false;
+      for (int S : g.fseg) any_seg |= S > 0;
+      // the shared-memory mixed kernel has a variant with the segmented chains' tasks (which 9)
+      const int whichA = any_seg && !streamed ? 9 : 1;
+      if (!(mixed && tensor_chain(ctx, n, whichA, three, ntA, A)))
+        A = fp64_phase(ctx, n, R_FWD, 1, ntA);
+      if (A.mixed && !A.big && whichA == 9) {
+        A.which = 1;
+        A.seg = 1;
+      }
       const bool two_rhs = (kind & K_GTAU) && (kind & (K_FORCE | K_RESP));
-      Phase B = any_split ? fp64_phase(ctx, n, R_BOUNDM, 9, std::max(1, (int)g.tB.size()))
-                          : fp64_phase(ctx, n, two_rhs ? R_BOUND2 : R_BOUND, 2,
-                                       std::max(1, (int)g.tB.size()));
+      // halves or segments: the boundary variant that merges / waits on segment flags
+      const bool bvar = any_split || (any_seg && !streamed);
+      Phase B = bvar ? fp64_phase(ctx, n, R_BOUNDM, 9, std::max(1, (int)g.tB.size()))
+                     : fp64_phase(ctx, n, two_rhs ? R_BOUND2 : R_BOUND, 2,
+                                  std::max(1, (int)g.tB.size()));
       B.which = 2;
-      B.merge = any_split ? 1 : 0;
+      B.merge = bvar ? 1 : 0;
       // the tensor-core wrap kernels cover the force rows (the shared-memory one also the
       // response traces); G(tau, 0) wraps run in FP64
       const bool mixed_wrap = mixed && !(kind & K_GTAU);
@@ -1071,7 +1085,7 @@ int enqueue(fd_ctx* ctx, std::vector<Group>& groups, Desc* d_desc, fd::Task* d_t
         case 1:
           if (P.mixed)
             fd::launch_chain_mixed(dd, d_tasks + g.tA_off, (int)g.tA.size(), d_queue + qi,
-                                   d_status, scr, P.ML, P.grid, s);
+                                   d_status, scr, P.ML, P.grid, s, P.seg != 0);
           else
             fd::launch_chain_fp64(dd, d_tasks + g.tA_off, (int)g.tA.size(), d_queue + qi,
                                   d_status, scr, P.L, P.grid, s);

@@ -130,25 +130,21 @@ __device__ __forceinline__ int flag_load(const int* f) {
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
   return v;
 }
-// CTA-wide wait until flags[idx[i]] >= thr[i] for i < np (np <= 4); as cta_wait_flags.
-__device__ __forceinline__ bool cta_wait_pairs(const int* flags, const int* idx, const int* thr,
-                                               int np, volatile int* bcast) {
+// CTA-wide wait until flags[i0] >= t0 and (i1 < 0 or) flags[i1] >= t1; as cta_wait_flags.
+__device__ __forceinline__ bool cta_wait_pairs(const int* flags, int i0, int t0, int i1, int t1,
+                                               volatile int* bcast) {
   if (threadIdx.x == 0) {
-    long long t0 = clock64();
+    long long c0 = clock64();
     int ok = 1, last = -1;
     for (;;) {
-      int sum = 0, done = 1;
-      for (int i = 0; i < np; ++i) {
-        const int f = flag_load(flags + idx[i]);
-        sum += f;
-        done &= f >= thr[i];
-      }
-      if (done) break;
+      const int f0 = flag_load(flags + i0), f1 = i1 >= 0 ? flag_load(flags + i1) : 0;
+      if (f0 >= t0 && (i1 < 0 || f1 >= t1)) break;
+      const int sum = f0 + f1;
       const long long now = clock64();
       if (sum != last) {
         last = sum;
-        t0 = now;
-      } else if (now - t0 > FD_SYNC_WAIT_CYCLES) {
+        c0 = now;
+      } else if (now - c0 > FD_SYNC_WAIT_CYCLES) {
         ok = 0;
         break;
       }

@@ -53,9 +53,10 @@ cudaError_t attrs_fp64(int which, cudaFuncAttributes* a);
 // mixed path (tcgen05 slice GEMMs)
 void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, char* scratch,
                       const MLayout& L, int grid, cudaStream_t stream);
+// seg: the variant with the segmented chains' tasks (attrs/occupancy: which 9)
 void launch_chain_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue,
                         int* status, char* scratch, const MLayout& L, int grid,
-                        cudaStream_t stream);
+                        cudaStream_t stream, bool seg);
 void launch_wrap_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                        char* scratch, const MLayout& L, int grid, cudaStream_t stream, bool pdl);
 cudaError_t set_smem_mixed(int bytes);

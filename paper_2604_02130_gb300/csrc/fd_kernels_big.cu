@@ -543,9 +543,8 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
       if (pre) {
         fail_flag[0] = FPRE + S - 1;
         for (int kk = 2; kk < S; ++kk) {
-          const int wi[2] = {FLS + kk - 1, kk == 2 ? FSEG : FPRE + kk - 1};
-          const int wt[2] = {1, kk == 2 ? mb : 1};
-          if (!cta_wait_pairs(d.sync, wi, wt, 2, m.qslot + 1) && tid() == 0)
+          if (!cta_wait_pairs(d.sync, FLS + kk - 1, 1, kk == 2 ? FSEG : FPRE + kk - 1,
+                              kk == 2 ? mb : 1, m.qslot + 1) && tid() == 0)
             atomicMax(status + d.user_index, ST_TIMEOUT);
           const int a = pre_c(kk - 1), c = pre_c(kk), li = loc(kk - 1);
           cta_merge_df(n, W.XX(li), W.XT(li), W.XD(li), ckx(a), ckt(a), ckd(a), Xc, Xn, T, To,
@@ -563,8 +562,8 @@ __global__ void __launch_bounds__(256, 1) k_chain_big(const Desc* __restrict__ d
         fail_flag[0] = FSEG + k;
         fail_flag[1] = pass2 ? (fw && k == S - 1 ? SF_FWD : -1) : FLS + k;
         if (pass2) {
-          const int wi[1] = {k == 1 ? FSEG : FPRE + k}, wt[1] = {k == 1 ? mb : 1};
-          if (!cta_wait_pairs(d.sync, wi, wt, 1, m.qslot + 1) && tid() == 0)
+          if (!cta_wait_pairs(d.sync, k == 1 ? FSEG : FPRE + k, k == 1 ? mb : 1, -1, 0,
+                              m.qslot + 1) && tid() == 0)
             atomicMax(status + d.user_index, ST_TIMEOUT);
           const int c = pre_c(k);
           load_state(ckx(c), ckt(c), ckd(c));
@@ -795,10 +794,10 @@ __global__ void __launch_bounds__(256, 2) k_boundary_big(const Desc* __restrict_
     bool waited = true;
     if (d.sync && d.fseg) {  // segmented chains: the flags of the two checkpoints' segments
       const int mb = nb / d.fseg;
-      int wi[2], wt[2];
-      seg_left_ready(b - 1, mb, wi[0], wt[0]);
-      seg_right_ready(b, nb, mb, wi[1], wt[1]);
-      waited = cta_wait_pairs(d.sync, wi, wt, 2, qs + 1);
+      int i0, t0, i1, t1;
+      seg_left_ready(b - 1, mb, i0, t0);
+      seg_right_ready(b, nb, mb, i1, t1);
+      waited = cta_wait_pairs(d.sync, i0, t0, i1, t1, qs + 1);
     } else if (d.sync) {
       waited = cta_wait_flags(d.sync, b - 1, nb - b + 1, 0, qs + 1);
     }

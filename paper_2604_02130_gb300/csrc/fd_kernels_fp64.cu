@@ -341,8 +341,10 @@ __global__ void __launch_bounds__(256, 3) k_chain_fp64(const Desc* __restrict__ 
 // and the right checkpoint b (Section 7 steps 7-9 with t1 = t2; Section 5.3).  With the chains
 // split at block h (ChainSpan) a left checkpoint beyond h is first merged with L_h and a right
 // one below h+1 with R_{h+1} (cta_merge), and task b = 1 forms the full product L'_nb L_h, the
-// assembly (log det, G_0) and the outputs of the forward chain.
-// MERGE: the variant for calls with split chains (the plain one keeps its register budget).
+// assembly (log det, G_0) and the outputs of the forward chain.  Segmented chains (SegPlan) leave
+// final checkpoints: only the waits differ.
+// MERGE: the variant for calls with split or segmented chains (the plain one keeps its register
+// budget).
 template <bool MERGE>
 __global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ descs,
                                                         const Task* __restrict__ tasks,
@@ -363,8 +365,17 @@ __global__ void __launch_bounds__(256) k_boundary_fp64(const Desc* __restrict__ 
     const bool ml = h > 0 && b - 1 > h, mr = h > 0 && b >= 2 && b <= h;
     const int wf = b == 1 ? h : (ml ? h : b - 1), wf2 = b == 1 ? nb - h : (ml ? b - 1 - h : 0);
     const int wb = b == 1 ? 0 : (mr ? nb - h : nb - b + 1), wb2 = mr ? h - b + 1 : 0;
-    if (d.sync && !cta_wait_flags(d.sync, wf, wb, 0, slot + 1, wf2, wb2) && tid() == 0)
-      atomicMax(status + d.user_index, ST_TIMEOUT);
+    bool waited = true;
+    if (MERGE && d.sync && d.fseg) {  // segmented chains: their two checkpoints' segment flags
+      const int mb = nb / d.fseg;
+      int i0, t0, i1, t1;
+      seg_left_ready(b - 1, mb, i0, t0);
+      seg_right_ready(b, nb, mb, i1, t1);
+      waited = cta_wait_pairs(d.sync, i0, t0, i1, t1, slot + 1);
+    } else if (d.sync) {
+      waited = cta_wait_flags(d.sync, wf, wb, 0, slot + 1, wf2, wb2);
+    }
+    if (!waited && tid() == 0) atomicMax(status + d.user_index, ST_TIMEOUT);
     Small s = carve_small(smem + L.small_off, n);
     if (tid() == 0) {
       s.misc[0] = 0;

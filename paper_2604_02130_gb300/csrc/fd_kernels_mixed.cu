@@ -365,12 +365,15 @@ __global__ void __launch_bounds__(256) k_fwd_mixed(const Desc* __restrict__ desc
 }
 
 // ------------------------------------------------------------------ force (mixed)
-// Phase A: the forward and backward chains of the force as separate tasks (task q:
-// configuration q/2, direction q%2); slices on the tensor core, QR in FP64; checkpoints and
-// G_0 go to the configuration's global workspace (FWork).  The backward chain multiplies the
-// right products as adjoints, X_R <- diag(e^{-i phi_s}) E X_R, the conjugate phase applied in the
-// epilogue.
-__global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ descs,
+// Phase A: the forward and backward chains of the force as separate tasks (a ChainCode: whole
+// chains, halves, log det/G segments; or a SegCode: the segmented chains of SegPlan, joined by
+// FP64 merges); slices on the tensor core, QR in FP64; checkpoints and G_0 go to the
+// configuration's global workspace (FWork).  The backward chain multiplies the right products as
+// adjoints, X_R <- diag(e^{-i phi_s}) E X_R, the conjugate phase applied in the epilogue.  The
+// chain state between blocks is (m.Xn = Q of the last QR, T, log D).  SEG: the variant with the
+// segmented chains' tasks (its FP64 merges need more registers; the plain one keeps 2 CTAs/SM).
+template <bool SEG>
+__global__ void __launch_bounds__(256, SEG ? 1 : 2) k_chain_mixed(const Desc* __restrict__ descs,
                                                       const Task* __restrict__ tasks, int ntasks,
                                                       int* queue, int* status, char* scratch,
                                                       MLayout L) {
@@ -394,11 +397,7 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
     if (q >= ntasks) break;
     const Task tk = tasks[q];
     const Desc d = descs[tk.desc];
-    // Task.b: a ChainCode (forward/backward chain, its second half, or a log det/G segment)
     const int ns = d.nstab, nb = d.nt / d.nstab;
-    const int sg = (tk.b >= CT_SEG && tk.b < CT_FWD2) ? tk.b - CT_SEG : -1;
-    const ChainSpan sp = chain_span(tk.b, nb, d.fsplit);
-    const bool fwd = sg >= 0 || sp.fwd;
     const FWork W{d.fws, n, nb};
     Small s = carve_small(smem + L.small_off, n);
     float2* pf = (float2*)s.ph;  // FP32 phases: two halves of n
@@ -411,93 +410,189 @@ __global__ void __launch_bounds__(256) k_chain_mixed(const Desc* __restrict__ de
     cta_identity(n, T);
     for (int k = tid(); k < n; k += nthr()) s.logD[k] = 0.0;
     bool ok = true;
-    if (fwd) {
-      // a segment of a time-parallel split runs blocks sg*kb+1 .. (sg+1)*kb from the identity
-      const int kb = sg >= 0 ? nb / d.nseg : sp.last - sp.first + 1;
-      const int b_first = sg >= 0 ? sg * kb + 1 : sp.first;
-      for (int b = b_first; b < b_first + kb && ok; ++b) {
-        const int t0 = (b - 1) * ns;
-        cta_phase32(n, pf, d.phi + (size_t)t0 * n, 1.f);
-        __syncthreads();
-        fill_b2(L, m, b == b_first ? nullptr : m.Xn, Scale{pf, false}, one);
-        for (int t = t0; t < t0 + ns; ++t) {
-          const bool last = t + 1 == t0 + ns;
-          float2* phn = pf + ((t - t0 + 1) & 1) * n;
-          if (!last) cta_phase32(n, phn, d.phi + (size_t)(t + 1) * n, 1.f);
-          if (!slice_mma(L, m, tbase, phase)) { ok = false; break; }
-          slice_epilogue(L, m, tbase, phn, !last, To);  // To is free until the QR
-        }
-        if (!ok) break;
-        cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
-        double2* t2 = T; T = To; To = t2;
-        if (sg < 0 && (b < nb || !sp.assemble)) {  // checkpoint (a split half's product: SX)
-          cta_copy(n * n, b < nb ? W.LX(b) : W.SX(), m.Xn);
-          cta_copy(n * n, b < nb ? W.LT(b) : W.ST(), T);
-          double* ldst = b < nb ? W.LD(b) : W.SD();
-          for (int k = tid(); k < n; k += nthr()) ldst[k] = s.logD[k];
-          __syncthreads();
-          if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
+    // one forward block b: its slices on the tensor core, then the QR (the state advances)
+    auto fwd_block = [&](int b, bool from_id) -> bool {
+      const int t0 = (b - 1) * ns;
+      cta_phase32(n, pf, d.phi + (size_t)t0 * n, 1.f);
+      __syncthreads();
+      fill_b2(L, m, from_id ? nullptr : m.Xn, Scale{pf, false}, one);
+      for (int t = t0; t < t0 + ns; ++t) {
+        const bool last = t + 1 == t0 + ns;
+        float2* phn = pf + ((t - t0 + 1) & 1) * n;
+        if (!last) cta_phase32(n, phn, d.phi + (size_t)(t + 1) * n, 1.f);
+        if (!slice_mma(L, m, tbase, phase)) return false;
+        slice_epilogue(L, m, tbase, phn, !last, To);  // To is free until the QR
+      }
+      cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
+      double2* t2 = T; T = To; To = t2;
+      return true;
+    };
+    // one backward block b (right products as adjoints)
+    auto bwd_block = [&](int b, bool from_id) -> bool {
+      const int t0 = (b - 1) * ns;
+      fill_b2(L, m, from_id ? nullptr : m.Xn, one, one);
+      for (int t = b * ns - 1; t >= t0; --t) {
+        const bool last = t == t0;
+        cta_phase32(n, pf, d.phi + (size_t)t * n, -1.f);
+        if (!slice_mma(L, m, tbase, phase)) return false;
+        if (last) {
+          epilogue<TO_F32>(L, m, tbase, Scale{pf, false}, one, To, nullptr);
+          stage_to_fp64(n, (const float2*)To, m.Xc);
+        } else {
+          epilogue<TO_B_K>(L, m, tbase, Scale{pf, false}, one, nullptr, nullptr);
         }
       }
-      if (ok && sg >= 0) {  // segment result in the checkpoint storage of block sg+1
-        cta_copy(n * n, W.LX(sg + 1), m.Xn);
-        cta_copy(n * n, W.LT(sg + 1), T);
-        for (int k = tid(); k < n; k += nthr()) W.LD(sg + 1)[k] = s.logD[k];
-        if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
-      } else if (ok && !sp.assemble) {
-        if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
-      } else if (ok) {
-        double2* G0 = W.Gb(1);
-        cta_assemble(n, m.Xn, T, s.logD, m.Xc, G0, s, s.red + 2, s.red + 3);
-        const double re = s.red[2], im = wrap_pi(s.red[3]);
-        if (tid() == 0) {
-          d.logdet[0] = re;
-          d.logdet[1] = im;
-          atomicMax(status + d.user_index,
-                    (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
+      cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
+      double2* t2 = T; T = To; To = t2;
+      return true;
+    };
+    auto store_state = [&](double2* x, double2* t, double* dl) {
+      cta_copy(n * n, x, m.Xn);
+      cta_copy(n * n, t, T);
+      for (int k = tid(); k < n; k += nthr()) dl[k] = s.logD[k];
+      __syncthreads();
+    };
+    auto load_state = [&](const double2* x, const double2* t, const double* dl) {
+      cta_copy(n * n, m.Xn, x);
+      cta_copy(n * n, T, t);
+      for (int k = tid(); k < n; k += nthr()) s.logD[k] = dl[k];
+      __syncthreads();
+    };
+    // the end of the forward chain: log det, G_0 and the outputs
+    auto assemble_out = [&]() {
+      double2* G0 = W.Gb(1);
+      cta_assemble(n, m.Xn, T, s.logD, m.Xc, G0, s, s.red + 2, s.red + 3);
+      const double re = s.red[2], im = wrap_pi(s.red[3]);
+      if (tid() == 0) {
+        d.logdet[0] = re;
+        d.logdet[1] = im;
+        atomicMax(status + d.user_index,
+                  (s.misc[0] || !isfinite(re) || !isfinite(im)) ? ST_NUMERIC : ST_OK);
+      }
+      if (d.G)
+        for (int e = tid(); e < n * n; e += nthr()) d.G[e] = G0[(e / n) + (e % n) * n];
+      if (d.Gt)  // G(0, 0) = G
+        for (int e = tid(); e < n * n; e += nthr()) d.Gt[e] = G0[(e / n) + (e % n) * n];
+      if (d.nf) cta_fermion_number(n, G0, d.nf);
+      if (d.O) {  // FP32 copy of the response operator for the wrap epilogues
+        float* of = W.OF(d.Gt != nullptr);
+        for (int e = tid(); e < n * n; e += nthr()) of[e] = (float)d.O[e];
+      }
+      __syncthreads();
+      if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, nb);  // G_0 written
+    };
+    auto numeric_status = [&]() {
+      if (tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
+    };
+    int fail_flag[3] = {-1, -1, -1};  // flags a failed task releases (set to nb)
+    if (SEG && tk.b >= CT_SFA) {
+      // ---- segmented chains (SegPlan), joined by FP64 merges
+      const int S = d.fseg, mb = nb / S;
+      const bool pre = tk.b >= CT_SFP;
+      const int code = pre ? tk.b : (tk.b & ~15), k = pre ? 0 : (tk.b & 15);
+      const bool fw = pre ? tk.b == CT_SFP : (code == CT_SFA || code == CT_SFB);
+      const int FSEG = fw ? SF_SEGF : SF_SEGB, FPRE = fw ? SF_PREF : SF_PREB;
+      const int FLS = fw ? SF_LSF : SF_LSB;
+      // checkpoint c of this direction, the prefix checkpoint of segment kk, local product kk
+      auto ckx = [&](int c) { return fw ? W.LX(c) : W.RX(c); };
+      auto ckt = [&](int c) { return fw ? W.LT(c) : W.RT(c); };
+      auto ckd = [&](int c) { return fw ? W.LD(c) : W.RD(c); };
+      auto pre_c = [&](int kk) { return fw ? kk * mb : nb - kk * mb + 1; };
+      auto loc = [&](int kk) { return (fw ? 0 : S - 2) + kk - 1; };
+      __syncthreads();
+      if (pre) {
+        fail_flag[0] = FPRE + S - 1;
+        for (int kk = 2; kk < S; ++kk) {
+          if (!cta_wait_pairs(d.sync, FLS + kk - 1, 1, kk == 2 ? FSEG : FPRE + kk - 1,
+                              kk == 2 ? mb : 1, m.qslot + 1) && tid() == 0)
+            atomicMax(status + d.user_index, ST_TIMEOUT);
+          const int a = pre_c(kk - 1), c = pre_c(kk), li = loc(kk - 1);
+          cta_merge(n, W.XX(li), W.XT(li), W.XD(li), ckx(a), ckt(a), ckd(a), m.Xc, m.Xn, ckx(c),
+                    To, s.logD, s);
+          cta_copy(n * n, ckt(c), To);
+          for (int e = tid(); e < n; e += nthr()) ckd(c)[e] = s.logD[e];
+          __syncthreads();
+          if (tid() == 0) flag_store(d.sync + FPRE + kk, 1);
         }
-        if (d.G)
-          for (int e = tid(); e < n * n; e += nthr()) d.G[e] = G0[(e / n) + (e % n) * n];
-        if (d.Gt)  // G(0, 0) = G
-          for (int e = tid(); e < n * n; e += nthr()) d.Gt[e] = G0[(e / n) + (e % n) * n];
-        if (d.nf) cta_fermion_number(n, G0, d.nf);
-        if (d.O) {  // FP32 copy of the response operator for the wrap epilogues
-          float* of = W.OF(d.Gt != nullptr);
-          for (int e = tid(); e < n * n; e += nthr()) of[e] = (float)d.O[e];
+        numeric_status();
+      } else {
+        const bool pass2 = code == CT_SFB || code == CT_SBB;
+        const int first = fw ? k * mb + 1 : nb - k * mb;
+        const int last = fw ? (k + 1) * mb : max(2, nb - (k + 1) * mb + 1);
+        fail_flag[0] = FSEG + k;
+        fail_flag[1] = pass2 ? (fw && k == S - 1 ? SF_FWD : -1) : FLS + k;
+        if (pass2) {
+          if (!cta_wait_pairs(d.sync, k == 1 ? FSEG : FPRE + k, k == 1 ? mb : 1, -1, 0,
+                              m.qslot + 1) && tid() == 0)
+            atomicMax(status + d.user_index, ST_TIMEOUT);
+          const int c = pre_c(k);
+          load_state(ckx(c), ckt(c), ckd(c));
         }
-        __syncthreads();
-        if (tid() == 0 && d.sync) flag_store(d.sync + SF_FWD, nb);  // G_0 written
+        const int step = fw ? 1 : -1;
+        for (int b = first; ok; b += step) {
+          ok = fw ? fwd_block(b, !pass2 && b == first) : bwd_block(b, !pass2 && b == first);
+          if (!ok) break;
+          const bool lastb = b == last;
+          // final checkpoints: pass 1 of segment 0, and pass 2 but for a segment's last block
+          // (formed by the next prefix) and the forward chain's end (the assembly)
+          if ((!pass2 && k == 0) || (pass2 && !(lastb && k < S - 1) && !(fw && b == nb))) {
+            store_state(ckx(b), ckt(b), ckd(b));
+            if (tid() == 0) flag_store(d.sync + FSEG + k, fw ? b - first + 1 : first - b + 1);
+          }
+          if (lastb) break;
+        }
+        if (ok && !pass2 && k > 0) {  // pass 1: the segment's local product
+          const int li = loc(k);
+          store_state(W.XX(li), W.XT(li), W.XD(li));
+          if (tid() == 0) flag_store(d.sync + FLS + k, 1);
+        }
+        if (ok && fw && pass2 && k == S - 1) assemble_out();
+        else if (ok) numeric_status();
       }
     } else {
-      for (int b = sp.first; b >= sp.last && ok; --b) {
-        const int t0 = (b - 1) * ns;
-        fill_b2(L, m, b == sp.first ? nullptr : m.Xn, one, one);
-        for (int t = b * ns - 1; t >= t0; --t) {
-          const bool last = t == t0;
-          cta_phase32(n, pf, d.phi + (size_t)t * n, -1.f);
-          if (!slice_mma(L, m, tbase, phase)) { ok = false; break; }
-          if (last) {
-            epilogue<TO_F32>(L, m, tbase, Scale{pf, false}, one, To, nullptr);
-            stage_to_fp64(n, (const float2*)To, m.Xc);
-          } else
-            epilogue<TO_B_K>(L, m, tbase, Scale{pf, false}, one, nullptr, nullptr);
+      // ---- whole chains, split halves, or log det/G segments
+      const int sg = (tk.b >= CT_SEG && tk.b < CT_FWD2) ? tk.b - CT_SEG : -1;
+      const ChainSpan sp = chain_span(tk.b, nb, d.fsplit);
+      const bool fwd = sg >= 0 || sp.fwd;
+      fail_flag[0] = sg >= 0 ? SF_FWD : sp.flag;
+      if (fwd) {
+        // a segment of a time-parallel log det/G split runs blocks sg*kb+1 .. (sg+1)*kb
+        const int kb = sg >= 0 ? nb / d.nseg : sp.last - sp.first + 1;
+        const int b_first = sg >= 0 ? sg * kb + 1 : sp.first;
+        for (int b = b_first; b < b_first + kb && ok; ++b) {
+          ok = fwd_block(b, b == b_first);
+          if (!ok) break;
+          if (sg < 0 && (b < nb || !sp.assemble)) {  // checkpoint (a split half's product: SX)
+            if (b < nb) store_state(W.LX(b), W.LT(b), W.LD(b));
+            else store_state(W.SX(), W.ST(), W.SD());
+            if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
+          }
         }
-        if (!ok) break;
-        cta_reortho(n, m.Xc, m.Xn, T, To, s.logD, s);
-        double2* t2 = T; T = To; To = t2;
-        cta_copy(n * n, W.RX(b), m.Xn);
-        cta_copy(n * n, W.RT(b), T);
-        for (int k = tid(); k < n; k += nthr()) W.RD(b)[k] = s.logD[k];
-        __syncthreads();
-        if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
+        if (ok && sg >= 0) {  // segment result in the checkpoint storage of block sg+1
+          store_state(W.LX(sg + 1), W.LT(sg + 1), W.LD(sg + 1));
+          numeric_status();
+        } else if (ok && !sp.assemble) {
+          numeric_status();
+        } else if (ok) {
+          assemble_out();
+        }
+      } else {
+        for (int b = sp.first; b >= sp.last && ok; --b) {
+          ok = bwd_block(b, b == sp.first);
+          if (!ok) break;
+          store_state(W.RX(b), W.RT(b), W.RD(b));
+          if (tid() == 0 && d.sync) flag_store(d.sync + sp.flag, sp.count(b));
+        }
+        if (ok) numeric_status();
       }
-      if (ok && tid() == 0 && s.misc[0]) atomicMax(status + d.user_index, ST_NUMERIC);
     }
     if (!ok) {
       if (tid() == 0) {
         atomicMax(status + d.user_index, ST_TIMEOUT);
         // release the dependent tasks (their inputs are invalid; the status says so)
-        if (d.sync) flag_store(d.sync + (sg >= 0 ? SF_FWD : sp.flag), nb);
+        if (d.sync)
+          for (int i = 0; i < 3; ++i)
+            if (fail_flag[i] >= 0) flag_store(d.sync + fail_flag[i], nb);
       }
       break;
     }
@@ -624,9 +719,13 @@ __global__ void __launch_bounds__(256) k_wrap_mixed(const Desc* __restrict__ des
 
 void launch_chain_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue,
                         int* status, char* scratch, const MLayout& L, int grid,
-                        cudaStream_t stream) {
-  k_chain_mixed<<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue, status,
-                                                             scratch, L);
+                        cudaStream_t stream, bool seg) {
+  if (seg)
+    k_chain_mixed<true><<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue,
+                                                                    status, scratch, L);
+  else
+    k_chain_mixed<false><<<grid, L.nthreads, L.smem_bytes, stream>>>(descs, tasks, ntasks, queue,
+                                                                     status, scratch, L);
 }
 void launch_wrap_mixed(const Desc* descs, const Task* tasks, int ntasks, int* queue, int* status,
                        char* scratch, const MLayout& L, int grid, cudaStream_t stream, bool pdl) {
@@ -641,7 +740,8 @@ void launch_fwd_mixed(const Desc* descs, int ndesc, int* queue, int* status, cha
 }
 cudaError_t set_smem_mixed(int bytes) {
   for (const void* k :
-       {(const void*)k_fwd_mixed, (const void*)k_chain_mixed, (const void*)k_wrap_mixed}) {
+       {(const void*)k_fwd_mixed, (const void*)k_chain_mixed<false>,
+        (const void*)k_chain_mixed<true>, (const void*)k_wrap_mixed}) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -652,7 +752,8 @@ cudaError_t set_smem_mixed(int bytes) {
 }
 static const void* mixed_kernel(int which) {
   switch (which) {
-    case 1: return (const void*)k_chain_mixed;
+    case 1: return (const void*)k_chain_mixed<false>;
+    case 9: return (const void*)k_chain_mixed<true>;
     case 3: return (const void*)k_wrap_mixed;
     default: return (const void*)k_fwd_mixed;
   }

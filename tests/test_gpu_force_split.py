@@ -1,9 +1,9 @@
 """Time-parallel force chains (fd_set_force_split).  Halves: each chain of a configuration runs
 as two halves in parallel, the boundary phase merges a second half's checkpoint with the first
 half's last one (Section 7's stabilised product of two factored matrices, FP64) and forms log det
-and G_0 from the forward halves.  Segments (the mixed path's streamed size classes): segments run
-from the identity, their prefixes are formed by double-float merges and the segments re-run from
-them.  Compared with the whole chains and with the CPU oracle, every entry, in FP64 (buffers in
+and G_0 from the forward halves.  Segments (the mixed path): segments run from the identity,
+their prefixes are formed by merges (double-float in the streamed size classes, FP64 in the
+shared-memory ones) and the segments re-run from them.  Compared with the whole chains and with the CPU oracle, every entry, in FP64 (buffers in
 shared memory and in global scratch) and in both mixed modes; odd block counts; short streamed
 chains stay whole; the automatic rule on the force workloads."""
 import numpy as np
@@ -104,10 +104,10 @@ def test_streamed_mixed_class_short_chains_stay_whole(ctx):
     assert _chain_tasks(plan) == 2 * len(probs)
 
 
-# Nx = 98, nb = 16 blocks.  Split TF32 runs it on the streamed kernels: forced segments S = 4 of
-# 4 blocks -- pass 1 (3 + 3 tasks), two prefix tasks, pass 2 (3 + 3) per configuration.  Plain
-# TF32 fits the shared-memory tile: halves with FP64 merges (4 tasks per configuration).
-@pytest.mark.parametrize("prec,kernels,per", [("3xtf32", [21, 18, 23], 14), ("tf32", [5, 2, 7], 4)])
+# Nx = 98, nb = 16 blocks, forced segments S = 4 of 4 blocks -- pass 1 (3 + 3 tasks), two prefix
+# tasks, pass 2 (3 + 3) per configuration.  Split TF32 runs it on the streamed kernels
+# (double-float merges), plain TF32 fits the shared-memory tile (FP64 merges).
+@pytest.mark.parametrize("prec,kernels,per", [("3xtf32", [21, 18, 23], 14), ("tf32", [5, 2, 7], 14)])
 def test_segmented_streamed_chains(ctx, prec, kernels, per):
     tol = MIXED_TOL[prec]
     probs = [fi.make_problem(7, 128, 8.0, 3.0, 8, 100, c) for c in range(2)]
@@ -146,9 +146,12 @@ def test_split_rule_on_force_workloads(ctx):
 
     # FP64 force72: 32 configurations, 4 * 32 <= 152 SMs -> every chain split
     assert tasks("force72", "fp64") == 4 * 32
-    # more configurations, or the mixed path: whole chains
+    # more configurations: whole chains
     assert tasks("cold72", "fp64") == 2 * 64
-    assert tasks("force72", "3xtf32") == 2 * 32
+    # mixed force72: one chain is 152 / 64 = 2.4 times an SM's share -> segments S = 4 of 8
+    # blocks; mixed cold72 (1.2 times) keeps whole chains
+    assert tasks("force72", "3xtf32") == 14 * 32
+    assert tasks("cold72", "3xtf32") == 2 * 64
     # never
     ctx.set_force_split(0)
     n0 = tasks("force72", "fp64")
