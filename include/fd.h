@@ -230,22 +230,24 @@ int fd_debug_skip_chains(fd_ctx* ctx, int on);
  * chains per configuration, the forward one (left checkpoints, then log det and G_0) and the
  * backward one (right checkpoints), so a long chain is serial work on one SM.  Two decompositions
  * (Section 7's stabilised product of two factored matrices joins the pieces):
- *  - halves (size classes whose boundary Green's functions run in FP64: the FP64 path, and the
- *    mixed path's shared-memory classes): each chain runs as two halves in parallel, the second
- *    from the identity; the boundary phase merges a second half's checkpoint with the first
- *    half's last one (FP64) and forms log det and G_0 from the forward halves.  A merge whose
- *    left factor spans more than e^700 marks the configuration FD_ERR_NUMERIC.
- *  - segments (the mixed path's streamed classes, Nx above the shared-memory tile): S segments
- *    of about 8 blocks (4..8 segments, a power of two dividing the block count) run from the
- *    identity in parallel, their prefixes are formed in order by double-float merges, and the
- *    segments are re-run from their exact prefixes, so every checkpoint is final.  A segment
- *    whose log D spans more than e^76 (beyond the double-float exponent range once squared)
- *    marks the configuration FD_ERR_NUMERIC.
- * mode -1 (default): halves in FP64 when 4 * batch <= the SM count; segments for a streamed
- * configuration whose chain would outlast an SM's share of all the call's chains (cost
- * nx^3 (nt + 150 nt / n_stab)).  0: never.  1: halves for every eligible configuration with at
- * least 4 blocks, segments of at least 4 blocks (S >= 4) for every streamed one that has them.
- * Results agree with the whole chains to rounding.  Returns FD_ERR_INVALID for another mode. */
+ *  - halves (the FP64 path, and the mixed path's shared-memory classes when forced): each chain
+ *    runs as two halves in parallel, the second from the identity; the boundary phase merges a
+ *    second half's checkpoint with the first half's last one (FP64) and forms log det and G_0
+ *    from the forward halves.  A merge whose left factor spans more than e^700 marks the
+ *    configuration FD_ERR_NUMERIC.
+ *  - segments (the mixed path): S segments of about 8 blocks (4..8 segments, a power of two
+ *    dividing the block count) run from the identity in parallel, their prefixes are formed in
+ *    order by merges (double-float in the streamed classes, Nx above the shared-memory tile;
+ *    FP64 in the others), and the segments are re-run from their exact prefixes, so every
+ *    checkpoint is final.  In the streamed classes a segment whose log D spans more than e^76
+ *    (beyond the double-float exponent range once squared) marks the configuration
+ *    FD_ERR_NUMERIC.
+ * mode -1 (default): halves in FP64 when 4 * batch <= the SM count; segments in the mixed path for
+ * a configuration whose chain would outlast 1.5 times an SM's share of all the call's chains
+ * (cost nx^3 (nt + 150 nt / n_stab)).  0: never.  1: segments of at least 4 blocks (S >= 4) in
+ * the mixed path where the configuration has them, else halves (not in the streamed classes)
+ * for every configuration with at least 4 blocks.  Results agree with the whole chains to
+ * rounding.  Returns FD_ERR_INVALID for another mode. */
 int fd_set_force_split(fd_ctx* ctx, int mode);
 
 /* Wait for `stream` and copy the per-configuration device status of the LAST call on this

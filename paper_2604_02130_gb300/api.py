@@ -71,8 +71,8 @@ class Context:
 
     def set_force_split(self, mode: int) -> None:
         """Time-parallel force chains (fd_set_force_split): -1 automatic (halves for FP64
-        calls with 4 * batch <= SMs, segments for long chains of the mixed path's streamed size
-        classes), 0 never, 1 wherever the configuration has enough blocks."""
+        calls with 4 * batch <= SMs, segments for long chains of the mixed path), 0 never,
+        1 wherever the configuration has enough blocks."""
         self.check(self.lib.fd_set_force_split(self.h, int(mode)))
 
     def last_launch_count(self) -> int:
