@@ -49,7 +49,7 @@ extern "C" {
 enum {
   FD_OK = 0,
   FD_ERR_INVALID = -1,     /* bad argument: null pointer, size out of range, nt % n_stab != 0 */
-  FD_ERR_UNSUPPORTED = -2, /* valid request that this build does not implement */
+  FD_ERR_UNSUPPORTED = -2, /* valid request that this library does not implement */
   FD_ERR_CUDA = -3,        /* a CUDA runtime call failed (text in fd_last_error) */
   FD_ERR_NUMERIC = -4,     /* device: non-finite value or zero pivot in a configuration */
   FD_ERR_TIMEOUT = -5,     /* device: a bounded wait gave up (kernel returned early) */
